@@ -1,0 +1,362 @@
+"""Seeded synthetic inputs for the MOFF imaging step.
+
+This module produces *inputs* only: antenna layouts, sampled aperture-illumination
+tables, point-source skies, channelised antenna voltages and their 4+4-bit / FP16
+encodings, and complex gains.  It contains none of the imaging method's arithmetic
+(no antenna-to-grid mapping, gridding, spatial transform, squaring or averaging), so
+the FP64 oracle and the CUDA library can both be fed from it without sharing code.
+
+Shapes follow the paper's workloads (Table 1: LWA1-like, HERA-331-like layouts) and
+the measurement equation of Sec. 2 (Eq. "measured-E-field"): each antenna sees
+    V_a(t) = sum_s A_s(t) exp(-2 pi i r_a . s_hat / lambda) + n_a(t)
+with an isotropic element response.  All generators take an explicit numpy
+Generator (PCG64) so every input is reproducible from a seed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+C_LIGHT = 299792458.0
+
+
+# ----------------------------------------------------------------------------------
+# layouts (metres, [A, 2] float64: x, y)
+# ----------------------------------------------------------------------------------
+def layout_rect(rng, n_ant, width, height):
+    return np.stack([rng.uniform(-width / 2, width / 2, n_ant),
+                     rng.uniform(-height / 2, height / 2, n_ant)], axis=1)
+
+
+def layout_ellipse(rng, n_ant, diam_x, diam_y):
+    """Uniform inside an ellipse of the given full axes."""
+    out = np.empty((0, 2))
+    while out.shape[0] < n_ant:
+        p = np.stack([rng.uniform(-1, 1, 4 * n_ant), rng.uniform(-1, 1, 4 * n_ant)], axis=1)
+        p = p[(p ** 2).sum(1) <= 1.0]
+        out = np.concatenate([out, p])
+    out = out[:n_ant]
+    return out * np.array([diam_x / 2, diam_y / 2])
+
+
+def layout_disk(rng, n_ant, diameter):
+    return layout_ellipse(rng, n_ant, diameter, diameter)
+
+
+def layout_hex(n_side, spacing):
+    """Hexagonal close-packed core with n_side antennas per side (3 n (n-1) + 1 total)."""
+    pts = []
+    r = n_side - 1
+    for q in range(-r, r + 1):
+        for s in range(max(-r, -q - r), min(r, -q + r) + 1):
+            x = spacing * (q + s / 2.0)
+            y = spacing * (s * math.sqrt(3) / 2.0)
+            pts.append((x, y))
+    return np.array(pts, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------------
+# sampled aperture illumination tables: offsets [K, 2] (m) and weights [K] complex,
+# normalised to sum 1 (Sec. 4.2: auto-correlation weights normalised to unit sum)
+# ----------------------------------------------------------------------------------
+def _lattice(half, h):
+    n = max(1, int(math.ceil(2 * half / h - 1e-9)))
+    hh = 2 * half / n
+    c = (np.arange(n) + 0.5) * hh - half
+    xx, yy = np.meshgrid(c, c, indexing="xy")
+    return np.stack([xx.ravel(), yy.ravel()], axis=1)
+
+
+def kernel_square(side, h):
+    """Uniform square aperture of the given side, sampled on a lattice of step <= h."""
+    d = _lattice(side / 2, h)
+    w = np.full(d.shape[0], 1.0 / d.shape[0], dtype=np.complex128)
+    return d, w
+
+
+def kernel_gaussian(sigma, h, n_sigma=3.0):
+    """Gaussian illumination, truncated at radius n_sigma * sigma."""
+    rad = n_sigma * sigma
+    d = _lattice(rad, h)
+    r2 = (d ** 2).sum(1)
+    keep = r2 <= rad * rad
+    d, r2 = d[keep], r2[keep]
+    w = np.exp(-0.5 * r2 / sigma ** 2)
+    return d, (w / w.sum()).astype(np.complex128)
+
+
+def kernel_disk(diameter, h):
+    """Uniformly illuminated circular aperture (far field: Airy pattern)."""
+    rad = diameter / 2
+    d = _lattice(rad, h)
+    keep = (d ** 2).sum(1) <= rad * rad
+    if not keep.any():
+        keep[np.argmin((d ** 2).sum(1))] = True
+    d = d[keep]
+    return d, np.full(d.shape[0], 1.0 / d.shape[0], dtype=np.complex128)
+
+
+def kernel_point():
+    return np.zeros((1, 2)), np.ones(1, dtype=np.complex128)
+
+
+def pack_kernels(kernels):
+    """List of (dxdy, w) per antenna -> CSR (kern_ptr [A+1] int32, dxdy [nt,2] f64, w [nt] c128)."""
+    ptr = np.zeros(len(kernels) + 1, dtype=np.int32)
+    ptr[1:] = np.cumsum([k[0].shape[0] for k in kernels])
+    dxdy = np.concatenate([k[0] for k in kernels]).astype(np.float64)
+    w = np.concatenate([k[1] for k in kernels]).astype(np.complex128)
+    return ptr, dxdy, w
+
+
+def centred_origin(pos, reach, dx, n_grid):
+    """Grid origin (centre of cell (0,0), metres) putting the array's bounding box,
+    widened by the kernel reach, in the middle of an n_grid x n_grid grid."""
+    lo = pos.min(0) - reach
+    hi = pos.max(0) + reach
+    mid = 0.5 * (lo + hi)
+    return mid - dx * (n_grid - 1) / 2.0
+
+
+# ----------------------------------------------------------------------------------
+# skies and voltages
+# ----------------------------------------------------------------------------------
+@dataclass
+class Sky:
+    l: np.ndarray
+    m: np.ndarray
+    flux: np.ndarray
+
+
+def sky_box(rng, n_src, lmax, flux_lo, flux_hi):
+    return Sky(rng.uniform(-lmax, lmax, n_src), rng.uniform(-lmax, lmax, n_src),
+               rng.uniform(flux_lo, flux_hi, n_src))
+
+
+def sky_powerlaw_hemisphere(rng, n_src, s_lo, s_hi, index=-1.5):
+    """dN/dS ~ S^index on [s_lo, s_hi]; directions uniform over the visible hemisphere."""
+    a = index + 1.0
+    u = rng.uniform(0, 1, n_src)
+    flux = (s_lo ** a + u * (s_hi ** a - s_lo ** a)) ** (1.0 / a)
+    z = rng.uniform(0, 1, n_src)
+    phi = rng.uniform(0, 2 * np.pi, n_src)
+    rho = np.sqrt(1 - z * z)
+    return Sky(rho * np.cos(phi), rho * np.sin(phi), flux)
+
+
+def voltages(rng, pos, freqs_hz, n_time, n_pol, sky: Sky, noise_sigma, dtype=np.complex64):
+    """V[t, c, p, a] = sum_s sqrt(S_s) e^{i phi_{t,p,s}} e^{-2 pi i r_a . s_s / lambda_c} + n.
+
+    Source phases are drawn independently per (time, channel, pol, source): each sample is
+    a fresh realisation of a stochastic sky.  Noise is circular complex Gaussian with
+    per-sample variance noise_sigma**2.
+    """
+    n_ant = pos.shape[0]
+    out = np.empty((n_time, len(freqs_hz), n_pol, n_ant), dtype=dtype)
+    work = np.complex128 if np.dtype(dtype) == np.complex128 else np.complex64
+    amp = np.sqrt(sky.flux)
+    for c, f in enumerate(freqs_hz):
+        lam = C_LIGHT / f
+        geo = np.outer(sky.l, pos[:, 0]) + np.outer(sky.m, pos[:, 1])      # [S, A] metres
+        steer = np.exp(-2j * np.pi * geo / lam).astype(work)
+        for p in range(n_pol):
+            ph = rng.uniform(0, 2 * np.pi, (n_time, sky.flux.size))
+            src = (amp * np.exp(1j * ph)).astype(work)                       # [T, S]
+            sig = src @ steer
+            nz = (rng.standard_normal((n_time, n_ant)) + 1j * rng.standard_normal((n_time, n_ant)))
+            nz *= noise_sigma / math.sqrt(2.0)
+            out[:, c, p, :] = sig + nz.astype(work)
+    return out
+
+
+def random_gains(rng, shape, amp_spread=0.2):
+    amp = 1.0 + rng.uniform(-amp_spread, amp_spread, shape)
+    ph = rng.uniform(0, 2 * np.pi, shape)
+    return (amp * np.exp(1j * ph)).astype(np.complex64)
+
+
+# ----------------------------------------------------------------------------------
+# encodings
+# ----------------------------------------------------------------------------------
+def quantize_ci4(v, rms_levels=2.0, scale=None):
+    """Complex -> signed 4+4-bit byte: high nibble = real, low nibble = imag, both
+    two's complement in [-7, 7] (-8 unused).  Scaled so the per-component rms is
+    rms_levels, rounded half away from zero, clipped."""
+    if scale is None:
+        rms = math.sqrt(float(np.mean(np.abs(v.astype(np.complex128)) ** 2)) / 2.0)
+        scale = rms_levels / rms
+    re = np.clip(_round_half_away(v.real * scale), -7, 7).astype(np.int8)
+    im = np.clip(_round_half_away(v.imag * scale), -7, 7).astype(np.int8)
+    b = ((re.astype(np.uint8) & 0xF) << 4) | (im.astype(np.uint8) & 0xF)
+    return b.astype(np.uint8), scale
+
+
+def _round_half_away(x):
+    return np.sign(x) * np.floor(np.abs(x) + 0.5)
+
+
+def decode_ci4(b):
+    """Signed 4+4-bit byte -> complex128 (exact)."""
+    b = np.asarray(b, dtype=np.uint8)
+    hi = (b >> 4).astype(np.int16)
+    lo = (b & 0xF).astype(np.int16)
+    hi = np.where(hi >= 8, hi - 16, hi)
+    lo = np.where(lo >= 8, lo - 16, lo)
+    return hi.astype(np.float64) + 1j * lo.astype(np.float64)
+
+
+def to_f16_pairs(v):
+    """Complex -> [..., 2] float16 (re, im)."""
+    return np.stack([v.real, v.imag], axis=-1).astype(np.float16)
+
+
+def from_f16_pairs(x):
+    x = np.asarray(x, dtype=np.float64)
+    return x[..., 0] + 1j * x[..., 1]
+
+
+def to_c64_pairs(v):
+    return np.stack([v.real, v.imag], axis=-1).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------------
+# the workloads
+# ----------------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    pos: np.ndarray                # [A, 2] f64, metres
+    kern_ptr: np.ndarray           # [A+1] int32
+    kern_dxdy: np.ndarray          # [nt, 2] f64, metres
+    kern_w: np.ndarray             # [nt] complex128
+    dx: float                      # grid spacing, metres
+    origin: np.ndarray             # [2] f64, centre of cell (0, 0)
+    n_grid: int                    # unpadded grid side N_g
+    n_pad: int                     # padded side N_p (= image side)
+    freqs: np.ndarray              # [C] Hz
+    n_pol: int
+    n_time: int
+    vdtype: str                    # "c64" | "f16" | "ci4"
+    volt_raw: np.ndarray = None    # encoded voltages as fed to the library
+    volt: np.ndarray = None        # the same voltages as complex128 (exact decode)
+    gains: np.ndarray = None       # [C, P, A] complex64 or None
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_ant(self):
+        return self.pos.shape[0]
+
+    @property
+    def n_chan(self):
+        return len(self.freqs)
+
+
+def _finish(wl: Workload, v, vdtype, rng=None):
+    wl.vdtype = vdtype
+    if vdtype == "ci4":
+        b, scale = quantize_ci4(v)
+        wl.volt_raw = b
+        wl.volt = decode_ci4(b)
+        wl.extra["ci4_scale"] = scale
+    elif vdtype == "f16":
+        wl.volt_raw = to_f16_pairs(v)
+        wl.volt = from_f16_pairs(wl.volt_raw)
+    else:
+        wl.volt_raw = to_c64_pairs(v)
+        wl.volt = wl.volt_raw[..., 0].astype(np.float64) + 1j * wl.volt_raw[..., 1].astype(np.float64)
+    return wl
+
+
+def workload_tiny(seed=1, n_time=64):
+    """16 antennas uniform in a 20 m x 20 m square, one pol, one channel at 60 MHz,
+    3 point sources + unit complex Gaussian noise, 2 m square apertures, spacing lambda/2,
+    N_p = 64 (N_g = 32), complex64 voltages."""
+    rng = np.random.default_rng(seed)
+    f = 60e6
+    lam = C_LIGHT / f
+    dx = lam / 2
+    pos = layout_rect(rng, 16, 20.0, 20.0)
+    kd, kw = kernel_square(2.0, dx / 4)
+    ptr, dxdy, w = pack_kernels([(kd, kw)] * 16)
+    n_grid, n_pad = 32, 64
+    origin = centred_origin(pos, 1.0, dx, n_grid)
+    sky = sky_box(rng, 3, 0.7, 1.0, 10.0)
+    v = voltages(rng, pos, [f], n_time, 1, sky, 1.0)
+    wl = Workload("tiny: 16 ant, 1 chan, 1 pol, T=%d, 64x64 image, c64" % n_time,
+                  pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, np.array([f]), 1, n_time, "c64")
+    wl.extra["sky"] = sky
+    return _finish(wl, v, "c64")
+
+
+def workload_lwa(seed=2, n_chan=128, n_time=1024, n_pol=2, chan_index=None, n_ant=256):
+    """LWA-like: 256 antennas uniform in a 100 m x 110 m ellipse, 2 pols, 128 channels over
+    30-80 MHz, 1024 samples, 200 power-law sources (index -1.5) over the visible hemisphere
+    at per-sample SNR 0.1, signed 4+4-bit voltages, Gaussian apertures (sigma 1.5 m, 3 sigma
+    support), spacing lambda/2 at 80 MHz, N_p = 128 (N_g = 64).
+
+    chan_index (optional) selects a subset of the 128 channel frequencies so reduced
+    slices keep the full-size layout and frequency axis."""
+    rng = np.random.default_rng(seed)
+    freqs_all = np.linspace(30e6, 80e6, 128)
+    freqs = freqs_all[:n_chan] if chan_index is None else freqs_all[np.asarray(chan_index)]
+    dx = C_LIGHT / 80e6 / 2
+    pos = layout_ellipse(rng, n_ant, 100.0, 110.0)
+    sigma = 1.5
+    kd, kw = kernel_gaussian(sigma, dx / 4)
+    ptr, dxdy, w = pack_kernels([(kd, kw)] * n_ant)
+    n_grid, n_pad = 64, 128
+    origin = centred_origin(pos, 3 * sigma, dx, n_grid)
+    sky = sky_powerlaw_hemisphere(rng, 200, 1.0, 100.0)
+    noise = math.sqrt(sky.flux.sum() / 0.1)
+    v = voltages(rng, pos, freqs, n_time, n_pol, sky, noise)
+    wl = Workload("LWA-like: %d ant, %d chan, %d pol, T=%d, 128x128 image, ci4"
+                  % (n_ant, len(freqs), n_pol, n_time),
+                  pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, freqs, n_pol, n_time, "ci4")
+    wl.extra["sky"] = sky
+    return _finish(wl, v, "ci4")
+
+
+def workload_hera(seed=3, n_chan=1024, n_time=256):
+    """Dense HERA-331-like hexagon (11 per side, 14 m spacing), 1 pol, channels over
+    100-200 MHz, FP16 voltages (50 sources + unit noise), 14 m uniform disk apertures
+    (far field: Airy disk) on a 2.5 m grid, N_p = 256 (N_g = 128)."""
+    rng = np.random.default_rng(seed)
+    freqs = np.linspace(100e6, 200e6, 1024)[:n_chan]
+    dx = 2.5
+    pos = layout_hex(11, 14.0)
+    kd, kw = kernel_disk(14.0, dx / 4)
+    ptr, dxdy, w = pack_kernels([(kd, kw)] * pos.shape[0])
+    n_grid, n_pad = 128, 256
+    origin = centred_origin(pos, 7.0, dx, n_grid)
+    sky = sky_box(rng, 50, 0.7, 1.0, 10.0)
+    v = voltages(rng, pos, freqs, n_time, 1, sky, 1.0)
+    wl = Workload("HERA-like: 331 ant, %d chan, 1 pol, T=%d, 256x256 image, f16" % (len(freqs), n_time),
+                  pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, freqs, 1, n_time, "f16")
+    wl.extra["sky"] = sky
+    return _finish(wl, v, "f16")
+
+
+def workload_calib(seed=5, n_chan=32, n_time=64, n_ant=1024):
+    """Gain calibration: 1024 antennas uniform in a 300 m (diameter) disk, 32 channels over
+    50-80 MHz, 64 samples, 1 pol, complex64; 50 sources; true gains amplitude 1 +- 0.2,
+    uniform phase; Gaussian apertures sigma 1.5 m; N_p = 256 (N_g = 128)."""
+    rng = np.random.default_rng(seed)
+    freqs = np.linspace(50e6, 80e6, 32)[:n_chan]
+    pos = layout_disk(rng, n_ant, 300.0)
+    sigma = 1.5
+    n_grid, n_pad = 128, 256
+    dx = (300.0 + 2 * 3 * sigma) / n_grid
+    kd, kw = kernel_gaussian(sigma, dx / 4)
+    ptr, dxdy, w = pack_kernels([(kd, kw)] * n_ant)
+    origin = centred_origin(pos, 3 * sigma, dx, n_grid)
+    sky = sky_box(rng, 50, 0.7, 1.0, 10.0)
+    v = voltages(rng, pos, freqs, n_time, 1, sky, 1.0)
+    g_true = random_gains(rng, (n_ant,))
+    v = v * g_true[None, None, None, :]
+    wl = Workload("calibration: %d ant, %d chan, 1 pol, T=%d, 256x256 image, c64" % (n_ant, len(freqs), n_time),
+                  pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, freqs, 1, n_time, "c64")
+    wl.extra["sky"] = sky
+    wl.extra["g_true"] = g_true
+    return _finish(wl, v, "c64")
