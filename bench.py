@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Throughput of the MOFF imaging step on one GB300 (or N, one process per GPU).
+
+Workload: the LWA-like array -- 256 antennas in a 100 m x 110 m ellipse, 2 polarisations,
+128 channels over 30-80 MHz, 1024 time samples per integration, signed 4+4-bit voltages
+(200 power-law point sources at per-sample SNR 0.1), Gaussian apertures (sigma 1.5 m),
+lambda/2 grid at 80 MHz, 128 x 128 padded grid (64 x 64 unpadded): 262,144 instantaneous
+images and 67.1 M antenna-samples per step.  Synthetic, seeded.
+
+One step = one epic_image call over the whole integration: decode + gains, gridding,
+zero-padded 2-D transform, |.|^2, time accumulation (float64), the averaged image and the
+antenna auto-correlation term.  Inputs are resident in HBM; the 67 MB of voltages fit in
+L2, so L2 is flushed (a 256 MB write) before every timed step, outside the timed events.
+
+Metric: antenna-samples/s (A * T * C * P per second, whole job); images/s is reported
+beside it.  `--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MOFF antenna-samples/s (images/s beside it), FP32 path, error vs FP64 oracle stated"
+UNIT = "antenna-samples/s"
+# Peak FP32 rate of the CUDA cores: SMs x 128 lanes x 2 FLOP (FMA) x max SM clock.
+SM_MAX_MHZ = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the forward kernel on this
+# workload, from ncu (profiles/moff_fwd_np128_ci4_lwa.md); None until captured for the
+# current kernel.
+FWD_TRAFFIC_BYTES = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_algorithmic_flops(wl, nnz):
+    """Per image: the paper's FFT operation count beta * N log2 N with beta = 5 on the
+    N = N_p^2 padded pixels (Sec. 6.1), + 8 FLOP per non-zero of M (complex multiply-add
+    in the gridding), + 4 FLOP per pixel (|.|^2 and the time accumulation)."""
+    n = wl.n_pad * wl.n_pad
+    return 5.0 * n * math.log2(n) + 8.0 * nnz + 4.0 * n
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_sample(wl_full, plan=None, torch=None):
+    """Time the FP64 oracle on a bounded sample: channel 127, pol 1, the first 256 samples
+    (65,536 antenna-samples), image + auto-correlation term.  If a plan is given, the CUDA
+    path images the same sample and its relative L2 error against the oracle is returned."""
+    import numpy as np
+    from oracle import moff
+    wl = wl_full
+    c, p, T = wl.n_chan - 1, wl.n_pol - 1, 256
+    v = wl.volt[:T, c:c + 1, p:p + 1, :]
+    t0 = time.perf_counter()
+    M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+    img = moff.moff_image(M, v, None, wl.n_grid, wl.n_pad)
+    moff.autocorr_term(M, v, None, wl.n_grid, wl.n_pad)
+    dt = time.perf_counter() - t0
+    err = None
+    if plan is not None:
+        from paper_1510_08318_gb300 import epic
+        sub = epic.Plan(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid, wl.n_pad,
+                        1, 1, wl.vdtype, plan.device)
+        raw = np.ascontiguousarray(wl.volt_raw[:T, c:c + 1, p:p + 1, :])
+        out = sub.image(torch.from_numpy(raw).cuda(plan.device))
+        got = out["image"].cpu().numpy()
+        err = float(np.linalg.norm(got - img) / np.linalg.norm(img))
+        sub.close()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rate = wl.n_ant * T / dt
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "channel %d, pol %d, samples 0-%d of the same workload (%d antenna-samples): FP64 "
+                      "gridding + separable DFT + |.|^2 + mean, and the auto-correlation term; %.2f s"
+                      % (c, p, T - 1, wl.n_ant * T, dt)}, err
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_1510_08318_gb300 import synth
+    wl = synth.workload_lwa()
+    for _ in range(args.warmup):
+        cpu_baseline_sample(wl)
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, _ = cpu_baseline_sample(wl)
+        rates.append(r["value"])
+        secs.append(wl.n_ant * 256 / r["value"])
+    sec_per_unit = sum(secs) / sum(wl.n_ant * 256 for _ in secs)
+    value = 1.0 / sec_per_unit
+    full = wl.n_ant * wl.n_time * wl.n_chan * wl.n_pol
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "step": "bounded sample per step "
+                                            "(channel 127, pol 1, 256 samples), ms_per_step extrapolated "
+                                            "to the full integration"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_1510_08318_gb300 import build, epic, synth
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    epic.load()
+
+    wl = synth.workload_lwa()
+    plan = epic.Plan.from_workload(wl, device=local)
+    A, T, C, P, NP = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_pad
+    volt = torch.from_numpy(wl.volt_raw).to(dev)
+    accum = torch.empty((C, P, NP, NP), dtype=torch.float64, device=dev)
+    power = torch.empty((C, P, A), dtype=torch.float64, device=dev)
+    image = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
+    autoc = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    h = plan._h
+
+    def step():
+        epic.epic_image(h, volt.data_ptr(), T, None, accum.data_ptr(), power.data_ptr(), 0,
+                        image.data_ptr(), autoc.data_ptr(), st.cuda_stream)
+
+    def kernel_only():
+        epic.epic_image(h, volt.data_ptr(), T, None, accum.data_ptr(), None, 0, None, None, st.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(st)
+        step()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier()
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if world > 1:
+        tt = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(tt.item())
+
+    # forward kernel alone (accumulator only), for the roofline
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        kev[i][0].record(st)
+        kernel_only()
+        kev[i][1].record(st)
+    torch.cuda.synchronize()
+    kern_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+
+    # end to end through the public API: pinned host voltages in, image back to the host
+    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
+    host_img = torch.empty((C, P, NP, NP), dtype=torch.float32).pin_memory()
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        eev[i][0].record(st)
+        volt.copy_(host_v, non_blocking=True)
+        step()
+        host_img.copy_(image, non_blocking=True)
+        eev[i][1].record(st)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eev) / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms, kern_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms, kern_ms = float(tt[0].item()), float(tt[1].item())
+
+    units = A * T * C * P
+    value = world * units / (step_ms / 1e3)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = n_sm * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * P
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "antennas": A, "time_samples": T, "channels": C, "pols": P,
+                   "grid": "%dx%d padded to %dx%d" % (wl.n_grid, wl.n_grid, NP, NP), "voltages": "ci4",
+                   "images_per_step": T * C * P, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "independent replicas per GPU" if world > 1 else "1 GPU"},
+        "images_per_s": world * T * C * P / (step_ms / 1e3),
+        "kernel_ms": kern_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": FWD_TRAFFIC_BYTES,
+                     "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, max clock)"
+                                   % (n_sm, SM_MAX_MHZ)},
+        "e2e": {"value": world * units / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
+                "d2h_bytes_per_step": int(host_img.numel() * host_img.element_size())},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, err = cpu_baseline_sample(wl, plan, torch)
+        line["cpu_baseline"] = cb
+        line["err_vs_oracle"] = {"relative_l2": err, "sample": "channel 127, pol 1, 256 samples, image"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * epic.h -- C ABI of the GB300 MOFF imaging library.
+ *
+ * The library implements the per-sample imaging step of the E-field Parallel Imaging
+ * Correlator (Thyagarajan, Beardsley, Bowman & Morales 2015, "A generic and efficient
+ * E-field parallel imaging correlator for next-generation radio telescopes"):
+ * for every time sample, channel and polarisation the calibrated antenna voltages are
+ * gridded with their aperture-illumination kernels (Sec. 3 "Gridding Convolution"),
+ * zero-padded and spatially Fourier transformed (Sec. 3 "Spatial Fourier Transform"),
+ * squared and time-averaged (Sec. 3 "Time-averaging"), which is the MOFF imaging
+ * equation (Eq. "dirty-image-MOFF").
+ *
+ * Conventions shared by every call:
+ *   - All sizes are plain ints; all device pointers are caller-owned (e.g. allocated
+ *     by PyTorch) and never freed by the library.  Host pointers are only read during
+ *     the call.
+ *   - Complex numbers are interleaved (re, im) pairs.
+ *   - Grid cell (gy, gx) of the N_g x N_g grid sits at origin + dx * (gx, gy) metres.
+ *     The padded grid is N_p x N_p with the gridded field in its corner [0, N_g)^2.
+ *   - Spatial transform: F(k) = sum_g E(g) exp(+2 pi i g.k / N_p), unnormalised (the
+ *     imaging sign of App. B; a source at direction s appears at +s).
+ *   - Images are N_p x N_p, row-major (iy, ix), with k = 0 at pixel (N_p/2, N_p/2):
+ *     pixel (iy, ix) is direction (l, m) = ((ix - N_p/2), (iy - N_p/2)) * lambda / (N_p dx).
+ *   - Every call returns an epic_status and never aborts; on failure epic_last_error()
+ *     returns a thread-local message.  Arguments are validated on the host before any
+ *     launch.  Calls are asynchronous on the caller's stream; a CUDA error raised by a
+ *     launch is reported as EPIC_ECUDA.
+ */
+#ifndef EPIC_H
+#define EPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct epic_plan epic_plan;
+
+typedef enum {
+    EPIC_OK = 0,
+    EPIC_EINVAL = 1,        /* invalid argument (message says which) */
+    EPIC_ENOMEM = 2,        /* the plan's device tables could not be allocated */
+    EPIC_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+    EPIC_EUNSUPPORTED = 4   /* valid, but outside what this build implements */
+} epic_status;
+
+typedef enum {
+    EPIC_VOLT_C64 = 0,      /* complex64: float re, float im (8 bytes) */
+    EPIC_VOLT_F16 = 1,      /* complex half: half re, half im (4 bytes) */
+    EPIC_VOLT_CI4 = 2       /* 4+4-bit: one byte, high nibble re, low nibble im,
+                               each a 4-bit two's-complement integer */
+} epic_volt_dtype;
+
+/*
+ * epic_create -- build the antenna-to-grid mapping and the device tables (once per
+ * array; Sec. 3 "Antenna-to-Grid Mapping").
+ *
+ *   plan        out: new plan, owned by the caller until epic_destroy.
+ *   n_ant       number of antennas A (1 .. 4096).
+ *   pos_xy      host [A][2] float64, antenna positions in metres (x, y).
+ *   kern_ptr    host [A+1] int32, CSR row pointers into the footprint tables: antenna a
+ *               owns samples kern_ptr[a] .. kern_ptr[a+1]-1 (kern_ptr[0] == 0).
+ *   kern_dxdy   host [nt][2] float64, footprint sample offsets from the antenna (m).
+ *   kern_w      host [nt][2] float64, complex sample weights of the illumination W_a.
+ *   dx          grid spacing in metres (> 0).
+ *   origin_xy   host [2] float64, position (m) of the centre of grid cell (0, 0).
+ *   n_grid      N_g, the unpadded grid side (1 .. n_pad/2).
+ *   n_pad       N_p, the padded grid and image side: 32, 64, 128 or 256.
+ *   n_chan      C, channels per call (>= 1).
+ *   n_pol       P, polarisations per call (>= 1).
+ *   volt_dtype  one of epic_volt_dtype.
+ *   device      CUDA device ordinal the plan lives on.
+ *
+ * Each footprint sample maps to its nearest grid cell, per axis
+ * floor((r_a + delta - origin) / dx + 0.5) evaluated in float64; the weights of samples
+ * landing in the same cell are summed (the sparse matrix M(r, a) of Sec. 3).  A sample
+ * outside [0, N_g)^2 is EPIC_EINVAL.  The mapping is shared by all channels: it is in
+ * metres, and channel c's pixel scale follows from its wavelength.
+ */
+epic_status epic_create(epic_plan **plan, int n_ant, const double *pos_xy,
+                        const int *kern_ptr, const double *kern_dxdy, const double *kern_w,
+                        double dx, const double *origin_xy, int n_grid, int n_pad,
+                        int n_chan, int n_pol, int volt_dtype, int device);
+
+/* Release the plan and its device tables.  NULL is accepted. */
+void epic_destroy(epic_plan *plan);
+
+/*
+ * epic_image -- the MOFF imaging step (Eq. "dirty-image-MOFF") for one block of samples.
+ *
+ *   volt      device [T][C][P][A] voltages in the plan's volt_dtype.
+ *   n_time    T >= 1.
+ *   gains     device [C][P][A] complex64 per-antenna gains applied before gridding
+ *             (Sec. 3 "Calibration"), or NULL for unit gains.
+ *   accum     device [C][P][N_p][N_p] float64: receives sum_t |F_t(k)|^2.  If t_prev > 0
+ *             the sum continues onto the values already there (the integration resumes);
+ *             if t_prev == 0 it is overwritten.
+ *   power     device [C][P][A] float64 or NULL: receives sum_t |g_a V_a(t)|^2 with the same
+ *             continue/overwrite rule.  Required when autocorr != NULL.
+ *   t_prev    number of samples already integrated into accum / power (>= 0).
+ *   image     device [C][P][N_p][N_p] float32 or NULL: accum / (t_prev + T), the
+ *             time-averaged image.
+ *   autocorr  device [C][P][N_p][N_p] float32 or NULL: the antenna auto-correlation term
+ *             of the averaged image (Sec. 4.2), A(k) = sum_a P_a |K_a(k)|^2 with
+ *             P_a = power_a / (t_prev + T) and K_a(k) the transform of antenna a's
+ *             gridded footprint.  image - autocorr is the cross-correlation-only image.
+ *   stream    cudaStream_t to launch on (NULL = the legacy default stream).
+ *
+ * Work is split across the whole GPU; accum and power are updated with float64 atomic
+ * adds, so their low-order bits may differ between runs.
+ */
+epic_status epic_image(const epic_plan *plan, const void *volt, int n_time, const float *gains,
+                       double *accum, double *power, int64_t t_prev,
+                       float *image, float *autocorr, void *stream);
+
+/*
+ * epic_image_backward -- adjoint of epic_image with respect to the gains.
+ *
+ * For a real loss L of the averaged image I = (1/T) sum_t |F_t|^2 of one call (t_prev = 0),
+ * given grad_image = dL/dI (device [C][P][N_p][N_p] float32, image pixel order), writes
+ * grad_gains = dL/dRe(g) + i dL/dIm(g) (device [C][P][A] complex64), i.e.
+ *   grad_a = (2/T) sum_t conj(V_a(t)) sum_g conj(M[g, a]) sum_k G(k) F_t(k) exp(-2 pi i g.k/N_p),
+ * the chain rule through Eq. "dirty-image-MOFF" with the gains applied as in Sec. 3
+ * "Calibration" (their use in feedback calibration).  The per-sample fields F_t are
+ * recomputed, not stored.  volt, n_time and gains are as for epic_image.
+ * grad_gains is overwritten (accumulated with float32 atomic adds).
+ */
+epic_status epic_image_backward(const epic_plan *plan, const void *volt, int n_time,
+                                const float *gains, const float *grad_image, float *grad_gains,
+                                void *stream);
+
+/*
+ * epic_plan_info -- sizes of the plan (any pointer may be NULL):
+ *   nnz       non-zeros of the mapping M(r, a) (cells x antennas);
+ *   n_cells   occupied grid cells;
+ *   lag_side  side L of the per-antenna footprint auto-correlation tables (L x L lags).
+ */
+epic_status epic_plan_info(const epic_plan *plan, int64_t *nnz, int64_t *n_cells, int *lag_side);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char *epic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPIC_H */

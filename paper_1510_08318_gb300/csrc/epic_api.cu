@@ -1,0 +1,393 @@
+// C ABI of the MOFF imaging library: plan construction (the antenna-to-grid mapping of
+// Sec. 3, built once in float64 on the host), argument validation and launches.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/epic.h"
+#include "epic_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+epic_status fail(epic_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+epic_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(EPIC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_pow2_size(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        if (ok && prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct epic_plan {
+    int n_ant = 0, n_grid = 0, n_pad = 0, n_chan = 0, n_pol = 0, vdt = 0, device = 0, n_sm = 0;
+    int lag_side = 0;
+    int64_t nnz = 0, n_cells = 0;
+    int* cell_ptr = nullptr;
+    int4* cell_ent = nullptr;
+    int* ant_ptr = nullptr;
+    int4* ant_ent = nullptr;
+    float2* twiddle = nullptr;
+    float2* lag_tab = nullptr;
+};
+
+namespace {
+
+void free_plan(epic_plan* p) {
+    if (!p) return;
+    cudaFree(p->cell_ptr);
+    cudaFree(p->cell_ent);
+    cudaFree(p->ant_ptr);
+    cudaFree(p->ant_ent);
+    cudaFree(p->twiddle);
+    cudaFree(p->lag_tab);
+    delete p;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+    const size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+int4 pack_entry(std::complex<double> w, int idx) {
+    const float wr = float(w.real()), wi = float(w.imag());
+    int4 e;
+    std::memcpy(&e.x, &wr, 4);
+    std::memcpy(&e.y, &wi, 4);
+    e.z = idx;
+    e.w = 0;
+    return e;
+}
+
+struct MapEntry {
+    int cell, ant, tap;
+    std::complex<double> w;
+};
+
+epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t st) {
+    cudaError_t e;
+    switch (p->n_pad) {
+        case 32: e = epic::launch_fwd_32(p->vdt, a, p->n_sm, st); break;
+        case 64: e = epic::launch_fwd_64(p->vdt, a, p->n_sm, st); break;
+        case 128: e = epic::launch_fwd_128(p->vdt, a, p->n_sm, st); break;
+        case 256: e = epic::launch_fwd_256(p->vdt, a, p->n_sm, st); break;
+        default: return fail(EPIC_EUNSUPPORTED, "n_pad %d", p->n_pad);
+    }
+    return e == cudaSuccess ? EPIC_OK : cuda_fail(e, "imaging kernel launch");
+}
+
+epic_status launch_bwd(const epic_plan* p, const epic::BwdArgs& a, cudaStream_t st) {
+    cudaError_t e;
+    switch (p->n_pad) {
+        case 32: e = epic::launch_bwd_32(p->vdt, a, p->n_sm, st); break;
+        case 64: e = epic::launch_bwd_64(p->vdt, a, p->n_sm, st); break;
+        case 128: e = epic::launch_bwd_128(p->vdt, a, p->n_sm, st); break;
+        case 256: e = epic::launch_bwd_256(p->vdt, a, p->n_sm, st); break;
+        default: return fail(EPIC_EUNSUPPORTED, "n_pad %d", p->n_pad);
+    }
+    return e == cudaSuccess ? EPIC_OK : cuda_fail(e, "adjoint kernel launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* epic_last_error(void) { return g_err.c_str(); }
+
+epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const int* kern_ptr,
+                        const double* kern_dxdy, const double* kern_w, double dx,
+                        const double* origin_xy, int n_grid, int n_pad, int n_chan, int n_pol,
+                        int volt_dtype, int device) {
+    g_err.clear();
+    if (!plan) return fail(EPIC_EINVAL, "plan out-pointer is NULL");
+    *plan = nullptr;
+    if (n_ant < 1 || n_ant > 4096) return fail(EPIC_EINVAL, "n_ant = %d outside 1..4096", n_ant);
+    if (!pos_xy || !kern_ptr || !origin_xy) return fail(EPIC_EINVAL, "NULL host array");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(EPIC_EINVAL, "grid spacing must be finite and > 0");
+    if (!std::isfinite(origin_xy[0]) || !std::isfinite(origin_xy[1])) return fail(EPIC_EINVAL, "origin not finite");
+    if (!is_pow2_size(n_pad)) return fail(EPIC_EUNSUPPORTED, "n_pad = %d (supported: 32, 64, 128, 256)", n_pad);
+    if (n_grid < 1 || 2 * n_grid > n_pad)
+        return fail(EPIC_EINVAL, "n_grid = %d must be in 1..n_pad/2 (2x zero padding)", n_grid);
+    if (n_chan < 1 || n_pol < 1) return fail(EPIC_EINVAL, "n_chan and n_pol must be >= 1");
+    if (volt_dtype < EPIC_VOLT_C64 || volt_dtype > EPIC_VOLT_CI4) return fail(EPIC_EINVAL, "volt_dtype %d", volt_dtype);
+    if (kern_ptr[0] != 0) return fail(EPIC_EINVAL, "kern_ptr[0] must be 0");
+    for (int a = 0; a < n_ant; ++a)
+        if (kern_ptr[a + 1] < kern_ptr[a]) return fail(EPIC_EINVAL, "kern_ptr not non-decreasing at antenna %d", a);
+    const int n_taps = kern_ptr[n_ant];
+    if (n_taps > 0 && (!kern_dxdy || !kern_w)) return fail(EPIC_EINVAL, "NULL footprint table");
+
+    const int NG = n_pad / 2;   // the kernels work on the N_p/2 grid; cells >= n_grid stay empty
+    const double ox = origin_xy[0], oy = origin_xy[1];
+    std::vector<MapEntry> ents;
+    ents.reserve(n_taps);
+    for (int a = 0; a < n_ant; ++a) {
+        const double px = pos_xy[2 * a], py = pos_xy[2 * a + 1];
+        if (!std::isfinite(px) || !std::isfinite(py)) return fail(EPIC_EINVAL, "antenna %d position not finite", a);
+        for (int k = kern_ptr[a]; k < kern_ptr[a + 1]; ++k) {
+            const double x = px + kern_dxdy[2 * k];
+            const double y = py + kern_dxdy[2 * k + 1];
+            const double ux = (x - ox) / dx + 0.5;
+            const double uy = (y - oy) / dx + 0.5;
+            if (!std::isfinite(ux) || !std::isfinite(uy))
+                return fail(EPIC_EINVAL, "footprint sample %d of antenna %d not finite", k, a);
+            const double fx = std::floor(ux), fy = std::floor(uy);
+            if (fx < 0 || fy < 0 || fx >= n_grid || fy >= n_grid)
+                return fail(EPIC_EINVAL, "footprint sample %d of antenna %d maps to cell (%g, %g) outside the %d x %d grid",
+                            k, a, fy, fx, n_grid, n_grid);
+            const std::complex<double> w(kern_w[2 * k], kern_w[2 * k + 1]);
+            if (!std::isfinite(w.real()) || !std::isfinite(w.imag()))
+                return fail(EPIC_EINVAL, "footprint weight %d not finite", k);
+            ents.push_back({int(fy) * NG + int(fx), a, k, w});
+        }
+    }
+    // M(r, a): sum the weights of samples of the same antenna landing in the same cell,
+    // in tap order.
+    std::stable_sort(ents.begin(), ents.end(), [](const MapEntry& l, const MapEntry& r) {
+        return l.cell != r.cell ? l.cell < r.cell : (l.ant != r.ant ? l.ant < r.ant : l.tap < r.tap);
+    });
+    std::vector<MapEntry> m;
+    for (const MapEntry& e : ents) {
+        if (!m.empty() && m.back().cell == e.cell && m.back().ant == e.ant)
+            m.back().w += e.w;
+        else
+            m.push_back(e);
+    }
+
+    epic_plan* p = new epic_plan;
+    p->n_ant = n_ant;
+    p->n_grid = n_grid;
+    p->n_pad = n_pad;
+    p->n_chan = n_chan;
+    p->n_pol = n_pol;
+    p->vdt = volt_dtype;
+    p->device = device;
+    p->nnz = (int64_t)m.size();
+
+    // cell-major CSR (gather side of the gridding)
+    std::vector<int> cptr((size_t)NG * NG + 1, 0);
+    std::vector<int4> cent;
+    cent.reserve(m.size());
+    for (const MapEntry& e : m) {
+        cptr[e.cell + 1]++;
+        cent.push_back(pack_entry(e.w, e.ant));
+    }
+    for (size_t i = 0; i + 1 < cptr.size(); ++i) {
+        if (cptr[i + 1] > 0) p->n_cells++;
+        cptr[i + 1] += cptr[i];
+    }
+
+    // antenna-major CSR per row block (degridding side of the adjoint); cells are stored as
+    // offsets into the adjoint kernel's shared-memory row buffer
+    const int rows = epic::grid_rows_per_block(n_pad);
+    const int nq = NG / rows;
+    const int rxs = epic::exchange_row_stride(n_pad);
+    std::vector<std::vector<std::pair<int, int4>>> per_ant((size_t)nq * n_ant);
+    for (const MapEntry& e : m) {
+        const int gy = e.cell / NG, gx = e.cell % NG;
+        const int q = gy / rows;
+        per_ant[(size_t)q * n_ant + e.ant].push_back({e.cell, pack_entry(e.w, (gy - q * rows) * rxs + gx)});
+    }
+    std::vector<int> aptr((size_t)nq * (n_ant + 1), 0);
+    std::vector<int4> aent;
+    aent.reserve(m.size());
+    for (int q = 0; q < nq; ++q) {
+        aptr[(size_t)q * (n_ant + 1)] = (int)aent.size();
+        for (int a = 0; a < n_ant; ++a) {
+            for (auto& pe : per_ant[(size_t)q * n_ant + a]) aent.push_back(pe.second);
+            aptr[(size_t)q * (n_ant + 1) + a + 1] = (int)aent.size();
+        }
+    }
+
+    // per-antenna footprint auto-correlation R_a(d) on the L x L lag window
+    std::vector<std::vector<const MapEntry*>> by_ant(n_ant);
+    for (const MapEntry& e : m) by_ant[e.ant].push_back(&e);
+    int ext = 1;
+    for (int a = 0; a < n_ant; ++a) {
+        if (by_ant[a].empty()) continue;
+        int x0 = 1 << 30, x1 = -1, y0 = 1 << 30, y1 = -1;
+        for (const MapEntry* e : by_ant[a]) {
+            const int gy = e->cell / NG, gx = e->cell % NG;
+            x0 = std::min(x0, gx); x1 = std::max(x1, gx);
+            y0 = std::min(y0, gy); y1 = std::max(y1, gy);
+        }
+        ext = std::max(ext, std::max(x1 - x0 + 1, y1 - y0 + 1));
+    }
+    const int L = 2 * ext - 1;
+    std::vector<float2> lag;
+    if (L <= 63) {
+        p->lag_side = L;
+        const int h = ext - 1;
+        lag.assign((size_t)n_ant * L * L, make_float2(0.f, 0.f));
+        std::vector<std::complex<double>> acc((size_t)L * L);
+        for (int a = 0; a < n_ant; ++a) {
+            std::fill(acc.begin(), acc.end(), std::complex<double>(0.0, 0.0));
+            for (const MapEntry* e : by_ant[a])
+                for (const MapEntry* f : by_ant[a]) {
+                    const int dy = e->cell / NG - f->cell / NG, dxl = e->cell % NG - f->cell % NG;
+                    acc[(size_t)(dy + h) * L + (dxl + h)] += e->w * std::conj(f->w);
+                }
+            for (size_t j = 0; j < acc.size(); ++j)
+                lag[(size_t)a * L * L + j] = make_float2(float(acc[j].real()), float(acc[j].imag()));
+        }
+    }
+
+    std::vector<float2> tw(n_pad);
+    for (int j = 0; j < n_pad; ++j) {
+        const double ang = 2.0 * M_PI * double(j) / double(n_pad);
+        tw[j] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+    }
+
+    DeviceGuard guard(device);
+    if (!guard.ok) {
+        delete p;
+        return fail(EPIC_ECUDA, "cannot select CUDA device %d", device);
+    }
+    cudaError_t e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    const size_t need = std::max(epic::fwd_smem_bytes(n_pad, n_ant), epic::bwd_smem_bytes(n_pad, n_ant));
+    if (need > (size_t)smem_optin) {
+        delete p;
+        return fail(EPIC_EUNSUPPORTED, "%d antennas need %zu bytes of shared memory per block (device limit %d)",
+                    n_ant, need, smem_optin);
+    }
+    if ((e = upload(&p->cell_ptr, cptr)) != cudaSuccess || (e = upload(&p->cell_ent, cent)) != cudaSuccess ||
+        (e = upload(&p->ant_ptr, aptr)) != cudaSuccess || (e = upload(&p->ant_ent, aent)) != cudaSuccess ||
+        (e = upload(&p->twiddle, tw)) != cudaSuccess || (e = upload(&p->lag_tab, lag)) != cudaSuccess) {
+        free_plan(p);
+        return e == cudaErrorMemoryAllocation ? fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
+                                              : cuda_fail(e, "plan upload");
+    }
+    *plan = p;
+    return EPIC_OK;
+}
+
+void epic_destroy(epic_plan* plan) {
+    if (!plan) return;
+    DeviceGuard guard(plan->device);
+    free_plan(plan);
+}
+
+epic_status epic_plan_info(const epic_plan* plan, int64_t* nnz, int64_t* n_cells, int* lag_side) {
+    g_err.clear();
+    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
+    if (nnz) *nnz = plan->nnz;
+    if (n_cells) *n_cells = plan->n_cells;
+    if (lag_side) *lag_side = plan->lag_side;
+    return EPIC_OK;
+}
+
+epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, const float* gains,
+                       double* accum, double* power, int64_t t_prev, float* image, float* autocorr,
+                       void* stream) {
+    g_err.clear();
+    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
+    if (n_time < 1) return fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
+    if (!volt) return fail(EPIC_EINVAL, "volt is NULL");
+    if (!accum) return fail(EPIC_EINVAL, "accum is NULL");
+    if (t_prev < 0) return fail(EPIC_EINVAL, "t_prev must be >= 0");
+    if (autocorr && !power) return fail(EPIC_EINVAL, "autocorr needs the power accumulator");
+    if (autocorr && plan->lag_side == 0)
+        return fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int cp = plan->n_chan * plan->n_pol;
+    const size_t npix = (size_t)cp * plan->n_pad * plan->n_pad;
+    cudaError_t e;
+    if (t_prev == 0) {
+        if ((e = cudaMemsetAsync(accum, 0, npix * sizeof(double), st)) != cudaSuccess) return cuda_fail(e, "memset accum");
+        if (power && (e = cudaMemsetAsync(power, 0, (size_t)cp * plan->n_ant * sizeof(double), st)) != cudaSuccess)
+            return cuda_fail(e, "memset power");
+    }
+    epic::FwdArgs a;
+    a.volt = volt;
+    a.n_time = n_time;
+    a.n_cp = cp;
+    a.n_ant = plan->n_ant;
+    a.gains = reinterpret_cast<const float2*>(gains);
+    a.cell_ptr = plan->cell_ptr;
+    a.cell_ent = plan->cell_ent;
+    a.twiddle = plan->twiddle;
+    a.accum = accum;
+    a.power = power;
+    a.n_items = (long long)cp * n_time;
+    a.flush_every = 1024;
+    epic_status s = launch_fwd(plan, a, st);
+    if (s != EPIC_OK) return s;
+    const double inv_t = 1.0 / double(t_prev + n_time);
+    if (image && (e = epic::launch_finalize_image(accum, image, (long long)npix, inv_t, st)) != cudaSuccess)
+        return cuda_fail(e, "image epilogue");
+    if (autocorr && (e = epic::launch_autocorr(power, plan->lag_tab, cp, plan->n_ant, plan->lag_side, plan->n_pad,
+                                               inv_t, autocorr, st)) != cudaSuccess)
+        return cuda_fail(e, "auto-correlation epilogue");
+    return EPIC_OK;
+}
+
+epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_time, const float* gains,
+                                const float* grad_image, float* grad_gains, void* stream) {
+    g_err.clear();
+    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
+    if (n_time < 1) return fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
+    if (!volt || !grad_image || !grad_gains) return fail(EPIC_EINVAL, "NULL device array");
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int cp = plan->n_chan * plan->n_pol;
+    cudaError_t e = cudaMemsetAsync(grad_gains, 0, (size_t)cp * plan->n_ant * 2 * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset grad_gains");
+    epic::BwdArgs a;
+    a.volt = volt;
+    a.n_time = n_time;
+    a.n_cp = cp;
+    a.n_ant = plan->n_ant;
+    a.gains = reinterpret_cast<const float2*>(gains);
+    a.cell_ptr = plan->cell_ptr;
+    a.cell_ent = plan->cell_ent;
+    a.ant_ptr = plan->ant_ptr;
+    a.ant_ent = plan->ant_ent;
+    a.twiddle = plan->twiddle;
+    a.grad_image = grad_image;
+    a.grad_gains = reinterpret_cast<float2*>(grad_gains);
+    a.n_items = (long long)cp * n_time;
+    a.scale = float(2.0 / double(n_time));
+    return launch_bwd(plan, a, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace epic {
+
+// Everything a launch needs, all device pointers.
+struct FwdArgs {
+    const void* volt;          // [T][C][P][A] raw voltages
+    int n_time, n_cp, n_ant;   // T, C*P, A
+    const float2* gains;       // [CP][A] or nullptr (unit gains)
+    const int* cell_ptr;       // [NG*NG + 1] CSR by grid cell (NG = N_p / 2)
+    const int4* cell_ent;      // {weight re bits, weight im bits, antenna, 0}
+    const float2* twiddle;     // [N_p] exp(+2 pi i j / N_p)
+    double* accum;             // [CP][N_p][N_p] sum_t |F_t|^2
+    double* power;             // [CP][A] sum_t |g V|^2 or nullptr
+    long long n_items;         // CP * T
+    int flush_every;           // samples per float32 partial before a float64 flush
+};
+
+struct BwdArgs {
+    const void* volt;
+    int n_time, n_cp, n_ant;
+    const float2* gains;
+    const int* cell_ptr;
+    const int4* cell_ent;
+    const int* ant_ptr;        // [Q][A+1] CSR by antenna, per row block of the grid
+    const int4* ant_ent;       // {weight re bits, weight im bits, cell (row-block local), 0}
+    const float2* twiddle;
+    const float* grad_image;   // [CP][N_p][N_p] dL/dI, image pixel order
+    float2* grad_gains;        // [CP][A]
+    long long n_items;
+    float scale;               // 2 / T
+};
+
+// Kernel launchers, one translation unit per padded size.  Return cudaSuccess or the
+// launch error.  `smem_bytes` is computed by the launcher.
+cudaError_t launch_fwd_32(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_64(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_128(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_256(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_bwd_32(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_bwd_64(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_bwd_128(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_bwd_256(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
+
+// Shared-memory bytes the forward / backward kernels need for a given size and antenna count.
+size_t fwd_smem_bytes(int n_pad, int n_ant);
+size_t bwd_smem_bytes(int n_pad, int n_ant);
+int grid_rows_per_block(int n_pad);   // rows of the N_g grid each CTA of a cluster owns
+int exchange_row_stride(int n_pad);   // row stride (float2) of the kernels' exchange buffer
+
+// Epilogue kernels (finalize.cu).
+cudaError_t launch_finalize_image(const double* accum, float* image, long long n, double inv_t,
+                                  cudaStream_t st);
+cudaError_t launch_autocorr(const double* power, const float2* lag_tab, int n_cp, int n_ant,
+                            int lag_side, int n_pad, double inv_t, float* out, cudaStream_t st);
+
+}  // namespace epic

@@ -1,0 +1,93 @@
+// Geometry, voltage decoding and shared-memory layout common to the forward and
+// adjoint MOFF kernels.
+#pragma once
+#include <cuda_fp16.h>
+#include <cooperative_groups.h>
+#include "dft.cuh"
+#include "epic_internal.h"
+
+namespace epic {
+namespace cg = cooperative_groups;
+
+// Per padded size N_p: S threads cooperate on each 1-D transform; a cluster of Q CTAs
+// shares one image (each CTA owns N_p/Q output columns and N_g/Q grid rows).
+template <int NP> struct Cfg;
+template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8; };
+template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2; };
+template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1; };
+template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1; };
+
+template <int NP> struct Geo {
+    static constexpr int NG = NP / 2;          // unpadded grid side (2x padding, Sec. 3)
+    static constexpr int S = Cfg<NP>::S;
+    static constexpr int Q = Cfg<NP>::Q;
+    static constexpr int MINB = Cfg<NP>::MINB;
+    static constexpr int R1 = NP / S;          // first-stage sub-transform length
+    static constexpr int NI = NG / S;          // its non-zero inputs (= R1 / 2)
+    static constexpr int KP = R1 / S;          // second-stage sub-transforms per thread
+    static constexpr int ROWS = NG / Q;        // grid rows per CTA in the row pass
+    static constexpr int COLS = NP / Q;        // image columns per CTA in the column pass
+    static constexpr int NT = ROWS * S;        // threads per CTA
+    static constexpr int LPC = 32 / S;         // rows (or columns) per warp
+    static constexpr int RXS = NP + 8;         // row stride of the exchange buffer (float2)
+    static constexpr int RBS = COLS + 2;       // row stride of the row-pass output (float2)
+    static constexpr int NACC = 2 * R1;        // image pixels owned by each thread
+    static constexpr int VPT = 4;              // voltages prefetched per thread
+    static_assert(NI * 2 == R1 && KP * S == R1 && KP >= 1, "bad factorisation");
+    static_assert(COLS % R1 == 0 || Q == 1, "row-pass outputs must map to one CTA per k1");
+    static_assert(NT % 32 == 0 || NT < 32, "threads");
+    // XOR swizzle of the exchange buffer: keeps the first-stage writes (one n1, all k2) and
+    // the second-stage reads (one k2 block, all n1) free of bank conflicts.
+    static __device__ __forceinline__ int swz(int k2) { return (k2 / KP) & (S - 1); }
+
+    static constexpr size_t smem_bytes(int n_ant) {
+        return sizeof(float2) * (size_t(ROWS) * RXS + size_t(NG) * RBS + NP)
+             + size_t(n_ant) * (2 * sizeof(float2) + sizeof(float));
+    }
+};
+
+// ---- raw voltage formats ---------------------------------------------------------------
+template <int VDT> struct Volt;
+template <> struct Volt<0> {                   // complex64
+    using T = float2;
+    static __device__ __forceinline__ float2 dec(T v) { return v; }
+};
+template <> struct Volt<1> {                   // complex half
+    using T = unsigned int;
+    static __device__ __forceinline__ float2 dec(T v) {
+        __half2 h = *reinterpret_cast<const __half2*>(&v);
+        return __half22float2(h);
+    }
+};
+template <> struct Volt<2> {                   // signed 4+4-bit
+    using T = unsigned char;
+    static __device__ __forceinline__ float2 dec(T v) {
+        const int b = v;
+        const int re = (b >> 4) - ((b & 0x80) >> 3);
+        const int im = (b & 0xF) - ((b & 0x8) << 1);
+        return make_float2(float(re), float(im));
+    }
+};
+
+__device__ __forceinline__ void cfma(float2& acc, float2 w, float2 v) {
+    acc.x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc.x));
+    acc.y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc.y));
+}
+
+template <int Q>
+__device__ __forceinline__ void block_or_cluster_sync() {
+    if constexpr (Q > 1) {
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+// Contiguous share [beg, end) of n items for worker w of nw.
+__device__ __forceinline__ void work_range(long long n, int w, int nw, long long& beg, long long& end) {
+    const long long per = n / nw, rem = n % nw;
+    beg = (long long)w * per + (w < rem ? w : rem);
+    end = beg + per + (w < rem ? 1 : 0);
+}
+
+}  // namespace epic

@@ -1,0 +1,264 @@
+// Forward MOFF kernel: for every (channel, pol, time) item, gain -> gridding ->
+// zero-padded 2-D spatial transform -> |.|^2 -> accumulation over time
+// (Eq. "dirty-image-MOFF"; Sec. 3 "Gridding Convolution", "Spatial Fourier Transform",
+// "Time-averaging").
+//
+// Persistent: each CTA (or cluster of Q CTAs for N_p = 256) walks a contiguous range of
+// items in (channel*pol)-major, time-minor order, keeping its share of the N_p x N_p
+// image of the current (channel, pol) in float32 registers, and adds it into the float64
+// accumulator with atomics when the (channel, pol) changes, every `flush_every`
+// samples, and at the end.
+//
+// Per item, inside one CTA:
+//   decode + gain    owner thread a % NT turns voltage a into g_a V_a in shared memory
+//                    (next item's raw voltages are prefetched into registers);
+//   row pass         thread (row y, n1) gathers its N_g/S cells E(y, n1 + S n2) from the
+//                    cell-major CSR of M(r, a) (atomics-free), runs the first-stage
+//                    sub-transform, twiddles, exchanges through shared memory within its
+//                    warp, runs the second stage, and writes row y of the row-transformed
+//                    grid (to the owning CTA of the cluster for Q > 1);
+//   column pass      thread (column, n1) reads the N_g non-zero rows of its column, does
+//                    the same two stages along y, squares and accumulates.
+// Two CTA (cluster) barriers per item; everything else is warp-synchronous.
+#pragma once
+#include "moff_common.cuh"
+
+namespace epic {
+
+template <int NP, int VDT>
+__global__ void __launch_bounds__(Geo<NP>::NT, Geo<NP>::MINB)
+moff_fwd_kernel(const FwdArgs a) {
+    using G = Geo<NP>;
+    constexpr int S = G::S, R1 = G::R1, NI = G::NI, KP = G::KP, NT = G::NT, NG = G::NG;
+    constexpr int Q = G::Q, VPT = G::VPT;
+    using VT = typename Volt<VDT>::T;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* RX = reinterpret_cast<float2*>(smem_raw);        // [ROWS][RXS] exchange
+    float2* RB = RX + G::ROWS * G::RXS;                      // [NG][RBS] row-pass output
+    float2* TW = RB + NG * G::RBS;                           // [NP] exp(+2 pi i j / NP)
+    float2* VB = TW + NP;                                    // [A] g_a V_a
+    float2* GN = VB + a.n_ant;                               // [A] gains
+    float* PW = reinterpret_cast<float*>(GN + a.n_ant);      // [A] partial sum |g V|^2
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n1 = lane % S;
+    const int r = tid / S;
+    const int cc = lane / S;
+    int rank = 0, wid = blockIdx.x, nw = gridDim.x;
+    if constexpr (Q > 1) {
+        rank = blockIdx.x % Q;
+        wid = blockIdx.x / Q;
+        nw = gridDim.x / Q;
+    }
+    const int y = rank * G::ROWS + r;
+    float2* RBq[Q];
+    if constexpr (Q > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+        for (int q = 0; q < Q; ++q) RBq[q] = cl.map_shared_rank(RB, q);
+    } else {
+        RBq[0] = RB;
+    }
+
+    for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[i];
+
+    long long beg, end;
+    work_range(a.n_items, wid, nw, beg, end);
+
+    const int A = a.n_ant, T = a.n_time;
+    const VT* V = static_cast<const VT*>(a.volt);
+
+    float acc[2][R1];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < R1; ++i) acc[s][i] = 0.f;
+
+    VT raw[VPT];
+    auto prefetch = [&](long long item) {
+        const long long cp = item / T, t = item - cp * T;
+        const VT* base = V + (t * a.n_cp + cp) * (long long)A;
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) {
+            const int aa = tid + NT * i;
+            if (aa < A) raw[i] = __ldg(base + aa);
+        }
+    };
+
+    auto flush = [&](int cp, bool with_power) {
+        double* dst = a.accum + (size_t)cp * NP * NP;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int kx = rank * G::COLS + s * G::ROWS + warp * G::LPC + cc;
+            const int ix = (kx + NP / 2) & (NP - 1);
+#pragma unroll
+            for (int q = 0; q < KP; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < S; ++k1) {
+                    const int ky = n1 * KP + q + R1 * k1;
+                    const int iy = (ky + NP / 2) & (NP - 1);
+                    atomicAdd(dst + iy * NP + ix, (double)acc[s][q * S + k1]);
+                    acc[s][q * S + k1] = 0.f;
+                }
+        }
+        if (with_power) {
+            for (int aa = tid; aa < A; aa += NT) {
+                if (a.power != nullptr && rank == 0) atomicAdd(a.power + (size_t)cp * A + aa, (double)PW[aa]);
+                PW[aa] = 0.f;
+            }
+        }
+    };
+
+    int cur = -1, since = 0;
+    if (beg < end) prefetch(beg);
+    for (long long item = beg; item < end; ++item) {
+        const int cp = (int)(item / T);
+        const int t = (int)(item - (long long)cp * T);
+        if (cp != cur || since == a.flush_every) {
+            if (cur >= 0) flush(cur, true);
+            if (cp != cur) {
+                for (int aa = tid; aa < A; aa += NT)
+                    GN[aa] = a.gains ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
+            }
+            cur = cp;
+            since = 0;
+        }
+        ++since;
+
+        // ---- decode + gain (owner threads), prefetch the next item ----
+        {
+            const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
+#pragma unroll
+            for (int i = 0; i < VPT; ++i) {
+                const int aa = tid + NT * i;
+                if (aa < A) {
+                    const float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[i]));
+                    VB[aa] = vp;
+                    PW[aa] += cnorm(vp);
+                }
+            }
+            for (int aa = tid + NT * VPT; aa < A; aa += NT) {
+                const float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
+                VB[aa] = vp;
+                PW[aa] += cnorm(vp);
+            }
+            if (item + 1 < end) prefetch(item + 1);
+        }
+        block_or_cluster_sync<Q>();
+
+        // ---- row pass: gridding + 1-D transform along x of row y ----
+        {
+            float2 x[NI];
+#pragma unroll
+            for (int n2 = 0; n2 < NI; ++n2) {
+                const int cell = y * NG + n1 + S * n2;
+                const int e0 = __ldg(a.cell_ptr + cell), e1 = __ldg(a.cell_ptr + cell + 1);
+                float2 s = make_float2(0.f, 0.f);
+                for (int e = e0; e < e1; ++e) {
+                    const int4 en = __ldg(a.cell_ent + e);
+                    cfma(s, make_float2(__int_as_float(en.x), __int_as_float(en.y)), VB[en.z]);
+                }
+                x[n2] = s;
+            }
+            float2 Y[R1];
+            dft_halfzero_in<R1, +1>(x, Y);
+            float2* rx = RX + r * G::RXS;
+#pragma unroll
+            for (int k2 = 0; k2 < R1; ++k2)
+                rx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[(n1 * k2) & (NP - 1)]);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < KP; ++q) {
+                const int k2 = n1 * KP + q;
+                float2 z[S];
+#pragma unroll
+                for (int m = 0; m < S; ++m) z[m] = rx[k2 * S + (m ^ n1)];
+                dft<S, +1>(z);
+#pragma unroll
+                for (int k1 = 0; k1 < S; ++k1) {
+                    const int kx = k2 + R1 * k1;
+                    if constexpr (Q > 1) {
+                        RBq[(R1 * k1) / G::COLS][y * G::RBS + (kx % G::COLS)] = z[k1];
+                    } else {
+                        RB[y * G::RBS + kx] = z[k1];
+                    }
+                }
+            }
+        }
+        block_or_cluster_sync<Q>();
+
+        // ---- column pass: 1-D transform along y of two columns, |.|^2, accumulate ----
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int c = s * G::ROWS + warp * G::LPC + cc;
+            float2 x[NI];
+#pragma unroll
+            for (int n2 = 0; n2 < NI; ++n2) x[n2] = RB[(n1 + S * n2) * G::RBS + c];
+            float2 Y[R1];
+            dft_halfzero_in<R1, +1>(x, Y);
+            float2* cx = RX + (warp * G::LPC + cc) * G::RXS;
+#pragma unroll
+            for (int k2 = 0; k2 < R1; ++k2)
+                cx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[(n1 * k2) & (NP - 1)]);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < KP; ++q) {
+                const int k2 = n1 * KP + q;
+                float2 z[S];
+#pragma unroll
+                for (int m = 0; m < S; ++m) z[m] = cx[k2 * S + (m ^ n1)];
+                dft<S, +1>(z);
+#pragma unroll
+                for (int k1 = 0; k1 < S; ++k1) acc[s][q * S + k1] += cnorm(z[k1]);
+            }
+            __syncwarp();
+        }
+    }
+    if (cur >= 0) flush(cur, true);
+}
+
+template <int NP, int VDT>
+cudaError_t launch_fwd_t(const FwdArgs& a, int n_sm, cudaStream_t st) {
+    using G = Geo<NP>;
+    auto kern = moff_fwd_kernel<NP, VDT>;
+    const size_t smem = G::smem_bytes(a.n_ant);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (a.n_items == 0) return cudaSuccess;
+    if constexpr (G::Q == 1) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        long long grid = (long long)per_sm * n_sm;
+        if (grid > a.n_items) grid = a.n_items;
+        kern<<<(unsigned)grid, G::NT, smem, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = G::Q;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(G::NT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(G::Q * n_sm);
+        int n_cl = 0;
+        e = cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (n_cl < 1) return cudaErrorInvalidConfiguration;
+        long long ncl = n_cl;
+        if (ncl > a.n_items) ncl = a.n_items;
+        cfg.gridDim = dim3((unsigned)(ncl * G::Q));
+        e = cudaLaunchKernelEx(&cfg, kern, a);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+}
+
+}  // namespace epic

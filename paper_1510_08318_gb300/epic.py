@@ -1,0 +1,236 @@
+"""Thin Python binding of the MOFF imaging C ABI (include/epic.h).
+
+The functions named like the C entry points (`epic_create`, `epic_image`,
+`epic_image_backward`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
+arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
+for torch tensors, and `MoffImage` is the autograd.Function whose backward is the
+library's adjoint kernel.  There is no CPU fallback: if the library has not been built
+(paper_1510_08318_gb300.build), loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libepic.so")
+
+EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
+VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
+SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
+           "epic_last_error")
+
+_lib = None
+
+
+class EpicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("epic status %d: %s" % (status, msg))
+        self.status = status
+
+
+def load(path=LIB_PATH):
+    """Load the shared library (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libepic.so not built at %s; run paper_1510_08318_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.epic_create.restype = i32
+    lib.epic_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, vp, dbl, vp, i32, i32, i32, i32, i32, i32]
+    lib.epic_destroy.restype = None
+    lib.epic_destroy.argtypes = [vp]
+    lib.epic_image.restype = i32
+    lib.epic_image.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
+    lib.epic_image_backward.restype = i32
+    lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
+    lib.epic_plan_info.restype = i32
+    lib.epic_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    lib.epic_last_error.restype = ctypes.c_char_p
+    lib.epic_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def epic_last_error():
+    return load().epic_last_error().decode()
+
+
+def _check(status):
+    if status != EPIC_OK:
+        raise EpicError(status, epic_last_error())
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array, or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+# ---- the C entry points, one to one ------------------------------------------------------
+def epic_create(n_ant, pos_xy, kern_ptr, kern_dxdy, kern_w, dx, origin_xy, n_grid, n_pad,
+                n_chan, n_pol, volt_dtype, device):
+    """Host numpy arrays in, opaque plan handle out (see include/epic.h)."""
+    lib = load()
+    pos = np.ascontiguousarray(pos_xy, dtype=np.float64)
+    kp = np.ascontiguousarray(kern_ptr, dtype=np.int32)
+    kd = np.ascontiguousarray(kern_dxdy, dtype=np.float64)
+    kw = np.ascontiguousarray(kern_w)
+    if np.iscomplexobj(kw):
+        kw = np.stack([kw.real, kw.imag], axis=-1)
+    kw = np.ascontiguousarray(kw, dtype=np.float64)
+    org = np.ascontiguousarray(origin_xy, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(lib.epic_create(ctypes.byref(h), int(n_ant), pos.ctypes.data, kp.ctypes.data,
+                           kd.ctypes.data if kd.size else None, kw.ctypes.data if kw.size else None,
+                           float(dx), org.ctypes.data, int(n_grid), int(n_pad), int(n_chan), int(n_pol),
+                           int(volt_dtype), int(device)))
+    return h
+
+
+def epic_destroy(plan):
+    load().epic_destroy(plan)
+
+
+def epic_image(plan, volt, n_time, gains, accum, power, t_prev, image, autocorr, stream):
+    _check(load().epic_image(plan, volt, int(n_time), gains, accum, power, int(t_prev), image, autocorr, stream))
+
+
+def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, stream):
+    _check(load().epic_image_backward(plan, volt, int(n_time), gains, grad_image, grad_gains, stream))
+
+
+def epic_plan_info(plan):
+    nnz, cells, lag = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(load().epic_plan_info(plan, ctypes.byref(nnz), ctypes.byref(cells), ctypes.byref(lag)))
+    return {"nnz": nnz.value, "n_cells": cells.value, "lag_side": lag.value}
+
+
+# ---- torch convenience layer --------------------------------------------------------------
+class Plan:
+    """An imaging plan on one CUDA device (antenna-to-grid mapping + device tables)."""
+
+    def __init__(self, pos, kern_ptr, kern_dxdy, kern_w, dx, origin, n_grid, n_pad, n_chan, n_pol,
+                 vdtype="c64", device=0):
+        self.n_ant = int(np.asarray(pos).shape[0])
+        self.n_grid, self.n_pad, self.n_chan, self.n_pol = int(n_grid), int(n_pad), int(n_chan), int(n_pol)
+        self.vdtype = vdtype
+        self.device = int(device)
+        self._h = epic_create(self.n_ant, pos, kern_ptr, kern_dxdy, kern_w, dx, origin, n_grid, n_pad,
+                              n_chan, n_pol, VOLT_DTYPES[vdtype], device)
+        self.info = epic_plan_info(self._h)
+
+    @classmethod
+    def from_workload(cls, wl, device=0, n_chan=None):
+        return cls(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid, wl.n_pad,
+                   wl.n_chan if n_chan is None else n_chan, wl.n_pol, wl.vdtype, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            epic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- argument checks (shape, dtype, device, contiguity) ---
+    def _volt_ptr(self, volt):
+        import torch
+        C, P, A = self.n_chan, self.n_pol, self.n_ant
+        if not volt.is_cuda or not volt.is_contiguous():
+            raise ValueError("voltages must be a contiguous CUDA tensor")
+        if self.vdtype == "ci4":
+            ok = volt.dtype == torch.uint8 and volt.dim() == 4 and tuple(volt.shape[1:]) == (C, P, A)
+        elif self.vdtype == "f16":
+            ok = volt.dtype == torch.float16 and volt.dim() == 5 and tuple(volt.shape[1:]) == (C, P, A, 2)
+        else:
+            ok = ((volt.dtype == torch.float32 and volt.dim() == 5 and tuple(volt.shape[1:]) == (C, P, A, 2))
+                  or (volt.dtype == torch.complex64 and volt.dim() == 4 and tuple(volt.shape[1:]) == (C, P, A)))
+        if not ok:
+            raise ValueError("voltages %s %s do not match the plan (%s, C=%d, P=%d, A=%d)"
+                             % (tuple(volt.shape), volt.dtype, self.vdtype, C, P, A))
+        return volt.data_ptr(), int(volt.shape[0])
+
+    def _gains_ptr(self, gains):
+        import torch
+        if gains is None:
+            return None
+        if gains.dtype != torch.complex64 or not gains.is_cuda or not gains.is_contiguous() \
+                or tuple(gains.shape) != (self.n_chan, self.n_pol, self.n_ant):
+            raise ValueError("gains must be a contiguous complex64 CUDA tensor [C, P, A]")
+        return gains.data_ptr()
+
+    def image(self, volt, gains=None, accum=None, power=None, t_prev=0, want_image=True,
+              want_autocorr=False, stream=None):
+        """Run epic_image; returns dict(image, autocorr, accum, power) of CUDA tensors."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        vptr, T = self._volt_ptr(volt)
+        C, P, NP, A = self.n_chan, self.n_pol, self.n_pad, self.n_ant
+        if accum is None:
+            accum = torch.empty((C, P, NP, NP), dtype=torch.float64, device=dev)
+        if want_autocorr and power is None:
+            power = torch.empty((C, P, A), dtype=torch.float64, device=dev)
+        img = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev) if want_image else None
+        ac = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev) if want_autocorr else None
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        epic_image(self._h, vptr, T, self._gains_ptr(gains), accum.data_ptr(), _ptr(power), t_prev,
+                   _ptr(img), _ptr(ac), st.cuda_stream)
+        return {"image": img, "autocorr": ac, "accum": accum, "power": power}
+
+    def image_backward(self, volt, gains, grad_image, stream=None):
+        import torch
+        dev = torch.device("cuda", self.device)
+        vptr, T = self._volt_ptr(volt)
+        g = grad_image.contiguous().to(torch.float32)
+        if tuple(g.shape) != (self.n_chan, self.n_pol, self.n_pad, self.n_pad) or not g.is_cuda:
+            raise ValueError("grad_image must be a CUDA tensor [C, P, N_p, N_p]")
+        out = torch.empty((self.n_chan, self.n_pol, self.n_ant), dtype=torch.complex64, device=dev)
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        epic_image_backward(self._h, vptr, T, self._gains_ptr(gains), g.data_ptr(), out.data_ptr(),
+                            st.cuda_stream)
+        return out
+
+
+def _autograd_function():
+    import torch
+
+    class MoffImage(torch.autograd.Function):
+        """image = MoffImage.apply(gains, volt, plan): the time-averaged MOFF image as a
+        differentiable function of the complex gains [C, P, A] (complex64)."""
+
+        @staticmethod
+        def forward(ctx, gains, volt, plan):
+            g = gains.detach().contiguous()
+            out = plan.image(volt, g)["image"]
+            ctx.save_for_backward(g)
+            ctx.volt, ctx.plan = volt, plan
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_image):
+            (g,) = ctx.saved_tensors
+            return ctx.plan.image_backward(ctx.volt, g, grad_image), None, None
+
+    return MoffImage
+
+
+_MOFF = None
+
+
+def moff_image(gains, volt, plan):
+    """Differentiable MOFF image (see MoffImage)."""
+    global _MOFF
+    if _MOFF is None:
+        _MOFF = _autograd_function()
+    return _MOFF.apply(gains, volt, plan)

@@ -1,0 +1,74 @@
+"""The C ABI without a GPU: the library builds, loads, exports every symbol declared in
+include/epic.h, and rejects bad arguments on the host before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1510_08318_gb300 import build, epic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return epic.load()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"\b(epic_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert {"epic_create", "epic_image", "epic_image_backward", "epic_destroy"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(epic.SYMBOLS) <= declared
+
+
+def _create(**kw):
+    args = dict(n_ant=2, pos_xy=np.array([[0.0, 0.0], [3.0, 1.0]]), kern_ptr=np.array([0, 1, 2]),
+                kern_dxdy=np.zeros((2, 2)), kern_w=np.ones(2, dtype=np.complex128), dx=1.0,
+                origin_xy=np.array([-2.0, -2.0]), n_grid=8, n_pad=16, n_chan=1, n_pol=1, volt_dtype=0, device=0)
+    args.update(kw)
+    return epic.epic_create(**args)
+
+
+@pytest.mark.parametrize("kw, status", [
+    (dict(n_pad=16), epic.EPIC_EUNSUPPORTED),                       # unsupported padded size
+    (dict(n_pad=64, n_grid=33), epic.EPIC_EINVAL),                  # less than 2x padding
+    (dict(n_pad=64, n_grid=0), epic.EPIC_EINVAL),
+    (dict(n_pad=64, n_ant=0), epic.EPIC_EINVAL),
+    (dict(n_pad=64, dx=0.0), epic.EPIC_EINVAL),
+    (dict(n_pad=64, dx=float("nan")), epic.EPIC_EINVAL),
+    (dict(n_pad=64, volt_dtype=7), epic.EPIC_EINVAL),
+    (dict(n_pad=64, n_chan=0), epic.EPIC_EINVAL),
+    (dict(n_pad=64, kern_ptr=np.array([1, 1, 2])), epic.EPIC_EINVAL),
+    (dict(n_pad=64, kern_ptr=np.array([0, 2, 1])), epic.EPIC_EINVAL),
+    (dict(n_pad=64, pos_xy=np.array([[0.0, 0.0], [40.0, 1.0]])), epic.EPIC_EINVAL),   # off the grid
+    (dict(n_pad=64, pos_xy=np.array([[0.0, np.inf], [3.0, 1.0]])), epic.EPIC_EINVAL),
+    (dict(n_pad=64, n_ant=5000, pos_xy=np.zeros((5000, 2)), kern_ptr=np.zeros(5001, dtype=np.int32)),
+     epic.EPIC_EINVAL),
+])
+def test_create_rejects(lib, kw, status):
+    with pytest.raises(epic.EpicError) as e:
+        _create(**kw)
+    assert e.value.status == status
+    assert epic.epic_last_error()
+
+
+def test_calls_reject_null_plan(lib):
+    assert lib.epic_image(None, None, 1, None, None, None, 0, None, None, None) == epic.EPIC_EINVAL
+    assert "plan" in epic.epic_last_error()
+    assert lib.epic_image_backward(None, None, 1, None, None, None, None) == epic.EPIC_EINVAL
+    assert lib.epic_plan_info(None, None, None, None) == epic.EPIC_EINVAL
+    lib.epic_destroy(None)

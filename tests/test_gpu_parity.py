@@ -1,0 +1,231 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (GPU only).
+
+Tolerance: the FP32 path must match the FP64 oracle within 1e-4 relative L2 per image
+cube, and every pixel within 1e-4 of the cube's peak (float32 gridding weights, float32
+transforms of at most 2 x 8 radix stages and float32 partial sums over at most 1024
+samples keep the error near 1e-6; the bound leaves two orders of margin).  Gradients:
+1e-3 relative L2 against the oracle's FP64 gradient.
+"""
+import numpy as np
+import pytest
+
+from oracle import moff
+from paper_1510_08318_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL_L2 = 1e-4
+PIX = 1e-4
+
+
+@pytest.fixture(scope="module")
+def epic():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_08318_gb300 import build, epic as ep
+    build.build()
+    ep.load()
+    return ep
+
+
+def to_dev(wl):
+    if wl.vdtype == "ci4":
+        return torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda()
+    return torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda()
+
+
+def gains_dev(g):
+    return None if g is None else torch.from_numpy(np.ascontiguousarray(g.astype(np.complex64))).cuda()
+
+
+def oracle_map(wl):
+    return moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+
+
+def check_close(got, want, what):
+    got = np.asarray(got, dtype=np.float64)
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    worst = np.abs(got - want).max() / np.abs(want).max()
+    assert rel < RTOL_L2, "%s: relative L2 %.3e" % (what, rel)
+    assert worst < PIX, "%s: worst pixel %.3e of peak" % (what, worst)
+    return rel
+
+
+def run(epic, wl, gains=None, autocorr=True):
+    plan = epic.Plan.from_workload(wl)
+    out = plan.image(to_dev(wl), gains_dev(gains), want_autocorr=autocorr)
+    torch.cuda.synchronize()
+    return plan, {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+def test_tiny_image_and_autocorr(epic):
+    """16 antennas, 2 m squares, N_p = 64, 64 samples, complex64."""
+    wl = synth.workload_tiny(n_time=64)
+    M = oracle_map(wl)
+    plan, out = run(epic, wl)
+    assert plan.info["nnz"] == M.nnz
+    want = moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad)
+    check_close(out["image"], want, "image")
+    np.testing.assert_allclose(out["accum"], want * wl.n_time, rtol=1e-4, atol=1e-4 * want.max() * wl.n_time)
+    ac = moff.autocorr_term(M, wl.volt, None, wl.n_grid, wl.n_pad)
+    check_close(out["autocorr"], ac, "autocorr")
+    pw = (np.abs(wl.volt) ** 2).sum(0)
+    np.testing.assert_allclose(out["power"], pw, rtol=1e-5)
+
+
+def test_lwa_slice_ci4_gains(epic):
+    """LWA-like layout and 4+4-bit voltages, N_p = 128, two channels (lowest and highest),
+    two pols, 48 samples, random gains."""
+    wl = synth.workload_lwa(n_chan=2, n_time=48, chan_index=[0, 127])
+    rng = np.random.default_rng(8)
+    g = synth.random_gains(rng, (wl.n_chan, wl.n_pol, wl.n_ant))
+    M = oracle_map(wl)
+    _, out = run(epic, wl, g)
+    want = moff.moff_image(M, wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad)
+    check_close(out["image"], want, "image")
+    check_close(out["autocorr"], moff.autocorr_term(M, wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad),
+                "autocorr")
+
+
+def test_hera_slice_f16_np256(epic):
+    """Dense 331-antenna hexagon, 14 m disks, FP16 voltages, N_p = 256 (4-CTA clusters)."""
+    wl = synth.workload_hera(n_chan=2, n_time=6)
+    M = oracle_map(wl)
+    _, out = run(epic, wl)
+    want = moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad)
+    check_close(out["image"], want, "image")
+    check_close(out["autocorr"], moff.autocorr_term(M, wl.volt, None, wl.n_grid, wl.n_pad), "autocorr")
+
+
+def test_calib_slice_np256_gains(epic):
+    """1024 antennas (more than one voltage per thread), N_p = 256, complex64, gains."""
+    wl = synth.workload_calib(n_chan=1, n_time=5)
+    rng = np.random.default_rng(9)
+    g = synth.random_gains(rng, (1, 1, wl.n_ant))
+    M = oracle_map(wl)
+    _, out = run(epic, wl, g, autocorr=False)
+    want = moff.moff_image(M, wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad)
+    check_close(out["image"], want, "image")
+
+
+def _small_workload(n_pad, n_grid, n_ant, n_time, n_chan, n_pol, seed, vdtype="c64", dx=1.0):
+    rng = np.random.default_rng(seed)
+    origin = np.zeros(2)
+    pos = rng.uniform(1.5 * dx, (n_grid - 2.5) * dx, (n_ant, 2))
+    kerns = [synth.kernel_square(rng.uniform(0.5, 2.5) * dx, dx / 3) for _ in range(n_ant)]
+    ptr, dxdy, w = synth.pack_kernels(kerns)
+    w = w * np.exp(1j * rng.uniform(0, 2 * np.pi, w.shape))     # complex weights
+    wl = synth.Workload("small", pos, ptr, dxdy, w, dx, origin, n_grid, n_pad,
+                        np.full(n_chan, 1e8), n_pol, n_time, vdtype)
+    v = (rng.standard_normal((n_time, n_chan, n_pol, n_ant))
+         + 1j * rng.standard_normal((n_time, n_chan, n_pol, n_ant)))
+    return synth._finish(wl, v, vdtype)
+
+
+@pytest.mark.parametrize("n_pad, n_grid, n_ant, n_time, n_chan, n_pol, vdtype", [
+    (32, 16, 5, 7, 3, 2, "c64"),       # smallest size, several (c, p) per CTA range
+    (32, 11, 40, 33, 1, 1, "f16"),     # unpadded grid smaller than N_p / 2
+    (64, 32, 1, 3, 1, 1, "c64"),       # a single antenna
+    (64, 20, 300, 17, 2, 1, "ci4"),    # ragged grid, A > threads per CTA
+    (128, 64, 700, 9, 1, 2, "c64"),    # A beyond the register prefetch (4 per thread)
+    (256, 100, 64, 3, 2, 1, "f16"),
+])
+def test_small_sizes(epic, n_pad, n_grid, n_ant, n_time, n_chan, n_pol, vdtype):
+    wl = _small_workload(n_pad, n_grid, n_ant, n_time, n_chan, n_pol, seed=n_pad + n_ant, vdtype=vdtype)
+    rng = np.random.default_rng(n_ant)
+    g = synth.random_gains(rng, (n_chan, n_pol, n_ant))
+    M = oracle_map(wl)
+    _, out = run(epic, wl, g)
+    gg = g.astype(np.complex128)
+    check_close(out["image"], moff.moff_image(M, wl.volt, gg, wl.n_grid, wl.n_pad), "image")
+    check_close(out["autocorr"], moff.autocorr_term(M, wl.volt, gg, wl.n_grid, wl.n_pad), "autocorr")
+
+
+def test_continuation_matches_single_call(epic):
+    """Resuming an integration (t_prev > 0) equals integrating all samples at once."""
+    wl = synth.workload_tiny(n_time=40)
+    plan = epic.Plan.from_workload(wl)
+    v = to_dev(wl)
+    full = plan.image(v, want_autocorr=True)
+    part = plan.image(v[:15].contiguous(), want_autocorr=True)
+    rest = plan.image(v[15:].contiguous(), accum=part["accum"], power=part["power"], t_prev=15, want_autocorr=True)
+    torch.cuda.synchronize()
+    for k in ("image", "autocorr", "accum", "power"):
+        a, b = full[k].cpu().numpy(), rest[k].cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max(), k
+
+
+def test_zero_gains_and_empty_antennas(epic):
+    wl = _small_workload(64, 32, 6, 4, 1, 1, seed=3)
+    # antennas 2 and 4 have no footprint samples
+    ptr = wl.kern_ptr.copy()
+    keep = np.ones(wl.kern_dxdy.shape[0], bool)
+    for a in (2, 4):
+        keep[ptr[a]:ptr[a + 1]] = False
+    counts = np.diff(ptr)
+    counts[[2, 4]] = 0
+    wl.kern_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    wl.kern_dxdy, wl.kern_w = wl.kern_dxdy[keep], wl.kern_w[keep]
+    M = oracle_map(wl)
+    _, out = run(epic, wl)
+    check_close(out["image"], moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad), "image")
+    _, out0 = run(epic, wl, np.zeros((1, 1, wl.n_ant), np.complex64))
+    assert np.abs(out0["image"]).max() == 0.0
+
+
+def test_determinism_of_mapping_counts(epic):
+    wl = synth.workload_lwa(n_chan=1, n_time=2, chan_index=[5])
+    plan = epic.Plan.from_workload(wl)
+    M = oracle_map(wl)
+    assert plan.info["nnz"] == M.nnz
+    assert plan.info["n_cells"] == len(np.unique(M.tocoo().row))
+
+
+@pytest.mark.parametrize("n_pad, n_grid, n_ant, n_time, n_chan, vdtype", [
+    (32, 16, 7, 5, 2, "c64"),
+    (64, 30, 40, 6, 1, "ci4"),
+    (128, 64, 90, 4, 1, "f16"),
+    (256, 128, 50, 3, 1, "c64"),
+])
+def test_gradient_matches_oracle(epic, n_pad, n_grid, n_ant, n_time, n_chan, vdtype):
+    wl = _small_workload(n_pad, n_grid, n_ant, n_time, n_chan, 1, seed=n_ant, vdtype=vdtype)
+    rng = np.random.default_rng(n_pad)
+    g = synth.random_gains(rng, (n_chan, 1, n_ant))
+    G = rng.standard_normal((n_chan, 1, n_pad, n_pad)).astype(np.float32)
+    M = oracle_map(wl)
+    want = moff.grad_gains(M, wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad, G.astype(np.float64))
+    plan = epic.Plan.from_workload(wl)
+    got = plan.image_backward(to_dev(wl), gains_dev(g), torch.from_numpy(G).cuda()).cpu().numpy()
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < 1e-3, rel
+
+
+def test_autograd_function(epic):
+    """torch.autograd through the library's adjoint equals the oracle gradient of
+    L = sum (I - I_model)^2."""
+    wl = _small_workload(64, 32, 12, 6, 1, 1, seed=21)
+    rng = np.random.default_rng(22)
+    g0 = synth.random_gains(rng, (1, 1, wl.n_ant))
+    I_model = rng.uniform(0, 1, (1, 1, 64, 64))
+    plan = epic.Plan.from_workload(wl)
+    g = gains_dev(g0).requires_grad_(True)
+    img = epic.moff_image(g, to_dev(wl), plan)
+    loss = ((img.double() - torch.from_numpy(I_model).cuda()) ** 2).sum()
+    loss.backward()
+    M = oracle_map(wl)
+    I = moff.moff_image(M, wl.volt, g0.astype(np.complex128), 32, 64)
+    want = moff.grad_gains(M, wl.volt, g0.astype(np.complex128), 32, 64, 2 * (I - I_model))
+    got = g.grad.cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-3
+
+
+def test_python_layer_rejects_bad_shapes(epic):
+    wl = synth.workload_tiny(n_time=4)
+    plan = epic.Plan.from_workload(wl)
+    with pytest.raises(ValueError):
+        plan.image(torch.zeros((4, 1, 1, wl.n_ant + 1), dtype=torch.complex64, device="cuda"))
+    with pytest.raises(ValueError):
+        plan.image(to_dev(wl), torch.ones((1, 1, 3), dtype=torch.complex64, device="cuda"))
+    with pytest.raises(epic.EpicError):
+        epic.epic_image(plan._h, to_dev(wl).data_ptr(), 0, None, None, None, 0, None, None, None)
