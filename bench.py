@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--channels", type=int, default=128,
+                   help="image only the first C of the 128 channels (small profiling case)")
     return p.parse_args()
 
 
@@ -189,7 +191,7 @@ def main():
     build.build()
     epic.load()
 
-    wl = synth.workload_lwa()
+    wl = synth.workload_lwa(n_chan=args.channels)
     plan = epic.Plan.from_workload(wl, device=local)
     A, T, C, P, NP = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_pad
     volt = torch.from_numpy(wl.volt_raw).to(dev)
@@ -292,7 +294,7 @@ def main():
         "clocks": clk,
         "wall_s_timed": t_wall,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.channels == 128:
         cb, err = cpu_baseline_sample(wl, plan, torch)
         line["cpu_baseline"] = cb
         line["err_vs_oracle"] = {"relative_l2": err, "sample": "channel 127, pol 1, 256 samples, image"}

@@ -62,6 +62,7 @@ moff_fwd_kernel(const FwdArgs a) {
     }
 
     for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[i];
+    for (int aa = tid; aa < a.n_ant; aa += NT) PW[aa] = 0.f;   // owner-thread entries
 
     long long beg, end;
     work_range(a.n_items, wid, nw, beg, end);
