@@ -52,9 +52,11 @@ struct epic_plan {
     int lag_side = 0;
     int64_t nnz = 0, n_cells = 0;
     int* cell_ptr = nullptr;
-    int4* cell_ent = nullptr;
+    int2* cell_ent = nullptr;
+    float* cell_wim = nullptr;   // nullptr when every weight is real
     int* ant_ptr = nullptr;
-    int4* ant_ent = nullptr;
+    int2* ant_ent = nullptr;
+    float* ant_wim = nullptr;
     float2* twiddle = nullptr;
     float2* lag_tab = nullptr;
 };
@@ -65,8 +67,10 @@ void free_plan(epic_plan* p) {
     if (!p) return;
     cudaFree(p->cell_ptr);
     cudaFree(p->cell_ent);
+    cudaFree(p->cell_wim);
     cudaFree(p->ant_ptr);
     cudaFree(p->ant_ent);
+    cudaFree(p->ant_wim);
     cudaFree(p->twiddle);
     cudaFree(p->lag_tab);
     delete p;
@@ -81,13 +85,11 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
     return e;
 }
 
-int4 pack_entry(std::complex<double> w, int idx) {
-    const float wr = float(w.real()), wi = float(w.imag());
-    int4 e;
+int2 pack_entry(std::complex<double> w, int idx) {
+    const float wr = float(w.real());
+    int2 e;
     std::memcpy(&e.x, &wr, 4);
-    std::memcpy(&e.y, &wi, 4);
-    e.z = idx;
-    e.w = 0;
+    e.y = idx;
     return e;
 }
 
@@ -197,11 +199,16 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
 
     // cell-major CSR (gather side of the gridding)
     std::vector<int> cptr((size_t)NG * NG + 1, 0);
-    std::vector<int4> cent;
+    std::vector<int2> cent;
+    std::vector<float> cwim;
     cent.reserve(m.size());
+    cwim.reserve(m.size());
+    bool complex_w = false;
     for (const MapEntry& e : m) {
         cptr[e.cell + 1]++;
         cent.push_back(pack_entry(e.w, e.ant));
+        cwim.push_back(float(e.w.imag()));
+        complex_w = complex_w || (float(e.w.imag()) != 0.0f);
     }
     for (size_t i = 0; i + 1 < cptr.size(); ++i) {
         if (cptr[i + 1] > 0) p->n_cells++;
@@ -213,19 +220,24 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     const int rows = epic::grid_rows_per_block(n_pad);
     const int nq = NG / rows;
     const int rxs = epic::exchange_row_stride(n_pad);
-    std::vector<std::vector<std::pair<int, int4>>> per_ant((size_t)nq * n_ant);
+    std::vector<std::vector<std::pair<int2, float>>> per_ant((size_t)nq * n_ant);
     for (const MapEntry& e : m) {
         const int gy = e.cell / NG, gx = e.cell % NG;
         const int q = gy / rows;
-        per_ant[(size_t)q * n_ant + e.ant].push_back({e.cell, pack_entry(e.w, (gy - q * rows) * rxs + gx)});
+        per_ant[(size_t)q * n_ant + e.ant].push_back({pack_entry(e.w, (gy - q * rows) * rxs + gx), float(e.w.imag())});
     }
     std::vector<int> aptr((size_t)nq * (n_ant + 1), 0);
-    std::vector<int4> aent;
+    std::vector<int2> aent;
+    std::vector<float> awim;
     aent.reserve(m.size());
+    awim.reserve(m.size());
     for (int q = 0; q < nq; ++q) {
         aptr[(size_t)q * (n_ant + 1)] = (int)aent.size();
         for (int a = 0; a < n_ant; ++a) {
-            for (auto& pe : per_ant[(size_t)q * n_ant + a]) aent.push_back(pe.second);
+            for (auto& pe : per_ant[(size_t)q * n_ant + a]) {
+                aent.push_back(pe.first);
+                awim.push_back(pe.second);
+            }
             aptr[(size_t)q * (n_ant + 1) + a + 1] = (int)aent.size();
         }
     }
@@ -246,7 +258,9 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     }
     const int L = 2 * ext - 1;
     std::vector<float2> lag;
-    if (L <= 63) {
+    int smem_optin_ac = 0;
+    cudaDeviceGetAttribute(&smem_optin_ac, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (L <= 63 && epic::autocorr_smem_bytes(L, n_pad, n_ant) <= (size_t)smem_optin_ac) {
         p->lag_side = L;
         const int h = ext - 1;
         lag.assign((size_t)n_ant * L * L, make_float2(0.f, 0.f));
@@ -289,7 +303,8 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     }
     if ((e = upload(&p->cell_ptr, cptr)) != cudaSuccess || (e = upload(&p->cell_ent, cent)) != cudaSuccess ||
         (e = upload(&p->ant_ptr, aptr)) != cudaSuccess || (e = upload(&p->ant_ent, aent)) != cudaSuccess ||
-        (e = upload(&p->twiddle, tw)) != cudaSuccess || (e = upload(&p->lag_tab, lag)) != cudaSuccess) {
+        (e = upload(&p->twiddle, tw)) != cudaSuccess || (e = upload(&p->lag_tab, lag)) != cudaSuccess ||
+        (complex_w && ((e = upload(&p->cell_wim, cwim)) != cudaSuccess || (e = upload(&p->ant_wim, awim)) != cudaSuccess))) {
         free_plan(p);
         return e == cudaErrorMemoryAllocation ? fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
                                               : cuda_fail(e, "plan upload");
@@ -325,6 +340,8 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
     if (autocorr && !power) return fail(EPIC_EINVAL, "autocorr needs the power accumulator");
     if (autocorr && plan->lag_side == 0)
         return fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
+    if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
+        return fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -344,6 +361,7 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
     a.gains = reinterpret_cast<const float2*>(gains);
     a.cell_ptr = plan->cell_ptr;
     a.cell_ent = plan->cell_ent;
+    a.cell_wim = plan->cell_wim;
     a.twiddle = plan->twiddle;
     a.accum = accum;
     a.power = power;
@@ -366,6 +384,8 @@ epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_t
     if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
     if (!volt || !grad_image || !grad_gains) return fail(EPIC_EINVAL, "NULL device array");
+    if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
+        return fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -380,8 +400,10 @@ epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_t
     a.gains = reinterpret_cast<const float2*>(gains);
     a.cell_ptr = plan->cell_ptr;
     a.cell_ent = plan->cell_ent;
+    a.cell_wim = plan->cell_wim;
     a.ant_ptr = plan->ant_ptr;
     a.ant_ent = plan->ant_ent;
+    a.ant_wim = plan->ant_wim;
     a.twiddle = plan->twiddle;
     a.grad_image = grad_image;
     a.grad_gains = reinterpret_cast<float2*>(grad_gains);

@@ -11,7 +11,8 @@ struct FwdArgs {
     int n_time, n_cp, n_ant;   // T, C*P, A
     const float2* gains;       // [CP][A] or nullptr (unit gains)
     const int* cell_ptr;       // [NG*NG + 1] CSR by grid cell (NG = N_p / 2)
-    const int4* cell_ent;      // {weight re bits, weight im bits, antenna, 0}
+    const int2* cell_ent;      // {weight re bits, antenna}
+    const float* cell_wim;     // weight imaginary parts, or nullptr when all weights are real
     const float2* twiddle;     // [N_p] exp(+2 pi i j / N_p)
     double* accum;             // [CP][N_p][N_p] sum_t |F_t|^2
     double* power;             // [CP][A] sum_t |g V|^2 or nullptr
@@ -24,9 +25,11 @@ struct BwdArgs {
     int n_time, n_cp, n_ant;
     const float2* gains;
     const int* cell_ptr;
-    const int4* cell_ent;
+    const int2* cell_ent;
+    const float* cell_wim;
     const int* ant_ptr;        // [Q][A+1] CSR by antenna, per row block of the grid
-    const int4* ant_ent;       // {weight re bits, weight im bits, cell (row-block local), 0}
+    const int2* ant_ent;       // {weight re bits, cell (row-block local shared-memory offset)}
+    const float* ant_wim;      // weight imaginary parts, or nullptr
     const float2* twiddle;
     const float* grad_image;   // [CP][N_p][N_p] dL/dI, image pixel order
     float2* grad_gains;        // [CP][A]
@@ -54,6 +57,7 @@ int exchange_row_stride(int n_pad);   // row stride (float2) of the kernels' exc
 // Epilogue kernels (finalize.cu).
 cudaError_t launch_finalize_image(const double* accum, float* image, long long n, double inv_t,
                                   cudaStream_t st);
+size_t autocorr_smem_bytes(int lag_side, int n_pad, int n_ant);
 cudaError_t launch_autocorr(const double* power, const float2* lag_tab, int n_cp, int n_ant,
                             int lag_side, int n_pad, double inv_t, float* out, cudaStream_t st);
 

@@ -6,8 +6,8 @@
 //                    of antenna a's gridded footprint.  Since |K_a(k)|^2 is the transform of
 //                    the footprint's auto-correlation R_a(d) = sum_g M[g,a] conj(M[g-d,a]),
 //                    A(k) = sum_d U(d) exp(+2 pi i d.k / N_p) with U(d) = sum_a P_a R_a(d):
-//                    a dense mat-vec over the small L x L lag window, then a direct 2-D sum
-//                    per output pixel (U is Hermitian, so A is real).
+//                    a dense mat-vec over the small L x L lag window, then a separable sum
+//                    onto the N_p x N_p pixels (U is Hermitian, so A is real).
 #include "moff_common.cuh"
 
 namespace epic {
@@ -28,26 +28,36 @@ cudaError_t launch_finalize_image(const double* accum, float* image, long long n
     return cudaGetLastError();
 }
 
-constexpr int kAcThreads = 256;
+constexpr int kAcThreads = 512;
 
-// grid: (pixel blocks, CP).  Shared: U [L*L] float2, twiddles [N_p] float2.
-__global__ void autocorr_kernel(const double* __restrict__ power, const float2* __restrict__ lag_tab,
-                                int n_ant, int L, int n_pad, double inv_t, float* __restrict__ out) {
+// One block per (channel, pol).  Shared: U [L*L] float2, T1 [L][N_p] float2, twiddles
+// [N_p] float2, P [A] float.  Three phases:
+//   U(d)        = sum_a P_a R_a(d)                       (L^2 x A multiply-adds)
+//   T1(dy, kx)  = sum_dx U(dy, dx) exp(+2 pi i dx kx / N_p) (L^2 x N_p)
+//   A(ky, kx)   = Re sum_dy T1(dy, kx) exp(+2 pi i dy ky / N_p)  (N_p^2 x L)
+// with k measured from the image centre (k = pixel - N_p/2; the exponent is periodic).
+__global__ void __launch_bounds__(kAcThreads)
+autocorr_kernel(const double* __restrict__ power, const float2* __restrict__ lag_tab,
+                int n_ant, int L, int n_pad, double inv_t, float* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* U = reinterpret_cast<float2*>(smem_raw);
-    float2* TWs = U + L * L;
-    const int cp = blockIdx.y;
-    const int LL = L * L;
+    float2* T1 = U + L * L;
+    float2* TWs = T1 + L * n_pad;
+    float* P = reinterpret_cast<float*>(TWs + n_pad);
+    const int cp = blockIdx.x;
+    const int LL = L * L, h = (L - 1) / 2, msk = n_pad - 1;
     for (int j = threadIdx.x; j < n_pad; j += blockDim.x) {
         double s, c;
         sincospi(2.0 * j / n_pad, &s, &c);
         TWs[j] = make_float2(float(c), float(s));
     }
     const double* pw = power + (size_t)cp * n_ant;
+    for (int aa = threadIdx.x; aa < n_ant; aa += blockDim.x) P[aa] = float(pw[aa] * inv_t);
+    __syncthreads();
     for (int j = threadIdx.x; j < LL; j += blockDim.x) {
         float2 u = make_float2(0.f, 0.f);
         for (int aa = 0; aa < n_ant; ++aa) {
-            const float p = float(pw[aa] * inv_t);
+            const float p = P[aa];
             const float2 rv = __ldg(lag_tab + (size_t)aa * LL + j);
             u.x = fmaf(p, rv.x, u.x);
             u.y = fmaf(p, rv.y, u.y);
@@ -55,34 +65,43 @@ __global__ void autocorr_kernel(const double* __restrict__ power, const float2* 
         U[j] = u;
     }
     __syncthreads();
-    const int h = (L - 1) / 2;
-    const int npix = n_pad * n_pad;
-    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= npix) return;
-    const int iy = pix / n_pad, ix = pix % n_pad;
-    const int ky = iy - n_pad / 2, kx = ix - n_pad / 2;
-    float accr = 0.f;
-    for (int dy = -h; dy <= h; ++dy) {
-        float2 inner = make_float2(0.f, 0.f);
-        const float2* urow = U + (dy + h) * L;
-        for (int dx = -h; dx <= h; ++dx) {
-            const float2 w = TWs[((dx * kx) % n_pad + n_pad) % n_pad];
-            const float2 u = urow[dx + h];
-            inner.x = fmaf(u.x, w.x, fmaf(-u.y, w.y, inner.x));
-            inner.y = fmaf(u.x, w.y, fmaf(u.y, w.x, inner.y));
+    for (int j = threadIdx.x; j < L * n_pad; j += blockDim.x) {
+        const int dy = j / n_pad, ix = j % n_pad, kx = ix - n_pad / 2;
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* urow = U + dy * L;
+        for (int dx = 0; dx < L; ++dx) {
+            const float2 w = TWs[((dx - h) * kx) & msk];
+            const float2 u = urow[dx];
+            acc.x = fmaf(u.x, w.x, fmaf(-u.y, w.y, acc.x));
+            acc.y = fmaf(u.x, w.y, fmaf(u.y, w.x, acc.y));
         }
-        const float2 w = TWs[((dy * ky) % n_pad + n_pad) % n_pad];
-        accr = fmaf(inner.x, w.x, fmaf(-inner.y, w.y, accr));
+        T1[j] = acc;
     }
-    out[(size_t)cp * npix + pix] = accr;
+    __syncthreads();
+    const int npix = n_pad * n_pad;
+    for (int pix = threadIdx.x; pix < npix; pix += blockDim.x) {
+        const int iy = pix / n_pad, ix = pix % n_pad, ky = iy - n_pad / 2;
+        float accr = 0.f;
+        for (int dy = 0; dy < L; ++dy) {
+            const float2 w = TWs[((dy - h) * ky) & msk];
+            const float2 t = T1[dy * n_pad + ix];
+            accr = fmaf(t.x, w.x, fmaf(-t.y, w.y, accr));
+        }
+        out[(size_t)cp * npix + pix] = accr;
+    }
+}
+
+size_t autocorr_smem_bytes(int lag_side, int n_pad, int n_ant) {
+    return sizeof(float2) * ((size_t)lag_side * lag_side + (size_t)lag_side * n_pad + n_pad)
+         + sizeof(float) * (size_t)n_ant;
 }
 
 cudaError_t launch_autocorr(const double* power, const float2* lag_tab, int n_cp, int n_ant,
                             int lag_side, int n_pad, double inv_t, float* out, cudaStream_t st) {
-    const int npix = n_pad * n_pad;
-    dim3 grid((npix + kAcThreads - 1) / kAcThreads, n_cp);
-    const size_t smem = sizeof(float2) * ((size_t)lag_side * lag_side + n_pad);
-    autocorr_kernel<<<grid, kAcThreads, smem, st>>>(power, lag_tab, n_ant, lag_side, n_pad, inv_t, out);
+    const size_t smem = autocorr_smem_bytes(lag_side, n_pad, n_ant);
+    cudaError_t e = cudaFuncSetAttribute(autocorr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    autocorr_kernel<<<n_cp, kAcThreads, smem, st>>>(power, lag_tab, n_ant, lag_side, n_pad, inv_t, out);
     return cudaGetLastError();
 }
 

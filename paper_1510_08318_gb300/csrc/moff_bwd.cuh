@@ -20,7 +20,7 @@ namespace epic {
 template <int NP>
 struct BwdLayout {
     using G = Geo<NP>;
-    static constexpr int IBS = NP + 2;   // row stride of the column-pass output, [ROWS][IBS]
+    static constexpr int IBS = NP + 1;   // row stride of the column-pass output, [ROWS][IBS]
     static_assert(G::ROWS * IBS <= G::NG * G::RBS, "inverse buffer must fit in the row-pass buffer");
     static constexpr size_t smem_bytes(int n_ant) {
         return sizeof(float2) * (size_t(G::ROWS) * G::RXS + size_t(G::NG) * G::RBS + NP)
@@ -39,7 +39,7 @@ moff_bwd_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* RX = reinterpret_cast<float2*>(smem_raw);        // [ROWS][RXS] exchange, then Q_t rows
     float2* RB = RX + G::ROWS * G::RXS;                      // [NG][RBS] row output; then [ROWS][IBS]
-    float2* TW = RB + NG * G::RBS;
+    float2* TW = RB + NG * G::RBS;                           // [R1][S] exp(+2 pi i n1 k2 / NP)
     float2* VB = TW + NP;                                    // [A] g_a V_a
     float2* VR = VB + a.n_ant;                               // [A] V_a
     float2* GN = VR + a.n_ant;                               // [A] gains
@@ -65,11 +65,12 @@ moff_bwd_kernel(const BwdArgs a) {
         RBq[0] = RB;
     }
 
-    for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[i];
+    for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[((i % S) * (i / S)) & (NP - 1)];
     for (int aa = tid; aa < a.n_ant; aa += NT) GA[aa] = make_float2(0.f, 0.f);
 
-    long long beg, end;
-    work_range(a.n_items, wid, nw, beg, end);
+    long long beg_l, end_l;
+    work_range(a.n_items, wid, nw, beg_l, end_l);
+    const int beg = (int)beg_l, end = (int)end_l;   // the host guarantees n_items < 2^31
     const int A = a.n_ant, T = a.n_time;
     const VT* V = static_cast<const VT*>(a.volt);
     const int* aptr = a.ant_ptr + (size_t)rank * (A + 1);
@@ -86,9 +87,9 @@ moff_bwd_kernel(const BwdArgs a) {
     };
 
     int cur = -1;
-    for (long long item = beg; item < end; ++item) {
-        const int cp = (int)(item / T);
-        const int t = (int)(item - (long long)cp * T);
+    for (int item = beg; item < end; ++item) {
+        const int cp = item / T;
+        const int t = item - cp * T;
         if (cp != cur) {
             if (cur >= 0) flush(cur);
             for (int aa = tid; aa < A; aa += NT)
@@ -96,7 +97,7 @@ moff_bwd_kernel(const BwdArgs a) {
             const float* gi = a.grad_image + (size_t)cp * NP * NP;
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const int kx = rank * G::COLS + s * G::ROWS + warp * G::LPC + cc;
+                const int kx = rank * G::COLS + G::col(s, warp, cc);
                 const int ix = (kx + NP / 2) & (NP - 1);
 #pragma unroll
                 for (int q = 0; q < KP; ++q)
@@ -128,9 +129,19 @@ moff_bwd_kernel(const BwdArgs a) {
                 const int cell = y * NG + n1 + S * n2;
                 const int e0 = __ldg(a.cell_ptr + cell), e1 = __ldg(a.cell_ptr + cell + 1);
                 float2 s = make_float2(0.f, 0.f);
-                for (int e = e0; e < e1; ++e) {
-                    const int4 en = __ldg(a.cell_ent + e);
-                    cfma(s, make_float2(__int_as_float(en.x), __int_as_float(en.y)), VB[en.z]);
+                if (a.cell_wim) {
+                    for (int e = e0; e < e1; ++e) {
+                        const int2 en = __ldg(a.cell_ent + e);
+                        cfma(s, make_float2(__int_as_float(en.x), __ldg(a.cell_wim + e)), VB[en.y]);
+                    }
+                } else {
+                    for (int e = e0; e < e1; ++e) {
+                        const int2 en = __ldg(a.cell_ent + e);
+                        const float w = __int_as_float(en.x);
+                        const float2 v = VB[en.y];
+                        s.x = fmaf(w, v.x, s.x);
+                        s.y = fmaf(w, v.y, s.y);
+                    }
                 }
                 x[n2] = s;
             }
@@ -139,7 +150,7 @@ moff_bwd_kernel(const BwdArgs a) {
             float2* rx = RX + r * G::RXS;
 #pragma unroll
             for (int k2 = 0; k2 < R1; ++k2)
-                rx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[(n1 * k2) & (NP - 1)]);
+                rx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
@@ -165,7 +176,7 @@ moff_bwd_kernel(const BwdArgs a) {
         float2 xc[2][NI];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const int c = s * G::ROWS + warp * G::LPC + cc;
+            const int c = G::col(s, warp, cc);
 #pragma unroll
             for (int n2 = 0; n2 < NI; ++n2) xc[s][n2] = RB[(n1 + S * n2) * G::RBS + c];
         }
@@ -174,13 +185,13 @@ moff_bwd_kernel(const BwdArgs a) {
         // ---- column pass: F_t, times G, transposed transform back to the N_g rows ----
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const int kxg = rank * G::COLS + s * G::ROWS + warp * G::LPC + cc;   // global column
+            const int kxg = rank * G::COLS + G::col(s, warp, cc);   // global column
             float2 Y[R1];
             dft_halfzero_in<R1, +1>(xc[s], Y);
             float2* cx = RX + (warp * G::LPC + cc) * G::RXS;
 #pragma unroll
             for (int k2 = 0; k2 < R1; ++k2)
-                cx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[(n1 * k2) & (NP - 1)]);
+                cx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
@@ -202,7 +213,7 @@ moff_bwd_kernel(const BwdArgs a) {
 #pragma unroll
             for (int k2 = 0; k2 < R1; ++k2) {
                 const float2 v = cx[k2 * S + (n1 ^ G::swz(k2))];
-                Y[k2] = (k2 == 0) ? v : cmulc(v, TW[(n1 * k2) & (NP - 1)]);
+                Y[k2] = (k2 == 0) ? v : cmulc(v, TW[k2 * S + n1]);
             }
             float2 xo[NI];
             dft_halfzero_out<R1, -1>(Y, xo);
@@ -238,7 +249,7 @@ moff_bwd_kernel(const BwdArgs a) {
 #pragma unroll
             for (int k2 = 0; k2 < R1; ++k2) {
                 const float2 v = rx[k2 * S + (n1 ^ G::swz(k2))];
-                Y[k2] = (k2 == 0) ? v : cmulc(v, TW[(n1 * k2) & (NP - 1)]);
+                Y[k2] = (k2 == 0) ? v : cmulc(v, TW[k2 * S + n1]);
             }
             float2 xo[NI];
             dft_halfzero_out<R1, -1>(Y, xo);
@@ -253,10 +264,10 @@ moff_bwd_kernel(const BwdArgs a) {
             float2 s = make_float2(0.f, 0.f);
             const int e1 = __ldg(aptr + aa + 1);
             for (int e = __ldg(aptr + aa); e < e1; ++e) {
-                const int4 en = __ldg(a.ant_ent + e);
-                const float2 qv = RX[en.z];
+                const int2 en = __ldg(a.ant_ent + e);
+                const float2 qv = RX[en.y];
                 // conj(w) * q
-                const float wr = __int_as_float(en.x), wi = __int_as_float(en.y);
+                const float wr = __int_as_float(en.x), wi = a.ant_wim ? __ldg(a.ant_wim + e) : 0.f;
                 s.x = fmaf(wr, qv.x, fmaf(wi, qv.y, s.x));
                 s.y = fmaf(wr, qv.y, fmaf(-wi, qv.x, s.y));
             }

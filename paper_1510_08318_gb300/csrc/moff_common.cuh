@@ -12,10 +12,12 @@ namespace cg = cooperative_groups;
 // Per padded size N_p: S threads cooperate on each 1-D transform; a cluster of Q CTAs
 // shares one image (each CTA owns N_p/Q output columns and N_g/Q grid rows).
 template <int NP> struct Cfg;
-template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8; };
-template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2; };
-template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1; };
-template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1; };
+// S, Q, minimum CTAs per SM, and the shared-memory row strides (in float2) chosen so that
+// every warp-wide exchange access is free of bank conflicts.
+template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8, RXS = 40,  RBS = 34; };
+template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2, RXS = 72,  RBS = 66; };
+template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1, RXS = 136, RBS = 129; };
+template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1, RXS = 264, RBS = 65; };
 
 template <int NP> struct Geo {
     static constexpr int NG = NP / 2;          // unpadded grid side (2x padding, Sec. 3)
@@ -29,16 +31,26 @@ template <int NP> struct Geo {
     static constexpr int COLS = NP / Q;        // image columns per CTA in the column pass
     static constexpr int NT = ROWS * S;        // threads per CTA
     static constexpr int LPC = 32 / S;         // rows (or columns) per warp
-    static constexpr int RXS = NP + 8;         // row stride of the exchange buffer (float2)
-    static constexpr int RBS = COLS + 2;       // row stride of the row-pass output (float2)
+    static constexpr int RXS = Cfg<NP>::RXS;   // row stride of the exchange buffer (float2)
+    static constexpr int RBS = Cfg<NP>::RBS;   // row stride of the row-pass output (float2)
     static constexpr int NACC = 2 * R1;        // image pixels owned by each thread
-    static constexpr int VPT = 4;              // voltages prefetched per thread
+    static constexpr int VPT = 2;              // voltages prefetched per thread
     static_assert(NI * 2 == R1 && KP * S == R1 && KP >= 1, "bad factorisation");
     static_assert(COLS % R1 == 0 || Q == 1, "row-pass outputs must map to one CTA per k1");
-    static_assert(NT % 32 == 0 || NT < 32, "threads");
+    static_assert(RXS >= NP && RBS >= COLS, "strides");
     // XOR swizzle of the exchange buffer: keeps the first-stage writes (one n1, all k2) and
     // the second-stage reads (one k2 block, all n1) free of bank conflicts.
     static __device__ __forceinline__ int swz(int k2) { return (k2 / KP) & (S - 1); }
+    // Local column (of this CTA's COLS) handled by lane group cc of `warp` in column set s.
+    // For N_p = 128 the two columns read by one half-warp are 8 apart, which with an odd
+    // row stride (129) makes the column loads conflict-free.
+    static __device__ __forceinline__ int col(int s, int warp, int cc) {
+        if constexpr (NP == 128) {
+            return s * ROWS + 16 * (warp >> 2) + 2 * (warp & 3) + (cc >> 1) + 8 * (cc & 1);
+        } else {
+            return s * ROWS + warp * LPC + cc;
+        }
+    }
 
     static constexpr size_t smem_bytes(int n_ant) {
         return sizeof(float2) * (size_t(ROWS) * RXS + size_t(NG) * RBS + NP)

@@ -36,7 +36,7 @@ moff_fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* RX = reinterpret_cast<float2*>(smem_raw);        // [ROWS][RXS] exchange
     float2* RB = RX + G::ROWS * G::RXS;                      // [NG][RBS] row-pass output
-    float2* TW = RB + NG * G::RBS;                           // [NP] exp(+2 pi i j / NP)
+    float2* TW = RB + NG * G::RBS;                           // [R1][S] exp(+2 pi i n1 k2 / NP)
     float2* VB = TW + NP;                                    // [A] g_a V_a
     float2* GN = VB + a.n_ant;                               // [A] gains
     float* PW = reinterpret_cast<float*>(GN + a.n_ant);      // [A] partial sum |g V|^2
@@ -61,11 +61,12 @@ moff_fwd_kernel(const FwdArgs a) {
         RBq[0] = RB;
     }
 
-    for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[i];
+    for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[((i % S) * (i / S)) & (NP - 1)];
     for (int aa = tid; aa < a.n_ant; aa += NT) PW[aa] = 0.f;   // owner-thread entries
 
-    long long beg, end;
-    work_range(a.n_items, wid, nw, beg, end);
+    long long beg_l, end_l;
+    work_range(a.n_items, wid, nw, beg_l, end_l);
+    const int beg = (int)beg_l, end = (int)end_l;   // the host guarantees n_items < 2^31
 
     const int A = a.n_ant, T = a.n_time;
     const VT* V = static_cast<const VT*>(a.volt);
@@ -77,9 +78,9 @@ moff_fwd_kernel(const FwdArgs a) {
         for (int i = 0; i < R1; ++i) acc[s][i] = 0.f;
 
     VT raw[VPT];
-    auto prefetch = [&](long long item) {
-        const long long cp = item / T, t = item - cp * T;
-        const VT* base = V + (t * a.n_cp + cp) * (long long)A;
+    auto prefetch = [&](int item) {
+        const int cp = item / T, t = item - cp * T;
+        const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
 #pragma unroll
         for (int i = 0; i < VPT; ++i) {
             const int aa = tid + NT * i;
@@ -91,7 +92,7 @@ moff_fwd_kernel(const FwdArgs a) {
         double* dst = a.accum + (size_t)cp * NP * NP;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const int kx = rank * G::COLS + s * G::ROWS + warp * G::LPC + cc;
+            const int kx = rank * G::COLS + G::col(s, warp, cc);
             const int ix = (kx + NP / 2) & (NP - 1);
 #pragma unroll
             for (int q = 0; q < KP; ++q)
@@ -113,9 +114,9 @@ moff_fwd_kernel(const FwdArgs a) {
 
     int cur = -1, since = 0;
     if (beg < end) prefetch(beg);
-    for (long long item = beg; item < end; ++item) {
-        const int cp = (int)(item / T);
-        const int t = (int)(item - (long long)cp * T);
+    for (int item = beg; item < end; ++item) {
+        const int cp = item / T;
+        const int t = item - cp * T;
         if (cp != cur || since == a.flush_every) {
             if (cur >= 0) flush(cur, true);
             if (cp != cur) {
@@ -156,9 +157,19 @@ moff_fwd_kernel(const FwdArgs a) {
                 const int cell = y * NG + n1 + S * n2;
                 const int e0 = __ldg(a.cell_ptr + cell), e1 = __ldg(a.cell_ptr + cell + 1);
                 float2 s = make_float2(0.f, 0.f);
-                for (int e = e0; e < e1; ++e) {
-                    const int4 en = __ldg(a.cell_ent + e);
-                    cfma(s, make_float2(__int_as_float(en.x), __int_as_float(en.y)), VB[en.z]);
+                if (a.cell_wim) {
+                    for (int e = e0; e < e1; ++e) {
+                        const int2 en = __ldg(a.cell_ent + e);
+                        cfma(s, make_float2(__int_as_float(en.x), __ldg(a.cell_wim + e)), VB[en.y]);
+                    }
+                } else {
+                    for (int e = e0; e < e1; ++e) {
+                        const int2 en = __ldg(a.cell_ent + e);
+                        const float w = __int_as_float(en.x);
+                        const float2 v = VB[en.y];
+                        s.x = fmaf(w, v.x, s.x);
+                        s.y = fmaf(w, v.y, s.y);
+                    }
                 }
                 x[n2] = s;
             }
@@ -167,7 +178,7 @@ moff_fwd_kernel(const FwdArgs a) {
             float2* rx = RX + r * G::RXS;
 #pragma unroll
             for (int k2 = 0; k2 < R1; ++k2)
-                rx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[(n1 * k2) & (NP - 1)]);
+                rx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
@@ -192,7 +203,7 @@ moff_fwd_kernel(const FwdArgs a) {
         // ---- column pass: 1-D transform along y of two columns, |.|^2, accumulate ----
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const int c = s * G::ROWS + warp * G::LPC + cc;
+            const int c = G::col(s, warp, cc);
             float2 x[NI];
 #pragma unroll
             for (int n2 = 0; n2 < NI; ++n2) x[n2] = RB[(n1 + S * n2) * G::RBS + c];
@@ -201,7 +212,7 @@ moff_fwd_kernel(const FwdArgs a) {
             float2* cx = RX + (warp * G::LPC + cc) * G::RXS;
 #pragma unroll
             for (int k2 = 0; k2 < R1; ++k2)
-                cx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[(n1 * k2) & (NP - 1)]);
+                cx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
