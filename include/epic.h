@@ -52,6 +52,12 @@ typedef enum {
                                each a 4-bit two's-complement integer */
 } epic_volt_dtype;
 
+typedef enum {
+    EPIC_XFORM_FFT = 0,     /* FP32 shared-memory FFT (all sizes; the default) */
+    EPIC_XFORM_DFTGEMM = 1  /* dense DFT on the tensor cores, FP16 hi+lo operands, FP32
+                               accumulation (N_p = 128 only) */
+} epic_xform;
+
 /*
  * epic_create -- build the antenna-to-grid mapping and the device tables (once per
  * array; Sec. 3 "Antenna-to-Grid Mapping").
@@ -82,6 +88,19 @@ epic_status epic_create(epic_plan **plan, int n_ant, const double *pos_xy,
                         const int *kern_ptr, const double *kern_dxdy, const double *kern_w,
                         double dx, const double *origin_xy, int n_grid, int n_pad,
                         int n_chan, int n_pol, int volt_dtype, int device);
+
+/*
+ * epic_set_transform -- choose how epic_image computes the zero-padded 2-D spatial transform
+ * (Sec. 3 "Spatial Fourier Transform").  EPIC_XFORM_FFT (default) is a float32 radix FFT in
+ * shared memory.  EPIC_XFORM_DFTGEMM writes the transform as two dense matrix products with the
+ * DFT matrix W[k][n] = exp(+2 pi i n k / N_p) on the tensor cores: every operand is split into
+ * two FP16 numbers (hi + lo) and each real product is accumulated as hi*hi + hi*lo + lo*hi in
+ * FP32 (per image the gridded field is scaled by a power of two to keep the operands in range).
+ * It is available for n_pad == 128; otherwise EPIC_EUNSUPPORTED.  The first call with
+ * EPIC_XFORM_DFTGEMM uploads the plan's DFT operand tables (96 KB).  epic_image_backward
+ * always uses the FFT form.
+ */
+epic_status epic_set_transform(epic_plan *plan, int xform);
 
 /* Release the plan and its device tables.  NULL is accepted. */
 void epic_destroy(epic_plan *plan);

@@ -59,6 +59,9 @@ struct epic_plan {
     float* ant_wim = nullptr;
     float2* twiddle = nullptr;
     float2* lag_tab = nullptr;
+    int xform = EPIC_XFORM_FFT;
+    uint16_t* dg_tab = nullptr;   // DFT operand tables of the tensor-core form
+    float wsum_max = 0.f;         // max over cells of sum_a |M[g, a]|
 };
 
 namespace {
@@ -73,6 +76,7 @@ void free_plan(epic_plan* p) {
     cudaFree(p->ant_wim);
     cudaFree(p->twiddle);
     cudaFree(p->lag_tab);
+    cudaFree(p->dg_tab);
     delete p;
 }
 
@@ -214,6 +218,13 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         if (cptr[i + 1] > 0) p->n_cells++;
         cptr[i + 1] += cptr[i];
     }
+    {
+        std::vector<double> wsum((size_t)NG * NG, 0.0);
+        for (const MapEntry& e : m) wsum[e.cell] += std::abs(e.w);
+        double wm = 0.0;
+        for (double v : wsum) wm = std::max(wm, v);
+        p->wsum_max = float(wm * (1.0 + 1e-6));
+    }
 
     // antenna-major CSR per row block (degridding side of the adjoint); cells are stored as
     // offsets into the adjoint kernel's shared-memory row buffer
@@ -313,6 +324,35 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     return EPIC_OK;
 }
 
+epic_status epic_set_transform(epic_plan* plan, int xform) {
+    g_err.clear();
+    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
+    if (xform == EPIC_XFORM_FFT) {
+        plan->xform = xform;
+        return EPIC_OK;
+    }
+    if (xform != EPIC_XFORM_DFTGEMM) return fail(EPIC_EINVAL, "xform %d", xform);
+    if (plan->n_pad != 128) return fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad == 128 (plan: %d)", plan->n_pad);
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    if (epic::dftgemm_smem_bytes(plan->n_ant) > (size_t)smem_optin)
+        return fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the tensor-core kernel's shared memory", plan->n_ant);
+    if (!plan->dg_tab) {
+        std::vector<uint16_t> tab;
+        epic::dftgemm_tables(tab);
+        cudaError_t e = upload(&plan->dg_tab, tab);
+        if (e != cudaSuccess) {
+            cudaFree(plan->dg_tab);
+            plan->dg_tab = nullptr;
+            return cuda_fail(e, "DFT operand tables");
+        }
+    }
+    plan->xform = xform;
+    return EPIC_OK;
+}
+
 void epic_destroy(epic_plan* plan) {
     if (!plan) return;
     DeviceGuard guard(plan->device);
@@ -367,7 +407,14 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
     a.power = power;
     a.n_items = (long long)cp * n_time;
     a.flush_every = 1024;
-    epic_status s = launch_fwd(plan, a, st);
+    a.wsum_max = plan->wsum_max;
+    epic_status s;
+    if (plan->xform == EPIC_XFORM_DFTGEMM) {
+        e = epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, plan->n_sm, st);
+        s = e == cudaSuccess ? EPIC_OK : cuda_fail(e, "tensor-core imaging kernel launch");
+    } else {
+        s = launch_fwd(plan, a, st);
+    }
     if (s != EPIC_OK) return s;
     const double inv_t = 1.0 / double(t_prev + n_time);
     if (image && (e = epic::launch_finalize_image(accum, image, (long long)npix, inv_t, st)) != cudaSuccess)

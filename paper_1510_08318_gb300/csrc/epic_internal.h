@@ -1,6 +1,7 @@
 // Internal declarations shared by the host API and the kernel translation units.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace epic {
@@ -18,6 +19,7 @@ struct FwdArgs {
     double* power;             // [CP][A] sum_t |g V|^2 or nullptr
     long long n_items;         // CP * T
     int flush_every;           // samples per float32 partial before a float64 flush
+    float wsum_max;            // max over cells of sum_a |M[g, a]| (scales the FP16 operands)
 };
 
 struct BwdArgs {
@@ -53,6 +55,11 @@ size_t fwd_smem_bytes(int n_pad, int n_ant);
 size_t bwd_smem_bytes(int n_pad, int n_ant);
 int grid_rows_per_block(int n_pad);   // rows of the N_g grid each CTA of a cluster owns
 int exchange_row_stride(int n_pad);   // row stride (float2) of the kernels' exchange buffer
+
+// Tensor-core DFT form of the forward kernel, N_p = 128 (moff_dftgemm.cu).
+size_t dftgemm_smem_bytes(int n_ant);
+void dftgemm_tables(std::vector<uint16_t>& out);
+cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm, cudaStream_t st);
 
 // Epilogue kernels (finalize.cu).
 cudaError_t launch_finalize_image(const double* accum, float* image, long long n, double inv_t,

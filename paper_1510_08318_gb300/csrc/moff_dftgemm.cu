@@ -1,0 +1,432 @@
+// MOFF imaging with the spatial transform as a dense DFT on the 5th-generation tensor cores
+// (Eq. "dirty-image-MOFF"; the transform of Sec. 3 "Spatial Fourier Transform" written as two
+// matrix products), N_p = 128 (N_g = 64):
+//
+//   X(ky, x)  = sum_y  W[ky][y] E(y, x)          stage 1, M = 128 (ky), N = 64 (x),   K = 64 (y)
+//   F(ky, kx) = sum_x  X(ky, x) W[kx][x]         stage 2, M = 128 (ky), N = 128 (kx), K = 64 (x)
+//   I(ky, kx) += |F|^2
+//
+// with W[k][n] = exp(+2 pi i n k / N_p).  Complex products are four real products; every real
+// operand v is split as v = hi + lo (two FP16 numbers, hi = fp16(v), lo = fp16(v - hi)) and each
+// real product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory (about 22 bits of
+// operand precision).  Per image the gridded field is scaled by a power of two, chosen from a
+// bound (largest |g V| of the sample times the largest sum_a |M[g, a]| of the plan), so that
+// the FP16 operands stay in range; |F|^2 is scaled back exactly.
+//
+// One CTA (512 threads) per SM owns all 512 TMEM columns:
+//   [0, 128)    stage-1 accumulator X (re 0..63, im 64..127), FP32
+//   [128, 256)  stage-2 A operand: X re hi, re lo, im hi, im lo (FP16 pairs, 32 columns each)
+//   [256, 512)  stage-2 accumulator F (re 256..383, im 384..511), FP32
+// Shared memory holds the six W operand tables (re hi/lo, im hi/lo, -im hi/lo) and the four
+// E^T operand tables (re/im, hi/lo), all K-major in 8 x 8 core matrices, no swizzle.
+// Pipeline per image i: grid(i) + stage 2(i-1) on the tensor cores, then stage 1(i) issue,
+// |F|^2 epilogue of i-1, decode of i+1, split of X(i) into TMEM, stage 2(i) issue.
+// Every wait on the tensor cores is bounded; on a timeout the CTA writes NaN into its
+// accumulator block and stops.
+#include <cuda_fp16.h>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+#include "moff_common.cuh"
+
+namespace epic {
+namespace dg {
+
+constexpr int NP = 128, NG = 64, NT = 512;
+constexpr int WTAB = NP * NG;     // halves per W table
+constexpr int ETAB = NG * NG;     // halves per E^T table
+enum { WR_HI, WR_LO, WI_HI, WI_LO, NWI_HI, NWI_LO, N_WTAB };
+enum { ER_HI, ER_LO, EI_HI, EI_LO, N_ETAB };
+
+// offset (in halves) of element (row r, k) of a K-major operand with Kdim columns, stored as
+// [r/8][k/8][r%8][k%8] (8 x 8 core matrices of 128 bytes)
+__host__ __device__ inline int koff(int r, int k, int kdim) {
+    return ((r >> 3) * (kdim >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start >> 4, leading (K-direction) core-matrix step 128 B,
+// stride (row-direction) core-matrix step 8 * 16 * (kdim / 8) B, descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulate, FP16 A and B, both K-major, N, M = 128.
+constexpr uint32_t idesc(int n) { return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24); }
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                 :: "r"(d), "r"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Bounded wait for an mbarrier phase (false on timeout).  Each try suspends the thread for up
+// to 1 ms (hint) instead of spinning, so waiting warps leave the issue slots to the others;
+// at most 1000 tries.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    for (int i = 0; i < 1000; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(addr), "r"(parity), "r"(1000000u) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int NR>
+__device__ __forceinline__ void tld(uint32_t taddr, float (&v)[NR]);
+template <>
+__device__ __forceinline__ void tld<16>(uint32_t t, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(t));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tst8(uint32_t t, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(t), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tst_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// (a, b) -> packed FP16 pairs hi = fp16(a, b), lo = fp16((a, b) - hi)
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+constexpr int kWStep = 2 * WTAB / 16;    // descriptor start-field step per W table
+constexpr int kEStep = 2 * ETAB / 16;    // ... per E^T table
+
+constexpr size_t smem_fixed() {
+    return sizeof(__half) * ((size_t)N_WTAB * WTAB + (size_t)N_ETAB * ETAB) + 64;
+}
+
+template <int VDT>
+__global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab) {
+    using VT = typename Volt<VDT>::T;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __half* sW = reinterpret_cast<__half*>(smem_raw);                  // [N_WTAB][WTAB]
+    __half* sE = sW + N_WTAB * WTAB;                                  // [N_ETAB][ETAB]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + N_ETAB * ETAB); // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    unsigned int* vmax = reinterpret_cast<unsigned int*>(tslot + 2);  // [2] max |g V| (float bits) per parity
+    float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed());
+    float2* GN = VB + a.n_ant;
+    float* PW = reinterpret_cast<float*>(GN + a.n_ant);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int A = a.n_ant, T = a.n_time;
+    const VT* V = static_cast<const VT*>(a.volt);
+
+    for (int i = tid; i < N_WTAB * WTAB / 8; i += NT)
+        reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wtab) + i);
+    for (int aa = tid; aa < A; aa += NT) PW[aa] = 0.f;
+    const uint32_t mb1 = smem_u32(&mbar[0]), mb2 = smem_u32(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mb1), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mb2), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid < 2) vmax[tid] = 0u;
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tX = tmem, tXop = tmem + 128, tF = tmem + 256;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    // descriptors of the first W and E^T tables; the others differ only in the start-address
+    // field (table size / 16 per table, 256 B / 16 per K step of 16 elements)
+    const uint64_t dW0 = sdesc(smem_u32(sW), 1024), dE0 = sdesc(smem_u32(sE), 1024);
+    const int qt = warp >> 2;                 // column quarter owned in the TMEM passes
+    const int ky = 32 * (warp & 3) + lane;    // TMEM lane = output row
+
+    long long beg_l, end_l;
+    work_range(a.n_items, blockIdx.x, gridDim.x, beg_l, end_l);
+    const int beg = (int)beg_l, n = (int)(end_l - beg_l);
+
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+
+    // decode + gain; the largest component magnitude goes to vmax[slot] (positive float bits
+    // order like unsigned integers)
+    auto decode = [&](int item, int slot) {
+        const int cp = item / T, t = item - cp * T;
+        const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
+        float m = 0.f;
+        for (int aa = tid; aa < A; aa += NT) {
+            const float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
+            VB[aa] = vp;
+            PW[aa] += cnorm(vp);
+            m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && m > 0.f) atomicMax(vmax + slot, __float_as_uint(m));
+    };
+    auto load_gains = [&](int cp) {
+        for (int aa = tid; aa < A; aa += NT)
+            GN[aa] = a.gains ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
+    };
+    auto flush_power = [&](int cp) {
+        for (int aa = tid; aa < A; aa += NT) {
+            if (a.power != nullptr) atomicAdd(a.power + (size_t)cp * A + aa, (double)PW[aa]);
+            PW[aa] = 0.f;
+        }
+    };
+    auto flush_acc = [&](int cp) {
+        double* dst = a.accum + (size_t)cp * NP * NP;
+        const int iy = (ky + NP / 2) & (NP - 1);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int ix = (32 * qt + j + NP / 2) & (NP - 1);
+            atomicAdd(dst + iy * NP + ix, (double)acc[j]);
+            acc[j] = 0.f;
+        }
+    };
+
+    bool failed = false;
+    int issued2 = 0;            // stage-2 batches committed
+    float scale_prev = 1.f;     // 4^s of the image whose stage 2 is in flight
+    int since = 0;
+    if (n > 0) {
+        load_gains(beg / T);
+        decode(beg, 0);
+    }
+    __syncthreads();
+
+    for (int i = 0; i <= n && !failed; ++i) {
+        const int item = beg + i;
+        float scale_cur = 1.f;
+        if (i < n) {
+            // ---- gridding into the E^T operand tables (scaled, FP16 hi/lo) ----
+            // scale: |E| <= (largest sum_a |M[g, a]|) * sqrt(2) * (largest |g V| component)
+            const float bound = a.wsum_max * 1.5f * __uint_as_float(vmax[i & 1]);
+            int ex = 0;
+            if (bound > 0.f) {
+                frexpf(bound, &ex);
+                ex = max(-100, min(100, ex - 9));    // scaled bound in [256, 512)
+            }
+            const float down = ldexpf(1.f, -ex);
+            scale_cur = ldexpf(1.f, 2 * ex);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cm = warp * 4 + j, xb = cm >> 3, yb = cm & 7;
+                const int x = 8 * xb + (lane & 7), y = 8 * yb + 2 * (lane >> 3);
+                float2 ev[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int cell = (y + u) * NG + x;
+                    const int e0 = __ldg(a.cell_ptr + cell), e1 = __ldg(a.cell_ptr + cell + 1);
+                    float2 s = make_float2(0.f, 0.f);
+                    if (a.cell_wim) {
+                        for (int e = e0; e < e1; ++e) {
+                            const int2 en = __ldg(a.cell_ent + e);
+                            cfma(s, make_float2(__int_as_float(en.x), __ldg(a.cell_wim + e)), VB[en.y]);
+                        }
+                    } else {
+                        for (int e = e0; e < e1; ++e) {
+                            const int2 en = __ldg(a.cell_ent + e);
+                            const float w = __int_as_float(en.x);
+                            const float2 v = VB[en.y];
+                            s.x = fmaf(w, v.x, s.x);
+                            s.y = fmaf(w, v.y, s.y);
+                        }
+                    }
+                    ev[u] = s;
+                }
+                uint32_t rh, rl, ih, il;
+                split2(ev[0].x * down, ev[1].x * down, rh, rl);
+                split2(ev[0].y * down, ev[1].y * down, ih, il);
+                const int off = koff(x, y, NG);
+                *reinterpret_cast<uint32_t*>(sE + ER_HI * ETAB + off) = rh;
+                *reinterpret_cast<uint32_t*>(sE + ER_LO * ETAB + off) = rl;
+                *reinterpret_cast<uint32_t*>(sE + EI_HI * ETAB + off) = ih;
+                *reinterpret_cast<uint32_t*>(sE + EI_LO * ETAB + off) = il;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) vmax[i & 1] = 0u;   // free for the sample after next
+            // ---- stage 1 issue: X = W E (columns transformed) ----
+            if (tid == 0) {
+                fence_after();
+                constexpr uint32_t id1 = idesc(64);
+                constexpr int tr[6][2] = {{WR_HI, ER_HI}, {WR_HI, ER_LO}, {WR_LO, ER_HI},
+                                          {NWI_HI, EI_HI}, {NWI_HI, EI_LO}, {NWI_LO, EI_HI}};
+                constexpr int ti[6][2] = {{WR_HI, EI_HI}, {WR_HI, EI_LO}, {WR_LO, EI_HI},
+                                          {WI_HI, ER_HI}, {WI_HI, ER_LO}, {WI_LO, ER_HI}};
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        mma_ss(tX, dW0 + (uint64_t)(tr[q][0] * kWStep + 16 * j),
+                               dE0 + (uint64_t)(tr[q][1] * kEStep + 16 * j), id1, (q | j) != 0);
+                        mma_ss(tX + 64, dW0 + (uint64_t)(ti[q][0] * kWStep + 16 * j),
+                               dE0 + (uint64_t)(ti[q][1] * kEStep + 16 * j), id1, (q | j) != 0);
+                    }
+                commit(mb1);
+            }
+        }
+        // ---- epilogue of image i-1: |F|^2 into the accumulators ----
+        if (i >= 1) {
+            if (!mbar_wait(mb2, (i - 1) & 1)) failed = true;
+            fence_after();
+#pragma unroll
+            for (int c = 0; c < 32; c += 16) {
+                float fr[16], fi[16];
+                tld<16>(tF + lane_base + 32 * qt + c, fr);
+                tld<16>(tF + 128 + lane_base + 32 * qt + c, fi);
+                tld_wait();
+#pragma unroll
+                for (int u = 0; u < 16; ++u) acc[c + u] = fmaf(fmaf(fr[u], fr[u], fi[u] * fi[u]), scale_prev, acc[c + u]);
+            }
+            ++since;
+            const int prev = item - 1, cp_prev = prev / T;
+            const bool last = (i == n) || ((prev + 1) / T != cp_prev);
+            if (last || since == a.flush_every) {
+                flush_acc(cp_prev);
+                since = 0;
+            }
+        }
+        if (i < n) {
+            // ---- decode of the next item (the gridding of this one has finished) ----
+            if (i + 1 < n) {
+                const int cp = item / T, cpn = (item + 1) / T;
+                if (cpn != cp) {
+                    flush_power(cp);
+                    load_gains(cpn);
+                }
+                decode(item + 1, (i + 1) & 1);
+            } else {
+                flush_power(item / T);
+            }
+            // ---- split X(i) into the stage-2 operands in TMEM ----
+            if (!mbar_wait(mb1, i & 1)) failed = true;
+            fence_after();
+            {
+                // quarter qt: part (re / im) = qt >> 1, x range 32 * (qt & 1) .. + 32
+                const int part = qt >> 1, hx = qt & 1;
+                const uint32_t src = tX + lane_base + 64 * part + 32 * hx;
+                const uint32_t dhi = tXop + lane_base + 64 * part + 16 * hx;
+                const uint32_t dlo = dhi + 32;
+#pragma unroll
+                for (int c = 0; c < 32; c += 16) {
+                    float xv[16];
+                    tld<16>(src + c, xv);
+                    tld_wait();
+                    uint32_t ph[8], pl[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) split2(xv[2 * u], xv[2 * u + 1], ph[u], pl[u]);
+                    tst8(dhi + c / 2, ph);
+                    tst8(dlo + c / 2, pl);
+                }
+            }
+            tst_wait();
+            fence_before();
+            failed = __syncthreads_or(failed) != 0;   // uniform across the CTA
+            // ---- stage 2 issue: F = X W^T (rows transformed) ----
+            if (tid == 0 && !failed) {
+                fence_after();
+                constexpr uint32_t id2 = idesc(128);
+                // A operand columns: X re hi/lo at +0/+32, X im hi/lo at +64/+96
+                constexpr int ar[6] = {0, 0, 32, 64, 64, 96};
+                constexpr int br[6] = {WR_HI, WR_LO, WR_HI, NWI_HI, NWI_LO, NWI_HI};
+                constexpr int bi[6] = {WI_HI, WI_LO, WI_HI, WR_HI, WR_LO, WR_HI};
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        mma_ts(tF, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(br[q] * kWStep + 16 * j), id2, (q | j) != 0);
+                        mma_ts(tF + 128, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(bi[q] * kWStep + 16 * j), id2,
+                               (q | j) != 0);
+                    }
+                commit(mb2);
+            }
+            if (!failed) ++issued2;
+            scale_prev = scale_cur;
+        }
+    }
+    if (failed) {
+        // a tensor-core wait ran out: mark this CTA's first (channel, pol) block with NaN,
+        // wait (bounded) for the last stage-2 batch still in flight, and stop
+        if (n > 0 && tid == 0) a.accum[(size_t)(beg / T) * NP * NP] = __longlong_as_double(0x7ff8000000000000LL);
+        if (issued2 > 0) mbar_wait(mb2, (issued2 - 1) & 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512) : "memory");
+}
+
+}  // namespace dg
+
+size_t dftgemm_smem_bytes(int n_ant) {
+    return dg::smem_fixed() + (size_t)n_ant * (2 * sizeof(float2) + sizeof(float));
+}
+
+// W operand tables for N_p = 128: six [128][64] K-major FP16 tables (re hi/lo, im hi/lo,
+// -im hi/lo) of W[k][n] = exp(+2 pi i n k / 128), computed in float64.
+void dftgemm_tables(std::vector<uint16_t>& out) {
+    using namespace dg;
+    out.assign((size_t)N_WTAB * WTAB, 0);
+    for (int k = 0; k < NP; ++k)
+        for (int n = 0; n < NG; ++n) {
+            const double ang = 2.0 * 3.14159265358979323846 * double((n * k) % NP) / double(NP);
+            const double re = std::cos(ang), im = std::sin(ang);
+            const double vals[3] = {re, im, -im};
+            for (int c = 0; c < 3; ++c) {
+                const __half hi = __double2half(vals[c]);
+                const __half lo = __double2half(vals[c] - (double)__half2float(hi));
+                out[(size_t)(2 * c) * WTAB + koff(k, n, NG)] = __half_as_ushort(hi);
+                out[(size_t)(2 * c + 1) * WTAB + koff(k, n, NG)] = __half_as_ushort(lo);
+            }
+        }
+}
+
+cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm, cudaStream_t st) {
+    const size_t smem = dftgemm_smem_bytes(a.n_ant);
+    const __half* w = static_cast<const __half*>(wtab);
+    cudaError_t e;
+    long long grid = n_sm;
+    if (grid > a.n_items) grid = a.n_items;
+    switch (vdt) {
+#define EPIC_DG_CASE(V)                                                                                      \
+    case V:                                                                                                  \
+        e = cudaFuncSetAttribute(dg::moff_dftgemm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                      \
+        if (grid > 0) dg::moff_dftgemm_kernel<V><<<(unsigned)grid, dg::NT, smem, st>>>(a, w);                \
+        return cudaGetLastError();
+        EPIC_DG_CASE(0)
+        EPIC_DG_CASE(1)
+        EPIC_DG_CASE(2)
+#undef EPIC_DG_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace epic

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libepic.so")
 EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
-           "epic_last_error")
+           "epic_last_error", "epic_set_transform")
+XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
 
@@ -50,6 +51,8 @@ def load(path=LIB_PATH):
     lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.epic_plan_info.restype = i32
     lib.epic_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    lib.epic_set_transform.restype = i32
+    lib.epic_set_transform.argtypes = [vp, i32]
     lib.epic_last_error.restype = ctypes.c_char_p
     lib.epic_last_error.argtypes = []
     _lib = lib
@@ -107,6 +110,10 @@ def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, strea
     _check(load().epic_image_backward(plan, volt, int(n_time), gains, grad_image, grad_gains, stream))
 
 
+def epic_set_transform(plan, xform):
+    _check(load().epic_set_transform(plan, int(xform)))
+
+
 def epic_plan_info(plan):
     nnz, cells, lag = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
     _check(load().epic_plan_info(plan, ctypes.byref(nnz), ctypes.byref(cells), ctypes.byref(lag)))
@@ -126,6 +133,12 @@ class Plan:
         self._h = epic_create(self.n_ant, pos, kern_ptr, kern_dxdy, kern_w, dx, origin, n_grid, n_pad,
                               n_chan, n_pol, VOLT_DTYPES[vdtype], device)
         self.info = epic_plan_info(self._h)
+
+    def set_transform(self, xform):
+        """'fft' (FP32 shared-memory FFT) or 'dftgemm' (tensor-core DFT, FP16 hi+lo, N_p = 128)."""
+        epic_set_transform(self._h, {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM}[xform])
+        self.xform = xform
+        return self
 
     @classmethod
     def from_workload(cls, wl, device=0, n_chan=None):

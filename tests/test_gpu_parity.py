@@ -229,3 +229,51 @@ def test_python_layer_rejects_bad_shapes(epic):
         plan.image(to_dev(wl), torch.ones((1, 1, 3), dtype=torch.complex64, device="cuda"))
     with pytest.raises(epic.EpicError):
         epic.epic_image(plan._h, to_dev(wl).data_ptr(), 0, None, None, None, 0, None, None, None)
+
+
+# ---------------------------------------------------------------------------------------------
+# the tensor-core DFT form (N_p = 128), same oracle and same tolerance as the FP32 FFT form
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n_grid, n_ant, n_time, n_chan, n_pol, vdtype", [
+    (64, 40, 5, 2, 1, "c64"),       # complex weights, two channels
+    (37, 300, 9, 1, 2, "f16"),      # ragged grid, A above the threads per CTA
+    (64, 700, 4, 1, 1, "ci4"),      # many antennas
+])
+def test_dftgemm_small(epic, n_grid, n_ant, n_time, n_chan, n_pol, vdtype):
+    wl = _small_workload(128, n_grid, n_ant, n_time, n_chan, n_pol, seed=n_ant + 7, vdtype=vdtype)
+    rng = np.random.default_rng(n_ant + 1)
+    g = synth.random_gains(rng, (n_chan, n_pol, n_ant))
+    M = oracle_map(wl)
+    plan = epic.Plan.from_workload(wl).set_transform("dftgemm")
+    out = plan.image(to_dev(wl), gains_dev(g), want_autocorr=True)
+    torch.cuda.synchronize()
+    gg = g.astype(np.complex128)
+    check_close(out["image"].cpu().numpy(), moff.moff_image(M, wl.volt, gg, wl.n_grid, wl.n_pad), "image")
+    check_close(out["autocorr"].cpu().numpy(), moff.autocorr_term(M, wl.volt, gg, wl.n_grid, wl.n_pad), "autocorr")
+    np.testing.assert_allclose(out["power"].cpu().numpy(), (np.abs(wl.volt * gg[None]) ** 2).sum(0), rtol=1e-5)
+
+
+def test_dftgemm_lwa_slice_matches_fft(epic):
+    """LWA-like slice (4+4-bit, 2 channels, 2 pols, 48 samples): tensor-core form vs the oracle
+    and vs the FP32 FFT form; the continuation rule holds for it too."""
+    wl = synth.workload_lwa(n_chan=2, n_time=48, chan_index=[3, 120])
+    M = oracle_map(wl)
+    v = to_dev(wl)
+    plan = epic.Plan.from_workload(wl)
+    ref = plan.image(v)["image"].cpu().numpy()
+    plan.set_transform("dftgemm")
+    got = plan.image(v)["image"].cpu().numpy()
+    want = moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad)
+    check_close(got, want, "tensor-core image")
+    check_close(ref, want, "fft image")
+    part = plan.image(v[:20].contiguous())
+    rest = plan.image(v[20:].contiguous(), accum=part["accum"], t_prev=20)["image"].cpu().numpy()
+    assert np.abs(rest - got).max() <= 1e-6 * np.abs(got).max()
+
+
+def test_dftgemm_rejects_other_sizes(epic):
+    wl = synth.workload_tiny(n_time=2)
+    plan = epic.Plan.from_workload(wl)
+    with pytest.raises(epic.EpicError) as e:
+        plan.set_transform("dftgemm")
+    assert e.value.status == epic.EPIC_EUNSUPPORTED
