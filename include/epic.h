@@ -72,7 +72,7 @@ typedef enum {
  *   dx          grid spacing in metres (> 0).
  *   origin_xy   host [2] float64, position (m) of the centre of grid cell (0, 0).
  *   n_grid      N_g, the unpadded grid side (1 .. n_pad/2).
- *   n_pad       N_p, the padded grid and image side: 32, 64, 128 or 256.
+ *   n_pad       N_p, the padded grid and image side: 32, 64, 128, 256 or 512.
  *   n_chan      C, channels per call (>= 1).
  *   n_pol       P, polarisations per call (>= 1).
  *   volt_dtype  one of epic_volt_dtype.

@@ -30,7 +30,7 @@ epic_status cuda_fail(cudaError_t e, const char* what) {
     return fail(EPIC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-bool is_pow2_size(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+bool is_pow2_size(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
@@ -102,15 +102,26 @@ struct MapEntry {
     std::complex<double> w;
 };
 
-epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t st) {
-    cudaError_t e;
-    switch (p->n_pad) {
-        case 32: e = epic::launch_fwd_32(p->vdt, a, p->n_sm, st); break;
-        case 64: e = epic::launch_fwd_64(p->vdt, a, p->n_sm, st); break;
-        case 128: e = epic::launch_fwd_128(p->vdt, a, p->n_sm, st); break;
-        case 256: e = epic::launch_fwd_256(p->vdt, a, p->n_sm, st); break;
-        default: return fail(EPIC_EUNSUPPORTED, "n_pad %d", p->n_pad);
+cudaError_t launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st) {
+    switch (n_pad) {
+        case 32: return epic::launch_fwd_32(vdt, L, n_sm, st);
+        case 64: return epic::launch_fwd_64(vdt, L, n_sm, st);
+        case 128: return epic::launch_fwd_128(vdt, L, n_sm, st);
+        case 256: return epic::launch_fwd_256(vdt, L, n_sm, st);
+        case 512: return epic::launch_fwd_512(vdt, L, n_sm, st);
+        default: return cudaErrorInvalidValue;
     }
+}
+
+epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t st) {
+    epic::SegList L;
+    L.seg[0] = a;
+    L.first[0] = 0;
+    L.first[1] = (int)a.n_items;
+    L.n_seg = 1;
+    L.max_ant = a.n_ant;
+    L.max_workers = 0;
+    const cudaError_t e = launch_fwd_list(p->n_pad, p->vdt, L, p->n_sm, st);
     return e == cudaSuccess ? EPIC_OK : cuda_fail(e, "imaging kernel launch");
 }
 
@@ -121,6 +132,7 @@ epic_status launch_bwd(const epic_plan* p, const epic::BwdArgs& a, cudaStream_t 
         case 64: e = epic::launch_bwd_64(p->vdt, a, p->n_sm, st); break;
         case 128: e = epic::launch_bwd_128(p->vdt, a, p->n_sm, st); break;
         case 256: e = epic::launch_bwd_256(p->vdt, a, p->n_sm, st); break;
+        case 512: e = epic::launch_bwd_512(p->vdt, a, p->n_sm, st); break;
         default: return fail(EPIC_EUNSUPPORTED, "n_pad %d", p->n_pad);
     }
     return e == cudaSuccess ? EPIC_OK : cuda_fail(e, "adjoint kernel launch");
@@ -143,7 +155,7 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     if (!pos_xy || !kern_ptr || !origin_xy) return fail(EPIC_EINVAL, "NULL host array");
     if (!(dx > 0.0) || !std::isfinite(dx)) return fail(EPIC_EINVAL, "grid spacing must be finite and > 0");
     if (!std::isfinite(origin_xy[0]) || !std::isfinite(origin_xy[1])) return fail(EPIC_EINVAL, "origin not finite");
-    if (!is_pow2_size(n_pad)) return fail(EPIC_EUNSUPPORTED, "n_pad = %d (supported: 32, 64, 128, 256)", n_pad);
+    if (!is_pow2_size(n_pad)) return fail(EPIC_EUNSUPPORTED, "n_pad = %d (supported: 32, 64, 128, 256, 512)", n_pad);
     if (n_grid < 1 || 2 * n_grid > n_pad)
         return fail(EPIC_EINVAL, "n_grid = %d must be in 1..n_pad/2 (2x zero padding)", n_grid);
     if (n_chan < 1 || n_pol < 1) return fail(EPIC_EINVAL, "n_chan and n_pol must be >= 1");

@@ -22,6 +22,17 @@ struct FwdArgs {
     float wsum_max;            // max over cells of sum_a |M[g, a]| (scales the FP16 operands)
 };
 
+// Sub-array calls imaged by one persistent forward launch (same N_p and voltage format);
+// a single epic_image call is a one-entry list.  Passed by value as a kernel parameter.
+constexpr int kMaxSeg = 64;
+struct SegList {
+    FwdArgs seg[kMaxSeg];      // per sub-array (n_items of each = C * P * T)
+    int first[kMaxSeg + 1];    // first global item of each sub-array; first[n_seg] = total
+    int n_seg;
+    int max_ant;               // largest antenna count (shared-memory sizing)
+    int max_workers;           // cap on CTAs (clusters) launched, 0 = every resident one
+};
+
 struct BwdArgs {
     const void* volt;
     int n_time, n_cp, n_ant;
@@ -40,15 +51,17 @@ struct BwdArgs {
 };
 
 // Kernel launchers, one translation unit per padded size.  Return cudaSuccess or the
-// launch error.  `smem_bytes` is computed by the launcher.
-cudaError_t launch_fwd_32(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
-cudaError_t launch_fwd_64(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
-cudaError_t launch_fwd_128(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
-cudaError_t launch_fwd_256(int vdt, const FwdArgs& a, int n_sm, cudaStream_t st);
+// launch error.  Shared memory is sized by the launcher.
+cudaError_t launch_fwd_32(int vdt, const SegList& L, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_64(int vdt, const SegList& L, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_128(int vdt, const SegList& L, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_256(int vdt, const SegList& L, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_512(int vdt, const SegList& L, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_32(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_64(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_128(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_256(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_bwd_512(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 
 // Shared-memory bytes the forward / backward kernels need for a given size and antenna count.
 size_t fwd_smem_bytes(int n_pad, int n_ant);

@@ -111,6 +111,7 @@ size_t fwd_smem_bytes(int n_pad, int n_ant) {
         case 64: return Geo<64>::smem_bytes(n_ant);
         case 128: return Geo<128>::smem_bytes(n_ant);
         case 256: return Geo<256>::smem_bytes(n_ant);
+        case 512: return Geo<512>::smem_bytes(n_ant);
         default: return 0;
     }
 }
@@ -126,6 +127,7 @@ int grid_rows_per_block(int n_pad) {
         case 64: return Geo<64>::ROWS;
         case 128: return Geo<128>::ROWS;
         case 256: return Geo<256>::ROWS;
+        case 512: return Geo<512>::ROWS;
         default: return 0;
     }
 }
@@ -136,6 +138,7 @@ int exchange_row_stride(int n_pad) {
         case 64: return Geo<64>::RXS;
         case 128: return Geo<128>::RXS;
         case 256: return Geo<256>::RXS;
+        case 512: return Geo<512>::RXS;
         default: return 0;
     }
 }

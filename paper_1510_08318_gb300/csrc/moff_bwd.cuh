@@ -56,14 +56,6 @@ moff_bwd_kernel(const BwdArgs a) {
         nw = gridDim.x / Q;
     }
     const int y = rank * G::ROWS + r;
-    float2* RBq[Q];
-    if constexpr (Q > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-#pragma unroll
-        for (int q = 0; q < Q; ++q) RBq[q] = cl.map_shared_rank(RB, q);
-    } else {
-        RBq[0] = RB;
-    }
 
     for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[((i % S) * (i / S)) & (NP - 1)];
     for (int aa = tid; aa < a.n_ant; aa += NT) GA[aa] = make_float2(0.f, 0.f);
@@ -163,7 +155,7 @@ moff_bwd_kernel(const BwdArgs a) {
                 for (int k1 = 0; k1 < S; ++k1) {
                     const int kx = k2 + R1 * k1;
                     if constexpr (Q > 1) {
-                        RBq[(R1 * k1) / G::COLS][y * G::RBS + (kx % G::COLS)] = z[k1];
+                        cluster_ptr(RB, (R1 * k1) / G::COLS)[y * G::RBS + (kx % G::COLS)] = z[k1];
                     } else {
                         RB[y * G::RBS + kx] = z[k1];
                     }
@@ -221,7 +213,7 @@ moff_bwd_kernel(const BwdArgs a) {
             for (int n2 = 0; n2 < NI; ++n2) {
                 const int yy = n1 + S * n2;
                 if constexpr (Q > 1) {
-                    RBq[yy / G::ROWS][(yy % G::ROWS) * IBS + kxg] = xo[n2];
+                    cluster_ptr(RB, yy / G::ROWS)[(yy % G::ROWS) * IBS + kxg] = xo[n2];
                 } else {
                     RB[yy * IBS + kxg] = xo[n2];
                 }
@@ -310,6 +302,10 @@ cudaError_t launch_bwd_t(const BwdArgs& a, int n_sm, cudaStream_t st) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cfg.gridDim = dim3(G::Q * n_sm);
+        if constexpr (G::Q > 8) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
         int n_cl = 0;
         e = cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg);
         if (e != cudaSuccess) return e;

@@ -10,7 +10,8 @@ namespace epic {
 namespace cg = cooperative_groups;
 
 // Per padded size N_p: S threads cooperate on each 1-D transform; a cluster of Q CTAs
-// shares one image (each CTA owns N_p/Q output columns and N_g/Q grid rows).
+// shares one image (each CTA owns N_p/Q output columns and N_g/Q grid rows).  N_p = 512 uses
+// 16-CTA clusters (a non-portable cluster size).
 template <int NP> struct Cfg;
 // S, Q, minimum CTAs per SM, and the shared-memory row strides (in float2) chosen so that
 // every warp-wide exchange access is free of bank conflicts.
@@ -18,6 +19,7 @@ template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8, RXS 
 template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2, RXS = 72,  RBS = 66; };
 template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1, RXS = 136, RBS = 129; };
 template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1, RXS = 264, RBS = 65; };
+template <> struct Cfg<512> { static constexpr int S = 16, Q = 16, MINB = 1, RXS = 520, RBS = 33; };
 
 template <int NP> struct Geo {
     static constexpr int NG = NP / 2;          // unpadded grid side (2x padding, Sec. 3)
@@ -84,6 +86,12 @@ template <> struct Volt<2> {                   // signed 4+4-bit
 __device__ __forceinline__ void cfma(float2& acc, float2 w, float2 v) {
     acc.x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc.x));
     acc.y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc.y));
+}
+
+// Shared-memory pointer p of cluster rank q (distributed shared memory).
+template <typename T>
+__device__ __forceinline__ T* cluster_ptr(T* p, int q) {
+    return cg::this_cluster().map_shared_rank(p, q);
 }
 
 template <int Q>

@@ -27,7 +27,7 @@ namespace epic {
 
 template <int NP, int VDT>
 __global__ void __launch_bounds__(Geo<NP>::NT, Geo<NP>::MINB)
-moff_fwd_kernel(const FwdArgs a) {
+moff_fwd_kernel(const __grid_constant__ SegList L) {
     using G = Geo<NP>;
     constexpr int S = G::S, R1 = G::R1, NI = G::NI, KP = G::KP, NT = G::NT, NG = G::NG;
     constexpr int Q = G::Q, VPT = G::VPT;
@@ -38,38 +38,34 @@ moff_fwd_kernel(const FwdArgs a) {
     float2* RB = RX + G::ROWS * G::RXS;                      // [NG][RBS] row-pass output
     float2* TW = RB + NG * G::RBS;                           // [R1][S] exp(+2 pi i n1 k2 / NP)
     float2* VB = TW + NP;                                    // [A] g_a V_a
-    float2* GN = VB + a.n_ant;                               // [A] gains
-    float* PW = reinterpret_cast<float*>(GN + a.n_ant);      // [A] partial sum |g V|^2
+    float2* GN = VB + L.max_ant;                             // [A] gains
+    float* PW = reinterpret_cast<float*>(GN + L.max_ant);    // [A] partial sum |g V|^2
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n1 = lane % S;
     const int r = tid / S;
     const int cc = lane / S;
-    int rank = 0, wid = blockIdx.x, nw = gridDim.x;
+    int rank = 0, wid = blockIdx.x, nw = gridDim.x;     // worker = CTA (or cluster)
     if constexpr (Q > 1) {
         rank = blockIdx.x % Q;
         wid = blockIdx.x / Q;
         nw = gridDim.x / Q;
     }
     const int y = rank * G::ROWS + r;
-    float2* RBq[Q];
-    if constexpr (Q > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-#pragma unroll
-        for (int q = 0; q < Q; ++q) RBq[q] = cl.map_shared_rank(RB, q);
-    } else {
-        RBq[0] = RB;
-    }
 
-    for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[((i % S) * (i / S)) & (NP - 1)];
-    for (int aa = tid; aa < a.n_ant; aa += NT) PW[aa] = 0.f;   // owner-thread entries
+    for (int i = tid; i < NP; i += NT) TW[i] = L.seg[0].twiddle[((i % S) * (i / S)) & (NP - 1)];
+    for (int aa = tid; aa < L.max_ant; aa += NT) PW[aa] = 0.f;   // owner-thread entries
 
+    // global items [0, first[n_seg]) of all sub-arrays, split evenly over the workers
     long long beg_l, end_l;
-    work_range(a.n_items, wid, nw, beg_l, end_l);
-    const int beg = (int)beg_l, end = (int)end_l;   // the host guarantees n_items < 2^31
-
-    const int A = a.n_ant, T = a.n_time;
-    const VT* V = static_cast<const VT*>(a.volt);
+    work_range(L.first[L.n_seg], wid, nw, beg_l, end_l);
+    const int beg = (int)beg_l, end = (int)end_l;   // the host guarantees fewer than 2^31 items
+    int sg = 0;
+    while (sg + 1 < L.n_seg && L.first[sg + 1] <= beg) ++sg;
+    const FwdArgs* ap = &L.seg[sg];
+    int A = ap->n_ant, T = ap->n_time, seg_first = L.first[sg], seg_end = L.first[sg + 1];
+    const VT* V = static_cast<const VT*>(ap->volt);
+#define a (*ap)
 
     float acc[2][R1];
 #pragma unroll
@@ -78,13 +74,17 @@ moff_fwd_kernel(const FwdArgs a) {
         for (int i = 0; i < R1; ++i) acc[s][i] = 0.f;
 
     VT raw[VPT];
-    auto prefetch = [&](int item) {
-        const int cp = item / T, t = item - cp * T;
-        const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
+    // raw voltages of global item g (which may belong to the next sub-array)
+    auto prefetch = [&](int g) {
+        const FwdArgs* sp = (g < seg_end) ? ap : ap + 1;
+        const int li = g - ((g < seg_end) ? seg_first : seg_end);
+        const int Tq = sp->n_time, Aq = sp->n_ant;
+        const int cp = li / Tq, t = li - cp * Tq;
+        const VT* base = static_cast<const VT*>(sp->volt) + ((long long)t * sp->n_cp + cp) * (long long)Aq;
 #pragma unroll
         for (int i = 0; i < VPT; ++i) {
             const int aa = tid + NT * i;
-            if (aa < A) raw[i] = __ldg(base + aa);
+            if (aa < Aq) raw[i] = __ldg(base + aa);
         }
     };
 
@@ -114,7 +114,18 @@ moff_fwd_kernel(const FwdArgs a) {
 
     int cur = -1, since = 0;
     if (beg < end) prefetch(beg);
-    for (int item = beg; item < end; ++item) {
+    for (int g = beg; g < end; ++g) {
+        if (g == seg_end) {          // next sub-array: flush, then switch tables and sizes
+            if (cur >= 0) flush(cur, true);
+            cur = -1;
+            ++ap;
+            A = ap->n_ant;
+            T = ap->n_time;
+            V = static_cast<const VT*>(ap->volt);
+            seg_first = seg_end;
+            seg_end += ap->n_cp * T;
+        }
+        const int item = g - seg_first;
         const int cp = item / T;
         const int t = item - cp * T;
         if (cp != cur || since == a.flush_every) {
@@ -145,7 +156,7 @@ moff_fwd_kernel(const FwdArgs a) {
                 VB[aa] = vp;
                 PW[aa] += cnorm(vp);
             }
-            if (item + 1 < end) prefetch(item + 1);
+            if (g + 1 < end) prefetch(g + 1);
         }
         block_or_cluster_sync<Q>();
 
@@ -191,7 +202,7 @@ moff_fwd_kernel(const FwdArgs a) {
                 for (int k1 = 0; k1 < S; ++k1) {
                     const int kx = k2 + R1 * k1;
                     if constexpr (Q > 1) {
-                        RBq[(R1 * k1) / G::COLS][y * G::RBS + (kx % G::COLS)] = z[k1];
+                        cluster_ptr(RB, (R1 * k1) / G::COLS)[y * G::RBS + (kx % G::COLS)] = z[k1];
                     } else {
                         RB[y * G::RBS + kx] = z[k1];
                     }
@@ -228,24 +239,27 @@ moff_fwd_kernel(const FwdArgs a) {
         }
     }
     if (cur >= 0) flush(cur, true);
+#undef a
 }
 
 template <int NP, int VDT>
-cudaError_t launch_fwd_t(const FwdArgs& a, int n_sm, cudaStream_t st) {
+cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
     using G = Geo<NP>;
     auto kern = moff_fwd_kernel<NP, VDT>;
-    const size_t smem = G::smem_bytes(a.n_ant);
+    const size_t smem = G::smem_bytes(L.max_ant);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (a.n_items == 0) return cudaSuccess;
+    const long long n_items = L.first[L.n_seg];
+    if (n_items == 0) return cudaSuccess;
     if constexpr (G::Q == 1) {
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         long long grid = (long long)per_sm * n_sm;
-        if (grid > a.n_items) grid = a.n_items;
-        kern<<<(unsigned)grid, G::NT, smem, st>>>(a);
+        if (L.max_workers > 0 && grid > L.max_workers) grid = L.max_workers;
+        if (grid > n_items) grid = n_items;
+        kern<<<(unsigned)grid, G::NT, smem, st>>>(L);
         return cudaGetLastError();
     } else {
         cudaLaunchConfig_t cfg = {};
@@ -260,14 +274,19 @@ cudaError_t launch_fwd_t(const FwdArgs& a, int n_sm, cudaStream_t st) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cfg.gridDim = dim3(G::Q * n_sm);
+        if constexpr (G::Q > 8) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
         int n_cl = 0;
         e = cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg);
         if (e != cudaSuccess) return e;
         if (n_cl < 1) return cudaErrorInvalidConfiguration;
         long long ncl = n_cl;
-        if (ncl > a.n_items) ncl = a.n_items;
+        if (L.max_workers > 0 && ncl > L.max_workers) ncl = L.max_workers;
+        if (ncl > n_items) ncl = n_items;
         cfg.gridDim = dim3((unsigned)(ncl * G::Q));
-        e = cudaLaunchKernelEx(&cfg, kern, a);
+        e = cudaLaunchKernelEx(&cfg, kern, L);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }

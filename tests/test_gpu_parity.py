@@ -130,6 +130,8 @@ def _small_workload(n_pad, n_grid, n_ant, n_time, n_chan, n_pol, seed, vdtype="c
     (64, 20, 300, 17, 2, 1, "ci4"),    # ragged grid, A > threads per CTA
     (128, 64, 700, 9, 1, 2, "c64"),    # A beyond the register prefetch (4 per thread)
     (256, 100, 64, 3, 2, 1, "f16"),
+    (512, 40, 30, 3, 1, 1, "c64"),     # 16-CTA clusters
+    (512, 256, 12, 2, 1, 1, "f16"),    # full 256 x 256 unpadded grid
 ])
 def test_small_sizes(epic, n_pad, n_grid, n_ant, n_time, n_chan, n_pol, vdtype):
     wl = _small_workload(n_pad, n_grid, n_ant, n_time, n_chan, n_pol, seed=n_pad + n_ant, vdtype=vdtype)
@@ -187,6 +189,7 @@ def test_determinism_of_mapping_counts(epic):
     (64, 30, 40, 6, 1, "ci4"),
     (128, 64, 90, 4, 1, "f16"),
     (256, 128, 50, 3, 1, "c64"),
+    (512, 60, 20, 2, 1, "f16"),
 ])
 def test_gradient_matches_oracle(epic, n_pad, n_grid, n_ant, n_time, n_chan, vdtype):
     wl = _small_workload(n_pad, n_grid, n_ant, n_time, n_chan, 1, seed=n_ant, vdtype=vdtype)
