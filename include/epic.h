@@ -157,6 +157,47 @@ epic_status epic_image_backward(const epic_plan *plan, const void *volt, int n_t
  */
 epic_status epic_plan_info(const epic_plan *plan, int64_t *nnz, int64_t *n_cells, int *lag_side);
 
+/*
+ * Batches: many plans (e.g. heterogeneous sub-arrays, each with its own antennas, kernels,
+ * grid and channels) imaged by one persistent launch per padded-size class, the classes
+ * forked onto internal streams and joined back into the caller's stream.  The stacking of
+ * data streams for array operations is App. A.3's; the batch object owns its streams and
+ * events only, so epic_batch_image allocates nothing and can be captured in a CUDA graph.
+ * Plans must share the device and the voltage format; at most 64 plans per size class are
+ * walked by one launch (more are split into further launches).
+ */
+typedef struct epic_batch epic_batch;
+
+/* Group n_plans plans (the plans must outlive the batch). */
+epic_status epic_batch_create(epic_batch **batch, int n_plans, epic_plan *const *plans);
+
+/*
+ * Image every plan of the batch: host arrays of n_plans entries; volt[i], n_time[i],
+ * gains[i] (or gains == NULL, or gains[i] == NULL, for unit gains) are as for epic_image;
+ * accum[i] is overwritten with sum_t |F_t|^2; image[i] (image == NULL or image[i] == NULL to
+ * skip) receives accum[i] / n_time[i].  The FFT form is used for every class.
+ */
+epic_status epic_batch_image(epic_batch *batch, const void *const *volt, const int *n_time,
+                             const float *const *gains, double *const *accum, float *const *image,
+                             void *stream);
+
+/*
+ * Autotune the batch on representative inputs (same arguments as epic_batch_image; accum is
+ * overwritten): for each size class, the number of resident CTAs (all, 3/4 or 1/2) that runs it
+ * fastest, then whether the classes run faster concurrently or back to back.  Synchronises the
+ * stream; not capturable.  The choice is kept in the batch.
+ */
+epic_status epic_batch_autotune(epic_batch *batch, const void *const *volt, const int *n_time,
+                                const float *const *gains, double *const *accum, void *stream);
+
+/* The batch's size classes, whether they run concurrently, and the worker cap of each class
+ * (0 = all resident; at most max_workers entries written).  Any pointer may be NULL. */
+epic_status epic_batch_info(const epic_batch *batch, int *n_classes, int *concurrent, int *workers,
+                            int max_workers);
+
+/* Release the batch (not its plans).  NULL is accepted. */
+void epic_batch_destroy(epic_batch *batch);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char *epic_last_error(void);
 

@@ -11,12 +11,16 @@
 
 #include "../../include/epic.h"
 #include "epic_internal.h"
+#include "epic_plan.h"
 
 namespace {
-
 thread_local std::string g_err;
+bool is_pow2_size(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+}  // namespace
 
-epic_status fail(epic_status st, const char* fmt, ...) {
+void epic_clear_error() { g_err.clear(); }
+
+epic_status epic_fail(epic_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -26,43 +30,9 @@ epic_status fail(epic_status st, const char* fmt, ...) {
     return st;
 }
 
-epic_status cuda_fail(cudaError_t e, const char* what) {
-    return fail(EPIC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+epic_status epic_cuda_fail(cudaError_t e, const char* what) {
+    return epic_fail(EPIC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-bool is_pow2_size(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) return;
-        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
-    }
-    ~DeviceGuard() {
-        if (ok && prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-}  // namespace
-
-struct epic_plan {
-    int n_ant = 0, n_grid = 0, n_pad = 0, n_chan = 0, n_pol = 0, vdt = 0, device = 0, n_sm = 0;
-    int lag_side = 0;
-    int64_t nnz = 0, n_cells = 0;
-    int* cell_ptr = nullptr;
-    int2* cell_ent = nullptr;
-    float* cell_wim = nullptr;   // nullptr when every weight is real
-    int* ant_ptr = nullptr;
-    int2* ant_ent = nullptr;
-    float* ant_wim = nullptr;
-    float2* twiddle = nullptr;
-    float2* lag_tab = nullptr;
-    int xform = EPIC_XFORM_FFT;
-    uint16_t* dg_tab = nullptr;   // DFT operand tables of the tensor-core form
-    float wsum_max = 0.f;         // max over cells of sum_a |M[g, a]|
-};
 
 namespace {
 
@@ -102,7 +72,9 @@ struct MapEntry {
     std::complex<double> w;
 };
 
-cudaError_t launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st) {
+}  // namespace
+
+cudaError_t epic_launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st) {
     switch (n_pad) {
         case 32: return epic::launch_fwd_32(vdt, L, n_sm, st);
         case 64: return epic::launch_fwd_64(vdt, L, n_sm, st);
@@ -113,6 +85,35 @@ cudaError_t launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm
     }
 }
 
+int epic_resident_workers(int n_pad, int vdt, const std::vector<epic_plan*>& plans, const std::vector<int>& members,
+                          int n_sm) {
+    int max_ant = 0;
+    for (int i : members) max_ant = std::max(max_ant, plans[i]->n_ant);
+    return epic::resident_fwd_workers(n_pad, vdt, max_ant, n_sm);
+}
+
+epic::FwdArgs epic_plan_fwd_args(const epic_plan* plan, const void* volt, int n_time, const float2* gains,
+                                 double* accum, double* power) {
+    epic::FwdArgs a;
+    a.volt = volt;
+    a.n_time = n_time;
+    a.n_cp = plan->n_chan * plan->n_pol;
+    a.n_ant = plan->n_ant;
+    a.gains = gains;
+    a.cell_ptr = plan->cell_ptr;
+    a.cell_ent = plan->cell_ent;
+    a.cell_wim = plan->cell_wim;
+    a.twiddle = plan->twiddle;
+    a.accum = accum;
+    a.power = power;
+    a.n_items = (long long)a.n_cp * n_time;
+    a.flush_every = 1024;
+    a.wsum_max = plan->wsum_max;
+    return a;
+}
+
+namespace {
+
 epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t st) {
     epic::SegList L;
     L.seg[0] = a;
@@ -121,8 +122,8 @@ epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t 
     L.n_seg = 1;
     L.max_ant = a.n_ant;
     L.max_workers = 0;
-    const cudaError_t e = launch_fwd_list(p->n_pad, p->vdt, L, p->n_sm, st);
-    return e == cudaSuccess ? EPIC_OK : cuda_fail(e, "imaging kernel launch");
+    const cudaError_t e = epic_launch_fwd_list(p->n_pad, p->vdt, L, p->n_sm, st);
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "imaging kernel launch");
 }
 
 epic_status launch_bwd(const epic_plan* p, const epic::BwdArgs& a, cudaStream_t st) {
@@ -133,9 +134,9 @@ epic_status launch_bwd(const epic_plan* p, const epic::BwdArgs& a, cudaStream_t 
         case 128: e = epic::launch_bwd_128(p->vdt, a, p->n_sm, st); break;
         case 256: e = epic::launch_bwd_256(p->vdt, a, p->n_sm, st); break;
         case 512: e = epic::launch_bwd_512(p->vdt, a, p->n_sm, st); break;
-        default: return fail(EPIC_EUNSUPPORTED, "n_pad %d", p->n_pad);
+        default: return epic_fail(EPIC_EUNSUPPORTED, "n_pad %d", p->n_pad);
     }
-    return e == cudaSuccess ? EPIC_OK : cuda_fail(e, "adjoint kernel launch");
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "adjoint kernel launch");
 }
 
 }  // namespace
@@ -144,27 +145,28 @@ extern "C" {
 
 const char* epic_last_error(void) { return g_err.c_str(); }
 
+
 epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const int* kern_ptr,
                         const double* kern_dxdy, const double* kern_w, double dx,
                         const double* origin_xy, int n_grid, int n_pad, int n_chan, int n_pol,
                         int volt_dtype, int device) {
-    g_err.clear();
-    if (!plan) return fail(EPIC_EINVAL, "plan out-pointer is NULL");
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan out-pointer is NULL");
     *plan = nullptr;
-    if (n_ant < 1 || n_ant > 4096) return fail(EPIC_EINVAL, "n_ant = %d outside 1..4096", n_ant);
-    if (!pos_xy || !kern_ptr || !origin_xy) return fail(EPIC_EINVAL, "NULL host array");
-    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(EPIC_EINVAL, "grid spacing must be finite and > 0");
-    if (!std::isfinite(origin_xy[0]) || !std::isfinite(origin_xy[1])) return fail(EPIC_EINVAL, "origin not finite");
-    if (!is_pow2_size(n_pad)) return fail(EPIC_EUNSUPPORTED, "n_pad = %d (supported: 32, 64, 128, 256, 512)", n_pad);
+    if (n_ant < 1 || n_ant > 4096) return epic_fail(EPIC_EINVAL, "n_ant = %d outside 1..4096", n_ant);
+    if (!pos_xy || !kern_ptr || !origin_xy) return epic_fail(EPIC_EINVAL, "NULL host array");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return epic_fail(EPIC_EINVAL, "grid spacing must be finite and > 0");
+    if (!std::isfinite(origin_xy[0]) || !std::isfinite(origin_xy[1])) return epic_fail(EPIC_EINVAL, "origin not finite");
+    if (!is_pow2_size(n_pad)) return epic_fail(EPIC_EUNSUPPORTED, "n_pad = %d (supported: 32, 64, 128, 256, 512)", n_pad);
     if (n_grid < 1 || 2 * n_grid > n_pad)
-        return fail(EPIC_EINVAL, "n_grid = %d must be in 1..n_pad/2 (2x zero padding)", n_grid);
-    if (n_chan < 1 || n_pol < 1) return fail(EPIC_EINVAL, "n_chan and n_pol must be >= 1");
-    if (volt_dtype < EPIC_VOLT_C64 || volt_dtype > EPIC_VOLT_CI4) return fail(EPIC_EINVAL, "volt_dtype %d", volt_dtype);
-    if (kern_ptr[0] != 0) return fail(EPIC_EINVAL, "kern_ptr[0] must be 0");
+        return epic_fail(EPIC_EINVAL, "n_grid = %d must be in 1..n_pad/2 (2x zero padding)", n_grid);
+    if (n_chan < 1 || n_pol < 1) return epic_fail(EPIC_EINVAL, "n_chan and n_pol must be >= 1");
+    if (volt_dtype < EPIC_VOLT_C64 || volt_dtype > EPIC_VOLT_CI4) return epic_fail(EPIC_EINVAL, "volt_dtype %d", volt_dtype);
+    if (kern_ptr[0] != 0) return epic_fail(EPIC_EINVAL, "kern_ptr[0] must be 0");
     for (int a = 0; a < n_ant; ++a)
-        if (kern_ptr[a + 1] < kern_ptr[a]) return fail(EPIC_EINVAL, "kern_ptr not non-decreasing at antenna %d", a);
+        if (kern_ptr[a + 1] < kern_ptr[a]) return epic_fail(EPIC_EINVAL, "kern_ptr not non-decreasing at antenna %d", a);
     const int n_taps = kern_ptr[n_ant];
-    if (n_taps > 0 && (!kern_dxdy || !kern_w)) return fail(EPIC_EINVAL, "NULL footprint table");
+    if (n_taps > 0 && (!kern_dxdy || !kern_w)) return epic_fail(EPIC_EINVAL, "NULL footprint table");
 
     const int NG = n_pad / 2;   // the kernels work on the N_p/2 grid; cells >= n_grid stay empty
     const double ox = origin_xy[0], oy = origin_xy[1];
@@ -172,21 +174,21 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     ents.reserve(n_taps);
     for (int a = 0; a < n_ant; ++a) {
         const double px = pos_xy[2 * a], py = pos_xy[2 * a + 1];
-        if (!std::isfinite(px) || !std::isfinite(py)) return fail(EPIC_EINVAL, "antenna %d position not finite", a);
+        if (!std::isfinite(px) || !std::isfinite(py)) return epic_fail(EPIC_EINVAL, "antenna %d position not finite", a);
         for (int k = kern_ptr[a]; k < kern_ptr[a + 1]; ++k) {
             const double x = px + kern_dxdy[2 * k];
             const double y = py + kern_dxdy[2 * k + 1];
             const double ux = (x - ox) / dx + 0.5;
             const double uy = (y - oy) / dx + 0.5;
             if (!std::isfinite(ux) || !std::isfinite(uy))
-                return fail(EPIC_EINVAL, "footprint sample %d of antenna %d not finite", k, a);
+                return epic_fail(EPIC_EINVAL, "footprint sample %d of antenna %d not finite", k, a);
             const double fx = std::floor(ux), fy = std::floor(uy);
             if (fx < 0 || fy < 0 || fx >= n_grid || fy >= n_grid)
-                return fail(EPIC_EINVAL, "footprint sample %d of antenna %d maps to cell (%g, %g) outside the %d x %d grid",
+                return epic_fail(EPIC_EINVAL, "footprint sample %d of antenna %d maps to cell (%g, %g) outside the %d x %d grid",
                             k, a, fy, fx, n_grid, n_grid);
             const std::complex<double> w(kern_w[2 * k], kern_w[2 * k + 1]);
             if (!std::isfinite(w.real()) || !std::isfinite(w.imag()))
-                return fail(EPIC_EINVAL, "footprint weight %d not finite", k);
+                return epic_fail(EPIC_EINVAL, "footprint weight %d not finite", k);
             ents.push_back({int(fy) * NG + int(fx), a, k, w});
         }
     }
@@ -306,22 +308,22 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         tw[j] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
     }
 
-    DeviceGuard guard(device);
+    EpicDeviceGuard guard(device);
     if (!guard.ok) {
         delete p;
-        return fail(EPIC_ECUDA, "cannot select CUDA device %d", device);
+        return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", device);
     }
     cudaError_t e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         delete p;
-        return cuda_fail(e, "cudaDeviceGetAttribute");
+        return epic_cuda_fail(e, "cudaDeviceGetAttribute");
     }
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     const size_t need = std::max(epic::fwd_smem_bytes(n_pad, n_ant), epic::bwd_smem_bytes(n_pad, n_ant));
     if (need > (size_t)smem_optin) {
         delete p;
-        return fail(EPIC_EUNSUPPORTED, "%d antennas need %zu bytes of shared memory per block (device limit %d)",
+        return epic_fail(EPIC_EUNSUPPORTED, "%d antennas need %zu bytes of shared memory per block (device limit %d)",
                     n_ant, need, smem_optin);
     }
     if ((e = upload(&p->cell_ptr, cptr)) != cudaSuccess || (e = upload(&p->cell_ent, cent)) != cudaSuccess ||
@@ -329,28 +331,28 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         (e = upload(&p->twiddle, tw)) != cudaSuccess || (e = upload(&p->lag_tab, lag)) != cudaSuccess ||
         (complex_w && ((e = upload(&p->cell_wim, cwim)) != cudaSuccess || (e = upload(&p->ant_wim, awim)) != cudaSuccess))) {
         free_plan(p);
-        return e == cudaErrorMemoryAllocation ? fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
-                                              : cuda_fail(e, "plan upload");
+        return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
+                                              : epic_cuda_fail(e, "plan upload");
     }
     *plan = p;
     return EPIC_OK;
 }
 
 epic_status epic_set_transform(epic_plan* plan, int xform) {
-    g_err.clear();
-    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (xform == EPIC_XFORM_FFT) {
         plan->xform = xform;
         return EPIC_OK;
     }
-    if (xform != EPIC_XFORM_DFTGEMM) return fail(EPIC_EINVAL, "xform %d", xform);
-    if (plan->n_pad != 128) return fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad == 128 (plan: %d)", plan->n_pad);
-    DeviceGuard guard(plan->device);
-    if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    if (xform != EPIC_XFORM_DFTGEMM) return epic_fail(EPIC_EINVAL, "xform %d", xform);
+    if (plan->n_pad != 128) return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad == 128 (plan: %d)", plan->n_pad);
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
     if (epic::dftgemm_smem_bytes(plan->n_ant) > (size_t)smem_optin)
-        return fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the tensor-core kernel's shared memory", plan->n_ant);
+        return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the tensor-core kernel's shared memory", plan->n_ant);
     if (!plan->dg_tab) {
         std::vector<uint16_t> tab;
         epic::dftgemm_tables(tab);
@@ -358,7 +360,7 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
         if (e != cudaSuccess) {
             cudaFree(plan->dg_tab);
             plan->dg_tab = nullptr;
-            return cuda_fail(e, "DFT operand tables");
+            return epic_cuda_fail(e, "DFT operand tables");
         }
     }
     plan->xform = xform;
@@ -367,13 +369,13 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
 
 void epic_destroy(epic_plan* plan) {
     if (!plan) return;
-    DeviceGuard guard(plan->device);
+    EpicDeviceGuard guard(plan->device);
     free_plan(plan);
 }
 
 epic_status epic_plan_info(const epic_plan* plan, int64_t* nnz, int64_t* n_cells, int* lag_side) {
-    g_err.clear();
-    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (nnz) *nnz = plan->nnz;
     if (n_cells) *n_cells = plan->n_cells;
     if (lag_side) *lag_side = plan->lag_side;
@@ -383,74 +385,61 @@ epic_status epic_plan_info(const epic_plan* plan, int64_t* nnz, int64_t* n_cells
 epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, const float* gains,
                        double* accum, double* power, int64_t t_prev, float* image, float* autocorr,
                        void* stream) {
-    g_err.clear();
-    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
-    if (n_time < 1) return fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
-    if (!volt) return fail(EPIC_EINVAL, "volt is NULL");
-    if (!accum) return fail(EPIC_EINVAL, "accum is NULL");
-    if (t_prev < 0) return fail(EPIC_EINVAL, "t_prev must be >= 0");
-    if (autocorr && !power) return fail(EPIC_EINVAL, "autocorr needs the power accumulator");
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
+    if (!volt) return epic_fail(EPIC_EINVAL, "volt is NULL");
+    if (!accum) return epic_fail(EPIC_EINVAL, "accum is NULL");
+    if (t_prev < 0) return epic_fail(EPIC_EINVAL, "t_prev must be >= 0");
+    if (autocorr && !power) return epic_fail(EPIC_EINVAL, "autocorr needs the power accumulator");
     if (autocorr && plan->lag_side == 0)
-        return fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
+        return epic_fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
     if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
-        return fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
-    DeviceGuard guard(plan->device);
-    if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+        return epic_fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int cp = plan->n_chan * plan->n_pol;
     const size_t npix = (size_t)cp * plan->n_pad * plan->n_pad;
     cudaError_t e;
     if (t_prev == 0) {
-        if ((e = cudaMemsetAsync(accum, 0, npix * sizeof(double), st)) != cudaSuccess) return cuda_fail(e, "memset accum");
+        if ((e = cudaMemsetAsync(accum, 0, npix * sizeof(double), st)) != cudaSuccess) return epic_cuda_fail(e, "memset accum");
         if (power && (e = cudaMemsetAsync(power, 0, (size_t)cp * plan->n_ant * sizeof(double), st)) != cudaSuccess)
-            return cuda_fail(e, "memset power");
+            return epic_cuda_fail(e, "memset power");
     }
-    epic::FwdArgs a;
-    a.volt = volt;
-    a.n_time = n_time;
-    a.n_cp = cp;
-    a.n_ant = plan->n_ant;
-    a.gains = reinterpret_cast<const float2*>(gains);
-    a.cell_ptr = plan->cell_ptr;
-    a.cell_ent = plan->cell_ent;
-    a.cell_wim = plan->cell_wim;
-    a.twiddle = plan->twiddle;
-    a.accum = accum;
-    a.power = power;
-    a.n_items = (long long)cp * n_time;
-    a.flush_every = 1024;
-    a.wsum_max = plan->wsum_max;
+    const epic::FwdArgs a =
+        epic_plan_fwd_args(plan, volt, n_time, reinterpret_cast<const float2*>(gains), accum, power);
     epic_status s;
     if (plan->xform == EPIC_XFORM_DFTGEMM) {
         e = epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, plan->n_sm, st);
-        s = e == cudaSuccess ? EPIC_OK : cuda_fail(e, "tensor-core imaging kernel launch");
+        s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core imaging kernel launch");
     } else {
         s = launch_fwd(plan, a, st);
     }
     if (s != EPIC_OK) return s;
     const double inv_t = 1.0 / double(t_prev + n_time);
     if (image && (e = epic::launch_finalize_image(accum, image, (long long)npix, inv_t, st)) != cudaSuccess)
-        return cuda_fail(e, "image epilogue");
+        return epic_cuda_fail(e, "image epilogue");
     if (autocorr && (e = epic::launch_autocorr(power, plan->lag_tab, cp, plan->n_ant, plan->lag_side, plan->n_pad,
                                                inv_t, autocorr, st)) != cudaSuccess)
-        return cuda_fail(e, "auto-correlation epilogue");
+        return epic_cuda_fail(e, "auto-correlation epilogue");
     return EPIC_OK;
 }
 
 epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_time, const float* gains,
                                 const float* grad_image, float* grad_gains, void* stream) {
-    g_err.clear();
-    if (!plan) return fail(EPIC_EINVAL, "plan is NULL");
-    if (n_time < 1) return fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
-    if (!volt || !grad_image || !grad_gains) return fail(EPIC_EINVAL, "NULL device array");
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
+    if (!volt || !grad_image || !grad_gains) return epic_fail(EPIC_EINVAL, "NULL device array");
     if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
-        return fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
-    DeviceGuard guard(plan->device);
-    if (!guard.ok) return fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+        return epic_fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int cp = plan->n_chan * plan->n_pol;
     cudaError_t e = cudaMemsetAsync(grad_gains, 0, (size_t)cp * plan->n_ant * 2 * sizeof(float), st);
-    if (e != cudaSuccess) return cuda_fail(e, "memset grad_gains");
+    if (e != cudaSuccess) return epic_cuda_fail(e, "memset grad_gains");
     epic::BwdArgs a;
     a.volt = volt;
     a.n_time = n_time;

@@ -1,0 +1,255 @@
+// Batched imaging of many (heterogeneous) sub-arrays: one persistent launch per padded-size
+// class, the classes forked onto internal streams and joined back into the caller's stream.
+// The EPIC software stacks data streams of several arrays for array operations (App. A.3);
+// here the stacking is a list of sub-array segments walked by one kernel.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/epic.h"
+#include "epic_internal.h"
+#include "epic_plan.h"
+
+namespace {
+
+struct ClassRun {
+    int n_pad = 0;
+    std::vector<int> members;      // plan indices (at most epic::kMaxSeg)
+    cudaStream_t stream = nullptr;
+    cudaEvent_t join = nullptr;
+    int max_workers = 0;           // 0 = every resident CTA (cluster)
+};
+
+}  // namespace
+
+struct epic_batch {
+    std::vector<epic_plan*> plans;
+    std::vector<ClassRun> classes;
+    int device = 0, vdt = 0, n_sm = 0;
+    bool concurrent = true;        // classes on forked streams (else back to back)
+    cudaEvent_t fork = nullptr;
+};
+
+namespace {
+
+void destroy_batch(epic_batch* b) {
+    if (!b) return;
+    for (ClassRun& c : b->classes) {
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.join) cudaEventDestroy(c.join);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+epic_status check_call(const epic_batch* b, const void* const* volt, const int* n_time, double* const* accum) {
+    if (!b) return epic_fail(EPIC_EINVAL, "batch is NULL");
+    if (!volt || !n_time || !accum) return epic_fail(EPIC_EINVAL, "NULL argument array");
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        if (!volt[i] || !accum[i]) return epic_fail(EPIC_EINVAL, "NULL device array for plan %zu", i);
+        if (n_time[i] < 1) return epic_fail(EPIC_EINVAL, "n_time[%zu] = %d must be >= 1", i, n_time[i]);
+        const long long items = (long long)b->plans[i]->n_chan * b->plans[i]->n_pol * n_time[i];
+        if (items > 2147483647LL) return epic_fail(EPIC_EUNSUPPORTED, "plan %zu: C * P * T must stay below 2^31", i);
+    }
+    for (const ClassRun& c : b->classes) {
+        long long tot = 0;
+        for (int i : c.members)
+            tot += (long long)b->plans[i]->n_chan * b->plans[i]->n_pol * n_time[i];
+        if (tot > 2147483647LL) return epic_fail(EPIC_EUNSUPPORTED, "a size class exceeds 2^31 items per call");
+    }
+    return EPIC_OK;
+}
+
+// Enqueue one class on stream st: zero its accumulators, one persistent launch, epilogues.
+epic_status run_class(const epic_batch* b, const ClassRun& c, const void* const* volt, const int* n_time,
+                      const float* const* gains, double* const* accum, float* const* image, cudaStream_t st,
+                      int max_workers) {
+    epic::SegList L;
+    L.n_seg = (int)c.members.size();
+    L.max_ant = 0;
+    L.max_workers = max_workers;
+    L.first[0] = 0;
+    for (int s = 0; s < L.n_seg; ++s) {
+        const int i = c.members[s];
+        const epic_plan* p = b->plans[i];
+        const int cp = p->n_chan * p->n_pol;
+        cudaError_t e = cudaMemsetAsync(accum[i], 0, (size_t)cp * p->n_pad * p->n_pad * sizeof(double), st);
+        if (e != cudaSuccess) return epic_cuda_fail(e, "memset accum");
+        epic::FwdArgs& a = L.seg[s];
+        a = epic_plan_fwd_args(p, volt[i], n_time[i], gains ? reinterpret_cast<const float2*>(gains[i]) : nullptr,
+                               accum[i], nullptr);
+        L.first[s + 1] = L.first[s] + (int)a.n_items;
+        L.max_ant = std::max(L.max_ant, p->n_ant);
+    }
+    cudaError_t e = epic_launch_fwd_list(c.n_pad, b->vdt, L, b->n_sm, st);
+    if (e != cudaSuccess) return epic_cuda_fail(e, "batched imaging kernel launch");
+    if (image) {
+        for (int i : c.members) {
+            if (!image[i]) continue;
+            const epic_plan* p = b->plans[i];
+            const long long n = (long long)p->n_chan * p->n_pol * p->n_pad * p->n_pad;
+            e = epic::launch_finalize_image(accum[i], image[i], n, 1.0 / n_time[i], st);
+            if (e != cudaSuccess) return epic_cuda_fail(e, "image epilogue");
+        }
+    }
+    return EPIC_OK;
+}
+
+epic_status enqueue(epic_batch* b, const void* const* volt, const int* n_time, const float* const* gains,
+                    double* const* accum, float* const* image, cudaStream_t st) {
+    if (!b->concurrent) {
+        for (const ClassRun& c : b->classes) {
+            epic_status s = run_class(b, c, volt, n_time, gains, accum, image, st, c.max_workers);
+            if (s != EPIC_OK) return s;
+        }
+        return EPIC_OK;
+    }
+    cudaError_t e = cudaEventRecord(b->fork, st);
+    if (e != cudaSuccess) return epic_cuda_fail(e, "fork event");
+    for (ClassRun& c : b->classes) {
+        if ((e = cudaStreamWaitEvent(c.stream, b->fork, 0)) != cudaSuccess) return epic_cuda_fail(e, "fork wait");
+        epic_status s = run_class(b, c, volt, n_time, gains, accum, image, c.stream, c.max_workers);
+        if (s != EPIC_OK) return s;
+        if ((e = cudaEventRecord(c.join, c.stream)) != cudaSuccess) return epic_cuda_fail(e, "join event");
+        if ((e = cudaStreamWaitEvent(st, c.join, 0)) != cudaSuccess) return epic_cuda_fail(e, "join wait");
+    }
+    return EPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+epic_status epic_batch_create(epic_batch** batch, int n_plans, epic_plan* const* plans) {
+    epic_clear_error();
+    if (!batch) return epic_fail(EPIC_EINVAL, "batch out-pointer is NULL");
+    *batch = nullptr;
+    if (n_plans < 1 || !plans) return epic_fail(EPIC_EINVAL, "need at least one plan");
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i]) return epic_fail(EPIC_EINVAL, "plan %d is NULL", i);
+        if (plans[i]->device != plans[0]->device || plans[i]->vdt != plans[0]->vdt)
+            return epic_fail(EPIC_EINVAL, "plan %d: all plans of a batch share the device and voltage format", i);
+    }
+    epic_batch* b = new epic_batch;
+    b->plans.assign(plans, plans + n_plans);
+    b->device = plans[0]->device;
+    b->vdt = plans[0]->vdt;
+    b->n_sm = plans[0]->n_sm;
+    for (int np : {512, 256, 128, 64, 32}) {
+        std::vector<int> m;
+        for (int i = 0; i < n_plans; ++i)
+            if (plans[i]->n_pad == np) m.push_back(i);
+        for (size_t o = 0; o < m.size(); o += epic::kMaxSeg) {
+            ClassRun c;
+            c.n_pad = np;
+            c.members.assign(m.begin() + o, m.begin() + std::min(m.size(), o + (size_t)epic::kMaxSeg));
+            b->classes.push_back(c);
+        }
+    }
+    EpicDeviceGuard guard(b->device);
+    cudaError_t e = guard.ok ? cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) : cudaErrorInvalidDevice;
+    for (ClassRun& c : b->classes) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        destroy_batch(b);
+        return epic_cuda_fail(e, "batch streams");
+    }
+    *batch = b;
+    return EPIC_OK;
+}
+
+void epic_batch_destroy(epic_batch* batch) {
+    if (!batch) return;
+    EpicDeviceGuard guard(batch->device);
+    destroy_batch(batch);
+}
+
+epic_status epic_batch_image(epic_batch* batch, const void* const* volt, const int* n_time, const float* const* gains,
+                             double* const* accum, float* const* image, void* stream) {
+    epic_clear_error();
+    epic_status s = check_call(batch, volt, n_time, accum);
+    if (s != EPIC_OK) return s;
+    EpicDeviceGuard guard(batch->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", batch->device);
+    return enqueue(batch, volt, n_time, gains, accum, image, static_cast<cudaStream_t>(stream));
+}
+
+epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, const int* n_time,
+                                const float* const* gains, double* const* accum, void* stream) {
+    epic_clear_error();
+    epic_status s = check_call(batch, volt, n_time, accum);
+    if (s != EPIC_OK) return s;
+    EpicDeviceGuard guard(batch->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", batch->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return epic_cuda_fail(e, "autotune events");
+    auto time_it = [&](auto&& body, float& ms) -> epic_status {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            epic_status r = body();
+            if (r != EPIC_OK) return r;
+            cudaEventRecord(e1, st);
+            cudaError_t err = cudaEventSynchronize(e1);
+            if (err != cudaSuccess) return epic_cuda_fail(err, "autotune run");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, t);
+        }
+        ms = best;
+        return EPIC_OK;
+    };
+    // 1) per class: the worker count (all resident, 3/4, 1/2 of them) that runs it fastest alone
+    std::vector<float> alone(batch->classes.size(), 0.f);
+    for (size_t k = 0; k < batch->classes.size() && s == EPIC_OK; ++k) {
+        ClassRun& c = batch->classes[k];
+        const int full = epic_resident_workers(c.n_pad, batch->vdt, batch->plans, c.members, batch->n_sm);
+        int best_w = 0;
+        float best_t = 1e30f;
+        for (int frac4 : {4, 3, 2}) {
+            const int w = frac4 == 4 ? 0 : std::max(1, full * frac4 / 4);
+            float t = 0.f;
+            s = time_it([&] { return run_class(batch, c, volt, n_time, gains, accum, nullptr, st, w); }, t);
+            if (s != EPIC_OK) break;
+            if (t < best_t) {
+                best_t = t;
+                best_w = w;
+            }
+        }
+        c.max_workers = best_w;
+        alone[k] = best_t;
+    }
+    // 2) classes back to back vs concurrently (forked streams)
+    if (s == EPIC_OK && batch->classes.size() > 1) {
+        float t_seq = 0.f, t_con = 0.f;
+        batch->concurrent = false;
+        s = time_it([&] { return enqueue(batch, volt, n_time, gains, accum, nullptr, st); }, t_seq);
+        if (s == EPIC_OK) {
+            batch->concurrent = true;
+            s = time_it([&] { return enqueue(batch, volt, n_time, gains, accum, nullptr, st); }, t_con);
+        }
+        if (s == EPIC_OK) batch->concurrent = t_con < t_seq;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}
+
+epic_status epic_batch_info(const epic_batch* batch, int* n_classes, int* concurrent, int* workers, int max_workers) {
+    epic_clear_error();
+    if (!batch) return epic_fail(EPIC_EINVAL, "batch is NULL");
+    if (n_classes) *n_classes = (int)batch->classes.size();
+    if (concurrent) *concurrent = batch->concurrent ? 1 : 0;
+    if (workers)
+        for (int k = 0; k < (int)batch->classes.size() && k < max_workers; ++k) workers[k] = batch->classes[k].max_workers;
+    return EPIC_OK;
+}
+
+}  // extern "C"

@@ -63,6 +63,10 @@ cudaError_t launch_bwd_128(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st)
 cudaError_t launch_bwd_256(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_512(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 
+// CTAs (Q = 1) or clusters (Q > 1) of the forward kernel resident on the whole GPU.
+int resident_fwd_workers(int n_pad, int vdt, int max_ant, int n_sm);
+template <int NP, int VDT> int resident_fwd_workers_t(int max_ant, int n_sm);
+
 // Shared-memory bytes the forward / backward kernels need for a given size and antenna count.
 size_t fwd_smem_bytes(int n_pad, int n_ant);
 size_t bwd_smem_bytes(int n_pad, int n_ant);

@@ -1,0 +1,52 @@
+// The plan object and host helpers shared by the C ABI translation units.
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/epic.h"
+#include "epic_internal.h"
+
+struct epic_plan {
+    int n_ant = 0, n_grid = 0, n_pad = 0, n_chan = 0, n_pol = 0, vdt = 0, device = 0, n_sm = 0;
+    int lag_side = 0;
+    int64_t nnz = 0, n_cells = 0;
+    int* cell_ptr = nullptr;
+    int2* cell_ent = nullptr;
+    float* cell_wim = nullptr;   // nullptr when every weight is real
+    int* ant_ptr = nullptr;
+    int2* ant_ent = nullptr;
+    float* ant_wim = nullptr;
+    float2* twiddle = nullptr;
+    float2* lag_tab = nullptr;
+    int xform = EPIC_XFORM_FFT;
+    uint16_t* dg_tab = nullptr;   // DFT operand tables of the tensor-core form
+    float wsum_max = 0.f;         // max over cells of sum_a |M[g, a]|
+};
+
+// Thread-local error message of the C ABI.
+void epic_clear_error();
+epic_status epic_fail(epic_status st, const char* fmt, ...);
+epic_status epic_cuda_fail(cudaError_t e, const char* what);
+
+// Selects a device for the scope and restores the caller's current device afterwards.
+struct EpicDeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit EpicDeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~EpicDeviceGuard() {
+        if (ok && prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Forward-kernel arguments of one plan for one call (power may be nullptr).
+epic::FwdArgs epic_plan_fwd_args(const epic_plan* p, const void* volt, int n_time, const float2* gains,
+                                 double* accum, double* power);
+// One persistent forward launch over a list of sub-arrays of padded size n_pad.
+cudaError_t epic_launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st);
+// CTAs (or clusters) of the forward kernel of a size class resident on the whole GPU.
+int epic_resident_workers(int n_pad, int vdt, const std::vector<epic_plan*>& plans, const std::vector<int>& members,
+                          int n_sm);

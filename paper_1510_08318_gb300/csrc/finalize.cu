@@ -99,10 +99,27 @@ size_t autocorr_smem_bytes(int lag_side, int n_pad, int n_ant) {
 cudaError_t launch_autocorr(const double* power, const float2* lag_tab, int n_cp, int n_ant,
                             int lag_side, int n_pad, double inv_t, float* out, cudaStream_t st) {
     const size_t smem = autocorr_smem_bytes(lag_side, n_pad, n_ant);
-    cudaError_t e = cudaFuncSetAttribute(autocorr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem<autocorr_kernel>(smem);
     if (e != cudaSuccess) return e;
     autocorr_kernel<<<n_cp, kAcThreads, smem, st>>>(power, lag_tab, n_ant, lag_side, n_pad, inv_t, out);
     return cudaGetLastError();
+}
+
+int resident_fwd_workers_32(int vdt, int max_ant, int n_sm);
+int resident_fwd_workers_64(int vdt, int max_ant, int n_sm);
+int resident_fwd_workers_128(int vdt, int max_ant, int n_sm);
+int resident_fwd_workers_256(int vdt, int max_ant, int n_sm);
+int resident_fwd_workers_512(int vdt, int max_ant, int n_sm);
+
+int resident_fwd_workers(int n_pad, int vdt, int max_ant, int n_sm) {
+    switch (n_pad) {
+        case 32: return resident_fwd_workers_32(vdt, max_ant, n_sm);
+        case 64: return resident_fwd_workers_64(vdt, max_ant, n_sm);
+        case 128: return resident_fwd_workers_128(vdt, max_ant, n_sm);
+        case 256: return resident_fwd_workers_256(vdt, max_ant, n_sm);
+        case 512: return resident_fwd_workers_512(vdt, max_ant, n_sm);
+        default: return 0;
+    }
 }
 
 size_t fwd_smem_bytes(int n_pad, int n_ant) {

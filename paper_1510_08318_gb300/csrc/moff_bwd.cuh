@@ -277,7 +277,7 @@ cudaError_t launch_bwd_t(const BwdArgs& a, int n_sm, cudaStream_t st) {
     using G = Geo<NP>;
     auto kern = moff_bwd_kernel<NP, VDT>;
     const size_t smem = BwdLayout<NP>::smem_bytes(a.n_ant);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem<moff_bwd_kernel<NP, VDT>>(smem);
     if (e != cudaSuccess) return e;
     if (a.n_items == 0) return cudaSuccess;
     if constexpr (G::Q == 1) {

@@ -103,6 +103,21 @@ __device__ __forceinline__ void block_or_cluster_sync() {
     }
 }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more than was set
+// before on the current device, so that steady-state launches make no attribute calls.
+// KEY is the kernel itself (one cache per kernel, not per kernel type).
+template <auto KEY>
+cudaError_t ensure_smem(size_t bytes) {
+    static size_t done[16] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 16 && done[dev] >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(KEY, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 16) done[dev] = bytes;
+    return e;
+}
+
 // Contiguous share [beg, end) of n items for worker w of nw.
 __device__ __forceinline__ void work_range(long long n, int w, int nw, long long& beg, long long& end) {
     const long long per = n / nw, rem = n % nw;

@@ -416,7 +416,7 @@ cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm
     switch (vdt) {
 #define EPIC_DG_CASE(V)                                                                                      \
     case V:                                                                                                  \
-        e = cudaFuncSetAttribute(dg::moff_dftgemm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        e = ensure_smem<dg::moff_dftgemm_kernel<V>>(smem);                                              \
         if (e != cudaSuccess) return e;                                                                      \
         if (grid > 0) dg::moff_dftgemm_kernel<V><<<(unsigned)grid, dg::NT, smem, st>>>(a, w);                \
         return cudaGetLastError();

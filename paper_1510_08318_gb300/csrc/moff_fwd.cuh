@@ -247,7 +247,7 @@ cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
     using G = Geo<NP>;
     auto kern = moff_fwd_kernel<NP, VDT>;
     const size_t smem = G::smem_bytes(L.max_ant);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem<moff_fwd_kernel<NP, VDT>>(smem);
     if (e != cudaSuccess) return e;
     const long long n_items = L.first[L.n_seg];
     if (n_items == 0) return cudaSuccess;
@@ -289,6 +289,35 @@ cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
         e = cudaLaunchKernelEx(&cfg, kern, L);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
+    }
+}
+
+template <int NP, int VDT>
+int resident_fwd_workers_t(int max_ant, int n_sm) {
+    using G = Geo<NP>;
+    auto kern = moff_fwd_kernel<NP, VDT>;
+    const size_t smem = G::smem_bytes(max_ant);
+    if (ensure_smem<moff_fwd_kernel<NP, VDT>>(smem) != cudaSuccess) return 0;
+    if constexpr (G::Q == 1) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem) != cudaSuccess) return 0;
+        return per_sm * n_sm;
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = G::Q;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(G::NT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(G::Q * n_sm);
+        if constexpr (G::Q > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        int n_cl = 0;
+        if (cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg) != cudaSuccess) return 0;
+        return n_cl;
     }
 }
 

@@ -22,4 +22,13 @@ cudaError_t launch_bwd_64(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st) 
     }
 }
 
+int resident_fwd_workers_64(int vdt, int max_ant, int n_sm) {
+    switch (vdt) {
+        case 0: return resident_fwd_workers_t<64, 0>(max_ant, n_sm);
+        case 1: return resident_fwd_workers_t<64, 1>(max_ant, n_sm);
+        case 2: return resident_fwd_workers_t<64, 2>(max_ant, n_sm);
+        default: return 0;
+    }
+}
+
 }  // namespace epic

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libepic.so")
 EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
-           "epic_last_error", "epic_set_transform")
+           "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
+           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy")
 XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
@@ -53,6 +54,17 @@ def load(path=LIB_PATH):
     lib.epic_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
     lib.epic_set_transform.restype = i32
     lib.epic_set_transform.argtypes = [vp, i32]
+    pp = ctypes.POINTER(vp)
+    lib.epic_batch_create.restype = i32
+    lib.epic_batch_create.argtypes = [pp, i32, pp]
+    lib.epic_batch_image.restype = i32
+    lib.epic_batch_image.argtypes = [vp, pp, ctypes.POINTER(i32), pp, pp, pp, vp]
+    lib.epic_batch_autotune.restype = i32
+    lib.epic_batch_autotune.argtypes = [vp, pp, ctypes.POINTER(i32), pp, pp, vp]
+    lib.epic_batch_info.restype = i32
+    lib.epic_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i32]
+    lib.epic_batch_destroy.restype = None
+    lib.epic_batch_destroy.argtypes = [vp]
     lib.epic_last_error.restype = ctypes.c_char_p
     lib.epic_last_error.argtypes = []
     _lib = lib
@@ -69,9 +81,9 @@ def _check(status):
 
 
 def _ptr(x):
-    """Device or host address of a torch tensor / numpy array, or None."""
-    if x is None:
-        return None
+    """Device or host address of a torch tensor / numpy array (an int passes through), or None."""
+    if x is None or isinstance(x, int):
+        return x
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     return x.data_ptr()
@@ -112,6 +124,42 @@ def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, strea
 
 def epic_set_transform(plan, xform):
     _check(load().epic_set_transform(plan, int(xform)))
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+
+
+def epic_batch_create(plans):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    _check(load().epic_batch_create(ctypes.byref(h), len(plans), arr))
+    return h
+
+
+def epic_batch_image(batch, volt, n_time, gains, accum, image, stream):
+    n = len(volt)
+    nt = (ctypes.c_int * n)(*[int(t) for t in n_time])
+    _check(load().epic_batch_image(batch, _ptr_array(volt), nt, None if gains is None else _ptr_array(gains),
+                                   _ptr_array(accum), None if image is None else _ptr_array(image), stream))
+
+
+def epic_batch_autotune(batch, volt, n_time, gains, accum, stream):
+    n = len(volt)
+    nt = (ctypes.c_int * n)(*[int(t) for t in n_time])
+    _check(load().epic_batch_autotune(batch, _ptr_array(volt), nt, None if gains is None else _ptr_array(gains),
+                                      _ptr_array(accum), stream))
+
+
+def epic_batch_info(batch, max_classes=16):
+    nc, conc = ctypes.c_int(), ctypes.c_int()
+    w = (ctypes.c_int * max_classes)()
+    _check(load().epic_batch_info(batch, ctypes.byref(nc), ctypes.byref(conc), w, max_classes))
+    return {"n_classes": nc.value, "concurrent": bool(conc.value), "workers": list(w)[:nc.value]}
+
+
+def epic_batch_destroy(batch):
+    load().epic_batch_destroy(batch)
 
 
 def epic_plan_info(plan):
@@ -213,6 +261,60 @@ class Plan:
         epic_image_backward(self._h, vptr, T, self._gains_ptr(gains), g.data_ptr(), out.data_ptr(),
                             st.cuda_stream)
         return out
+
+
+class Batch:
+    """Many plans imaged by one launch per padded-size class (epic_batch_*)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self._h = epic_batch_create([p._h for p in self.plans])
+
+    def _bufs(self, volts):
+        import torch
+        ptrs, nts = [], []
+        for p, v in zip(self.plans, volts):
+            ptr, T = p._volt_ptr(v)
+            ptrs.append(ptr)
+            nts.append(T)
+        return ptrs, nts
+
+    def alloc(self):
+        import torch
+        acc = [torch.empty((p.n_chan, p.n_pol, p.n_pad, p.n_pad), dtype=torch.float64,
+                           device=torch.device("cuda", p.device)) for p in self.plans]
+        img = [torch.empty((p.n_chan, p.n_pol, p.n_pad, p.n_pad), dtype=torch.float32,
+                           device=torch.device("cuda", p.device)) for p in self.plans]
+        return acc, img
+
+    def image(self, volts, accum, image=None, gains=None, stream=None):
+        import torch
+        ptrs, nts = self._bufs(volts)
+        st = torch.cuda.current_stream(torch.device("cuda", self.plans[0].device)) if stream is None else stream
+        g = None if gains is None else [None if x is None else self.plans[i]._gains_ptr(x) for i, x in enumerate(gains)]
+        epic_batch_image(self._h, ptrs, nts, g, accum, image, st.cuda_stream)
+
+    def autotune(self, volts, accum, gains=None, stream=None):
+        import torch
+        ptrs, nts = self._bufs(volts)
+        st = torch.cuda.current_stream(torch.device("cuda", self.plans[0].device)) if stream is None else stream
+        g = None if gains is None else [None if x is None else self.plans[i]._gains_ptr(x) for i, x in enumerate(gains)]
+        epic_batch_autotune(self._h, ptrs, nts, g, accum, st.cuda_stream)
+        return epic_batch_info(self._h)
+
+    def info(self):
+        return epic_batch_info(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            epic_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd_function():

@@ -360,3 +360,50 @@ def workload_calib(seed=5, n_chan=32, n_time=64, n_ant=1024):
     wl.extra["sky"] = sky
     wl.extra["g_true"] = g_true
     return _finish(wl, v, "c64")
+
+
+def workload_batch(seed=4, n_sub=64, n_time=128, max_chan=None, max_ant=None, n_src=20):
+    """Heterogeneous sub-arrays: antenna counts log-uniform in [32, 2048], positions uniform in
+    disks of diameter U(30, 300) m, padded grids N_p uniform over {32, 64, 128, 256, 512}
+    (N_g = N_p / 2, spacing (D_array + 21 m) / (N_g - 1) so the array plus the widest aperture
+    reach, 10.5 m, fits the grid), channel counts log-uniform in [8, 256] over
+    50-200 MHz, FP16 voltages (n_src sources + unit noise).  Every antenna draws its own
+    aperture: a square, a Gaussian (sigma = D / 4, 3 sigma support) or a uniform disk, of size
+    D ~ U(1, 14) m, sampled on a lattice of step max(dx / 2, D / 64).
+
+    max_chan / max_ant (optional) cap the channel and antenna draws (the layouts keep their
+    distributions otherwise) so reduced instances stay cheap to generate and check."""
+    rng = np.random.default_rng(seed)
+    subs = []
+    for s in range(n_sub):
+        n_ant = int(round(math.exp(rng.uniform(math.log(32), math.log(2048)))))
+        if max_ant is not None:
+            n_ant = min(n_ant, max_ant)
+        diam = rng.uniform(30.0, 300.0)
+        n_pad = int(rng.choice([32, 64, 128, 256, 512]))
+        n_chan = int(round(math.exp(rng.uniform(math.log(8), math.log(256)))))
+        if max_chan is not None:
+            n_chan = min(n_chan, max_chan)
+        n_grid = n_pad // 2
+        dx = (diam + 21.0) / (n_grid - 1)
+        pos = layout_disk(rng, n_ant, diam)
+        kerns = []
+        for _ in range(n_ant):
+            size = rng.uniform(1.0, 14.0)
+            kind = rng.integers(0, 3)
+            if kind == 0:
+                kerns.append(kernel_square(size, max(dx / 2, size / 64)))
+            elif kind == 1:
+                kerns.append(kernel_gaussian(size / 4, max(dx / 2, size / 64)))
+            else:
+                kerns.append(kernel_disk(size, max(dx / 2, size / 64)))
+        ptr, dxdy, w = pack_kernels(kerns)
+        reach = np.abs(dxdy).max() if dxdy.size else 0.0
+        origin = centred_origin(pos, reach, dx, n_grid)
+        freqs = np.linspace(50e6, 200e6, n_chan)
+        sky = sky_box(rng, n_src, 0.7, 1.0, 10.0)
+        v = voltages(rng, pos, freqs, n_time, 1, sky, 1.0)
+        wl = Workload("sub-array %d: %d ant, %d chan, T=%d, %dx%d image, f16" % (s, n_ant, n_chan, n_time, n_pad, n_pad),
+                      pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, freqs, 1, n_time, "f16")
+        subs.append(_finish(wl, v, "f16"))
+    return subs
