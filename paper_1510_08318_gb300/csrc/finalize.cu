@@ -9,6 +9,7 @@
 //                    a dense mat-vec over the small L x L lag window, then a separable sum
 //                    onto the N_p x N_p pixels (U is Hermitian, so A is real).
 #include "moff_common.cuh"
+#include "moff_bwd.cuh"
 
 namespace epic {
 
@@ -134,8 +135,14 @@ size_t fwd_smem_bytes(int n_pad, int n_ant) {
 }
 
 size_t bwd_smem_bytes(int n_pad, int n_ant) {
-    const size_t fixed_f = fwd_smem_bytes(n_pad, 0);
-    return fixed_f == 0 ? 0 : fixed_f + size_t(n_ant) * 4 * sizeof(float2);
+    switch (n_pad) {
+        case 32: return BwdLayout<32>::smem_bytes(n_ant);
+        case 64: return BwdLayout<64>::smem_bytes(n_ant);
+        case 128: return BwdLayout<128>::smem_bytes(n_ant);
+        case 256: return BwdLayout<256>::smem_bytes(n_ant);
+        case 512: return BwdLayout<512>::smem_bytes(n_ant);
+        default: return 0;
+    }
 }
 
 int grid_rows_per_block(int n_pad) {

@@ -23,7 +23,7 @@ struct BwdLayout {
     static constexpr int IBS = NP + 1;   // row stride of the column-pass output, [ROWS][IBS]
     static_assert(G::ROWS * IBS <= G::NG * G::RBS, "inverse buffer must fit in the row-pass buffer");
     static constexpr size_t smem_bytes(int n_ant) {
-        return sizeof(float2) * (size_t(G::ROWS) * G::RXS + size_t(G::NG) * G::RBS + NP)
+        return sizeof(float2) * (size_t(G::ROWS) * G::RXS + size_t(G::NG) * G::RBS + G::TWN)
              + size_t(n_ant) * 4 * sizeof(float2);
     }
 };
@@ -39,8 +39,8 @@ moff_bwd_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* RX = reinterpret_cast<float2*>(smem_raw);        // [ROWS][RXS] exchange, then Q_t rows
     float2* RB = RX + G::ROWS * G::RXS;                      // [NG][RBS] row output; then [ROWS][IBS]
-    float2* TW = RB + NG * G::RBS;                           // [R1][S] exp(+2 pi i n1 k2 / NP)
-    float2* VB = TW + NP;                                    // [A] g_a V_a
+    float2* TW = RB + NG * G::RBS;                           // [S][TWS] exp(+2 pi i n1 k2 / NP)
+    float2* VB = TW + G::TWN;                                    // [A] g_a V_a
     float2* VR = VB + a.n_ant;                               // [A] V_a
     float2* GN = VR + a.n_ant;                               // [A] gains
     float2* GA = GN + a.n_ant;                               // [A] partial gradient sums
@@ -57,7 +57,7 @@ moff_bwd_kernel(const BwdArgs a) {
     }
     const int y = rank * G::ROWS + r;
 
-    for (int i = tid; i < NP; i += NT) TW[i] = a.twiddle[((i % S) * (i / S)) & (NP - 1)];
+    G::load_twiddles(TW, a.twiddle, tid, NT);
     for (int aa = tid; aa < a.n_ant; aa += NT) GA[aa] = make_float2(0.f, 0.f);
 
     long long beg_l, end_l;
@@ -140,9 +140,7 @@ moff_bwd_kernel(const BwdArgs a) {
             float2 Y[R1];
             dft_halfzero_in<R1, +1>(x, Y);
             float2* rx = RX + r * G::RXS;
-#pragma unroll
-            for (int k2 = 0; k2 < R1; ++k2)
-                rx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
+            G::twiddle_store(rx, Y, TW, n1);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
@@ -181,9 +179,7 @@ moff_bwd_kernel(const BwdArgs a) {
             float2 Y[R1];
             dft_halfzero_in<R1, +1>(xc[s], Y);
             float2* cx = RX + (warp * G::LPC + cc) * G::RXS;
-#pragma unroll
-            for (int k2 = 0; k2 < R1; ++k2)
-                cx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
+            G::twiddle_store(cx, Y, TW, n1);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
@@ -202,11 +198,7 @@ moff_bwd_kernel(const BwdArgs a) {
                 for (int m = 0; m < S; ++m) cx[k2 * S + (m ^ n1)] = z[m];
             }
             __syncwarp();
-#pragma unroll
-            for (int k2 = 0; k2 < R1; ++k2) {
-                const float2 v = cx[k2 * S + (n1 ^ G::swz(k2))];
-                Y[k2] = (k2 == 0) ? v : cmulc(v, TW[k2 * S + n1]);
-            }
+            G::twiddle_load_conj(cx, Y, TW, n1);
             float2 xo[NI];
             dft_halfzero_out<R1, -1>(Y, xo);
 #pragma unroll
@@ -238,11 +230,7 @@ moff_bwd_kernel(const BwdArgs a) {
             }
             __syncwarp();
             float2 Y[R1];
-#pragma unroll
-            for (int k2 = 0; k2 < R1; ++k2) {
-                const float2 v = rx[k2 * S + (n1 ^ G::swz(k2))];
-                Y[k2] = (k2 == 0) ? v : cmulc(v, TW[k2 * S + n1]);
-            }
+            G::twiddle_load_conj(rx, Y, TW, n1);
             float2 xo[NI];
             dft_halfzero_out<R1, -1>(Y, xo);
             __syncwarp();

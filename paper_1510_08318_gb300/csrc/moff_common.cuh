@@ -54,11 +54,50 @@ template <int NP> struct Geo {
         }
     }
 
+    static constexpr int TWS = R1 + 2;         // twiddle row stride: [S][TWS], exp(+2 pi i n1 k2 / NP)
+    static constexpr int TWN = S * TWS;        // twiddle table entries
+    static_assert((ROWS * RXS + NG * RBS) % 2 == 0, "twiddle table must stay 16-byte aligned");
+
     static constexpr size_t smem_bytes(int n_ant) {
-        return sizeof(float2) * (size_t(ROWS) * RXS + size_t(NG) * RBS + NP)
+        return sizeof(float2) * (size_t(ROWS) * RXS + size_t(NG) * RBS + TWN)
              + size_t(n_ant) * (2 * sizeof(float2) + sizeof(float));
     }
+
+    // Fill the twiddle table from the plan's exp(+2 pi i j / NP) table.
+    static __device__ __forceinline__ void load_twiddles(float2* TW, const float2* tw, int tid, int nt) {
+        for (int i = tid; i < TWN; i += nt) {
+            const int n1 = i / TWS, k2 = i % TWS;
+            TW[i] = k2 < R1 ? tw[(n1 * k2) & (NP - 1)] : make_float2(0.f, 0.f);
+        }
+    }
+
+    // Second stage of the first sub-transform: Y[k2] * exp(+2 pi i n1 k2 / NP), written to the
+    // exchange row `dst` in swizzled [k2][n1] order.  Twiddles are read two at a time (16 B).
+    static __device__ __forceinline__ void twiddle_store(float2* dst, const float2 (&Y)[R1], const float2* TW, int n1) {
+        const float4* tw4 = reinterpret_cast<const float4*>(TW + n1 * TWS);
+#pragma unroll
+        for (int k2 = 0; k2 < R1; k2 += 2) {
+            const float4 t = tw4[k2 / 2];
+            dst[k2 * S + (n1 ^ swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], make_float2(t.x, t.y));
+            dst[(k2 + 1) * S + (n1 ^ swz(k2 + 1))] = cmul(Y[k2 + 1], make_float2(t.z, t.w));
+        }
+    }
+
+    // Transpose of twiddle_store: read row n1 of the exchange and undo the twiddle.
+    static __device__ __forceinline__ void twiddle_load_conj(const float2* src, float2 (&Y)[R1], const float2* TW, int n1) {
+        const float4* tw4 = reinterpret_cast<const float4*>(TW + n1 * TWS);
+#pragma unroll
+        for (int k2 = 0; k2 < R1; k2 += 2) {
+            const float4 t = tw4[k2 / 2];
+            const float2 v0 = src[k2 * S + (n1 ^ swz(k2))], v1 = src[(k2 + 1) * S + (n1 ^ swz(k2 + 1))];
+            Y[k2] = (k2 == 0) ? v0 : cmulc(v0, make_float2(t.x, t.y));
+            Y[k2 + 1] = cmulc(v1, make_float2(t.z, t.w));
+        }
+    }
 };
+
+// acc += |z|^2 as two fused multiply-adds
+__device__ __forceinline__ void acc_norm(float& acc, float2 z) { acc = fmaf(z.y, z.y, fmaf(z.x, z.x, acc)); }
 
 // ---- raw voltage formats ---------------------------------------------------------------
 template <int VDT> struct Volt;

@@ -36,8 +36,8 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* RX = reinterpret_cast<float2*>(smem_raw);        // [ROWS][RXS] exchange
     float2* RB = RX + G::ROWS * G::RXS;                      // [NG][RBS] row-pass output
-    float2* TW = RB + NG * G::RBS;                           // [R1][S] exp(+2 pi i n1 k2 / NP)
-    float2* VB = TW + NP;                                    // [A] g_a V_a
+    float2* TW = RB + NG * G::RBS;                           // [S][TWS] exp(+2 pi i n1 k2 / NP)
+    float2* VB = TW + G::TWN;                                    // [A] g_a V_a
     float2* GN = VB + L.max_ant;                             // [A] gains
     float* PW = reinterpret_cast<float*>(GN + L.max_ant);    // [A] partial sum |g V|^2
 
@@ -53,7 +53,7 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
     }
     const int y = rank * G::ROWS + r;
 
-    for (int i = tid; i < NP; i += NT) TW[i] = L.seg[0].twiddle[((i % S) * (i / S)) & (NP - 1)];
+    G::load_twiddles(TW, L.seg[0].twiddle, tid, NT);
     for (int aa = tid; aa < L.max_ant; aa += NT) PW[aa] = 0.f;   // owner-thread entries
 
     // global items [0, first[n_seg]) of all sub-arrays, split evenly over the workers
@@ -187,9 +187,7 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
             float2 Y[R1];
             dft_halfzero_in<R1, +1>(x, Y);
             float2* rx = RX + r * G::RXS;
-#pragma unroll
-            for (int k2 = 0; k2 < R1; ++k2)
-                rx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
+            G::twiddle_store(rx, Y, TW, n1);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
@@ -221,9 +219,7 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
             float2 Y[R1];
             dft_halfzero_in<R1, +1>(x, Y);
             float2* cx = RX + (warp * G::LPC + cc) * G::RXS;
-#pragma unroll
-            for (int k2 = 0; k2 < R1; ++k2)
-                cx[k2 * S + (n1 ^ G::swz(k2))] = (k2 == 0) ? Y[0] : cmul(Y[k2], TW[k2 * S + n1]);
+            G::twiddle_store(cx, Y, TW, n1);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
@@ -233,7 +229,7 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
                 for (int m = 0; m < S; ++m) z[m] = cx[k2 * S + (m ^ n1)];
                 dft<S, +1>(z);
 #pragma unroll
-                for (int k1 = 0; k1 < S; ++k1) acc[s][q * S + k1] += cnorm(z[k1]);
+                for (int k1 = 0; k1 < S; ++k1) acc_norm(acc[s][q * S + k1], z[k1]);
             }
             __syncwarp();
         }
