@@ -53,8 +53,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--channels", type=int, default=128,
                    help="image only the first C of the 128 channels (small profiling case)")
-    p.add_argument("--workload", default="lwa", choices=["lwa", "batch"],
-                   help="lwa: the headline workload; batch: 64 heterogeneous sub-arrays, one graph launch")
+    p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib"],
+                   help="lwa: the headline workload; batch: 64 heterogeneous sub-arrays, one graph launch; "
+                        "calib: forward + adjoint of the gain-calibration workload")
     return p.parse_args()
 
 
@@ -237,12 +238,64 @@ def run_batch(args):
         print(json.dumps(line))
 
 
+def run_calib(args):
+    """Gain calibration workload (1024 antennas, 32 channels, 64 samples, N_p = 256, complex64):
+    one step = forward image + adjoint (gradient of the image loss with respect to the gains)."""
+    import numpy as np
+    import torch
+    from paper_1510_08318_gb300 import build, epic, synth
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = synth.workload_calib()
+    plan = epic.Plan.from_workload(wl, device=local)
+    volt = torch.from_numpy(wl.volt_raw).to(dev)
+    g = torch.from_numpy(np.ones((wl.n_chan, 1, wl.n_ant), np.complex64)).to(dev)
+    G = torch.ones((wl.n_chan, 1, wl.n_pad, wl.n_pad), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    cur = torch.cuda.current_stream(dev)
+
+    def fwd():
+        plan.image(volt, g)
+
+    def bwd():
+        plan.image_backward(volt, g, G)
+
+    res = {}
+    for name, fn in (("forward", fwd), ("adjoint", bwd)):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(cur)
+            fn()
+            ev[i][1].record(cur)
+        torch.cuda.synchronize()
+        res[name] = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    units = wl.n_ant * wl.n_time * wl.n_chan * wl.n_pol
+    ms = res["forward"] + res["adjoint"]
+    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "step": "forward image + adjoint w.r.t. gains",
+                       "images_per_step": wl.n_time * wl.n_chan * wl.n_pol,
+                       "l2": "flushed (256 MB write) before every timed call"},
+            "forward_ms": res["forward"], "adjoint_ms": res["adjoint"]}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "calib":
+        return run_calib(args)
     import numpy as np
     import torch
     from paper_1510_08318_gb300 import build, epic, synth

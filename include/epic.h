@@ -42,7 +42,7 @@ typedef enum {
     EPIC_EINVAL = 1,        /* invalid argument (message says which) */
     EPIC_ENOMEM = 2,        /* the plan's device tables could not be allocated */
     EPIC_ECUDA = 3,         /* a CUDA runtime call or launch failed */
-    EPIC_EUNSUPPORTED = 4   /* valid, but outside what this build implements */
+    EPIC_EUNSUPPORTED = 4   /* valid, but outside what this library implements */
 } epic_status;
 
 typedef enum {
