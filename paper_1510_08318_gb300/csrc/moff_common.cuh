@@ -15,11 +15,12 @@ namespace cg = cooperative_groups;
 template <int NP> struct Cfg;
 // S, Q, minimum CTAs per SM, and the shared-memory row strides (in float2) chosen so that
 // every warp-wide exchange access is free of bank conflicts.
-template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8, RXS = 40,  RBS = 34; };
-template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2, RXS = 72,  RBS = 66; };
-template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1, RXS = 136, RBS = 129; };
-template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1, RXS = 264, RBS = 65; };
-template <> struct Cfg<512> { static constexpr int S = 16, Q = 16, MINB = 1, RXS = 520, RBS = 33; };
+// RR: gather the cells round-robin (measured faster for the cluster sizes) or cell by cell.
+template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8, RXS = 40,  RBS = 34; static constexpr bool RR = false; };
+template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2, RXS = 72,  RBS = 66; static constexpr bool RR = false; };
+template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1, RXS = 136, RBS = 129; static constexpr bool RR = false; };
+template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1, RXS = 264, RBS = 65; static constexpr bool RR = true; };
+template <> struct Cfg<512> { static constexpr int S = 16, Q = 16, MINB = 1, RXS = 520, RBS = 33; static constexpr bool RR = true; };
 
 template <int NP> struct Geo {
     static constexpr int NG = NP / 2;          // unpadded grid side (2x padding, Sec. 3)
@@ -131,6 +132,72 @@ __device__ __forceinline__ void cfma(float2& acc, float2 w, float2 v) {
 template <typename T>
 __device__ __forceinline__ T* cluster_ptr(T* p, int q) {
     return cg::this_cluster().map_shared_rank(p, q);
+}
+
+// Gridding gather for NI cells of one thread: x[n2] = sum over the CSR row of cell
+// cell0 + n2 * cstep of w * VB[antenna] (atomics-free).  RR: entries are taken round-robin over
+// the cells, so that up to NI independent loads are in flight; otherwise cell by cell.
+template <int NI, bool RR>
+__device__ __forceinline__ void gather_cells(float2 (&x)[NI], const int* __restrict__ cell_ptr, int cell0, int cstep,
+                                             const int2* __restrict__ ent, const float* __restrict__ wim,
+                                             const float2* VB) {
+    if constexpr (!RR) {
+#pragma unroll
+        for (int n2 = 0; n2 < NI; ++n2) {
+            const int cell = cell0 + n2 * cstep;
+            const int e0 = __ldg(cell_ptr + cell), e1 = __ldg(cell_ptr + cell + 1);
+            float2 s = make_float2(0.f, 0.f);
+            if (wim) {
+                for (int e = e0; e < e1; ++e) {
+                    const int2 en = __ldg(ent + e);
+                    cfma(s, make_float2(__int_as_float(en.x), __ldg(wim + e)), VB[en.y]);
+                }
+            } else {
+                for (int e = e0; e < e1; ++e) {
+                    const int2 en = __ldg(ent + e);
+                    const float w = __int_as_float(en.x);
+                    const float2 v = VB[en.y];
+                    s.x = fmaf(w, v.x, s.x);
+                    s.y = fmaf(w, v.y, s.y);
+                }
+            }
+            x[n2] = s;
+        }
+        return;
+    }
+    int e[NI], c[NI], cmax = 0;
+#pragma unroll
+    for (int n2 = 0; n2 < NI; ++n2) {
+        const int cell = cell0 + n2 * cstep;
+        e[n2] = __ldg(cell_ptr + cell);
+        c[n2] = __ldg(cell_ptr + cell + 1) - e[n2];
+        cmax = max(cmax, c[n2]);
+        x[n2] = make_float2(0.f, 0.f);
+    }
+    if (wim) {
+        for (int j = 0; j < cmax; ++j) {
+#pragma unroll
+            for (int n2 = 0; n2 < NI; ++n2) {
+                if (j < c[n2]) {
+                    const int2 en = __ldg(ent + e[n2] + j);
+                    cfma(x[n2], make_float2(__int_as_float(en.x), __ldg(wim + e[n2] + j)), VB[en.y]);
+                }
+            }
+        }
+    } else {
+        for (int j = 0; j < cmax; ++j) {
+#pragma unroll
+            for (int n2 = 0; n2 < NI; ++n2) {
+                if (j < c[n2]) {
+                    const int2 en = __ldg(ent + e[n2] + j);
+                    const float w = __int_as_float(en.x);
+                    const float2 v = VB[en.y];
+                    x[n2].x = fmaf(w, v.x, x[n2].x);
+                    x[n2].y = fmaf(w, v.y, x[n2].y);
+                }
+            }
+        }
+    }
 }
 
 template <int Q>

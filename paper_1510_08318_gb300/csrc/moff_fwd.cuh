@@ -163,27 +163,7 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
         // ---- row pass: gridding + 1-D transform along x of row y ----
         {
             float2 x[NI];
-#pragma unroll
-            for (int n2 = 0; n2 < NI; ++n2) {
-                const int cell = y * NG + n1 + S * n2;
-                const int e0 = __ldg(a.cell_ptr + cell), e1 = __ldg(a.cell_ptr + cell + 1);
-                float2 s = make_float2(0.f, 0.f);
-                if (a.cell_wim) {
-                    for (int e = e0; e < e1; ++e) {
-                        const int2 en = __ldg(a.cell_ent + e);
-                        cfma(s, make_float2(__int_as_float(en.x), __ldg(a.cell_wim + e)), VB[en.y]);
-                    }
-                } else {
-                    for (int e = e0; e < e1; ++e) {
-                        const int2 en = __ldg(a.cell_ent + e);
-                        const float w = __int_as_float(en.x);
-                        const float2 v = VB[en.y];
-                        s.x = fmaf(w, v.x, s.x);
-                        s.y = fmaf(w, v.y, s.y);
-                    }
-                }
-                x[n2] = s;
-            }
+            gather_cells<NI, Cfg<NP>::RR>(x, a.cell_ptr, y * NG + n1, S, a.cell_ent, a.cell_wim, VB);
             float2 Y[R1];
             dft_halfzero_in<R1, +1>(x, Y);
             float2* rx = RX + r * G::RXS;
