@@ -119,6 +119,9 @@ epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t 
     L.seg[0] = a;
     L.first[0] = 0;
     L.first[1] = (int)a.n_items;
+    L.weight[0] = 1;
+    L.cost[0] = 0;
+    L.cost[1] = a.n_items;
     L.n_seg = 1;
     L.max_ant = a.n_ant;
     L.max_workers = 0;

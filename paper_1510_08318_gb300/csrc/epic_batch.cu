@@ -71,6 +71,7 @@ epic_status run_class(const epic_batch* b, const ClassRun& c, const void* const*
     L.max_ant = 0;
     L.max_workers = max_workers;
     L.first[0] = 0;
+    L.cost[0] = 0;
     for (int s = 0; s < L.n_seg; ++s) {
         const int i = c.members[s];
         const epic_plan* p = b->plans[i];
@@ -81,6 +82,8 @@ epic_status run_class(const epic_batch* b, const ClassRun& c, const void* const*
         a = epic_plan_fwd_args(p, volt[i], n_time[i], gains ? reinterpret_cast<const float2*>(gains[i]) : nullptr,
                                accum[i], nullptr);
         L.first[s + 1] = L.first[s] + (int)a.n_items;
+        L.weight[s] = epic::item_weight(p->n_pad, p->nnz);
+        L.cost[s + 1] = L.cost[s] + L.weight[s] * a.n_items;
         L.max_ant = std::max(L.max_ant, p->n_ant);
     }
     cudaError_t e = epic_launch_fwd_list(c.n_pad, b->vdt, L, b->n_sm, st);

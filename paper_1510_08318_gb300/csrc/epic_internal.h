@@ -28,10 +28,20 @@ constexpr int kMaxSeg = 64;
 struct SegList {
     FwdArgs seg[kMaxSeg];      // per sub-array (n_items of each = C * P * T)
     int first[kMaxSeg + 1];    // first global item of each sub-array; first[n_seg] = total
+    long long weight[kMaxSeg]; // estimated cost of one item of each sub-array (any unit)
+    long long cost[kMaxSeg + 1];  // cumulative cost before each sub-array; cost[n_seg] = total
     int n_seg;
     int max_ant;               // largest antenna count (shared-memory sizing)
     int max_workers;           // cap on CTAs (clusters) launched, 0 = every resident one
 };
+
+// Per-item cost estimate of a sub-array (relative units): transform work per padded pixel
+// (measured on GB300, in units of one mapping entry's gridding cost) times N_p^2, plus the
+// mapping's entries.
+inline long long item_weight(int n_pad, long long nnz) {
+    const double per_pixel = n_pad >= 512 ? 1.15 : n_pad >= 256 ? 0.85 : n_pad >= 128 ? 0.38 : 0.3;
+    return (long long)(per_pixel * double(n_pad) * double(n_pad)) + nnz + 1;
+}
 
 struct BwdArgs {
     const void* volt;

@@ -25,6 +25,17 @@
 
 namespace epic {
 
+// First item whose cost position is >= c: items of sub-array s occupy the cost interval
+// [cost[s] + i w_s, cost[s] + (i + 1) w_s); consecutive workers' ranges tile the items exactly.
+__device__ __forceinline__ int item_at_cost(const SegList& L, long long c) {
+    int s = 0;
+    while (s + 1 < L.n_seg && L.cost[s + 1] <= c) ++s;
+    const long long off = c - L.cost[s];
+    const long long i = (off + L.weight[s] - 1) / L.weight[s];
+    const long long n_s = L.first[s + 1] - L.first[s];
+    return L.first[s] + (int)(i < n_s ? i : n_s);
+}
+
 template <int NP, int VDT>
 __global__ void __launch_bounds__(Geo<NP>::NT, Geo<NP>::MINB)
 moff_fwd_kernel(const __grid_constant__ SegList L) {
@@ -56,10 +67,11 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
     G::load_twiddles(TW, L.seg[0].twiddle, tid, NT);
     for (int aa = tid; aa < L.max_ant; aa += NT) PW[aa] = 0.f;   // owner-thread entries
 
-    // global items [0, first[n_seg]) of all sub-arrays, split evenly over the workers
-    long long beg_l, end_l;
-    work_range(L.first[L.n_seg], wid, nw, beg_l, end_l);
-    const int beg = (int)beg_l, end = (int)end_l;   // the host guarantees fewer than 2^31 items
+    // global items [0, first[n_seg]) of all sub-arrays, split over the workers in equal shares of
+    // estimated cost (equal item counts for a single sub-array)
+    const int beg = L.n_seg == 1 ? (int)((long long)L.first[1] * wid / nw) : item_at_cost(L, L.cost[L.n_seg] / nw * wid + L.cost[L.n_seg] % nw * wid / nw);
+    const int end = L.n_seg == 1 ? (int)((long long)L.first[1] * (wid + 1) / nw)
+                                 : item_at_cost(L, L.cost[L.n_seg] / nw * (wid + 1) + L.cost[L.n_seg] % nw * (wid + 1) / nw);
     int sg = 0;
     while (sg + 1 < L.n_seg && L.first[sg + 1] <= beg) ++sg;
     const FwdArgs* ap = &L.seg[sg];

@@ -144,6 +144,29 @@ def test_small_sizes(epic, n_pad, n_grid, n_ant, n_time, n_chan, n_pol, vdtype):
     check_close(out["autocorr"], moff.autocorr_term(M, wl.volt, gg, wl.n_grid, wl.n_pad), "autocorr")
 
 
+def test_dense_footprints(epic):
+    """Apertures much wider than the grid spacing (more than 24 mapping entries per occupied
+    cell on average, long CSR rows in the gridding gather); same bound against the oracle, at
+    N_p = 64 and at N_p = 256 (clusters, round-robin gather), forward and gradient."""
+    for n_pad, n_grid, n_ant in ((64, 32, 300), (256, 40, 450)):
+        rng = np.random.default_rng(n_pad)
+        dx = 1.0
+        pos = rng.uniform(7.0, n_grid - 8.0, (n_ant, 2))
+        kerns = [synth.kernel_square(rng.uniform(8.0, 11.0), 0.5) for _ in range(n_ant)]
+        ptr, dxdy, w = synth.pack_kernels(kerns)
+        wl = synth.Workload("dense", pos, ptr, dxdy, w, dx, np.zeros(2), n_grid, n_pad, np.full(2, 1e8), 1, 5, "c64")
+        v = rng.standard_normal((5, 2, 1, n_ant)) + 1j * rng.standard_normal((5, 2, 1, n_ant))
+        wl = synth._finish(wl, v, "c64")
+        M = oracle_map(wl)
+        plan, out = run(epic, wl)
+        assert plan.info["nnz"] / plan.info["n_cells"] >= 24.0
+        check_close(out["image"], moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad), "image")
+        G = rng.standard_normal((2, 1, n_pad, n_pad)).astype(np.float32)
+        want = moff.grad_gains(M, wl.volt, np.ones((2, 1, n_ant)), wl.n_grid, wl.n_pad, G.astype(np.float64))
+        got = plan.image_backward(to_dev(wl), None, torch.from_numpy(G).cuda()).cpu().numpy()
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-3
+
+
 def test_continuation_matches_single_call(epic):
     """Resuming an integration (t_prev > 0) equals integrating all samples at once."""
     wl = synth.workload_tiny(n_time=40)
