@@ -36,6 +36,9 @@ SM_MAX_MHZ = 2070.0
 # (profiles/moff_fwd_np128_ci4_lwa.md); None until captured for the current kernel.
 FWD_TRAFFIC_BYTES = 103.7e6
 DG_TRAFFIC_BYTES = None
+# standalone gridder on the same workload: 8-channel capture (480.3 MB) x 16
+# (profiles/grid_kernel_ci4_lwa.md)
+GRID_TRAFFIC_BYTES = 7.685e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 try:
     with open(MEASURED_PEAKS) as _f:
@@ -53,9 +56,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--channels", type=int, default=128,
                    help="image only the first C of the 128 channels (small profiling case)")
-    p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib"],
+    p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid"],
                    help="lwa: the headline workload; batch: 64 heterogeneous sub-arrays, one graph launch; "
-                        "calib: forward + adjoint of the gain-calibration workload")
+                        "calib: forward + adjoint of the gain-calibration workload; "
+                        "grid: the standalone gridder (epic_grid) on the headline workload")
     return p.parse_args()
 
 
@@ -304,6 +308,102 @@ def run_calib(args):
         print(json.dumps(line))
 
 
+def run_grid(args):
+    """The standalone gridder on the headline workload: every one of the 262,144 samples
+    gridded onto its 64 x 64 grid and written to HBM (8.6 GB of complex64 per step).  Bound by
+    HBM; roofline = algorithmic bytes (voltages + mapping tables read once, grids written
+    once) / kernel time against the measured copy bandwidth."""
+    import numpy as np
+    import torch
+    from oracle import moff
+    from paper_1510_08318_gb300 import build, epic, synth
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = synth.workload_lwa(n_chan=args.channels)
+    plan = epic.Plan.from_workload(wl, device=local)
+    A, T, C, P, NG = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_grid
+    volt = torch.from_numpy(wl.volt_raw).to(dev)
+    out = torch.empty((T, C, P, NG, NG), dtype=torch.complex64, device=dev)
+    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
+    host_out = torch.empty(out.shape, dtype=torch.complex64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    h = plan._h
+
+    def step():
+        epic.epic_grid(h, volt.data_ptr(), T, None, out.data_ptr(), st.cuda_stream)
+
+    def e2e_step():
+        volt.copy_(host_v, non_blocking=True)
+        step()
+        host_out.copy_(out, non_blocking=True)
+
+    def timed(fn, clocks=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ms, clk = timed(step, Clocks(local))
+    e2e_ms, _ = timed(e2e_step)
+    units = A * T * C * P
+    nnz = plan.info["nnz"]
+    alg_bytes = (host_v.numel() * host_v.element_size() + out.numel() * out.element_size()
+                 + nnz * 8 + ((wl.n_pad // 2) ** 2 + 1) * 4)
+    peak = MEASURED["hbm_gbs"]
+    roof = {"bound": "hbm", "achieved": alg_bytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+            "traffic": GRID_TRAFFIC_BYTES,
+            "peak_basis": "measured STREAM-style copy (read + write bytes), of measured",
+            "algorithmic_bytes": alg_bytes}
+    roof["frac"] = roof["achieved"] / peak
+    # oracle parity on sampled grids of the timed call, and the oracle's own rate on a sample
+    cb, err = None, None
+    if rank == 0:
+        M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+        c_s = list(range(max(C - 16, 0), C))
+        t0 = time.perf_counter()
+        want = [moff.grid_efields(M, wl.volt[:, c, 1 % P, :], np.ones(A), NG) for c in c_s]
+        dt = time.perf_counter() - t0
+        ts = [0, T // 2, T - 1]
+        got = out[ts][:, c_s, 1 % P].cpu().numpy()
+        ref = np.stack([w[ts] for w in want], 1)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        if not args.no_cpu_baseline:
+            cb = {"value": A * T * len(c_s) / dt, "unit": UNIT,
+                  "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+                  "sample": "channels %d-%d, pol %d, all %d samples (%d antenna-samples): FP64 sparse "
+                            "gridding; %.2f s" % (c_s[0], c_s[-1], 1 % P, T, A * T * len(c_s), dt)}
+    line = {"metric": METRIC, "value": job_throughput(units, world, ms), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name + ", standalone gridder (epic_grid)", "grids_per_step": T * C * P,
+                       "grid": "%dx%d complex64" % (NG, NG), "output_bytes": out.numel() * out.element_size(),
+                       "l2": "output (8.6 GB) larger than L2; 256 MB flush write before every timed step"},
+            "roofline": roof,
+            "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": UNIT,
+                    "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
+                    "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size())},
+            "gpu_launches": args.steps, "clocks": clk,
+            "err_vs_oracle": {"relative_l2": err, "sample": "3 samples x 16 channels of the timed output"}}
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -312,6 +412,8 @@ def main():
         return run_batch(args)
     if args.workload == "calib":
         return run_calib(args)
+    if args.workload == "grid":
+        return run_grid(args)
     import numpy as np
     import torch
     from paper_1510_08318_gb300 import build, epic, synth

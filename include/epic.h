@@ -150,6 +150,22 @@ epic_status epic_image_backward(const epic_plan *plan, const void *volt, int n_t
                                 void *stream);
 
 /*
+ * epic_grid -- the gridding step alone (Sec. 3, gridding convolution): for every sample
+ * t and (channel, pol), E_t(g) = sum_a M[g, a] g_a V_a(t) on the plan's N_g x N_g grid
+ * (no zero padding, no transform), written to device memory.
+ *
+ *   volt, n_time, gains  as for epic_image.
+ *   grid      device [T][C][P][N_g][N_g] complex64 (interleaved re, im float32), row-major
+ *             over (y, x); 8-byte aligned.  Overwritten; caller-owned.
+ *
+ * This is the form in which the gridded fields leave the chip (e.g. for an external
+ * transform); epic_image keeps them on chip.  Returns EPIC_EINVAL for NULL or misaligned
+ * arrays and n_time < 1.
+ */
+epic_status epic_grid(const epic_plan *plan, const void *volt, int n_time, const float *gains,
+                      float *grid, void *stream);
+
+/*
  * epic_plan_info -- sizes of the plan (any pointer may be NULL):
  *   nnz       non-zeros of the mapping M(r, a) (cells x antennas);
  *   n_cells   occupied grid cells;

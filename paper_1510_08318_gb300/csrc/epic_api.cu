@@ -463,4 +463,36 @@ epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_t
     return launch_bwd(plan, a, st);
 }
 
+epic_status epic_grid(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* grid,
+                      void* stream) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
+    if (!volt || !grid) return epic_fail(EPIC_EINVAL, "NULL device array");
+    if (reinterpret_cast<uintptr_t>(grid) % 8 != 0) return epic_fail(EPIC_EINVAL, "grid must be 8-byte aligned");
+    if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
+        return epic_fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    const int tb = epic::grid_samples_per_unit(plan->n_ant, (size_t)smem_optin);
+    if (epic::grid_smem_bytes(plan->n_ant, tb) > (size_t)smem_optin)
+        return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the gridder's shared memory", plan->n_ant);
+    epic::GridArgs a;
+    a.volt = volt;
+    a.n_time = n_time;
+    a.n_cp = plan->n_chan * plan->n_pol;
+    a.n_ant = plan->n_ant;
+    a.gains = reinterpret_cast<const float2*>(gains);
+    a.cell_ptr = plan->cell_ptr;
+    a.cell_ent = plan->cell_ent;
+    a.cell_wim = plan->cell_wim;
+    a.csr_width = plan->n_pad / 2;
+    a.n_grid = plan->n_grid;
+    a.out = reinterpret_cast<float2*>(grid);
+    const cudaError_t e = epic::launch_grid(plan->vdt, tb, a, plan->n_sm, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "gridding kernel launch");
+}
+
 }  // extern "C"

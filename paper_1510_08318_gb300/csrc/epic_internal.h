@@ -60,6 +60,19 @@ struct BwdArgs {
     float scale;               // 2 / T
 };
 
+// Standalone gridder (grid.cu): E_t(g) for every sample of a call, written to device memory.
+struct GridArgs {
+    const void* volt;          // [T][C][P][A] raw voltages
+    int n_time, n_cp, n_ant;
+    const float2* gains;       // [CP][A] or nullptr (unit gains)
+    const int* cell_ptr;       // cell-major mapping CSR, rows csr_width cells wide
+    const int2* cell_ent;
+    const float* cell_wim;
+    int csr_width;             // N_p / 2
+    int n_grid;                // N_g (output rows and columns)
+    float2* out;               // [T][CP][N_g][N_g]
+};
+
 // Kernel launchers, one translation unit per padded size.  Return cudaSuccess or the
 // launch error.  Shared memory is sized by the launcher.
 cudaError_t launch_fwd_32(int vdt, const SegList& L, int n_sm, cudaStream_t st);
@@ -87,6 +100,11 @@ int exchange_row_stride(int n_pad);   // row stride (float2) of the kernels' exc
 size_t dftgemm_smem_bytes(int n_ant);
 void dftgemm_tables(std::vector<uint16_t>& out);
 cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm, cudaStream_t st);
+
+// Standalone gridder: samples per work unit (8, or 4 when 8 do not fit shared memory) and launch.
+size_t grid_smem_bytes(int n_ant, int tb);
+int grid_samples_per_unit(int n_ant, size_t smem_optin);
+cudaError_t launch_grid(int vdt, int tb, const GridArgs& a, int n_sm, cudaStream_t st);
 
 // Epilogue kernels (finalize.cu).
 cudaError_t launch_finalize_image(const double* accum, float* image, long long n, double inv_t,

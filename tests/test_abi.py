@@ -70,5 +70,6 @@ def test_calls_reject_null_plan(lib):
     assert lib.epic_image(None, None, 1, None, None, None, 0, None, None, None) == epic.EPIC_EINVAL
     assert "plan" in epic.epic_last_error()
     assert lib.epic_image_backward(None, None, 1, None, None, None, None) == epic.EPIC_EINVAL
+    assert lib.epic_grid(None, None, 1, None, None, None) == epic.EPIC_EINVAL
     assert lib.epic_plan_info(None, None, None, None) == epic.EPIC_EINVAL
     lib.epic_destroy(None)
