@@ -84,12 +84,20 @@ class Clocks:
         self.p = None
 
     def start(self):
+        """Start sampling and return once the first sample is written, so that nvidia-smi's own
+        start-up (which can hold the driver for a while) stays outside the timed region."""
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 15.0 and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.p is None:

@@ -41,6 +41,10 @@ void free_plan(epic_plan* p) {
     cudaFree(p->cell_ptr);
     cudaFree(p->cell_ent);
     cudaFree(p->cell_wim);
+    cudaFree(p->wlane);
+    cudaFree(p->wbase);
+    cudaFree(p->went);
+    cudaFree(p->wwim);
     cudaFree(p->ant_ptr);
     cudaFree(p->ant_ent);
     cudaFree(p->ant_wim);
@@ -103,6 +107,10 @@ epic::FwdArgs epic_plan_fwd_args(const epic_plan* plan, const void* volt, int n_
     a.cell_ptr = plan->cell_ptr;
     a.cell_ent = plan->cell_ent;
     a.cell_wim = plan->cell_wim;
+    a.wlane = plan->wlane;
+    a.wbase = plan->wbase;
+    a.went = plan->went;
+    a.wwim = plan->wwim;
     a.twiddle = plan->twiddle;
     a.accum = accum;
     a.power = power;
@@ -243,6 +251,45 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         p->wsum_max = float(wm * (1.0 + 1e-6));
     }
 
+    // warp-interleaved copy of the cell-major mapping for the forward kernels that gather cell
+    // by cell: group (row block yb, n2) serves the warp whose lane l owns cell
+    // (yb * 32/S + l / S, l % S + S * n2); the lanes are ranked by decreasing entry count, and
+    // step k stores the k-th entry of the lanes of rank 0 .. n_k - 1 (those with more than k
+    // entries), so the active lanes of a step read one contiguous run.
+    std::vector<int> wlane, wbase;
+    std::vector<int2> went;
+    std::vector<float> wwim;
+    const int SL = epic::fwd_interleave_lanes(n_pad);
+    if (SL > 0) {
+        const int LPC = 32 / SL, NI = NG / SL, n_blk = NG / LPC;
+        wlane.resize((size_t)n_blk * NI * 32);
+        wbase.resize((size_t)n_blk * NI);
+        went.reserve(m.size());
+        wwim.reserve(m.size());
+        for (int yb = 0; yb < n_blk; ++yb) {
+            for (int n2 = 0; n2 < NI; ++n2) {
+                const int g = yb * NI + n2;
+                int cell[32], cnt[32], order[32], rank[32];
+                for (int l = 0; l < 32; ++l) {
+                    cell[l] = (yb * LPC + l / SL) * NG + (l % SL) + SL * n2;
+                    cnt[l] = cptr[cell[l] + 1] - cptr[cell[l]];
+                    order[l] = l;
+                }
+                std::stable_sort(order, order + 32, [&](int x, int y) { return cnt[x] > cnt[y]; });
+                for (int i = 0; i < 32; ++i) rank[order[i]] = i;
+                wbase[g] = (int)went.size();
+                for (int l = 0; l < 32; ++l) wlane[(size_t)g * 32 + l] = cnt[l] | (rank[l] << 16);
+                for (int k = 0; k < cnt[order[0]]; ++k) {
+                    for (int i = 0; i < 32 && cnt[order[i]] > k; ++i) {
+                        const int e = cptr[cell[order[i]]] + k;
+                        went.push_back(cent[e]);
+                        wwim.push_back(cwim[e]);
+                    }
+                }
+            }
+        }
+    }
+
     // antenna-major CSR per row block (degridding side of the adjoint); cells are stored as
     // offsets into the adjoint kernel's shared-memory row buffer
     const int rows = epic::grid_rows_per_block(n_pad);
@@ -332,7 +379,10 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     if ((e = upload(&p->cell_ptr, cptr)) != cudaSuccess || (e = upload(&p->cell_ent, cent)) != cudaSuccess ||
         (e = upload(&p->ant_ptr, aptr)) != cudaSuccess || (e = upload(&p->ant_ent, aent)) != cudaSuccess ||
         (e = upload(&p->twiddle, tw)) != cudaSuccess || (e = upload(&p->lag_tab, lag)) != cudaSuccess ||
-        (complex_w && ((e = upload(&p->cell_wim, cwim)) != cudaSuccess || (e = upload(&p->ant_wim, awim)) != cudaSuccess))) {
+        (complex_w && ((e = upload(&p->cell_wim, cwim)) != cudaSuccess || (e = upload(&p->ant_wim, awim)) != cudaSuccess)) ||
+        (SL > 0 && ((e = upload(&p->wlane, wlane)) != cudaSuccess || (e = upload(&p->wbase, wbase)) != cudaSuccess ||
+                    (e = upload(&p->went, went)) != cudaSuccess ||
+                    (complex_w && (e = upload(&p->wwim, wwim)) != cudaSuccess)))) {
         free_plan(p);
         return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
                                               : epic_cuda_fail(e, "plan upload");

@@ -14,6 +14,14 @@ struct FwdArgs {
     const int* cell_ptr;       // [NG*NG + 1] CSR by grid cell (NG = N_p / 2)
     const int2* cell_ent;      // {weight re bits, antenna}
     const float* cell_wim;     // weight imaginary parts, or nullptr when all weights are real
+    // The same mapping in warp-interleaved order (forward kernels with N_p <= 128): one group
+    // per (block of 32/S grid rows, n2) whose 32 lanes own the cells the row-pass threads of a
+    // warp gather; step k of a group holds the k-th entry of every lane with more than k
+    // entries, lanes ordered by decreasing entry count.
+    const int* wlane;          // [groups][32] entry count | (rank of the lane in that order) << 16
+    const int* wbase;          // [groups] first entry of the group
+    const int2* went;          // entries, {weight re bits, antenna}
+    const float* wwim;         // weight imaginary parts, or nullptr
     const float2* twiddle;     // [N_p] exp(+2 pi i j / N_p)
     double* accum;             // [CP][N_p][N_p] sum_t |F_t|^2
     double* power;             // [CP][A] sum_t |g V|^2 or nullptr
@@ -94,6 +102,7 @@ template <int NP, int VDT> int resident_fwd_workers_t(int max_ant, int n_sm);
 size_t fwd_smem_bytes(int n_pad, int n_ant);
 size_t bwd_smem_bytes(int n_pad, int n_ant);
 int grid_rows_per_block(int n_pad);   // rows of the N_g grid each CTA of a cluster owns
+int fwd_interleave_lanes(int n_pad);  // S of the warp-interleaved mapping, 0 if the size does not use it
 int exchange_row_stride(int n_pad);   // row stride (float2) of the kernels' exchange buffer
 
 // Tensor-core DFT form of the forward kernel, N_p = 128 (moff_dftgemm.cu).

@@ -14,6 +14,10 @@ struct epic_plan {
     int* cell_ptr = nullptr;
     int2* cell_ent = nullptr;
     float* cell_wim = nullptr;   // nullptr when every weight is real
+    int* wlane = nullptr;        // warp-interleaved copy of the cell-major mapping (N_p <= 128)
+    int* wbase = nullptr;
+    int2* went = nullptr;
+    float* wwim = nullptr;
     int* ant_ptr = nullptr;
     int2* ant_ent = nullptr;
     float* ant_wim = nullptr;

@@ -156,6 +156,15 @@ int grid_rows_per_block(int n_pad) {
     }
 }
 
+int fwd_interleave_lanes(int n_pad) {
+    switch (n_pad) {
+        case 32: return Cfg<32>::RR ? 0 : Geo<32>::S;
+        case 64: return Cfg<64>::RR ? 0 : Geo<64>::S;
+        case 128: return Cfg<128>::RR ? 0 : Geo<128>::S;
+        default: return 0;
+    }
+}
+
 int exchange_row_stride(int n_pad) {
     switch (n_pad) {
         case 32: return Geo<32>::RXS;

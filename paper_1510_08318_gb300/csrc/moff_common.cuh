@@ -200,6 +200,52 @@ __device__ __forceinline__ void gather_cells(float2 (&x)[NI], const int* __restr
     }
 }
 
+// Gridding gather over the warp-interleaved copy of the mapping: x[n2] = sum over the entries
+// of this lane's cell in group g0 + n2.  The whole warp walks k = 0 .. (largest count of the
+// group) - 1; at step k the lanes with more than k entries (ranks 0 .. n_k - 1) read entry
+// (start of step k) + rank, so one step's loads are one contiguous run, and the start of step
+// k + 1 is that of step k plus n_k (a ballot count).  Entries of one cell are summed in the
+// cell-major order, as in gather_cells.  All 32 lanes must call it together.
+template <int NI>
+__device__ __forceinline__ void gather_interleaved(float2 (&x)[NI], const int* __restrict__ wlane,
+                                                   const int* __restrict__ wbase, const int2* __restrict__ ent,
+                                                   const float* __restrict__ wim, int g0, int lane,
+                                                   const float2* VB) {
+#pragma unroll
+    for (int n2 = 0; n2 < NI; ++n2) {
+        const int word = __ldg(wlane + (g0 + n2) * 32 + lane);
+        const int cnt = word & 0xffff;
+        int e = __ldg(wbase + g0 + n2) + (word >> 16);
+        const int kmax = __reduce_max_sync(0xffffffffu, cnt);
+        float2 s = make_float2(0.f, 0.f);
+        if (wim) {
+            for (int k = 0; k < kmax; ++k) {
+                const bool on = k < cnt;
+                const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                if (on) {
+                    const int2 en = __ldg(ent + e);
+                    cfma(s, make_float2(__int_as_float(en.x), __ldg(wim + e)), VB[en.y]);
+                }
+                e += n_k;
+            }
+        } else {
+            for (int k = 0; k < kmax; ++k) {
+                const bool on = k < cnt;
+                const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                if (on) {
+                    const int2 en = __ldg(ent + e);
+                    const float w = __int_as_float(en.x);
+                    const float2 v = VB[en.y];
+                    s.x = fmaf(w, v.x, s.x);
+                    s.y = fmaf(w, v.y, s.y);
+                }
+                e += n_k;
+            }
+        }
+        x[n2] = s;
+    }
+}
+
 template <int Q>
 __device__ __forceinline__ void block_or_cluster_sync() {
     if constexpr (Q > 1) {

@@ -175,7 +175,12 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
         // ---- row pass: gridding + 1-D transform along x of row y ----
         {
             float2 x[NI];
-            gather_cells<NI, Cfg<NP>::RR>(x, a.cell_ptr, y * NG + n1, S, a.cell_ent, a.cell_wim, VB);
+            if constexpr (Cfg<NP>::RR) {
+                gather_cells<NI, true>(x, a.cell_ptr, y * NG + n1, S, a.cell_ent, a.cell_wim, VB);
+            } else {
+                static_assert(Q == 1, "the interleaved mapping assumes one CTA per image");
+                gather_interleaved<NI>(x, a.wlane, a.wbase, a.went, a.wwim, (y / G::LPC) * NI, lane, VB);
+            }
             float2 Y[R1];
             dft_halfzero_in<R1, +1>(x, Y);
             float2* rx = RX + r * G::RXS;
