@@ -31,13 +31,12 @@ METRIC = "MOFF antenna-samples/s (images/s beside it), FP32 path, error vs FP64 
 UNIT = "antenna-samples/s"
 # Peak FP32 rate of the CUDA cores: SMs x 128 lanes x 2 FLOP (FMA) x max SM clock.
 SM_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the forward kernels on this
-# workload, from ncu captures of an 8-channel case scaled by the images per launch
-# (profiles/moff_fwd_np128_ci4_lwa.md); None until captured for the current kernel.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch on this workload, from ncu captures
+# of the 8-channel case (16,384 images) scaled by the units per launch (x16); None until
+# captured for the current kernel.  Forward FFT kernel: 6.48 MB per capture.
 FWD_TRAFFIC_BYTES = 103.7e6
 DG_TRAFFIC_BYTES = None
-# standalone gridder on the same workload: 8-channel capture (480.3 MB) x 16
-# (profiles/grid_kernel_ci4_lwa.md)
+# standalone gridder: 480.3 MB per capture
 GRID_TRAFFIC_BYTES = 7.685e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 try:
@@ -56,10 +55,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--channels", type=int, default=128,
                    help="image only the first C of the 128 channels (small profiling case)")
-    p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid"],
+    p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid", "xpol"],
                    help="lwa: the headline workload; batch: 64 heterogeneous sub-arrays, one graph launch; "
                         "calib: forward + adjoint of the gain-calibration workload; "
-                        "grid: the standalone gridder (epic_grid) on the headline workload")
+                        "grid: the standalone gridder (epic_grid) on the headline workload; "
+                        "xpol: all four cross-polarisation images (epic_image_xpol) of the headline workload")
     return p.parse_args()
 
 
@@ -412,6 +412,114 @@ def run_grid(args):
         print(json.dumps(line))
 
 
+def run_xpol(args):
+    """All four cross-polarisation images of the headline workload (XX, YY, XY; YX = conj XY)
+    with epic_image_xpol: the forward kernel runs 4 virtual pols per channel (X, Y, X + Y,
+    X + iY) and the epilogue forms XY by the polarisation identity.  Same metric as the
+    headline (antenna-samples/s of the dual-pol data)."""
+    import numpy as np
+    import torch
+    from oracle import moff
+    from paper_1510_08318_gb300 import build, epic, synth
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = synth.workload_lwa(n_chan=args.channels)
+    plan = epic.Plan.from_workload(wl, device=local)
+    A, T, C, P, NP = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_pad
+    volt = torch.from_numpy(wl.volt_raw).to(dev)
+    acc4 = torch.empty((C, 4, NP, NP), dtype=torch.float64, device=dev)
+    img = torch.empty((C, 2, NP, NP), dtype=torch.float32, device=dev)
+    cross = torch.empty((C, NP, NP), dtype=torch.complex64, device=dev)
+    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
+    host_img = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+    host_cross = torch.empty(cross.shape, dtype=torch.complex64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def step():
+        epic.epic_image_xpol(plan._h, volt.data_ptr(), T, None, acc4.data_ptr(), 0, img.data_ptr(),
+                             cross.data_ptr(), st.cuda_stream)
+
+    def kernel_only():
+        epic.epic_image_xpol(plan._h, volt.data_ptr(), T, None, acc4.data_ptr(), 0, None, None, st.cuda_stream)
+
+    def e2e_step():
+        volt.copy_(host_v, non_blocking=True)
+        step()
+        host_img.copy_(img, non_blocking=True)
+        host_cross.copy_(cross, non_blocking=True)
+
+    def timed(fn, clocks=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ms, clk = timed(step, Clocks(local))
+    kern_ms, _ = timed(kernel_only)
+    e2e_ms, _ = timed(e2e_step)
+    units = A * T * C * P
+    flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * 4
+    peak = n_sm * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": flops / (kern_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "traffic": None, "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, max clock)"
+                                          % (n_sm, SM_MAX_MHZ),
+            "flop_basis": "per virtual-pol image as the headline (5 N log2 N + 8 nnz + 4 N), 4 per channel-sample"}
+    roof["frac"] = roof["achieved"] / peak
+    cb, err = None, None
+    if rank == 0:
+        # the oracle's four products on a bounded sample: the last 8 channels, all samples
+        n_s = min(C, 8)
+        c0, Ts = C - n_s, T
+        t0 = time.perf_counter()
+        M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+        want = moff.moff_cross_image(M, wl.volt[:Ts, c0:], None, wl.n_grid, NP)
+        dt = time.perf_counter() - t0
+        sub = epic.Plan(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid, NP, n_s, 2,
+                        wl.vdtype, local)
+        got = sub.image_xpol(torch.from_numpy(np.ascontiguousarray(wl.volt_raw[:Ts, c0:])).to(dev))
+        gi, gc = got["image"].cpu().numpy(), got["cross"].cpu().numpy()
+        xx, yy, xy = want[:, 0, 0].real, want[:, 1, 1].real, want[:, 0, 1]
+        err = {"XX": float(np.linalg.norm(gi[:, 0] - xx) / np.linalg.norm(xx)),
+               "YY": float(np.linalg.norm(gi[:, 1] - yy) / np.linalg.norm(yy)),
+               "XY_vs_sqrt_XX_YY": float(np.linalg.norm(gc - xy) / np.sqrt(np.linalg.norm(xx) * np.linalg.norm(yy)))}
+        sub.close()
+        if not args.no_cpu_baseline:
+            cb = {"value": A * Ts * 2 * n_s / dt, "unit": UNIT,
+                  "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+                  "sample": "channels %d-%d, both pols, samples 0-%d (%d antenna-samples): FP64 gridding + "
+                            "separable DFT + the four products; %.2f s" % (c0, C - 1, Ts - 1, A * Ts * 2 * n_s, dt)}
+    line = {"metric": METRIC, "value": job_throughput(units, world, ms), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name + ", four cross-polarisation products (epic_image_xpol)",
+                       "images_per_step": T * C * 4, "l2": "flushed (256 MB write) before every timed step"},
+            "kernel_ms": kern_ms, "roofline": roof,
+            "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": UNIT,
+                    "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
+                    "d2h_bytes_per_step": int(host_img.numel() * 4 + host_cross.numel() * 8)},
+            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "err_vs_oracle": {"relative_l2": err, "sample": "last 8 channels, all samples"}}
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -422,6 +530,8 @@ def main():
         return run_calib(args)
     if args.workload == "grid":
         return run_grid(args)
+    if args.workload == "xpol":
+        return run_xpol(args)
     import numpy as np
     import torch
     from paper_1510_08318_gb300 import build, epic, synth

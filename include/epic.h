@@ -150,6 +150,29 @@ epic_status epic_image_backward(const epic_plan *plan, const void *volt, int n_t
                                 void *stream);
 
 /*
+ * epic_image_xpol -- the four instrumental cross-polarisation images of dual-polarisation
+ * data (Sec. 3 and the image module of App. A produce all four; Eq. "dirty-image-MOFF" with
+ * F_p conj(F_q) in place of |F_p|^2): XX = <|F_X|^2>, YY = <|F_Y|^2>, XY = <F_X conj(F_Y)>,
+ * YX = conj(XY), averaged over time, for a plan with n_pol == 2 (pol 0 = X, pol 1 = Y).
+ *
+ *   volt, n_time, gains  as for epic_image ([T][C][2][A], gains [C][2][A] or NULL).
+ *   accum4    device [C][4][N_p][N_p] float64: per channel the time sums of |F_v|^2 for
+ *             v = X, Y, X + Y, X + iY (the gridded fields g_X V_X, g_Y V_Y, g_X V_X + g_Y V_Y,
+ *             g_X V_X + i g_Y V_Y).  Continued if t_prev > 0, overwritten if t_prev == 0.
+ *   t_prev    samples already integrated into accum4 (>= 0).
+ *   image     device [C][2][N_p][N_p] float32 (XX, YY), or NULL.
+ *   cross     device [C][N_p][N_p] complex64 (XY, interleaved re, im), or NULL.
+ *
+ * XY follows from the four sums by the polarisation identity, evaluated in float64:
+ * Re XY = (S_{X+Y} - S_X - S_Y) / 2T, Im XY = (S_{X+iY} - S_X - S_Y) / 2T.  The forward
+ * kernel therefore runs 4 C instead of 2 C (channel, pol) images.  The FFT form is used
+ * whatever epic_set_transform chose; no auto-correlation term.  EPIC_EINVAL if the plan
+ * does not have two pols.
+ */
+epic_status epic_image_xpol(const epic_plan *plan, const void *volt, int n_time, const float *gains,
+                            double *accum4, int64_t t_prev, float *image, float *cross, void *stream);
+
+/*
  * epic_grid -- the gridding step alone (Sec. 3, gridding convolution): for every sample
  * t and (channel, pol), E_t(g) = sum_a M[g, a] g_a V_a(t) on the plan's N_g x N_g grid
  * (no zero padding, no transform), written to device memory.

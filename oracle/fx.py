@@ -72,3 +72,25 @@ def fx_image(M, volt, gains, n_grid, n_pad, exclude_auto=False):
             V = visibilities(volt[:, c, p, :], g, exclude_auto)
             out[c, p] = image_from_uv(uv_plane(M, V, n_grid), n_grid, n_pad)
     return out
+
+
+def cross_visibilities(volt_p, gain_p, volt_q, gain_q):
+    """V^{pq}_ab = mean_t (g_ap V_ap)(g_bq V_bq)^*: [A, A] (all pairs, autos included)."""
+    vp = volt_p * gain_p[None, :]
+    vq = volt_q * gain_q[None, :]
+    return vp.T @ np.conj(vq) / volt_p.shape[0]
+
+
+def fx_cross_image(M, volt, gains, n_grid, n_pad):
+    """FX-route cross-polarisation images [C, 2, 2, N_p, N_p]: I^{pq} from the visibilities
+    V^{pq} of pol p of antenna a with pol q of antenna b, gridded and transformed as above."""
+    T, C, P, A = volt.shape
+    out = np.empty((C, 2, 2, n_pad, n_pad), dtype=np.complex128)
+    for c in range(C):
+        g = [np.ones(A, dtype=np.complex128) if gains is None else gains[c, p].astype(np.complex128)
+             for p in range(2)]
+        for p in range(2):
+            for q in range(2):
+                V = cross_visibilities(volt[:, c, p, :], g[p], volt[:, c, q, :], g[q])
+                out[c, p, q] = image_from_uv(uv_plane(M, V, n_grid), n_grid, n_pad)
+    return out

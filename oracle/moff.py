@@ -19,10 +19,12 @@ in numpy/scipy float64, with no blocking, fusion or reordering:
                  A(k) = sum_a P_a |K_a(k)|^2 with P_a the mean antenna power and K_a
                  the spatial transform of antenna a's sampled footprint (the
                  per-antenna form Sec. 4.3 proposes).
+  moff_cross_image  the four cross-polarisation products mean_t F_p conj(F_q) of
+                 dual-polarisation data (Sec. 3; App. A image module).
   grad_gains     derivative of a real loss L(I) with respect to the complex gains,
                  by the chain rule through Eq. "dirty-image-MOFF".
 
-Conventions (the readings listed in the design doc):
+Conventions (readings of points the paper leaves open):
   * cell index per axis = floor((x - x0) / dx + 0.5) in float64, x = r_a + delta_k;
   * grid cell g = (gy, gx), flattened gy * N_g + gx; the N_g x N_g grid sits in the
     corner [0, N_g)^2 of the N_p x N_p zero-padded grid;
@@ -125,6 +127,27 @@ def moff_image(M, volt, gains, n_grid, n_pad):
         for p in range(P):
             g = np.ones(A, dtype=np.complex128) if gains is None else gains[c, p].astype(np.complex128)
             out[c, p] = moff_image_cp(M, volt[:, c, p, :], g, n_grid, n_pad)[0]
+    return out
+
+
+def moff_cross_image(M, volt, gains, n_grid, n_pad):
+    """The four instrumental cross-polarisation images of a dual-polarisation cube (Sec. 3
+    and the image module of App. A; Eq. "dirty-image-MOFF" with F_p conj(F_q) in place of
+    |F_p|^2): volt [T, C, 2, A], gains [C, 2, A] or None ->
+    I [C, 2, 2, N_p, N_p] complex128, I[c, p, q] = mean_t F_p(k) conj(F_q(k)), shifted.
+    I[c, p, p] is moff_image's image; I[c, 1, 0] = conj(I[c, 0, 1])."""
+    T, C, P, A = volt.shape
+    if P != 2:
+        raise ValueError("cross-polarisation images need two polarisations")
+    out = np.empty((C, 2, 2, n_pad, n_pad), dtype=np.complex128)
+    for c in range(C):
+        F = []
+        for p in range(2):
+            g = np.ones(A, dtype=np.complex128) if gains is None else gains[c, p].astype(np.complex128)
+            F.append(spatial_transform(grid_efields(M, volt[:, c, p, :], g, n_grid), n_pad))
+        for p in range(2):
+            for q in range(2):
+                out[c, p, q] = fftshift2((F[p] * np.conj(F[q])).mean(0))
     return out
 
 

@@ -78,13 +78,13 @@ struct MapEntry {
 
 }  // namespace
 
-cudaError_t epic_launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st) {
+cudaError_t epic_launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st, bool xpol) {
     switch (n_pad) {
-        case 32: return epic::launch_fwd_32(vdt, L, n_sm, st);
-        case 64: return epic::launch_fwd_64(vdt, L, n_sm, st);
-        case 128: return epic::launch_fwd_128(vdt, L, n_sm, st);
-        case 256: return epic::launch_fwd_256(vdt, L, n_sm, st);
-        case 512: return epic::launch_fwd_512(vdt, L, n_sm, st);
+        case 32: return epic::launch_fwd_32(vdt, L, n_sm, st, xpol);
+        case 64: return epic::launch_fwd_64(vdt, L, n_sm, st, xpol);
+        case 128: return epic::launch_fwd_128(vdt, L, n_sm, st, xpol);
+        case 256: return epic::launch_fwd_256(vdt, L, n_sm, st, xpol);
+        case 512: return epic::launch_fwd_512(vdt, L, n_sm, st, xpol);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -122,7 +122,7 @@ epic::FwdArgs epic_plan_fwd_args(const epic_plan* plan, const void* volt, int n_
 
 namespace {
 
-epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t st) {
+epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t st, bool xpol = false) {
     epic::SegList L;
     L.seg[0] = a;
     L.first[0] = 0;
@@ -133,7 +133,7 @@ epic_status launch_fwd(const epic_plan* p, const epic::FwdArgs& a, cudaStream_t 
     L.n_seg = 1;
     L.max_ant = a.n_ant;
     L.max_workers = 0;
-    const cudaError_t e = epic_launch_fwd_list(p->n_pad, p->vdt, L, p->n_sm, st);
+    const cudaError_t e = epic_launch_fwd_list(p->n_pad, p->vdt, L, p->n_sm, st, xpol);
     return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "imaging kernel launch");
 }
 
@@ -511,6 +511,39 @@ epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_t
     a.n_items = (long long)cp * n_time;
     a.scale = float(2.0 / double(n_time));
     return launch_bwd(plan, a, st);
+}
+
+epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time, const float* gains,
+                            double* accum4, int64_t t_prev, float* image, float* cross, void* stream) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (plan->n_pol != 2) return epic_fail(EPIC_EINVAL, "cross-polarisation images need a plan with 2 pols (has %d)", plan->n_pol);
+    if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
+    if (!volt || !accum4) return epic_fail(EPIC_EINVAL, "NULL device array");
+    if (t_prev < 0) return epic_fail(EPIC_EINVAL, "t_prev must be >= 0");
+    if ((long long)plan->n_chan * 4 * n_time > 2147483647LL)
+        return epic_fail(EPIC_EUNSUPPORTED, "4 * C * T must stay below 2^31 per call");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    if (epic::fwd_xpol_smem_bytes(plan->n_pad, plan->n_ant) > (size_t)smem_optin)
+        return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the cross-polarisation kernel's shared memory",
+                         plan->n_ant);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long npix = (long long)plan->n_pad * plan->n_pad;
+    cudaError_t e;
+    if (t_prev == 0 && (e = cudaMemsetAsync(accum4, 0, (size_t)plan->n_chan * 4 * npix * sizeof(double), st)) != cudaSuccess)
+        return epic_cuda_fail(e, "memset accum4");
+    epic::FwdArgs a = epic_plan_fwd_args(plan, volt, n_time, reinterpret_cast<const float2*>(gains), accum4, nullptr);
+    a.n_cp = plan->n_chan * 4;          // virtual pols X, Y, X + Y, X + iY per channel
+    a.n_items = (long long)a.n_cp * n_time;
+    const epic_status s = launch_fwd(plan, a, st, true);
+    if (s != EPIC_OK) return s;
+    if ((e = epic::launch_finalize_xpol(accum4, image, reinterpret_cast<float2*>(cross), plan->n_chan, npix,
+                                        1.0 / double(t_prev + n_time), st)) != cudaSuccess)
+        return epic_cuda_fail(e, "cross-polarisation epilogue");
+    return EPIC_OK;
 }
 
 epic_status epic_grid(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* grid,

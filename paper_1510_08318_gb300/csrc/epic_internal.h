@@ -82,12 +82,13 @@ struct GridArgs {
 };
 
 // Kernel launchers, one translation unit per padded size.  Return cudaSuccess or the
-// launch error.  Shared memory is sized by the launcher.
-cudaError_t launch_fwd_32(int vdt, const SegList& L, int n_sm, cudaStream_t st);
-cudaError_t launch_fwd_64(int vdt, const SegList& L, int n_sm, cudaStream_t st);
-cudaError_t launch_fwd_128(int vdt, const SegList& L, int n_sm, cudaStream_t st);
-cudaError_t launch_fwd_256(int vdt, const SegList& L, int n_sm, cudaStream_t st);
-cudaError_t launch_fwd_512(int vdt, const SegList& L, int n_sm, cudaStream_t st);
+// launch error.  Shared memory is sized by the launcher.  xpol: the cross-polarisation form of
+// the forward kernel (4 virtual pols per channel, see moff_fwd.cuh).
+cudaError_t launch_fwd_32(int vdt, const SegList& L, int n_sm, cudaStream_t st, bool xpol = false);
+cudaError_t launch_fwd_64(int vdt, const SegList& L, int n_sm, cudaStream_t st, bool xpol = false);
+cudaError_t launch_fwd_128(int vdt, const SegList& L, int n_sm, cudaStream_t st, bool xpol = false);
+cudaError_t launch_fwd_256(int vdt, const SegList& L, int n_sm, cudaStream_t st, bool xpol = false);
+cudaError_t launch_fwd_512(int vdt, const SegList& L, int n_sm, cudaStream_t st, bool xpol = false);
 cudaError_t launch_bwd_32(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_64(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_128(int vdt, const BwdArgs& a, int n_sm, cudaStream_t st);
@@ -100,6 +101,7 @@ template <int NP, int VDT> int resident_fwd_workers_t(int max_ant, int n_sm);
 
 // Shared-memory bytes the forward / backward kernels need for a given size and antenna count.
 size_t fwd_smem_bytes(int n_pad, int n_ant);
+size_t fwd_xpol_smem_bytes(int n_pad, int n_ant);
 size_t bwd_smem_bytes(int n_pad, int n_ant);
 int grid_rows_per_block(int n_pad);   // rows of the N_g grid each CTA of a cluster owns
 int fwd_interleave_lanes(int n_pad);  // S of the warp-interleaved mapping, 0 if the size does not use it
@@ -118,6 +120,8 @@ cudaError_t launch_grid(int vdt, int tb, const GridArgs& a, int n_sm, cudaStream
 // Epilogue kernels (finalize.cu).
 cudaError_t launch_finalize_image(const double* accum, float* image, long long n, double inv_t,
                                   cudaStream_t st);
+cudaError_t launch_finalize_xpol(const double* accum4, float* image, float2* cross, int n_chan, long long npix,
+                                 double inv_t, cudaStream_t st);
 size_t autocorr_smem_bytes(int lag_side, int n_pad, int n_ant);
 cudaError_t launch_autocorr(const double* power, const float2* lag_tab, int n_cp, int n_ant,
                             int lag_side, int n_pad, double inv_t, float* out, cudaStream_t st);

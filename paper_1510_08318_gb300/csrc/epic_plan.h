@@ -50,7 +50,8 @@ struct EpicDeviceGuard {
 epic::FwdArgs epic_plan_fwd_args(const epic_plan* p, const void* volt, int n_time, const float2* gains,
                                  double* accum, double* power);
 // One persistent forward launch over a list of sub-arrays of padded size n_pad.
-cudaError_t epic_launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st);
+cudaError_t epic_launch_fwd_list(int n_pad, int vdt, const epic::SegList& L, int n_sm, cudaStream_t st,
+                                 bool xpol = false);
 // CTAs (or clusters) of the forward kernel of a size class resident on the whole GPU.
 int epic_resident_workers(int n_pad, int vdt, const std::vector<epic_plan*>& plans, const std::vector<int>& members,
                           int n_sm);

@@ -29,6 +29,40 @@ cudaError_t launch_finalize_image(const double* accum, float* image, long long n
     return cudaGetLastError();
 }
 
+// Cross-polarisation epilogue.  accum4 holds per channel the time sums S_v(k) of |F_v|^2 for
+// the virtual pols v = X, Y, X + Y, X + iY; since |F_X + F_Y|^2 = |F_X|^2 + |F_Y|^2 +
+// 2 Re(F_X conj F_Y) and |F_X + i F_Y|^2 = |F_X|^2 + |F_Y|^2 + 2 Im(F_X conj F_Y),
+//   XX = S_0 / T, YY = S_1 / T, XY = ((S_2 - S_0 - S_1) + i (S_3 - S_0 - S_1)) / (2 T)
+// in float64, then rounded.  image [C][2][npix] (may be null), cross [C][npix] complex.
+__global__ void finalize_xpol_kernel(const double* __restrict__ accum4, float* __restrict__ image,
+                                     float2* __restrict__ cross, int n_chan, long long npix, double inv_t) {
+    const long long n = (long long)n_chan * npix;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i / npix, k = i - c * npix;
+        const double* s = accum4 + c * 4 * npix + k;
+        const double s0 = s[0], s1 = s[npix], s2 = s[2 * npix], s3 = s[3 * npix];
+        if (image) {
+            image[(2 * c) * npix + k] = float(s0 * inv_t);
+            image[(2 * c + 1) * npix + k] = float(s1 * inv_t);
+        }
+        if (cross) {
+            const double h = 0.5 * inv_t;
+            cross[c * npix + k] = make_float2(float((s2 - s0 - s1) * h), float((s3 - s0 - s1) * h));
+        }
+    }
+}
+
+cudaError_t launch_finalize_xpol(const double* accum4, float* image, float2* cross, int n_chan, long long npix,
+                                 double inv_t, cudaStream_t st) {
+    const long long n = (long long)n_chan * npix;
+    if (n == 0 || (!image && !cross)) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    finalize_xpol_kernel<<<(unsigned)blocks, 256, 0, st>>>(accum4, image, cross, n_chan, npix, inv_t);
+    return cudaGetLastError();
+}
+
 constexpr int kAcThreads = 512;
 
 // One block per (channel, pol).  Shared: U [L*L] float2, T1 [L][N_p] float2, twiddles
@@ -130,6 +164,17 @@ size_t fwd_smem_bytes(int n_pad, int n_ant) {
         case 128: return Geo<128>::smem_bytes(n_ant);
         case 256: return Geo<256>::smem_bytes(n_ant);
         case 512: return Geo<512>::smem_bytes(n_ant);
+        default: return 0;
+    }
+}
+
+size_t fwd_xpol_smem_bytes(int n_pad, int n_ant) {
+    switch (n_pad) {
+        case 32: return Geo<32>::smem_bytes_xpol(n_ant);
+        case 64: return Geo<64>::smem_bytes_xpol(n_ant);
+        case 128: return Geo<128>::smem_bytes_xpol(n_ant);
+        case 256: return Geo<256>::smem_bytes_xpol(n_ant);
+        case 512: return Geo<512>::smem_bytes_xpol(n_ant);
         default: return 0;
     }
 }

@@ -63,6 +63,8 @@ template <int NP> struct Geo {
         return sizeof(float2) * (size_t(ROWS) * RXS + size_t(NG) * RBS + TWN)
              + size_t(n_ant) * (2 * sizeof(float2) + sizeof(float));
     }
+    // the cross-polarisation form adds a table of phi_v g_Y per antenna (8-byte aligned)
+    static constexpr size_t smem_bytes_xpol(int n_ant) { return smem_bytes(n_ant) + size_t(n_ant + 2) * sizeof(float2); }
 
     // Fill the twiddle table from the plan's exp(+2 pi i j / NP) table.
     static __device__ __forceinline__ void load_twiddles(float2* TW, const float2* tw, int tid, int nt) {

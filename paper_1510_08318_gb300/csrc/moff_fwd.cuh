@@ -20,6 +20,12 @@
 //   column pass      thread (column, n1) reads the N_g non-zero rows of its column, does
 //                    the same two stages along y, squares and accumulates.
 // Two CTA (cluster) barriers per item; everything else is warp-synchronous.
+//
+// Cross-polarisation variant (XP): the sub-array has two pols and its (channel, pol) index
+// runs over 4 C virtual pols v = 0..3 per channel, v = 0: X, 1: Y, 2: X + Y, 3: X + iY, whose
+// gridded fields are g_X V_X (+ phi_v g_Y V_Y), phi_2 = 1, phi_3 = i.  Since the transform is
+// linear, the sums of |F_v|^2 give the cross power F_X conj(F_Y) through the polarisation
+// identity (Re = (S_2 - S_0 - S_1) / 2, Im = (S_3 - S_0 - S_1) / 2), evaluated in the epilogue.
 #pragma once
 #include "moff_common.cuh"
 
@@ -36,7 +42,7 @@ __device__ __forceinline__ int item_at_cost(const SegList& L, long long c) {
     return L.first[s] + (int)(i < n_s ? i : n_s);
 }
 
-template <int NP, int VDT>
+template <int NP, int VDT, bool XP>
 __global__ void __launch_bounds__(Geo<NP>::NT, Geo<NP>::MINB)
 moff_fwd_kernel(const __grid_constant__ SegList L) {
     using G = Geo<NP>;
@@ -51,6 +57,7 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
     float2* VB = TW + G::TWN;                                    // [A] g_a V_a
     float2* GN = VB + L.max_ant;                             // [A] gains
     float* PW = reinterpret_cast<float*>(GN + L.max_ant);    // [A] partial sum |g V|^2
+    float2* GY = reinterpret_cast<float2*>(PW + ((L.max_ant + 1) & ~1));   // XP: [A] phi_v g_Y
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n1 = lane % S;
@@ -85,18 +92,33 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
 #pragma unroll
         for (int i = 0; i < R1; ++i) acc[s][i] = 0.f;
 
-    VT raw[VPT];
+    // voltage row of (channel*pol cp, time t) of sub-array sp (volt = its voltages): for XP,
+    // cp is virtual and the row is that of pol X of the channel (pol Y follows it), or of
+    // pol Y for v = 1
+    auto volt_row = [&](const FwdArgs* sp, const VT* volt, int cp, int t) -> const VT* {
+        if constexpr (XP) {
+            const int c = cp >> 2, p = (cp & 3) == 1 ? 1 : 0;
+            return volt + ((long long)t * (sp->n_cp >> 1) + 2 * c + p) * (long long)sp->n_ant;
+        } else {
+            return volt + ((long long)t * sp->n_cp + cp) * (long long)sp->n_ant;
+        }
+    };
+
+    VT raw[VPT], rawy[XP ? VPT : 1];
     // raw voltages of global item g (which may belong to the next sub-array)
     auto prefetch = [&](int g) {
         const FwdArgs* sp = (g < seg_end) ? ap : ap + 1;
         const int li = g - ((g < seg_end) ? seg_first : seg_end);
         const int Tq = sp->n_time, Aq = sp->n_ant;
         const int cp = li / Tq, t = li - cp * Tq;
-        const VT* base = static_cast<const VT*>(sp->volt) + ((long long)t * sp->n_cp + cp) * (long long)Aq;
+        const VT* base = volt_row(sp, static_cast<const VT*>(sp->volt), cp, t);
 #pragma unroll
         for (int i = 0; i < VPT; ++i) {
             const int aa = tid + NT * i;
             if (aa < Aq) raw[i] = __ldg(base + aa);
+            if constexpr (XP) {
+                if (aa < Aq && (cp & 3) >= 2) rawy[i] = __ldg(base + Aq + aa);
+            }
         }
     };
 
@@ -143,8 +165,17 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
         if (cp != cur || since == a.flush_every) {
             if (cur >= 0) flush(cur, true);
             if (cp != cur) {
-                for (int aa = tid; aa < A; aa += NT)
-                    GN[aa] = a.gains ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
+                if constexpr (XP) {
+                    const int c = cp >> 2, v = cp & 3, p = v == 1 ? 1 : 0;
+                    for (int aa = tid; aa < A; aa += NT) {
+                        GN[aa] = a.gains ? a.gains[(size_t)(2 * c + p) * A + aa] : make_float2(1.f, 0.f);
+                        const float2 gy = a.gains ? a.gains[(size_t)(2 * c + 1) * A + aa] : make_float2(1.f, 0.f);
+                        GY[aa] = v == 3 ? make_float2(-gy.y, gy.x) : gy;
+                    }
+                } else {
+                    for (int aa = tid; aa < A; aa += NT)
+                        GN[aa] = a.gains ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
+                }
             }
             cur = cp;
             since = 0;
@@ -153,18 +184,31 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
 
         // ---- decode + gain (owner threads), prefetch the next item ----
         {
-            const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
+            const VT* base = XP ? volt_row(ap, V, cp, t) : V + ((long long)t * a.n_cp + cp) * (long long)A;
+            const bool two = XP && (cp & 3) >= 2;     // virtual pol combining X and Y
 #pragma unroll
             for (int i = 0; i < VPT; ++i) {
                 const int aa = tid + NT * i;
                 if (aa < A) {
-                    const float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[i]));
+                    float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[i]));
+                    if constexpr (XP) {
+                        if (two) {
+                            const float2 w = cmul(GY[aa], Volt<VDT>::dec(rawy[i]));
+                            vp.x += w.x;
+                            vp.y += w.y;
+                        }
+                    }
                     VB[aa] = vp;
                     PW[aa] += cnorm(vp);
                 }
             }
             for (int aa = tid + NT * VPT; aa < A; aa += NT) {
-                const float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
+                float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
+                if (two) {
+                    const float2 w = cmul(GY[aa], Volt<VDT>::dec(__ldg(base + A + aa)));
+                    vp.x += w.x;
+                    vp.y += w.y;
+                }
                 VB[aa] = vp;
                 PW[aa] += cnorm(vp);
             }
@@ -235,12 +279,12 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
 #undef a
 }
 
-template <int NP, int VDT>
+template <int NP, int VDT, bool XP = false>
 cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
     using G = Geo<NP>;
-    auto kern = moff_fwd_kernel<NP, VDT>;
-    const size_t smem = G::smem_bytes(L.max_ant);
-    cudaError_t e = ensure_smem<moff_fwd_kernel<NP, VDT>>(smem);
+    auto kern = moff_fwd_kernel<NP, VDT, XP>;
+    const size_t smem = XP ? G::smem_bytes_xpol(L.max_ant) : G::smem_bytes(L.max_ant);
+    cudaError_t e = ensure_smem<moff_fwd_kernel<NP, VDT, XP>>(smem);
     if (e != cudaSuccess) return e;
     const long long n_items = L.first[L.n_seg];
     if (n_items == 0) return cudaSuccess;
@@ -288,9 +332,9 @@ cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
 template <int NP, int VDT>
 int resident_fwd_workers_t(int max_ant, int n_sm) {
     using G = Geo<NP>;
-    auto kern = moff_fwd_kernel<NP, VDT>;
+    auto kern = moff_fwd_kernel<NP, VDT, false>;
     const size_t smem = G::smem_bytes(max_ant);
-    if (ensure_smem<moff_fwd_kernel<NP, VDT>>(smem) != cudaSuccess) return 0;
+    if (ensure_smem<moff_fwd_kernel<NP, VDT, false>>(smem) != cudaSuccess) return 0;
     if constexpr (G::Q == 1) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem) != cudaSuccess) return 0;

@@ -4,11 +4,11 @@
 
 namespace epic {
 
-cudaError_t launch_fwd_512(int vdt, const SegList& L, int n_sm, cudaStream_t st) {
+cudaError_t launch_fwd_512(int vdt, const SegList& L, int n_sm, cudaStream_t st, bool xpol) {
     switch (vdt) {
-        case 0: return launch_fwd_t<512, 0>(L, n_sm, st);
-        case 1: return launch_fwd_t<512, 1>(L, n_sm, st);
-        case 2: return launch_fwd_t<512, 2>(L, n_sm, st);
+        case 0: return xpol ? launch_fwd_t<512, 0, true>(L, n_sm, st) : launch_fwd_t<512, 0>(L, n_sm, st);
+        case 1: return xpol ? launch_fwd_t<512, 1, true>(L, n_sm, st) : launch_fwd_t<512, 1>(L, n_sm, st);
+        case 2: return xpol ? launch_fwd_t<512, 2, true>(L, n_sm, st) : launch_fwd_t<512, 2>(L, n_sm, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,7 +1,7 @@
 """Thin Python binding of the MOFF imaging C ABI (include/epic.h).
 
 The functions named like the C entry points (`epic_create`, `epic_image`,
-`epic_image_backward`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
+`epic_image_backward`, `epic_image_xpol`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
 arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
 for torch tensors, and `MoffImage` is the autograd.Function whose backward is the
 library's adjoint kernel.  There is no CPU fallback: if the library has not been built
@@ -21,7 +21,7 @@ EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
-           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid")
+           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol")
 XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
@@ -50,6 +50,8 @@ def load(path=LIB_PATH):
     lib.epic_image.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
     lib.epic_image_backward.restype = i32
     lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
+    lib.epic_image_xpol.restype = i32
+    lib.epic_image_xpol.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp, vp]
     lib.epic_grid.restype = i32
     lib.epic_grid.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.epic_plan_info.restype = i32
@@ -122,6 +124,10 @@ def epic_image(plan, volt, n_time, gains, accum, power, t_prev, image, autocorr,
 
 def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, stream):
     _check(load().epic_image_backward(plan, volt, int(n_time), gains, grad_image, grad_gains, stream))
+
+
+def epic_image_xpol(plan, volt, n_time, gains, accum4, t_prev, image, cross, stream):
+    _check(load().epic_image_xpol(plan, volt, int(n_time), gains, accum4, int(t_prev), image, cross, stream))
 
 
 def epic_grid(plan, volt, n_time, gains, grid, stream):
@@ -267,6 +273,22 @@ class Plan:
         epic_image_backward(self._h, vptr, T, self._gains_ptr(gains), g.data_ptr(), out.data_ptr(),
                             st.cuda_stream)
         return out
+
+    def image_xpol(self, volt, gains=None, accum4=None, t_prev=0, stream=None):
+        """Run epic_image_xpol: dict(image [C, 2, N_p, N_p] float32 (XX, YY), cross [C, N_p, N_p]
+        complex64 (XY = <F_X conj F_Y>), accum4 [C, 4, N_p, N_p] float64)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        vptr, T = self._volt_ptr(volt)
+        C, NP = self.n_chan, self.n_pad
+        if accum4 is None:
+            accum4 = torch.empty((C, 4, NP, NP), dtype=torch.float64, device=dev)
+        img = torch.empty((C, 2, NP, NP), dtype=torch.float32, device=dev)
+        cross = torch.empty((C, NP, NP), dtype=torch.complex64, device=dev)
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        epic_image_xpol(self._h, vptr, T, self._gains_ptr(gains), accum4.data_ptr(), t_prev, img.data_ptr(),
+                        cross.data_ptr(), st.cuda_stream)
+        return {"image": img, "cross": cross, "accum4": accum4}
 
     def grid(self, volt, gains=None, out=None, stream=None):
         """Run epic_grid: the gridded fields E_t(g), complex64 CUDA tensor [T, C, P, N_g, N_g]."""

@@ -297,3 +297,55 @@ def test_grad_gains_finite_difference():
                 d = (loss(gp) - loss(gm)) / (2 * h)
                 fd[c, 0, a] += d * part
     np.testing.assert_allclose(grad, fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+
+
+# ----------------------------------------------------------------------------------
+# cross-polarisation products (Sec. 3; App. A image module)
+# ----------------------------------------------------------------------------------
+def _dual_pol(wl, alpha, seed):
+    """[T, 1, 2, A]: pol X = the workload's voltages, pol Y = alpha X + independent noise."""
+    rng = np.random.default_rng(seed)
+    vx = wl.volt[:, :1, 0, :]
+    noise = rng.standard_normal(vx.shape) + 1j * rng.standard_normal(vx.shape)
+    return np.stack([vx, alpha * vx + 0.5 * noise], axis=2)
+
+
+def test_cross_pol_equals_fx_exact(tiny):
+    """MOFF cross-polarisation products equal the FX route with cross-polarised visibilities
+    V^{pq}_ab = <E_ap E_bq^*> (Sec. 2 equivalence, per polarisation pair)."""
+    wl, M, gains = tiny
+    v = _dual_pol(wl, 0.6 - 0.3j, 11)
+    g = np.stack([gains[:, 0], np.conj(gains[:, 0]) * 1.1], axis=1)     # [1, 2, A]
+    I_m = moff.moff_cross_image(M, v, g, wl.n_grid, wl.n_pad)
+    I_x = fx.fx_cross_image(M, v, g, wl.n_grid, wl.n_pad)
+    rel = np.linalg.norm(I_m - I_x) / np.linalg.norm(I_m)
+    assert rel < 1e-12
+    assert np.linalg.norm(I_m[0, 0, 1]) > 0.1 * np.linalg.norm(I_m[0, 0, 0])   # a real XY signal
+
+
+def test_cross_pol_special_cases(tiny):
+    """Diagonal = the single-pol image; YX = conj(XY); for a fully polarised field E_Y = alpha E_X
+    the products are XY = conj(alpha) XX and YY = |alpha|^2 XX (a swapped conjugate fails)."""
+    wl, M, _ = tiny
+    alpha = 0.7 + 0.4j
+    vx = wl.volt[:, :1, 0, :]
+    v = np.stack([vx, alpha * vx], axis=2)
+    I = moff.moff_cross_image(M, v, None, wl.n_grid, wl.n_pad)
+    xx = moff.moff_image(M, v, None, wl.n_grid, wl.n_pad)
+    np.testing.assert_allclose(I[0, 0, 0].real, xx[0, 0], rtol=1e-12, atol=1e-12 * xx.max())
+    np.testing.assert_allclose(I[0, 1, 1].real, xx[0, 1], rtol=1e-12, atol=1e-12 * xx.max())
+    np.testing.assert_allclose(I[0, 1, 0], np.conj(I[0, 0, 1]), rtol=0, atol=1e-12 * xx.max())
+    np.testing.assert_allclose(I[0, 0, 1], np.conj(alpha) * I[0, 0, 0], rtol=0, atol=1e-12 * xx.max())
+    np.testing.assert_allclose(I[0, 1, 1], abs(alpha) ** 2 * I[0, 0, 0], rtol=0, atol=1e-12 * xx.max())
+
+
+def test_cross_pol_parseval(tiny):
+    """sum_k I_XY(k) = N_p^2 mean_t sum_g E_X(g) conj(E_Y(g)) (Parseval for the product)."""
+    wl, M, _ = tiny
+    v = _dual_pol(wl, -0.2 + 0.9j, 12)
+    I = moff.moff_cross_image(M, v, None, wl.n_grid, wl.n_pad)
+    one = np.ones(wl.n_ant, dtype=np.complex128)
+    ex = moff.grid_efields(M, v[:, 0, 0, :], one, wl.n_grid)
+    ey = moff.grid_efields(M, v[:, 0, 1, :], one, wl.n_grid)
+    want = wl.n_pad ** 2 * (ex * np.conj(ey)).sum(axis=(1, 2)).mean()
+    assert abs(I[0, 0, 1].sum() - want) < 1e-10 * abs(want)
