@@ -173,6 +173,25 @@ epic_status epic_image_xpol(const epic_plan *plan, const void *volt, int n_time,
                             double *accum4, int64_t t_prev, float *image, float *cross, void *stream);
 
 /*
+ * epic_correlate -- the X-engine of the FX route (Sec. 3, the FX flow; Eq. "cc-vis"): the
+ * visibilities of every ordered antenna pair of every (channel, pol), autocorrelations
+ * included,
+ *   vis[c][p][a][b] = g_a conj(g_b) (1/T) sum_t V_a(t) conj(V_b(t)),
+ * i.e. the time average of E_a conj(E_b) of the calibrated fields.  vis is Hermitian in (a, b).
+ *
+ *   volt, n_time, gains  as for epic_image; the plan's voltages must be FP16 or 4+4-bit
+ *             (EPIC_EUNSUPPORTED for complex64).  n_time <= 131072.
+ *   vis       device [C][P][A][A] complex64, row-major (a, b); overwritten; 8-byte aligned.
+ *
+ * Computed on the tensor cores as two real products with FP16 operands (the voltages are exact
+ * in FP16) and FP32 accumulation: for 4+4-bit voltages the sums over the call are exact; the
+ * gains and 1/T are applied in FP32 afterwards.  Each call is one integration (no
+ * continuation).  The plan's mapping is not used.
+ */
+epic_status epic_correlate(const epic_plan *plan, const void *volt, int n_time, const float *gains,
+                           float *vis, void *stream);
+
+/*
  * epic_grid -- the gridding step alone (Sec. 3, gridding convolution): for every sample
  * t and (channel, pol), E_t(g) = sum_a M[g, a] g_a V_a(t) on the plan's N_g x N_g grid
  * (no zero padding, no transform), written to device memory.

@@ -546,6 +546,32 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     return EPIC_OK;
 }
 
+epic_status epic_correlate(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* vis,
+                           void* stream) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
+    if (!volt || !vis) return epic_fail(EPIC_EINVAL, "NULL device array");
+    if (reinterpret_cast<uintptr_t>(vis) % 8 != 0) return epic_fail(EPIC_EINVAL, "vis must be 8-byte aligned");
+    if (plan->vdt == EPIC_VOLT_C64)
+        return epic_fail(EPIC_EUNSUPPORTED, "the correlator takes FP16 or 4+4-bit voltages (exact FP16 operands)");
+    if (n_time > 131072) return epic_fail(EPIC_EUNSUPPORTED, "n_time = %d: at most 131072 samples per call", n_time);
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    if (epic::xeng_smem_bytes() > (size_t)smem_optin) return epic_fail(EPIC_EUNSUPPORTED, "shared memory");
+    epic::XengArgs a;
+    a.volt = volt;
+    a.n_time = n_time;
+    a.n_cp = plan->n_chan * plan->n_pol;
+    a.n_ant = plan->n_ant;
+    a.gains = reinterpret_cast<const float2*>(gains);
+    a.vis = reinterpret_cast<float2*>(vis);
+    const cudaError_t e = epic::launch_xeng(plan->vdt, a, plan->n_sm, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "correlator kernel launch");
+}
+
 epic_status epic_grid(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* grid,
                       void* stream) {
     epic_clear_error();

@@ -68,6 +68,16 @@ struct BwdArgs {
     float scale;               // 2 / T
 };
 
+// X-engine of the FX route (xeng.cu): visibilities of every antenna pair.
+struct XengArgs {
+    const void* volt;          // [T][C][P][A] raw voltages (FP16 or 4+4-bit)
+    int n_time, n_cp, n_ant;
+    const float2* gains;       // [CP][A] or nullptr (unit gains)
+    float2* vis;               // [CP][A][A]
+};
+size_t xeng_smem_bytes();
+cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st);
+
 // Standalone gridder (grid.cu): E_t(g) for every sample of a call, written to device memory.
 struct GridArgs {
     const void* volt;          // [T][C][P][A] raw voltages

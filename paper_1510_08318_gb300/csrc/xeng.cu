@@ -1,0 +1,228 @@
+// X-engine of the FX route (Sec. 3 "FX" flow; Eq. "cc-vis"): the visibilities
+//   V_ab = g_a conj(g_b) (1/T) sum_t V_a(t) conj(V_b(t))
+// of every antenna pair of every (channel, pol), as a Hermitian product E E^H on the
+// 5th-generation tensor cores.
+//
+// Per (channel, pol) the voltages form E [A x T] complex.  With the K index interleaving real
+// and imaginary parts, k = 2t + {0, 1}:
+//   X_a = (Re E_a(t), Im E_a(t))_t,    W_b = (-Im E_b(t), Re E_b(t))_t,
+//   Re V_ab = sum_k X_a[k] X_b[k],     Im V_ab = sum_k X_a[k] W_b[k],
+// two real matrix products D_re = X X^T and D_im = X W^T with K = 2T.  4+4-bit and FP16
+// voltages are exact in FP16, and each product (at most 64 in magnitude for 4+4-bit) is
+// accumulated in FP32 exactly while the sums stay below 2^24, so the raw sums are exact.
+//
+// Work unit: a 128 x 128 block (antenna rows a in block ab, columns b in block bb, bb >= ab:
+// the upper block triangle, the lower one follows by Hermitian symmetry) of one (channel,
+// pol).  K is walked in chunks of 32 samples (K = 64): all 512 threads decode the chunk's
+// voltages into K-major FP16 tiles (X of the row block, X and W of the column block; a
+// diagonal block reuses X of the column block for the rows) in one of two shared-memory
+// stages, then one thread issues 2 x 4 MMAs (M = N = 128, K = 16) into the unit's TMEM
+// accumulators and commits them to the stage's mbarrier, which releases the stage for the
+// chunk after next.  After a unit's last chunk its accumulators are read back (tcgen05.ld),
+// scaled by g_a conj(g_b) / T and written, with the mirrored conjugate block for off-diagonal
+// units.  Every wait on the tensor cores is bounded; on a timeout the CTA writes NaN into its
+// first output element and stops.
+#include <cuda_fp16.h>
+#include <cstdint>
+#include "moff_common.cuh"
+#include "tcgen05.cuh"
+
+namespace epic {
+namespace xe {
+using namespace tc;
+
+constexpr int NT = 512;
+constexpr int TC = 32;              // samples per K chunk
+constexpr int KC = 2 * TC;          // K per chunk (re/im interleaved)
+constexpr int TILE = 128 * KC;      // halves per operand tile (16 KB)
+enum { T_XA, T_XB, T_WB, N_TILE };
+constexpr int NSTAGE = 2;
+
+constexpr size_t smem_bytes() { return sizeof(__half) * (size_t)NSTAGE * N_TILE * TILE + 64; }
+
+// unit -> (cp, row block, column block), column block >= row block
+__device__ __forceinline__ void unit_coords(long long u, int nab, int& cp, int& ab, int& bb) {
+    const int upc = nab * (nab + 1) / 2;
+    cp = (int)(u / upc);
+    int r = (int)(u - (long long)cp * upc);
+    ab = 0;
+    while (r >= nab - ab) {
+        r -= nab - ab;
+        ++ab;
+    }
+    bb = ab + r;
+}
+
+template <int VDT>
+__global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
+    using VT = typename Volt<VDT>::T;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __half* sT = reinterpret_cast<__half*>(smem_raw);                           // [NSTAGE][N_TILE][TILE]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sT + NSTAGE * N_TILE * TILE);   // [NSTAGE] stages, [2] accumulator
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + NSTAGE + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int A = a.n_ant, T = a.n_time, CP = a.n_cp;
+    const int nab = (A + 127) / 128;
+    const long long n_units = (long long)CP * (nab * (nab + 1) / 2);
+    const int n_chunks = (T + TC - 1) / TC;
+    const VT* V = static_cast<const VT*>(a.volt);
+
+    if (tid == 0) {
+        for (int s = 0; s <= NSTAGE; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[s])), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(256) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tRe = tmem, tIm = tmem + 128;
+    const uint32_t mb_acc = smem_u32(&mbar[NSTAGE]);
+    const uint64_t d0 = sdesc(smem_u32(sT), 1024);
+    constexpr int kTileStep = 2 * TILE / 16;        // descriptor start-field step per tile
+    constexpr uint32_t id = idesc(128);
+
+    long long beg, end;
+    work_range(n_units, blockIdx.x, gridDim.x, beg, end);
+
+    // decode mapping: lane -> (row % 8, sample % 4), so that one warp's 4-byte stores cover 32
+    // distinct banks of a core-matrix row block; combination c = (row / 8, sample / 4)
+    const int lr = lane & 7, lt = lane >> 3;
+    bool failed = false;
+    int g = 0;            // chunks issued by this CTA
+    int n_done = 0;       // units finished by this CTA
+    for (long long u = beg; u < end && !failed; ++u) {
+        int cp, ab, bb;
+        unit_coords(u, nab, cp, ab, bb);
+        const bool diag = ab == bb;
+        const int a0 = ab * 128, b0 = bb * 128;
+        for (int kc = 0; kc < n_chunks && !failed; ++kc, ++g) {
+            const int s = g & 1;
+            if (g >= 2 && !mbar_wait(smem_u32(&mbar[s]), ((g - 2) >> 1) & 1)) failed = true;
+            failed = __syncthreads_or(failed) != 0;
+            if (failed) break;
+            __half* st = sT + s * N_TILE * TILE;
+            const int t0 = kc * TC;
+            // column block: X and W tiles
+            for (int c = warp; c < 16 * (TC / 4); c += NT / 32) {
+                const int r = (c & 15) * 8 + lr, tl = (c >> 4) * 4 + lt;
+                const int b = b0 + r, t = t0 + tl;
+                float2 v = make_float2(0.f, 0.f);
+                if (b < A && t < T) v = Volt<VDT>::dec(__ldg(V + ((long long)t * CP + cp) * A + b));
+                const int off = koff(r, 2 * tl, KC);
+                *reinterpret_cast<__half2*>(st + T_XB * TILE + off) = __floats2half2_rn(v.x, v.y);
+                *reinterpret_cast<__half2*>(st + T_WB * TILE + off) = __floats2half2_rn(-v.y, v.x);
+            }
+            if (!diag) {
+                for (int c = warp; c < 16 * (TC / 4); c += NT / 32) {
+                    const int r = (c & 15) * 8 + lr, tl = (c >> 4) * 4 + lt;
+                    const int aa = a0 + r, t = t0 + tl;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (aa < A && t < T) v = Volt<VDT>::dec(__ldg(V + ((long long)t * CP + cp) * A + aa));
+                    *reinterpret_cast<__half2*>(st + T_XA * TILE + koff(r, 2 * tl, KC)) = __floats2half2_rn(v.x, v.y);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                fence_after();
+                const uint64_t dS = d0 + (uint64_t)(s * N_TILE * kTileStep);
+                const uint64_t dA = dS + (uint64_t)((diag ? T_XB : T_XA) * kTileStep);
+                const uint64_t dX = dS + (uint64_t)(T_XB * kTileStep), dW = dS + (uint64_t)(T_WB * kTileStep);
+#pragma unroll
+                for (int j = 0; j < KC / 16; ++j) {
+                    const uint32_t acc = (kc | j) != 0;
+                    mma_ss(tRe, dA + 16 * j, dX + 16 * j, id, acc);
+                    mma_ss(tIm, dA + 16 * j, dW + 16 * j, id, acc);
+                }
+                commit(smem_u32(&mbar[s]));
+                if (kc == n_chunks - 1) commit(mb_acc);
+            }
+        }
+        if (failed) break;
+        // ---- epilogue: D -> V_ab = g_a conj(g_b) D / T (and the mirrored block) ----
+        if (!mbar_wait(mb_acc, n_done & 1)) failed = true;
+        failed = __syncthreads_or(failed) != 0;
+        if (failed) break;
+        fence_after();
+        {
+            const int q = warp & 3, part = warp >> 2;            // TMEM lane quarter, 32-column part
+            const int r = 32 * q + lane, aa = a0 + r;
+            const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+            const float inv_t = 1.f / float(T);
+            const float2 ga = (aa < A && a.gains) ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
+            float2* out = a.vis + (size_t)cp * A * A;
+#pragma unroll
+            for (int c = 0; c < 32; c += 16) {
+                float dr[16], di[16];
+                tld<16>(tRe + lane_base + 32 * part + c, dr);
+                tld<16>(tIm + lane_base + 32 * part + c, di);
+                tld_wait();
+                if (aa < A) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int b = b0 + 32 * part + c + j;
+                        if (b < A) {
+                            const float2 gb = a.gains ? __ldg(a.gains + (size_t)cp * A + b) : make_float2(1.f, 0.f);
+                            const float2 w = cmul(ga, make_float2(gb.x, -gb.y));
+                            const float2 v = cmul(w, make_float2(dr[j] * inv_t, di[j] * inv_t));
+                            out[(size_t)aa * A + b] = v;
+                            if (!diag) out[(size_t)b * A + aa] = make_float2(v.x, -v.y);
+                        }
+                    }
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();     // accumulators read before the next unit's first MMA overwrites them
+        ++n_done;
+    }
+    if (failed) {
+        if (tid == 0 && beg < end) {
+            int cp, ab, bb;
+            unit_coords(beg, nab, cp, ab, bb);
+            a.vis[(size_t)cp * A * A + (size_t)(ab * 128) * A + bb * 128] =
+                make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+        }
+        // wait (bounded) for the MMAs still in flight: each stage's last commit
+        for (int k = g - 1; k >= 0 && k >= g - 2; --k) mbar_wait(smem_u32(&mbar[k & 1]), (k >> 1) & 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256) : "memory");
+}
+
+}  // namespace xe
+
+size_t xeng_smem_bytes() { return xe::smem_bytes(); }
+
+cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st) {
+    const int nab = (a.n_ant + 127) / 128;
+    const long long n_units = (long long)a.n_cp * (nab * (nab + 1) / 2);
+    if (n_units == 0) return cudaSuccess;
+    const long long grid = n_units < n_sm ? n_units : n_sm;
+    const size_t smem = xe::smem_bytes();
+    cudaError_t e;
+    switch (vdt) {
+        case 1:
+            e = ensure_smem<xe::xeng_kernel<1>>(smem);
+            if (e != cudaSuccess) return e;
+            xe::xeng_kernel<1><<<(unsigned)grid, xe::NT, smem, st>>>(a);
+            return cudaGetLastError();
+        case 2:
+            e = ensure_smem<xe::xeng_kernel<2>>(smem);
+            if (e != cudaSuccess) return e;
+            xe::xeng_kernel<2><<<(unsigned)grid, xe::NT, smem, st>>>(a);
+            return cudaGetLastError();
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace epic

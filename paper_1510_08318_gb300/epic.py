@@ -1,7 +1,7 @@
 """Thin Python binding of the MOFF imaging C ABI (include/epic.h).
 
 The functions named like the C entry points (`epic_create`, `epic_image`,
-`epic_image_backward`, `epic_image_xpol`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
+`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
 arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
 for torch tensors, and `MoffImage` is the autograd.Function whose backward is the
 library's adjoint kernel.  There is no CPU fallback: if the library has not been built
@@ -21,7 +21,7 @@ EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
-           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol")
+           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate")
 XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
@@ -52,6 +52,8 @@ def load(path=LIB_PATH):
     lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.epic_image_xpol.restype = i32
     lib.epic_image_xpol.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp, vp]
+    lib.epic_correlate.restype = i32
+    lib.epic_correlate.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.epic_grid.restype = i32
     lib.epic_grid.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.epic_plan_info.restype = i32
@@ -128,6 +130,10 @@ def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, strea
 
 def epic_image_xpol(plan, volt, n_time, gains, accum4, t_prev, image, cross, stream):
     _check(load().epic_image_xpol(plan, volt, int(n_time), gains, accum4, int(t_prev), image, cross, stream))
+
+
+def epic_correlate(plan, volt, n_time, gains, vis, stream):
+    _check(load().epic_correlate(plan, volt, int(n_time), gains, vis, stream))
 
 
 def epic_grid(plan, volt, n_time, gains, grid, stream):
@@ -289,6 +295,21 @@ class Plan:
         epic_image_xpol(self._h, vptr, T, self._gains_ptr(gains), accum4.data_ptr(), t_prev, img.data_ptr(),
                         cross.data_ptr(), st.cuda_stream)
         return {"image": img, "cross": cross, "accum4": accum4}
+
+    def correlate(self, volt, gains=None, out=None, stream=None):
+        """Run epic_correlate: visibilities <g_a V_a conj(g_b V_b)>_t, complex64 [C, P, A, A]."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        vptr, T = self._volt_ptr(volt)
+        shape = (self.n_chan, self.n_pol, self.n_ant, self.n_ant)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device=dev)
+        elif (out.dtype != torch.complex64 or tuple(out.shape) != shape or not out.is_cuda
+              or not out.is_contiguous()):
+            raise ValueError("out must be a contiguous complex64 CUDA tensor %s" % (shape,))
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        epic_correlate(self._h, vptr, T, self._gains_ptr(gains), out.data_ptr(), st.cuda_stream)
+        return out
 
     def grid(self, volt, gains=None, out=None, stream=None):
         """Run epic_grid: the gridded fields E_t(g), complex64 CUDA tensor [T, C, P, N_g, N_g]."""

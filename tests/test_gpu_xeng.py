@@ -1,0 +1,123 @@
+"""X-engine of the FX route (epic_correlate) vs the FP64 oracle's visibilities (GPU only).
+
+Tolerance: for 4+4-bit voltages the tensor-core sums are exact integers (FP16 operands, FP32
+accumulation below 2^24), so the only rounding is the FP32 scaling by 1/T and the gains:
+relative L2 < 1e-6 per (channel, pol) matrix and every element within 1e-6 of the largest.
+FP16 voltages: products are exact in FP32, their sums round; the same bound holds with
+margin for the sample counts used here.
+"""
+import numpy as np
+import pytest
+
+from oracle import fx, moff
+from paper_1510_08318_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def epic():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_08318_gb300 import build, epic as ep
+    build.build()
+    ep.load()
+    return ep
+
+
+def run(epic, wl, gains=None):
+    plan = epic.Plan.from_workload(wl)
+    g = None if gains is None else torch.from_numpy(np.ascontiguousarray(gains.astype(np.complex64))).cuda()
+    vis = plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda(), g)
+    torch.cuda.synchronize()
+    return plan, vis.cpu().numpy()
+
+
+def check(got, wl, gains, what):
+    T, C, P, A = wl.volt.shape
+    for c in range(C):
+        for p in range(P):
+            g = np.ones(A, dtype=np.complex128) if gains is None else gains[c, p].astype(np.complex128)
+            want = fx.visibilities(wl.volt[:, c, p, :], g)
+            err = got[c, p] - want
+            assert np.linalg.norm(err) / np.linalg.norm(want) < TOL, (what, c, p)
+            assert np.abs(err).max() < TOL * np.abs(want).max(), (what, c, p)
+            # Hermitian (mirrored blocks are written as exact conjugates)
+            assert np.abs(got[c, p] - np.conj(got[c, p].T)).max() <= 1e-6 * np.abs(want).max(), (what, "hermitian")
+
+
+def _small(n_ant, n_time, n_chan, n_pol, vdtype, seed, n_grid=24, n_pad=64):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(2.0, n_grid - 3.0, (n_ant, 2))
+    kerns = [synth.kernel_square(rng.uniform(0.5, 2.5), 1 / 3) for _ in range(n_ant)]
+    ptr, dxdy, w = synth.pack_kernels(kerns)
+    wl = synth.Workload("xeng", pos, ptr, dxdy, w, 1.0, np.zeros(2), n_grid, n_pad,
+                        np.full(n_chan, 1e8), n_pol, n_time, vdtype)
+    v = (rng.standard_normal((n_time, n_chan, n_pol, n_ant))
+         + 1j * rng.standard_normal((n_time, n_chan, n_pol, n_ant)))
+    return synth._finish(wl, v, vdtype)
+
+
+def test_lwa_slice_ci4_gains(epic):
+    """LWA-like 4+4-bit voltages, 256 antennas (2 x 2 blocks), two channels x two pols, 70
+    samples (a ragged 32-sample chunk), random gains."""
+    wl = synth.workload_lwa(n_chan=2, n_time=70, chan_index=[0, 127])
+    g = synth.random_gains(np.random.default_rng(8), (wl.n_chan, wl.n_pol, wl.n_ant))
+    _, vis = run(epic, wl, g)
+    check(vis, wl, g, "lwa")
+
+
+def test_hera_slice_f16(epic):
+    """331 antennas (3 x 3 blocks with a 75-antenna tail), FP16 voltages, 40 samples."""
+    wl = synth.workload_hera(n_chan=2, n_time=40)
+    _, vis = run(epic, wl)
+    check(vis, wl, None, "hera")
+
+
+@pytest.mark.parametrize("n_ant, n_time, n_chan, n_pol, vdtype", [
+    (1, 1, 1, 1, "ci4"),        # one antenna, one sample
+    (129, 31, 1, 2, "f16"),     # a one-antenna tail block, less than one chunk
+    (300, 33, 2, 1, "ci4"),     # three blocks, one sample past a chunk
+    (640, 64, 1, 1, "ci4"),     # five full blocks, two full chunks
+])
+def test_small_shapes(epic, n_ant, n_time, n_chan, n_pol, vdtype):
+    wl = _small(n_ant, n_time, n_chan, n_pol, vdtype, seed=n_ant + n_time)
+    g = synth.random_gains(np.random.default_rng(n_ant), (n_chan, n_pol, n_ant))
+    _, vis = run(epic, wl, g)
+    check(vis, wl, g, "A=%d T=%d" % (n_ant, n_time))
+
+
+def test_fx_image_from_gpu_visibilities_equals_moff(epic):
+    """The two routes of Sec. 2 on the same data: the FX image formed (by the oracle's lag-plane
+    gridding and transform) from the GPU's visibilities equals the GPU's MOFF image."""
+    wl = _small(48, 40, 1, 1, "f16", seed=5, n_grid=24, n_pad=64)
+    plan, vis = run(epic, wl)
+    M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+    img_fx = fx.image_from_uv(fx.uv_plane(M, vis[0, 0].astype(np.complex128), wl.n_grid), wl.n_grid, wl.n_pad)
+    img = plan.image(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())["image"].cpu().numpy()[0, 0]
+    assert np.abs(img_fx.imag).max() < 1e-5 * img.max()
+    assert np.linalg.norm(img_fx.real - img) / np.linalg.norm(img) < 1e-5
+
+
+def test_full_lwa_workload_sampled(epic):
+    """The full LWA-like call (128 channels x 2 pols x 1024 samples) in the bench's launch;
+    three (channel, pol) matrices against the oracle."""
+    wl = synth.workload_lwa()
+    plan = epic.Plan.from_workload(wl)
+    vis = plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())
+    torch.cuda.synchronize()
+    one = np.ones(wl.n_ant, dtype=np.complex128)
+    for c, p in ((0, 0), (64, 1), (127, 1)):
+        want = fx.visibilities(wl.volt[:, c, p, :], one)
+        got = vis[c, p].cpu().numpy()
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < TOL, (c, p)
+
+
+def test_rejects_complex64(epic):
+    wl = synth.workload_tiny(n_time=2)
+    plan = epic.Plan.from_workload(wl)
+    with pytest.raises(epic.EpicError):
+        plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())
