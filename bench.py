@@ -55,11 +55,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--channels", type=int, default=128,
                    help="image only the first C of the 128 channels (small profiling case)")
-    p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid", "xpol"],
+    p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid", "xpol", "fx",
+                                                          "crossover"],
                    help="lwa: the headline workload; batch: 64 heterogeneous sub-arrays, one graph launch; "
                         "calib: forward + adjoint of the gain-calibration workload; "
                         "grid: the standalone gridder (epic_grid) on the headline workload; "
-                        "xpol: all four cross-polarisation images (epic_image_xpol) of the headline workload")
+                        "xpol: all four cross-polarisation images (epic_image_xpol) of the headline workload; "
+                        "fx: the FX-route correlator (epic_correlate) on the headline workload; "
+                        "crossover: MOFF imaging vs the FX correlator per sample over antenna counts")
     return p.parse_args()
 
 
@@ -520,6 +523,170 @@ def run_xpol(args):
         print(json.dumps(line))
 
 
+def _xeng_flops(n_ant, n_cp, n_time):
+    """Tensor-core FLOP the correlator executes: per (channel, pol) the upper triangle of
+    128 x 128 blocks, 2 real products (re, im) x 2 x 128 x 128 x (2 x 32 x chunks)."""
+    nab = (n_ant + 127) // 128
+    chunks = (n_time + 31) // 32
+    return n_cp * nab * (nab + 1) // 2 * 2 * 2.0 * 128 * 128 * 64 * chunks
+
+
+def run_fx(args):
+    """The FX route's X-engine on the headline workload: visibilities of all 256 x 256 antenna
+    pairs for 128 channels x 2 pols from 1024 samples (epic_correlate, tensor cores)."""
+    import numpy as np
+    import torch
+    from oracle import fx
+    from paper_1510_08318_gb300 import build, epic, synth
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = synth.workload_lwa(n_chan=args.channels)
+    plan = epic.Plan.from_workload(wl, device=local)
+    A, T, C, P = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol
+    volt = torch.from_numpy(wl.volt_raw).to(dev)
+    vis = torch.empty((C, P, A, A), dtype=torch.complex64, device=dev)
+    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
+    host_vis = torch.empty(vis.shape, dtype=torch.complex64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def step():
+        epic.epic_correlate(plan._h, volt.data_ptr(), T, None, vis.data_ptr(), st.cuda_stream)
+
+    def e2e_step():
+        volt.copy_(host_v, non_blocking=True)
+        step()
+        host_vis.copy_(vis, non_blocking=True)
+
+    def timed(fn, clocks=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ms, clk = timed(step, Clocks(local))
+    e2e_ms, _ = timed(e2e_step)
+    units = A * T * C * P
+    flop = _xeng_flops(A, C * P, T)
+    peak = MEASURED["bf16_tflops"]
+    roof = {"bound": "tensor", "achieved": flop / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "traffic": None, "executed_flop": flop,
+            "unique_flop": 4.0 * A * (A + 1) * T * C * P,
+            "peak_basis": "measured dense bf16 burst GEMM (FP16 has the same nominal rate), of measured"}
+    roof["frac"] = roof["achieved"] / peak
+    cb, err = None, None
+    if rank == 0:
+        n_s = min(C, 32)
+        one = np.ones(A, dtype=np.complex128)
+        t0 = time.perf_counter()
+        want = [fx.visibilities(wl.volt[:, c, p, :], one) for c in range(C - n_s, C) for p in range(P)]
+        dt = time.perf_counter() - t0
+        got = vis[C - n_s:].cpu().numpy().reshape(n_s * P, A, A)
+        err = float(max(np.linalg.norm(g - w) / np.linalg.norm(w) for g, w in zip(got, want)))
+        if not args.no_cpu_baseline:
+            cb = {"value": A * T * n_s * P / dt, "unit": UNIT,
+                  "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+                  "sample": "channels %d-%d, both pols, all %d samples (%d antenna-samples): FP64 V^T conj(V) "
+                            "(BLAS); %.2f s" % (C - n_s, C - 1, T, A * T * n_s * P, dt)}
+    line = {"metric": "FX correlator antenna-samples/s (visibilities of all pairs)", "value":
+            job_throughput(units, world, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16 operands, f32 accumulation", "data": "synthetic",
+            "config": {"workload": wl.name + ", FX-route correlator (epic_correlate)",
+                       "pairs_per_cp": A * A, "l2": "flushed (256 MB write) before every timed step"},
+            "roofline": roof,
+            "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": UNIT,
+                    "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
+                    "d2h_bytes_per_step": int(host_vis.numel() * 8)},
+            "gpu_launches": args.steps, "clocks": clk,
+            "err_vs_oracle": {"relative_l2_max": err, "sample": "last 32 channels, both pols"}}
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_crossover(args):
+    """MOFF imaging (epic_image, FP32 FFT form) against the FX route's correlator
+    (epic_correlate) per (channel, pol, sample), over antenna counts on the LWA-like grid
+    (N_p = 128, Gaussian apertures, the 100 m x 110 m ellipse filled ever more densely).
+    Voltages are seeded random 4+4-bit bytes (the kernels' work does not depend on values).
+    The FX route's once-per-integration gridding and transform are not included."""
+    import numpy as np
+    import torch
+    from paper_1510_08318_gb300 import build, epic, synth
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    C, P, T = 16, 2, 1024
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(6)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
+
+    rows = []
+    for A in (32, 64, 128, 256, 512, 1024, 2048, 4096):
+        lay = np.random.default_rng(A)
+        pos = synth.layout_ellipse(lay, A, 100.0, 110.0)
+        dx = synth.C_LIGHT / 80e6 / 2
+        kd, kw = synth.kernel_gaussian(1.5, dx / 4)
+        ptr, dxdy, w = synth.pack_kernels([(kd, kw)] * A)
+        origin = synth.centred_origin(pos, 4.5, dx, 64)
+        plan = epic.Plan(pos, ptr, dxdy, w, dx, origin, 64, 128, C, P, "ci4", local)
+        raw = torch.from_numpy(rng.integers(0, 256, (T, C, P, A), dtype=np.uint8)).to(dev)
+        acc = torch.empty((C, P, 128, 128), dtype=torch.float64, device=dev)
+        vis = torch.empty((C, P, A, A), dtype=torch.complex64, device=dev)
+        t_moff = timed(lambda: epic.epic_image(plan._h, raw.data_ptr(), T, None, acc.data_ptr(), None, 0, None,
+                                               None, st.cuda_stream))
+        t_fx = timed(lambda: epic.epic_correlate(plan._h, raw.data_ptr(), T, None, vis.data_ptr(), st.cuda_stream))
+        n = C * P * T
+        rows.append({"antennas": A, "nnz": plan.info["nnz"], "moff_ns_per_sample": 1e6 * t_moff / n,
+                     "fx_correlator_ns_per_sample": 1e6 * t_fx / n, "fx_over_moff": t_fx / t_moff})
+        plan.close()
+        del raw, acc, vis
+    cross = None
+    for r0, r1 in zip(rows, rows[1:]):
+        if r0["fx_over_moff"] < 1.0 <= r1["fx_over_moff"]:
+            # log-log interpolation of the antenna count where the two costs are equal
+            f = math.log(r0["fx_over_moff"]) / (math.log(r0["fx_over_moff"]) - math.log(r1["fx_over_moff"]))
+            cross = r0["antennas"] * (r1["antennas"] / r0["antennas"]) ** f
+    line = {"metric": "MOFF vs FX-correlator time per (channel, pol, sample)", "value": cross,
+            "unit": "antennas at equal cost (N_p = 128 grid)", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "higher_is_better": None, "data": "synthetic (random 4+4-bit bytes)",
+            "config": {"workload": "LWA-like ellipse 100 m x 110 m, Gaussian sigma 1.5 m apertures, N_g 64, "
+                                   "N_p 128, 16 channels x 2 pols x 1024 samples per call",
+                       "fx_scope": "correlator only (the per-integration gridding and transform are excluded)"},
+            "fx_over_moff_at_largest": rows[-1]["fx_over_moff"], "table": rows}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -532,6 +699,10 @@ def main():
         return run_grid(args)
     if args.workload == "xpol":
         return run_xpol(args)
+    if args.workload == "fx":
+        return run_fx(args)
+    if args.workload == "crossover":
+        return run_crossover(args)
     import numpy as np
     import torch
     from paper_1510_08318_gb300 import build, epic, synth

@@ -82,7 +82,9 @@ typedef enum {
  * floor((r_a + delta - origin) / dx + 0.5) evaluated in float64; the weights of samples
  * landing in the same cell are summed (the sparse matrix M(r, a) of Sec. 3).  A sample
  * outside [0, N_g)^2 is EPIC_EINVAL.  The mapping is shared by all channels: it is in
- * metres, and channel c's pixel scale follows from its wavelength.
+ * metres, and channel c's pixel scale follows from its wavelength.  EPIC_EUNSUPPORTED if the
+ * forward kernel's shared memory (per-antenna gains and voltages beside the transform
+ * buffers) cannot hold n_ant antennas at this n_pad.
  */
 epic_status epic_create(epic_plan **plan, int n_ant, const double *pos_xy,
                         const int *kern_ptr, const double *kern_dxdy, const double *kern_w,
@@ -143,7 +145,9 @@ epic_status epic_image(const epic_plan *plan, const void *volt, int n_time, cons
  * the chain rule through Eq. "dirty-image-MOFF" with the gains applied as in Sec. 3
  * "Calibration" (their use in feedback calibration).  The per-sample fields F_t are
  * recomputed, not stored.  volt, n_time and gains are as for epic_image.
- * grad_gains is overwritten (accumulated with float32 atomic adds).
+ * grad_gains is overwritten (accumulated with float32 atomic adds).  EPIC_EUNSUPPORTED if the
+ * adjoint kernel's shared memory cannot hold the plan's antennas at its n_pad (it keeps four
+ * per-antenna arrays; e.g. at most about 2,880 antennas at n_pad 128).
  */
 epic_status epic_image_backward(const epic_plan *plan, const void *volt, int n_time,
                                 const float *gains, const float *grad_image, float *grad_gains,

@@ -370,7 +370,7 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     }
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    const size_t need = std::max(epic::fwd_smem_bytes(n_pad, n_ant), epic::bwd_smem_bytes(n_pad, n_ant));
+    const size_t need = epic::fwd_smem_bytes(n_pad, n_ant);   // the adjoint's own need is checked by its call
     if (need > (size_t)smem_optin) {
         delete p;
         return epic_fail(EPIC_EUNSUPPORTED, "%d antennas need %zu bytes of shared memory per block (device limit %d)",
@@ -489,6 +489,11 @@ epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_t
         return epic_fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
     EpicDeviceGuard guard(plan->device);
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    if (epic::bwd_smem_bytes(plan->n_pad, plan->n_ant) > (size_t)smem_optin)
+        return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the adjoint kernel's shared memory at n_pad %d",
+                         plan->n_ant, plan->n_pad);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int cp = plan->n_chan * plan->n_pol;
     cudaError_t e = cudaMemsetAsync(grad_gains, 0, (size_t)cp * plan->n_ant * 2 * sizeof(float), st);

@@ -13,15 +13,17 @@
 //
 // Work unit: a 128 x 128 block (antenna rows a in block ab, columns b in block bb, bb >= ab:
 // the upper block triangle, the lower one follows by Hermitian symmetry) of one (channel,
-// pol).  K is walked in chunks of 32 samples (K = 64): all 512 threads decode the chunk's
-// voltages into K-major FP16 tiles (X of the row block, X and W of the column block; a
-// diagonal block reuses X of the column block for the rows) in one of two shared-memory
-// stages, then one thread issues 2 x 4 MMAs (M = N = 128, K = 16) into the unit's TMEM
+// pol).  K is walked in chunks of 32 samples (K = 64): the CTA's threads decode the chunk's
+// voltages (loaded into registers during the previous chunk) into K-major FP16 tiles (X of
+// the row block, X and W of the column block; a diagonal block reuses X of the column block
+// for the rows) in one of two shared-memory stages, then one thread issues 2 x 4 MMAs
+// (M = N = 128, K = 16) into the unit's TMEM
 // accumulators and commits them to the stage's mbarrier, which releases the stage for the
 // chunk after next.  After a unit's last chunk its accumulators are read back (tcgen05.ld),
 // scaled by g_a conj(g_b) / T and written, with the mirrored conjugate block for off-diagonal
-// units.  Every wait on the tensor cores is bounded; on a timeout the CTA writes NaN into its
-// first output element and stops.
+// units.  Two 256-thread CTAs share an SM (256 TMEM columns each), so one CTA's decode and
+// loads overlap the other's MMAs.  Every wait on the tensor cores is bounded; on a timeout
+// the CTA writes NaN into its first output element and stops.
 #include <cuda_fp16.h>
 #include <cstdint>
 #include "moff_common.cuh"
@@ -31,7 +33,7 @@ namespace epic {
 namespace xe {
 using namespace tc;
 
-constexpr int NT = 512;
+constexpr int NT = 256;             // two CTAs per SM, 256 TMEM columns each
 constexpr int TC = 32;              // samples per K chunk
 constexpr int KC = 2 * TC;          // K per chunk (re/im interleaved)
 constexpr int TILE = 128 * KC;      // halves per operand tile (16 KB)
@@ -39,6 +41,24 @@ enum { T_XA, T_XB, T_WB, N_TILE };
 constexpr int NSTAGE = 2;
 
 constexpr size_t smem_bytes() { return sizeof(__half) * (size_t)NSTAGE * N_TILE * TILE + 64; }
+
+// FP16 operand pairs of one voltage, as half2 bits: X = (re, im), W = (-im, re).  FP16 input
+// is already the pair.  A 4+4-bit byte holds two 4-bit two's-complement values; XOR with 8
+// biases each to n + 8 in [0, 15], which placed in the mantissa of 1024 (bits 0x6400 | (n + 8))
+// is exactly 1032 + n, so one packed subtraction of 1032 yields both components exactly.
+template <int VDT>
+__device__ __forceinline__ void operand_pairs(typename Volt<VDT>::T raw, uint32_t& x, uint32_t& w) {
+    if constexpr (VDT == 1) {
+        x = raw;
+    } else {
+        const uint32_t t = (uint32_t)raw ^ 0x88u;
+        const uint32_t u = ((t >> 4) & 0xFu) | ((t & 0xFu) << 16) | 0x64006400u;
+        const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&u), __halves2half2(__ushort_as_half(0x6408),
+                                                                                          __ushort_as_half(0x6408)));
+        x = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    w = __byte_perm(x, 0, 0x1032) ^ 0x8000u;     // swap the halves, negate the new low half
+}
 
 // unit -> (cp, row block, column block), column block >= row block
 __device__ __forceinline__ void unit_coords(long long u, int nab, int& cp, int& ab, int& bb) {
@@ -54,11 +74,11 @@ __device__ __forceinline__ void unit_coords(long long u, int nab, int& cp, int& 
 }
 
 template <int VDT>
-__global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
+__global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __half* sT = reinterpret_cast<__half*>(smem_raw);                           // [NSTAGE][N_TILE][TILE]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sT + NSTAGE * N_TILE * TILE);   // [NSTAGE] stages, [2] accumulator
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sT + NSTAGE * N_TILE * TILE);   // [NSTAGE] stages, [1] accumulator
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + NSTAGE + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -92,11 +112,40 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
     work_range(n_units, blockIdx.x, gridDim.x, beg, end);
 
     // decode mapping: lane -> (row % 8, sample % 4), so that one warp's 4-byte stores cover 32
-    // distinct banks of a core-matrix row block; combination c = (row / 8, sample / 4)
+    // distinct banks of a core-matrix row block.  Thread (warp w, lane) owns rows
+    // r0 = 8 w + lane % 8 and r0 + 64 of a tile and samples 4 j + lane / 8, j < TC / 4, of a
+    // chunk: its voltages are V[(t CP + cp) A + row] (one base pointer per tile and a sample
+    // stride), its tile words sit at a fixed offset + 32 j (+ 2048 for the second row).  The raw
+    // voltages of the next chunk are loaded into registers (all at once) while the current
+    // chunk is on the tensor cores.
+    static_assert(NT == 256, "two rows of a 128-row tile per thread");
+    constexpr int NJ = TC / 4;
     const int lr = lane & 7, lt = lane >> 3;
+    const int r0 = 8 * warp + lr;
+    const int sbase = 256 * warp + 4 * lr + lt;      // word offset of (r0, 2 lt) in a tile
+    const long long RS = (long long)CP * A;          // sample stride of the voltages
+    VT rb[2 * NJ], ra[2 * NJ];
+    auto load_chunk = [&](long long u, int kc) {
+        int cp, ab, bb;
+        unit_coords(u, nab, cp, ab, bb);
+        const int tq = kc * TC + lt;
+        const VT* pb = V + (long long)cp * A + bb * 128 + r0 + tq * RS;
+        const VT* pa = V + (long long)cp * A + ab * 128 + r0 + tq * RS;
+        const bool vb0 = bb * 128 + r0 < A, vb1 = bb * 128 + r0 + 64 < A;
+        const bool va0 = ab != bb && ab * 128 + r0 < A, va1 = ab != bb && ab * 128 + r0 + 64 < A;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const bool tin = tq + 4 * j < T;
+            rb[2 * j] = (tin && vb0) ? __ldg(pb + 4 * j * RS) : VT(0);
+            rb[2 * j + 1] = (tin && vb1) ? __ldg(pb + 4 * j * RS + 64) : VT(0);
+            ra[2 * j] = (tin && va0) ? __ldg(pa + 4 * j * RS) : VT(0);
+            ra[2 * j + 1] = (tin && va1) ? __ldg(pa + 4 * j * RS + 64) : VT(0);
+        }
+    };
     bool failed = false;
     int g = 0;            // chunks issued by this CTA
     int n_done = 0;       // units finished by this CTA
+    if (beg < end) load_chunk(beg, 0);
     for (long long u = beg; u < end && !failed; ++u) {
         int cp, ab, bb;
         unit_coords(u, nab, cp, ab, bb);
@@ -108,26 +157,22 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
             failed = __syncthreads_or(failed) != 0;
             if (failed) break;
             __half* st = sT + s * N_TILE * TILE;
-            const int t0 = kc * TC;
-            // column block: X and W tiles
-            for (int c = warp; c < 16 * (TC / 4); c += NT / 32) {
-                const int r = (c & 15) * 8 + lr, tl = (c >> 4) * 4 + lt;
-                const int b = b0 + r, t = t0 + tl;
-                float2 v = make_float2(0.f, 0.f);
-                if (b < A && t < T) v = Volt<VDT>::dec(__ldg(V + ((long long)t * CP + cp) * A + b));
-                const int off = koff(r, 2 * tl, KC);
-                *reinterpret_cast<__half2*>(st + T_XB * TILE + off) = __floats2half2_rn(v.x, v.y);
-                *reinterpret_cast<__half2*>(st + T_WB * TILE + off) = __floats2half2_rn(-v.y, v.x);
-            }
-            if (!diag) {
-                for (int c = warp; c < 16 * (TC / 4); c += NT / 32) {
-                    const int r = (c & 15) * 8 + lr, tl = (c >> 4) * 4 + lt;
-                    const int aa = a0 + r, t = t0 + tl;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (aa < A && t < T) v = Volt<VDT>::dec(__ldg(V + ((long long)t * CP + cp) * A + aa));
-                    *reinterpret_cast<__half2*>(st + T_XA * TILE + koff(r, 2 * tl, KC)) = __floats2half2_rn(v.x, v.y);
+            uint32_t* sxb = reinterpret_cast<uint32_t*>(st + T_XB * TILE) + sbase;
+            uint32_t* swb = reinterpret_cast<uint32_t*>(st + T_WB * TILE) + sbase;
+            uint32_t* sxa = reinterpret_cast<uint32_t*>(st + T_XA * TILE) + sbase;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t x, w;
+                    operand_pairs<VDT>(rb[2 * j + h], x, w);
+                    sxb[32 * j + 2048 * h] = x;
+                    swb[32 * j + 2048 * h] = w;
+                    if (!diag) {
+                        operand_pairs<VDT>(ra[2 * j + h], x, w);
+                        sxa[32 * j + 2048 * h] = x;
+                    }
                 }
-            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
@@ -144,6 +189,9 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
                 commit(smem_u32(&mbar[s]));
                 if (kc == n_chunks - 1) commit(mb_acc);
             }
+            // prefetch the next chunk (of this unit or of the next one)
+            if (kc + 1 < n_chunks) load_chunk(u, kc + 1);
+            else if (u + 1 < end) load_chunk(u + 1, 0);
         }
         if (failed) break;
         // ---- epilogue: D -> V_ab = g_a conj(g_b) D / T (and the mirrored block) ----
@@ -152,22 +200,23 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
         if (failed) break;
         fence_after();
         {
-            const int q = warp & 3, part = warp >> 2;            // TMEM lane quarter, 32-column part
+            constexpr int NPART = NT / 128, PW = 128 / NPART;    // column parts per lane quarter, width
+            const int q = warp & 3, part = warp >> 2;            // TMEM lane quarter, column part
             const int r = 32 * q + lane, aa = a0 + r;
             const uint32_t lane_base = (uint32_t)(32 * q) << 16;
             const float inv_t = 1.f / float(T);
             const float2 ga = (aa < A && a.gains) ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
             float2* out = a.vis + (size_t)cp * A * A;
-#pragma unroll
-            for (int c = 0; c < 32; c += 16) {
+#pragma unroll 1
+            for (int c = 0; c < PW; c += 16) {
                 float dr[16], di[16];
-                tld<16>(tRe + lane_base + 32 * part + c, dr);
-                tld<16>(tIm + lane_base + 32 * part + c, di);
+                tld<16>(tRe + lane_base + PW * part + c, dr);
+                tld<16>(tIm + lane_base + PW * part + c, di);
                 tld_wait();
                 if (aa < A) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int b = b0 + 32 * part + c + j;
+                        const int b = b0 + PW * part + c + j;
                         if (b < A) {
                             const float2 gb = a.gains ? __ldg(a.gains + (size_t)cp * A + b) : make_float2(1.f, 0.f);
                             const float2 w = cmul(ga, make_float2(gb.x, -gb.y));
@@ -206,7 +255,7 @@ cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st) {
     const int nab = (a.n_ant + 127) / 128;
     const long long n_units = (long long)a.n_cp * (nab * (nab + 1) / 2);
     if (n_units == 0) return cudaSuccess;
-    const long long grid = n_units < n_sm ? n_units : n_sm;
+    const long long grid = n_units < 2LL * n_sm ? n_units : 2LL * n_sm;
     const size_t smem = xe::smem_bytes();
     cudaError_t e;
     switch (vdt) {

@@ -303,3 +303,17 @@ def test_dftgemm_rejects_other_sizes(epic):
     with pytest.raises(epic.EpicError) as e:
         plan.set_transform("dftgemm")
     assert e.value.status == epic.EPIC_EUNSUPPORTED
+
+
+def test_forward_only_plan_beyond_adjoint_limit(epic):
+    """3000 antennas at N_p = 128 fit the forward kernel but not the adjoint's four per-antenna
+    arrays: the plan is created and images against the oracle, and the adjoint call is refused
+    on the host (EPIC_EUNSUPPORTED) before any launch."""
+    wl = _small_workload(128, 40, 3000, 3, 1, 1, seed=30, vdtype="ci4")
+    M = oracle_map(wl)
+    plan, out = run(epic, wl, autocorr=False)
+    check_close(out["image"], moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad), "image")
+    G = torch.ones((1, 1, wl.n_pad, wl.n_pad), dtype=torch.float32, device="cuda")
+    with pytest.raises(epic.EpicError) as e:
+        plan.image_backward(to_dev(wl), None, G)
+    assert e.value.status == epic.EPIC_EUNSUPPORTED
