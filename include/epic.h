@@ -177,6 +177,34 @@ epic_status epic_image_xpol(const epic_plan *plan, const void *volt, int n_time,
                             double *accum4, int64_t t_prev, float *image, float *cross, void *stream);
 
 /*
+ * epic_weff -- the effective weighting of the plan's (possibly heterogeneous) array in the
+ * optimally weighted image (Sec. 5, Eq. "effective-weighting-optimal"), on the image pixels:
+ *   weff(k) = (1 / (A (A - 1))) sum_{a != b} |K_a(k)|^2 |K_b(k)|^2,
+ * K_a(k) the transform of antenna a's gridded footprint (equal to its far-field pattern when
+ * the gridding kernels are the instrument's, W^G = W^I).  Channel independent: the pixel
+ * grid is in units of the aperture grid.
+ *
+ *   weff      device [N_p][N_p] float32, image pixel order (k = 0 at (N_p/2, N_p/2)).
+ *
+ * EPIC_EUNSUPPORTED for n_pad > 128 or footprints too wide for the lag tables; EPIC_EINVAL for
+ * fewer than two antennas.  One CTA; meant to be called once per plan.
+ */
+epic_status epic_weff(const epic_plan *plan, float *weff, void *stream);
+
+/*
+ * epic_isotropic -- the estimate of the isotropically weighted dirty image (Sec. 5,
+ * Eq. "effective-weighting"): iso = I' / weff with I' = (image - autocorr) / (A (A - 1)), the
+ * mean weighted fringe over antenna pairs a != b.
+ *
+ *   image, autocorr  device [C][P][N_p][N_p] float32 from epic_image (the same call).
+ *   weff      device [N_p][N_p] float32 from epic_weff.
+ *   rel_floor pixels where weff < rel_floor * max(weff) are set to NaN (0 <= rel_floor < 1).
+ *   iso       device [C][P][N_p][N_p] float32, overwritten.
+ */
+epic_status epic_isotropic(const epic_plan *plan, const float *image, const float *autocorr,
+                           const float *weff, float rel_floor, float *iso, void *stream);
+
+/*
  * epic_correlate -- the X-engine of the FX route (Sec. 3, the FX flow; Eq. "cc-vis"): the
  * visibilities of every ordered antenna pair of every (channel, pol), autocorrelations
  * included,

@@ -19,6 +19,8 @@ in numpy/scipy float64, with no blocking, fusion or reordering:
                  A(k) = sum_a P_a |K_a(k)|^2 with P_a the mean antenna power and K_a
                  the spatial transform of antenna a's sampled footprint (the
                  per-antenna form Sec. 4.3 proposes).
+  weff_opt, isotropic_image  Sec. 5: the effective weighting of the image of a
+                 heterogeneous array and the isotropic dirty-image estimate I' / W_eff.
   moff_cross_image  the four cross-polarisation products mean_t F_p conj(F_q) of
                  dual-polarisation data (Sec. 3; App. A image module).
   grad_gains     derivative of a real loss L(I) with respect to the complex gains,
@@ -184,6 +186,31 @@ def autocorr_term(M, volt, gains, n_grid, n_pad):
 # ----------------------------------------------------------------------------------
 # gradient of a real image-domain loss with respect to the complex gains
 # ----------------------------------------------------------------------------------
+# ----------------------------------------------------------------------------------
+# heterogeneous arrays: effective weighting and the isotropic image estimate (Sec. 5)
+# ----------------------------------------------------------------------------------
+def weff_opt(M, n_grid, n_pad):
+    """Eq. "effective-weighting-optimal" on the image pixels: the mean over ordered antenna
+    pairs a != b of |K_a(k)|^2 |K_b(k)|^2, K_a the transform of antenna a's gridded footprint
+    (the gridding weights equal to the instrument's, W^G = W^I), shifted: [N_p, N_p]."""
+    K = footprint_transforms(M, n_grid, n_pad)
+    P = np.abs(K) ** 2
+    A = P.shape[0]
+    total = np.zeros((n_pad, n_pad))
+    for a in range(A):
+        for b in range(A):
+            if a != b:
+                total += P[a] * P[b]
+    return total / (A * (A - 1))
+
+
+def isotropic_image(image, autocorr, weff, n_ant):
+    """Eq. "effective-weighting": the estimate of the isotropically weighted dirty image,
+    I_D^iso = I' / W_eff, with I' = (image - autocorr) / (N (N - 1)) the mean of the weighted
+    fringes over antenna pairs a != b (Eq. "wt-dirty-image-EPIC")."""
+    return (image - autocorr) / (n_ant * (n_ant - 1)) / weff
+
+
 def grad_gains(M, volt, gains, n_grid, n_pad, grad_image):
     """grad[c, p, a] = dL/dRe g + i dL/dIm g for a real loss L whose derivative with
     respect to the integrated image I[c, p] (shifted pixel order) is grad_image.

@@ -551,6 +551,41 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     return EPIC_OK;
 }
 
+epic_status epic_weff(const epic_plan* plan, float* weff, void* stream) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (!weff) return epic_fail(EPIC_EINVAL, "weff is NULL");
+    if (plan->n_ant < 2) return epic_fail(EPIC_EINVAL, "the effective weighting needs at least two antennas");
+    if (plan->n_pad > 128) return epic_fail(EPIC_EUNSUPPORTED, "effective weighting for n_pad <= 128 (plan: %d)", plan->n_pad);
+    if (plan->lag_side == 0)
+        return epic_fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    if (epic::weff_smem_bytes(plan->lag_side, plan->n_pad) > (size_t)smem_optin)
+        return epic_fail(EPIC_EUNSUPPORTED, "lag window %d does not fit the effective-weighting kernel", plan->lag_side);
+    const cudaError_t e = epic::launch_weff(plan->lag_tab, plan->n_ant, plan->lag_side, plan->n_pad, weff,
+                                            static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "effective-weighting kernel launch");
+}
+
+epic_status epic_isotropic(const epic_plan* plan, const float* image, const float* autocorr, const float* weff,
+                           float rel_floor, float* iso, void* stream) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (!image || !autocorr || !weff || !iso) return epic_fail(EPIC_EINVAL, "NULL device array");
+    if (plan->n_ant < 2) return epic_fail(EPIC_EINVAL, "the isotropic estimate needs at least two antennas");
+    if (!(rel_floor >= 0.f) || !(rel_floor < 1.f)) return epic_fail(EPIC_EINVAL, "rel_floor must be in [0, 1)");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    const int npix = plan->n_pad * plan->n_pad;
+    const long long n = (long long)plan->n_chan * plan->n_pol * npix;
+    const cudaError_t e = epic::launch_isotropic(image, autocorr, weff, rel_floor, plan->n_ant, n, npix, iso,
+                                                 static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "isotropic-estimate kernel launch");
+}
+
 epic_status epic_correlate(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* vis,
                            void* stream) {
     epic_clear_error();

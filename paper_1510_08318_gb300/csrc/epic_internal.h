@@ -133,6 +133,10 @@ cudaError_t launch_finalize_image(const double* accum, float* image, long long n
 cudaError_t launch_finalize_xpol(const double* accum4, float* image, float2* cross, int n_chan, long long npix,
                                  double inv_t, cudaStream_t st);
 size_t autocorr_smem_bytes(int lag_side, int n_pad, int n_ant);
+size_t weff_smem_bytes(int lag_side, int n_pad);
+cudaError_t launch_weff(const float2* lag_tab, int n_ant, int lag_side, int n_pad, float* out, cudaStream_t st);
+cudaError_t launch_isotropic(const float* image, const float* autocorr, const float* weff, float rel_floor,
+                             int n_ant, long long n, int npix, float* iso, cudaStream_t st);
 cudaError_t launch_autocorr(const double* power, const float2* lag_tab, int n_cp, int n_ant,
                             int lag_side, int n_pad, double inv_t, float* out, cudaStream_t st);
 

@@ -1,6 +1,8 @@
 // Once-per-integration epilogues of the MOFF imaging step, and host-visible geometry.
 //
 //   finalize_image   I = accum / T_total (Sec. 3 "Time-averaging").
+//   weff, isotropic  the effective weighting of a heterogeneous array and the isotropic
+//                    image estimate (Sec. 5).
 //   autocorr         the antenna auto-correlation term of Sec. 4.2 in its per-antenna form
 //                    (Sec. 4.3): A(k) = sum_a P_a |K_a(k)|^2 with K_a the spatial transform
 //                    of antenna a's gridded footprint.  Since |K_a(k)|^2 is the transform of
@@ -124,6 +126,110 @@ autocorr_kernel(const double* __restrict__ power, const float2* __restrict__ lag
         }
         out[(size_t)cp * npix + pix] = accr;
     }
+}
+
+// Effective weighting of a heterogeneous array (Sec. 5, Eq. "effective-weighting-optimal"):
+//   W_eff(k) = (1 / (A (A - 1))) sum_{a != b} |K_a(k)|^2 |K_b(k)|^2
+//            = ((sum_a P_a)^2 - sum_a P_a^2) / (A (A - 1)),  P_a(k) = |K_a(k)|^2,
+// with P_a the transform of the footprint auto-correlation R_a (the plan's lag tables),
+// evaluated antenna by antenna (separably: rows of the lag window, then the pixels) and
+// summed in shared memory by one CTA, image pixel order (k = 0 at the centre).
+constexpr int kWeffThreads = 512;
+
+__global__ void __launch_bounds__(kWeffThreads)
+weff_kernel(const float2* __restrict__ lag_tab, int n_ant, int L, int n_pad, float* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int npix = n_pad * n_pad, LL = L * L, h = (L - 1) / 2, msk = n_pad - 1;
+    float* S2 = reinterpret_cast<float*>(smem_raw);
+    float* S4 = S2 + npix;
+    float2* T1 = reinterpret_cast<float2*>(S4 + npix);     // [L][n_pad]
+    float2* TWs = T1 + L * n_pad;
+    for (int j = threadIdx.x; j < n_pad; j += blockDim.x) {
+        double s, c;
+        sincospi(2.0 * j / n_pad, &s, &c);
+        TWs[j] = make_float2(float(c), float(s));
+    }
+    for (int pix = threadIdx.x; pix < npix; pix += blockDim.x) S2[pix] = S4[pix] = 0.f;
+    __syncthreads();
+    for (int a = 0; a < n_ant; ++a) {
+        const float2* R = lag_tab + (size_t)a * LL;
+        for (int j = threadIdx.x; j < L * n_pad; j += blockDim.x) {
+            const int dy = j / n_pad, ix = j % n_pad, kx = ix - n_pad / 2;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int dx = 0; dx < L; ++dx) {
+                const float2 w = TWs[((dx - h) * kx) & msk];
+                const float2 r = __ldg(R + dy * L + dx);
+                acc.x = fmaf(r.x, w.x, fmaf(-r.y, w.y, acc.x));
+                acc.y = fmaf(r.x, w.y, fmaf(r.y, w.x, acc.y));
+            }
+            T1[j] = acc;
+        }
+        __syncthreads();
+        for (int pix = threadIdx.x; pix < npix; pix += blockDim.x) {
+            const int iy = pix / n_pad, ix = pix % n_pad, ky = iy - n_pad / 2;
+            float p = 0.f;
+            for (int dy = 0; dy < L; ++dy) {
+                const float2 w = TWs[((dy - h) * ky) & msk];
+                const float2 t = T1[dy * n_pad + ix];
+                p = fmaf(t.x, w.x, fmaf(-t.y, w.y, p));
+            }
+            S2[pix] += p;
+            S4[pix] = fmaf(p, p, S4[pix]);
+        }
+        __syncthreads();
+    }
+    const float norm = 1.f / (float(n_ant) * float(n_ant - 1));
+    for (int pix = threadIdx.x; pix < npix; pix += blockDim.x)
+        out[pix] = fmaf(S2[pix], S2[pix], -S4[pix]) * norm;
+}
+
+size_t weff_smem_bytes(int lag_side, int n_pad) {
+    return sizeof(float) * 2 * (size_t)n_pad * n_pad + sizeof(float2) * ((size_t)lag_side * n_pad + n_pad);
+}
+
+cudaError_t launch_weff(const float2* lag_tab, int n_ant, int lag_side, int n_pad, float* out, cudaStream_t st) {
+    const size_t smem = weff_smem_bytes(lag_side, n_pad);
+    cudaError_t e = ensure_smem<weff_kernel>(smem);
+    if (e != cudaSuccess) return e;
+    weff_kernel<<<1, kWeffThreads, smem, st>>>(lag_tab, n_ant, lag_side, n_pad, out);
+    return cudaGetLastError();
+}
+
+// Isotropic image estimate (Sec. 5, Eq. "effective-weighting"): I_D^iso = I' / W_eff with
+// I' = (image - autocorr) / (A (A - 1)) the mean weighted fringe over pairs a != b.  Pixels
+// where W_eff is below rel_floor times its largest value are set to NaN (outside the beam).
+__global__ void isotropic_kernel(const float* __restrict__ image, const float* __restrict__ autocorr,
+                                 const float* __restrict__ weff, float rel_floor, float pair_norm,
+                                 long long n, int npix, float* __restrict__ iso) {
+    __shared__ float red[32];
+    float m = 0.f;
+    for (int i = threadIdx.x; i < npix; i += blockDim.x) m = fmaxf(m, weff[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    const float floor_abs = rel_floor * red[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float w = weff[i % npix];
+        iso[i] = (w >= floor_abs && w > 0.f) ? (image[i] - autocorr[i]) * pair_norm / w : __int_as_float(0x7fc00000);
+    }
+}
+
+cudaError_t launch_isotropic(const float* image, const float* autocorr, const float* weff, float rel_floor,
+                             int n_ant, long long n, int npix, float* iso, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    const float pair_norm = 1.f / (float(n_ant) * float(n_ant - 1));
+    isotropic_kernel<<<(unsigned)blocks, 256, 0, st>>>(image, autocorr, weff, rel_floor, pair_norm, n, npix, iso);
+    return cudaGetLastError();
 }
 
 size_t autocorr_smem_bytes(int lag_side, int n_pad, int n_ant) {

@@ -1,7 +1,7 @@
 """Thin Python binding of the MOFF imaging C ABI (include/epic.h).
 
 The functions named like the C entry points (`epic_create`, `epic_image`,
-`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
+`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_weff`, `epic_isotropic`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
 arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
 for torch tensors, and `MoffImage` is the autograd.Function whose backward is the
 library's adjoint kernel.  There is no CPU fallback: if the library has not been built
@@ -21,7 +21,7 @@ EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
-           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate")
+           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic")
 XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
@@ -52,6 +52,10 @@ def load(path=LIB_PATH):
     lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.epic_image_xpol.restype = i32
     lib.epic_image_xpol.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp, vp]
+    lib.epic_weff.restype = i32
+    lib.epic_weff.argtypes = [vp, vp, vp]
+    lib.epic_isotropic.restype = i32
+    lib.epic_isotropic.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
     lib.epic_correlate.restype = i32
     lib.epic_correlate.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.epic_grid.restype = i32
@@ -130,6 +134,14 @@ def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, strea
 
 def epic_image_xpol(plan, volt, n_time, gains, accum4, t_prev, image, cross, stream):
     _check(load().epic_image_xpol(plan, volt, int(n_time), gains, accum4, int(t_prev), image, cross, stream))
+
+
+def epic_weff(plan, weff, stream):
+    _check(load().epic_weff(plan, weff, stream))
+
+
+def epic_isotropic(plan, image, autocorr, weff, rel_floor, iso, stream):
+    _check(load().epic_isotropic(plan, image, autocorr, weff, float(rel_floor), iso, stream))
 
 
 def epic_correlate(plan, volt, n_time, gains, vis, stream):
@@ -295,6 +307,32 @@ class Plan:
         epic_image_xpol(self._h, vptr, T, self._gains_ptr(gains), accum4.data_ptr(), t_prev, img.data_ptr(),
                         cross.data_ptr(), st.cuda_stream)
         return {"image": img, "cross": cross, "accum4": accum4}
+
+    def weff(self, stream=None):
+        """Run epic_weff: the effective weighting W_eff [N_p, N_p] (float32 CUDA tensor)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        out = torch.empty((self.n_pad, self.n_pad), dtype=torch.float32, device=dev)
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        epic_weff(self._h, out.data_ptr(), st.cuda_stream)
+        return out
+
+    def isotropic(self, image, autocorr, weff, rel_floor=1e-3, stream=None):
+        """Run epic_isotropic: (image - autocorr) / (A (A - 1) W_eff), NaN where W_eff is below
+        rel_floor of its peak."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        shape = (self.n_chan, self.n_pol, self.n_pad, self.n_pad)
+        for t in (image, autocorr):
+            if t.dtype != torch.float32 or tuple(t.shape) != shape or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("image and autocorr must be contiguous float32 CUDA tensors %s" % (shape,))
+        if tuple(weff.shape) != (self.n_pad, self.n_pad) or weff.dtype != torch.float32 or not weff.is_contiguous():
+            raise ValueError("weff must be a contiguous float32 tensor [N_p, N_p]")
+        out = torch.empty(shape, dtype=torch.float32, device=dev)
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        epic_isotropic(self._h, image.data_ptr(), autocorr.data_ptr(), weff.data_ptr(), rel_floor, out.data_ptr(),
+                       st.cuda_stream)
+        return out
 
     def correlate(self, volt, gains=None, out=None, stream=None):
         """Run epic_correlate: visibilities <g_a V_a conj(g_b V_b)>_t, complex64 [C, P, A, A]."""

@@ -9,8 +9,9 @@ the FP64 oracle and the CUDA library can both be fed from it without sharing cod
 Shapes follow the paper's workloads (Table 1: LWA1-like, HERA-331-like layouts) and
 the measurement equation of Sec. 2 (Eq. "measured-E-field"): each antenna sees
     V_a(t) = sum_s A_s(t) exp(-2 pi i r_a . s_hat / lambda) + n_a(t)
-with an isotropic element response.  All generators take an explicit numpy
-Generator (PCG64) so every input is reproducible from a seed.
+with an isotropic element response, or, for the heterogeneous-array workload of Sec. 5,
+each antenna's far-field pattern.  All generators take an explicit numpy Generator
+(PCG64) so every input is reproducible from a seed.
 """
 from __future__ import annotations
 
@@ -146,12 +147,15 @@ def sky_powerlaw_hemisphere(rng, n_src, s_lo, s_hi, index=-1.5):
     return Sky(rho * np.cos(phi), rho * np.sin(phi), flux)
 
 
-def voltages(rng, pos, freqs_hz, n_time, n_pol, sky: Sky, noise_sigma, dtype=np.complex64):
-    """V[t, c, p, a] = sum_s sqrt(S_s) e^{i phi_{t,p,s}} e^{-2 pi i r_a . s_s / lambda_c} + n.
+def voltages(rng, pos, freqs_hz, n_time, n_pol, sky: Sky, noise_sigma, dtype=np.complex64, apertures=None):
+    """V[t, c, p, a] = sum_s P_a(s_s) sqrt(S_s) e^{i phi_{t,p,s}} e^{-2 pi i r_a . s_s / lambda_c} + n.
 
     Source phases are drawn independently per (time, channel, pol, source): each sample is
     a fresh realisation of a stochastic sky.  Noise is circular complex Gaussian with
-    per-sample variance noise_sigma**2.
+    per-sample variance noise_sigma**2.  The element response P_a is isotropic (1) unless
+    `apertures` gives each antenna's aperture as a sample table (offsets [n, 2] m, weights
+    [n]); then P_a(s) = sum_k w_k e^{-2 pi i delta_k . s / lambda}, the far-field voltage
+    pattern of that aperture (the measurement equation of Sec. 2 with antenna beams).
     """
     n_ant = pos.shape[0]
     out = np.empty((n_time, len(freqs_hz), n_pol, n_ant), dtype=dtype)
@@ -160,7 +164,12 @@ def voltages(rng, pos, freqs_hz, n_time, n_pol, sky: Sky, noise_sigma, dtype=np.
     for c, f in enumerate(freqs_hz):
         lam = C_LIGHT / f
         geo = np.outer(sky.l, pos[:, 0]) + np.outer(sky.m, pos[:, 1])      # [S, A] metres
-        steer = np.exp(-2j * np.pi * geo / lam).astype(work)
+        steer = np.exp(-2j * np.pi * geo / lam)
+        if apertures is not None:
+            for a, (d, w) in enumerate(apertures):
+                ph = np.outer(sky.l, d[:, 0]) + np.outer(sky.m, d[:, 1])   # [S, n] metres
+                steer[:, a] *= np.exp(-2j * np.pi * ph / lam) @ w
+        steer = steer.astype(work)
         for p in range(n_pol):
             ph = rng.uniform(0, 2 * np.pi, (n_time, sky.flux.size))
             src = (amp * np.exp(1j * ph)).astype(work)                       # [T, S]
@@ -359,6 +368,37 @@ def workload_calib(seed=5, n_chan=32, n_time=64, n_ant=1024):
                   pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, freqs, 1, n_time, "c64")
     wl.extra["sky"] = sky
     wl.extra["g_true"] = g_true
+    return _finish(wl, v, "c64")
+
+
+def workload_twotype(seed=6, n_time=256, n_ant=51):
+    """Heterogeneous array after Sec. 5: n_ant antennas uniform in a 100 m disk, alternately
+    uniform squares of 1.1 m (type 1) and 6.6 m (type 2) sides; one channel at 150 MHz, one
+    pol, T samples; 8 point sources of 10-30 Jy at pixel centres along the westward and
+    south-westward directions within the type-2 main lobe; voltages carry each antenna's
+    far-field pattern; no noise.  Grid 2 m (N_g = 64), N_p = 128, complex64."""
+    rng = np.random.default_rng(seed)
+    freqs = np.array([150e6])
+    lam = C_LIGHT / freqs[0]
+    dx = 2.0
+    pos = layout_disk(rng, n_ant, 100.0)
+    kern = [kernel_square(1.1 if a % 2 == 0 else 6.6, dx / 4) for a in range(n_ant)]
+    ptr, dxdy, w = pack_kernels(kern)
+    n_grid, n_pad = 64, 128
+    origin = centred_origin(pos, 3.3, dx, n_grid)
+    step = lam / (n_pad * dx)                       # direction cosine per image pixel
+    k = np.array([6, 10, 14, 18])
+    l = np.concatenate([-k * step, -k * step / 1.0])
+    m = np.concatenate([np.zeros(4), -k * step])
+    flux = rng.uniform(10.0, 30.0, 8)
+    sky = Sky(l, m, flux)
+    v = voltages(rng, pos, freqs, n_time, 1, sky, 0.0, dtype=np.complex128, apertures=kern)
+    wl = Workload("two-type: %d ant (1.1 m / 6.6 m squares), 150 MHz, T=%d, 128x128 image, c64" % (n_ant, n_time),
+                  pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, freqs, 1, n_time, "c64")
+    wl.extra["sky"] = sky
+    wl.extra["src_pixel"] = [(int(round(mm / step)) + n_pad // 2, int(round(ll / step)) + n_pad // 2)
+                             for ll, mm in zip(l, m)]
+    wl.extra["types"] = np.array([a % 2 for a in range(n_ant)])
     return _finish(wl, v, "c64")
 
 

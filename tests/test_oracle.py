@@ -349,3 +349,73 @@ def test_cross_pol_parseval(tiny):
     ey = moff.grid_efields(M, v[:, 0, 1, :], one, wl.n_grid)
     want = wl.n_pad ** 2 * (ex * np.conj(ey)).sum(axis=(1, 2)).mean()
     assert abs(I[0, 0, 1].sum() - want) < 1e-10 * abs(want)
+
+
+# ----------------------------------------------------------------------------------
+# heterogeneous arrays: effective weighting and the isotropic estimate (Sec. 5)
+# ----------------------------------------------------------------------------------
+def _on_grid_square(n_cells, dx):
+    """Uniform square aperture whose samples sit exactly on cell centres (n_cells per side,
+    odd), so the gridded footprint equals the aperture table."""
+    c = (np.arange(n_cells) - (n_cells - 1) / 2) * dx
+    xx, yy = np.meshgrid(c, c, indexing="xy")
+    d = np.stack([xx.ravel(), yy.ravel()], axis=1)
+    return d, np.full(d.shape[0], 1.0 / d.shape[0], dtype=np.complex128)
+
+
+def _two_type_on_grid(n1, n2, n_grid=32, n_pad=64, dx=1.0, seed=2):
+    rng = np.random.default_rng(seed)
+    cells = rng.choice(np.arange(4, n_grid - 4), size=(n1 + n2, 2))
+    origin = np.zeros(2)
+    pos = _cells(cells, n_grid, dx, origin)
+    kern = [_on_grid_square(1, dx)] * n1 + [_on_grid_square(5, dx)] * n2
+    ptr, dxdy, w = synth.pack_kernels(kern)
+    M = moff.map_antennas(pos, ptr, dxdy, w, dx, origin, n_grid)
+    return pos, kern, ptr, dxdy, w, M, origin
+
+
+def _brute_K(d, w, n_pad, dx):
+    """|K(k)|^2 of one footprint table by a direct sum over its samples (shifted pixels)."""
+    k = np.arange(n_pad) - n_pad // 2
+    out = np.zeros((n_pad, n_pad), dtype=np.complex128)
+    for (x, y), wt in zip(d, w):
+        gx, gy = int(round(x / dx)), int(round(y / dx))
+        out += wt * np.exp(2j * np.pi * (gy * k[:, None] + gx * k[None, :]) / n_pad)
+    return np.abs(out) ** 2
+
+
+def test_weff_closed_forms():
+    """Sec. 5: homogeneous array -> W_eff = |K|^4; two types -> [n1 (n1-1) |K1|^4 +
+    n2 (n2-1) |K2|^4 + 2 n1 n2 |K1|^2 |K2|^2] / (N (N-1)) (ordered pairs, so the mixed
+    term counts twice); W_eff = 1 at k = 0 for unit-sum weights."""
+    n1, n2 = 7, 5
+    pos, kern, ptr, dxdy, w, M, origin = _two_type_on_grid(n1, n2)
+    W = moff.weff_opt(M, 32, 64)
+    P1 = _brute_K(*kern[0], 64, 1.0)
+    P2 = _brute_K(*kern[-1], 64, 1.0)
+    N = n1 + n2
+    want = (n1 * (n1 - 1) * P1 ** 2 + n2 * (n2 - 1) * P2 ** 2 + 2 * n1 * n2 * P1 * P2) / (N * (N - 1))
+    np.testing.assert_allclose(W, want, rtol=1e-10, atol=1e-13)
+    assert abs(W[32, 32] - 1.0) < 1e-12
+    Mh = moff.map_antennas(pos[:n2], ptr[:n2 + 1], dxdy, w, 1.0, origin, 32)   # first n2 antennas: type 1
+    np.testing.assert_allclose(moff.weff_opt(Mh, 32, 64), P1 ** 2, rtol=1e-10, atol=1e-13)
+
+
+def test_isotropic_estimate_recovers_flux():
+    """Sec. 5 with W^G = W^I: a single noiseless source at a pixel centre seen by a two-type
+    array whose apertures lie on the grid cells; the isotropic estimate at the source pixel
+    equals the flux exactly (cross-only image / W_eff), and the all-pairs image does not."""
+    n1, n2, n_grid, n_pad, dx = 6, 6, 32, 64, 1.0
+    pos, kern, ptr, dxdy, w, M, origin = _two_type_on_grid(n1, n2, n_grid, n_pad, dx)
+    lam = 4.0
+    step = lam / (n_pad * dx)
+    iy, ix = n_pad // 2 + 3, n_pad // 2 - 5
+    sky = synth.Sky(np.array([(ix - n_pad // 2) * step]), np.array([(iy - n_pad // 2) * step]), np.array([7.5]))
+    f = synth.C_LIGHT / lam
+    v = synth.voltages(np.random.default_rng(0), pos, np.array([f]), 16, 1, sky, 0.0, dtype=np.complex128,
+                       apertures=kern)
+    img = moff.moff_image(M, v, None, n_grid, n_pad)[0, 0]
+    ac = moff.autocorr_term(M, v, None, n_grid, n_pad)[0, 0]
+    iso = moff.isotropic_image(img, ac, moff.weff_opt(M, n_grid, n_pad), n1 + n2)
+    assert abs(iso[iy, ix] - 7.5) < 1e-9 * 7.5
+    assert abs(img[iy, ix] / (n1 + n2) ** 2 - 7.5) > 0.05      # without the normalisation it is off
