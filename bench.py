@@ -56,13 +56,14 @@ def parse():
     p.add_argument("--channels", type=int, default=128,
                    help="image only the first C of the 128 channels (small profiling case)")
     p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid", "xpol", "fx",
-                                                          "crossover"],
+                                                          "crossover", "fengine"],
                    help="lwa: the headline workload; batch: 64 heterogeneous sub-arrays, one graph launch; "
                         "calib: forward + adjoint of the gain-calibration workload; "
                         "grid: the standalone gridder (epic_grid) on the headline workload; "
                         "xpol: all four cross-polarisation images (epic_image_xpol) of the headline workload; "
                         "fx: the FX-route correlator (epic_correlate) on the headline workload; "
-                        "crossover: MOFF imaging vs the FX correlator per sample over antenna counts")
+                        "crossover: MOFF imaging vs the FX correlator per sample over antenna counts; "
+                        "fengine: the F-engine (time samples -> spectra) ahead of imaging, headline shapes")
     return p.parse_args()
 
 
@@ -687,6 +688,83 @@ def run_crossover(args):
         print(json.dumps(line))
 
 
+def run_fengine(args):
+    """The F-engine on the headline shapes: 256 antennas x 2 pols x 1024 spectra of 128
+    channels from 4+4-bit time samples (seeded random bytes), written as FP16 spectra, then
+    imaged (epic_image, FP16 plan).  Roofline of the F-engine: HBM bytes (samples read once,
+    spectra written once) against the measured copy bandwidth."""
+    import numpy as np
+    import torch
+    from oracle import moff
+    from paper_1510_08318_gb300 import build, epic, synth
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = synth.workload_lwa(n_chan=1, n_time=2, chan_index=[0])
+    A, P, C, T = wl.n_ant, 2, 128, 1024
+    rng = np.random.default_rng(11)
+    raw_h = rng.integers(0, 256, (T * C, P, A), dtype=np.uint8)
+    raw = torch.from_numpy(raw_h).to(dev)
+    spec = torch.empty((T, C, P, A, 2), dtype=torch.float16, device=dev)
+    plan = epic.Plan(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid, wl.n_pad, C, P,
+                     "f16", local)
+    acc = torch.empty((C, P, wl.n_pad, wl.n_pad), dtype=torch.float64, device=dev)
+    img = torch.empty((C, P, wl.n_pad, wl.n_pad), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def feng():
+        epic.epic_fengine(A, P, C, T, 2, raw.data_ptr(), 1, spec.data_ptr(), local, st.cuda_stream)
+
+    def chain():
+        feng()
+        epic.epic_image(plan._h, spec.data_ptr(), T, None, acc.data_ptr(), None, 0, img.data_ptr(), None,
+                        st.cuda_stream)
+
+    def timed(fn, clocks=None):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if clocks:
+            clocks.start()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps, clk
+
+    f_ms, clk = timed(feng, Clocks(local))
+    c_ms, _ = timed(chain)
+    nbytes = raw.numel() + spec.numel() * 2
+    peak = MEASURED["hbm_gbs"]
+    roof = {"bound": "hbm", "achieved": nbytes / (f_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s", "traffic": None,
+            "algorithmic_bytes": nbytes, "peak_basis": "measured STREAM-style copy (read + write bytes), of measured"}
+    roof["frac"] = roof["achieved"] / peak
+    err = None
+    if rank == 0:
+        # oracle spectra of 2 spectra x all channels, pol 1, against the FP16 output
+        want = moff.fengine(synth.decode_ci4(raw_h[:2 * C]), C)[:, :, 1]
+        got = spec[:2, :, 1].float().cpu().numpy()
+        got = got[..., 0] + 1j * got[..., 1]
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    units = A * T * C * P
+    line = {"metric": METRIC, "value": units / (c_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": c_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP16 spectra)", "data": "synthetic (random 4+4-bit time samples)",
+            "config": {"workload": "F-engine + imaging: 256 antennas, 2 pols, 1024 spectra x 128 channels from "
+                                   "4+4-bit time samples, FP16 spectra, LWA-like layout, 128x128 image",
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "fengine_ms": f_ms, "imaging_ms": c_ms - f_ms, "roofline": roof, "gpu_launches": 3 * args.steps,
+            "clocks": clk, "err_vs_oracle": {"fengine_fp16_relative_l2": err, "sample": "2 spectra, pol 1"}}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -703,6 +781,8 @@ def main():
         return run_fx(args)
     if args.workload == "crossover":
         return run_crossover(args)
+    if args.workload == "fengine":
+        return run_fengine(args)
     import numpy as np
     import torch
     from paper_1510_08318_gb300 import build, epic, synth

@@ -177,6 +177,26 @@ epic_status epic_image_xpol(const epic_plan *plan, const void *volt, int n_time,
                             double *accum4, int64_t t_prev, float *image, float *cross, void *stream);
 
 /*
+ * epic_fengine -- the F-engine (Sec. 3 "Temporal Fourier transform"): the time samples of
+ * every antenna, in blocks of n_chan consecutive samples, become electric-field spectra,
+ *   volt[t][c][p][a] = sum_{j < C} raw[t C + j][p][a] exp(-2 pi i j c / C),  c = 0 .. C-1,
+ * an unnormalised forward DFT without window (bins in FFT order: c > C/2 are negative
+ * frequencies), the layout epic_image reads (C channels per call).  No plan is needed.
+ *
+ *   n_ant, n_pol          A, P.
+ *   n_chan                C: 32, 64, 128, 256 or 512 (else EPIC_EUNSUPPORTED).
+ *   n_time                T, spectra per antenna (raw holds T C samples per antenna).
+ *   in_dtype              raw sample format (one of epic_volt_dtype).
+ *   raw                   device [T C][P][A] samples.
+ *   out_dtype             EPIC_VOLT_C64 (complex64) or EPIC_VOLT_F16 (FP16 pairs, rounded;
+ *                         |values| above 65504 overflow).
+ *   volt                  device [T][C][P][A], overwritten.
+ *   device                CUDA device of the arrays.
+ */
+epic_status epic_fengine(int n_ant, int n_pol, int n_chan, int n_time, int in_dtype, const void *raw,
+                         int out_dtype, void *volt, int device, void *stream);
+
+/*
  * epic_weff -- the effective weighting of the plan's (possibly heterogeneous) array in the
  * optimally weighted image (Sec. 5, Eq. "effective-weighting-optimal"), on the image pixels:
  *   weff(k) = (1 / (A (A - 1))) sum_{a != b} |K_a(k)|^2 |K_b(k)|^2,

@@ -19,6 +19,8 @@ in numpy/scipy float64, with no blocking, fusion or reordering:
                  A(k) = sum_a P_a |K_a(k)|^2 with P_a the mean antenna power and K_a
                  the spatial transform of antenna a's sampled footprint (the
                  per-antenna form Sec. 4.3 proposes).
+  fengine        Sec. 3 "Temporal Fourier transform": per-antenna spectra of blocks of
+                 time samples (numpy's FFT as the library step).
   weff_opt, isotropic_image  Sec. 5: the effective weighting of the image of a
                  heterogeneous array and the isotropic dirty-image estimate I' / W_eff.
   moff_cross_image  the four cross-polarisation products mean_t F_p conj(F_q) of
@@ -186,6 +188,18 @@ def autocorr_term(M, volt, gains, n_grid, n_pad):
 # ----------------------------------------------------------------------------------
 # gradient of a real image-domain loss with respect to the complex gains
 # ----------------------------------------------------------------------------------
+# ----------------------------------------------------------------------------------
+# the F-engine (Sec. 3 "Temporal Fourier transform")
+# ----------------------------------------------------------------------------------
+def fengine(raw, n_chan):
+    """Spectra of blocks of n_chan consecutive time samples of every antenna:
+    raw [T n_chan, P, A] complex -> V [T, n_chan, P, A] with
+    V[t, c] = sum_j raw[t n_chan + j] exp(-2 pi i j c / n_chan) (numpy's forward FFT)."""
+    n_samp, P, A = raw.shape
+    blocks = np.asarray(raw, dtype=np.complex128).reshape(n_samp // n_chan, n_chan, P, A)
+    return np.fft.fft(blocks, axis=1)
+
+
 # ----------------------------------------------------------------------------------
 # heterogeneous arrays: effective weighting and the isotropic image estimate (Sec. 5)
 # ----------------------------------------------------------------------------------

@@ -551,6 +551,33 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     return EPIC_OK;
 }
 
+epic_status epic_fengine(int n_ant, int n_pol, int n_chan, int n_time, int in_dtype, const void* raw, int out_dtype,
+                         void* volt, int device, void* stream) {
+    epic_clear_error();
+    if (n_ant < 1 || n_pol < 1 || n_time < 0) return epic_fail(EPIC_EINVAL, "bad sizes");
+    if (n_chan != 32 && n_chan != 64 && n_chan != 128 && n_chan != 256 && n_chan != 512)
+        return epic_fail(EPIC_EUNSUPPORTED, "n_chan = %d (supported: 32, 64, 128, 256, 512)", n_chan);
+    if (in_dtype < EPIC_VOLT_C64 || in_dtype > EPIC_VOLT_CI4) return epic_fail(EPIC_EINVAL, "in_dtype %d", in_dtype);
+    if (out_dtype != EPIC_VOLT_C64 && out_dtype != EPIC_VOLT_F16)
+        return epic_fail(EPIC_EINVAL, "out_dtype %d (complex64 or FP16 pairs)", out_dtype);
+    if (n_time == 0) return EPIC_OK;
+    if (!raw || !volt) return epic_fail(EPIC_EINVAL, "NULL device array");
+    EpicDeviceGuard guard(device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", device);
+    int n_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return epic_cuda_fail(e, "cudaDeviceGetAttribute");
+    epic::FengArgs a;
+    a.raw = raw;
+    a.volt = volt;
+    a.n_time = n_time;
+    a.n_pol = n_pol;
+    a.n_ant = n_ant;
+    e = epic::launch_fengine(n_chan, in_dtype, out_dtype == EPIC_VOLT_F16 ? 1 : 0, a, n_sm,
+                             static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "F-engine kernel launch");
+}
+
 epic_status epic_weff(const epic_plan* plan, float* weff, void* stream) {
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");

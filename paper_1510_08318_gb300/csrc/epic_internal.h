@@ -68,6 +68,15 @@ struct BwdArgs {
     float scale;               // 2 / T
 };
 
+// F-engine (fengine.cu): per-antenna temporal DFT of blocks of C samples.
+struct FengArgs {
+    const void* raw;           // [T * C][P][A] time samples
+    void* volt;                // [T][C][P][A] spectra (complex64 or FP16 pairs)
+    long long n_time;          // T, blocks (spectra) per antenna
+    int n_pol, n_ant;
+};
+cudaError_t launch_fengine(int n_chan, int vin, int vout, const FengArgs& a, int n_sm, cudaStream_t st);
+
 // X-engine of the FX route (xeng.cu): visibilities of every antenna pair.
 struct XengArgs {
     const void* volt;          // [T][C][P][A] raw voltages (FP16 or 4+4-bit)

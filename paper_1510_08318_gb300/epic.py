@@ -1,7 +1,7 @@
 """Thin Python binding of the MOFF imaging C ABI (include/epic.h).
 
 The functions named like the C entry points (`epic_create`, `epic_image`,
-`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_weff`, `epic_isotropic`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
+`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_weff`, `epic_isotropic`, `epic_fengine`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
 arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
 for torch tensors, and `MoffImage` is the autograd.Function whose backward is the
 library's adjoint kernel.  There is no CPU fallback: if the library has not been built
@@ -21,7 +21,7 @@ EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
-           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic")
+           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine")
 XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
@@ -52,6 +52,8 @@ def load(path=LIB_PATH):
     lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.epic_image_xpol.restype = i32
     lib.epic_image_xpol.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp, vp]
+    lib.epic_fengine.restype = i32
+    lib.epic_fengine.argtypes = [i32, i32, i32, i32, i32, vp, i32, vp, i32, vp]
     lib.epic_weff.restype = i32
     lib.epic_weff.argtypes = [vp, vp, vp]
     lib.epic_isotropic.restype = i32
@@ -134,6 +136,31 @@ def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, strea
 
 def epic_image_xpol(plan, volt, n_time, gains, accum4, t_prev, image, cross, stream):
     _check(load().epic_image_xpol(plan, volt, int(n_time), gains, accum4, int(t_prev), image, cross, stream))
+
+
+def epic_fengine(n_ant, n_pol, n_chan, n_time, in_dtype, raw, out_dtype, volt, device, stream):
+    _check(load().epic_fengine(int(n_ant), int(n_pol), int(n_chan), int(n_time), int(in_dtype), raw,
+                               int(out_dtype), volt, int(device), stream))
+
+
+def fengine(raw, n_chan, in_dtype, out_dtype="f16", stream=None):
+    """F-engine on a CUDA tensor of time samples [T C, P, A] (uint8 for "ci4", [.., 2] float16
+    for "f16", complex64 for "c64") -> spectra [T, C, P, A] (complex64, or [.., 2] float16)."""
+    import torch
+    if not raw.is_cuda or not raw.is_contiguous():
+        raise ValueError("raw samples must be a contiguous CUDA tensor")
+    n_samp, P, A = int(raw.shape[0]), int(raw.shape[1]), int(raw.shape[2])
+    if n_samp % n_chan:
+        raise ValueError("the number of samples must be a multiple of n_chan")
+    T = n_samp // n_chan
+    if out_dtype == "f16":
+        out = torch.empty((T, n_chan, P, A, 2), dtype=torch.float16, device=raw.device)
+    else:
+        out = torch.empty((T, n_chan, P, A), dtype=torch.complex64, device=raw.device)
+    st = torch.cuda.current_stream(raw.device) if stream is None else stream
+    epic_fengine(A, P, n_chan, T, VOLT_DTYPES[in_dtype], raw.data_ptr(), VOLT_DTYPES[out_dtype], out.data_ptr(),
+                 raw.device.index or 0, st.cuda_stream)
+    return out
 
 
 def epic_weff(plan, weff, stream):

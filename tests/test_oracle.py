@@ -419,3 +419,27 @@ def test_isotropic_estimate_recovers_flux():
     iso = moff.isotropic_image(img, ac, moff.weff_opt(M, n_grid, n_pad), n1 + n2)
     assert abs(iso[iy, ix] - 7.5) < 1e-9 * 7.5
     assert abs(img[iy, ix] / (n1 + n2) ** 2 - 7.5) > 0.05      # without the normalisation it is off
+
+
+# ----------------------------------------------------------------------------------
+# the F-engine (Sec. 3 "Temporal Fourier transform")
+# ----------------------------------------------------------------------------------
+def test_fengine_brute_force_tone_parseval():
+    rng = np.random.default_rng(3)
+    C, T, P, A = 16, 3, 2, 5
+    raw = rng.standard_normal((T * C, P, A)) + 1j * rng.standard_normal((T * C, P, A))
+    V = moff.fengine(raw, C)
+    # brute-force DFT of every block
+    j = np.arange(C)
+    for t in range(T):
+        for c in range(C):
+            want = (raw[t * C:(t + 1) * C] * np.exp(-2j * np.pi * j * c / C)[:, None, None]).sum(0)
+            np.testing.assert_allclose(V[t, c], want, rtol=1e-12, atol=1e-12)
+    # Parseval per block and antenna
+    np.testing.assert_allclose((np.abs(V) ** 2).sum(1), C * (np.abs(raw.reshape(T, C, P, A)) ** 2).sum(1),
+                               rtol=1e-12)
+    # a pure tone exp(+2 pi i c0 j / C) lands in bin c0 with value C (sign and bin order)
+    c0 = 5
+    tone = np.exp(2j * np.pi * c0 * np.arange(2 * C) / C)[:, None, None] * np.ones((1, 1, 2))
+    Vt = moff.fengine(tone, C)
+    assert np.allclose(Vt[:, c0], C) and np.abs(np.delete(Vt, c0, axis=1)).max() < 1e-9
