@@ -575,11 +575,19 @@ def run_fx(args):
         clk = clocks.stop() if clocks else None
         return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
 
+    fx_img = torch.empty((C, P, wl.n_pad, wl.n_pad), dtype=torch.float32, device=dev)
+
+    def fx_imaging():
+        epic.epic_fx_image(plan._h, vis.data_ptr(), fx_img.data_ptr(), st.cuda_stream)
+
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     ms, clk = timed(step, Clocks(local))
     e2e_ms, _ = timed(e2e_step)
+    for _ in range(2):
+        fx_imaging()
+    img_ms, _ = timed(fx_imaging)
     units = A * T * C * P
     flop = _xeng_flops(A, C * P, T)
     peak = MEASURED["bf16_tflops"]
@@ -613,6 +621,7 @@ def run_fx(args):
                     "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
                     "d2h_bytes_per_step": int(host_vis.numel() * 8)},
             "gpu_launches": args.steps, "clocks": clk,
+            "fx_imaging_ms_per_integration": img_ms, "fx_route_ms": ms + img_ms,
             "err_vs_oracle": {"relative_l2_max": err, "sample": "last 32 channels, both pols"}}
     if cb is not None:
         line["cpu_baseline"] = cb
@@ -666,11 +675,16 @@ def run_crossover(args):
         t_moff = timed(lambda: epic.epic_image(plan._h, raw.data_ptr(), T, None, acc.data_ptr(), None, 0, None,
                                                None, st.cuda_stream))
         t_fx = timed(lambda: epic.epic_correlate(plan._h, raw.data_ptr(), T, None, vis.data_ptr(), st.cuda_stream))
+        img = torch.empty((C, P, 128, 128), dtype=torch.float32, device=dev)
+        t_img = timed(lambda: epic.epic_fx_image(plan._h, vis.data_ptr(), img.data_ptr(), st.cuda_stream)) \
+            if A <= 1024 else None
         n = C * P * T
         rows.append({"antennas": A, "nnz": plan.info["nnz"], "moff_ns_per_sample": 1e6 * t_moff / n,
-                     "fx_correlator_ns_per_sample": 1e6 * t_fx / n, "fx_over_moff": t_fx / t_moff})
+                     "fx_correlator_ns_per_sample": 1e6 * t_fx / n, "fx_over_moff": t_fx / t_moff,
+                     "fx_imaging_ms_per_integration": t_img,
+                     "fx_route_over_moff": None if t_img is None else (t_fx + t_img) / t_moff})
         plan.close()
-        del raw, acc, vis
+        del raw, acc, vis, img
     cross = None
     for r0, r1 in zip(rows, rows[1:]):
         if r0["fx_over_moff"] < 1.0 <= r1["fx_over_moff"]:
@@ -682,7 +696,8 @@ def run_crossover(args):
             "warmup": max(args.warmup, 3), "higher_is_better": None, "data": "synthetic (random 4+4-bit bytes)",
             "config": {"workload": "LWA-like ellipse 100 m x 110 m, Gaussian sigma 1.5 m apertures, N_g 64, "
                                    "N_p 128, 16 channels x 2 pols x 1024 samples per call",
-                       "fx_scope": "correlator only (the per-integration gridding and transform are excluded)"},
+                       "fx_scope": "value and fx_over_moff: correlator only; fx_route_over_moff adds the FX "
+                                   "imaging of the integration (1024 samples; measured up to 1024 antennas)"},
             "fx_over_moff_at_largest": rows[-1]["fx_over_moff"], "table": rows}
     if rank == 0:
         print(json.dumps(line))

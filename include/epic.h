@@ -244,6 +244,23 @@ epic_status epic_correlate(const epic_plan *plan, const void *volt, int n_time, 
                            float *vis, void *stream);
 
 /*
+ * epic_fx_image -- the FX route's imaging of one integration's visibilities (Sec. 3, the FX
+ * flow; Eqs. "e-field-conv" and "dirty-image-FX"): the visibilities are gridded with the
+ * antenna-pair kernels B_ab(d) = sum_g M[g, a] conj(M[g - d, b]) (the cross-correlation of
+ * the two sampled footprints) onto the lag plane and transformed once:
+ *   image(k) = Re sum_d U(d) exp(+2 pi i d.k / N_p),  U(d) = sum_{a, b} vis_ab B_ab(d).
+ * With vis from epic_correlate (autocorrelations included, same gains) this equals
+ * epic_image's time-averaged image (Sec. 2: the two routes are equivalent).
+ *
+ *   vis       device [C][P][A][A] complex64.
+ *   image     device [C][P][N_p][N_p] float32, image pixel order; overwritten.
+ *
+ * n_pad <= 128 (the lag plane is held in shared memory), else EPIC_EUNSUPPORTED.  Work grows
+ * as (mapping entries)^2 per (channel, pol).
+ */
+epic_status epic_fx_image(const epic_plan *plan, const float *vis, float *image, void *stream);
+
+/*
  * epic_grid -- the gridding step alone (Sec. 3, gridding convolution): for every sample
  * t and (channel, pol), E_t(g) = sum_a M[g, a] g_a V_a(t) on the plan's N_g x N_g grid
  * (no zero padding, no transform), written to device memory.

@@ -41,6 +41,9 @@ void free_plan(epic_plan* p) {
     cudaFree(p->cell_ptr);
     cudaFree(p->cell_ent);
     cudaFree(p->cell_wim);
+    cudaFree(p->fx_ptr);
+    cudaFree(p->fx_ent);
+    cudaFree(p->fx_wim);
     cudaFree(p->wlane);
     cudaFree(p->wbase);
     cudaFree(p->went);
@@ -332,6 +335,23 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         ext = std::max(ext, std::max(x1 - x0 + 1, y1 - y0 + 1));
     }
     const int L = 2 * ext - 1;
+    // antenna-major copy of the mapping with (gy, gx) packed, for the FX route's gridding of
+    // visibilities with the antenna-pair kernels (N_p <= 128)
+    std::vector<int> fxptr;
+    std::vector<int2> fxent;
+    std::vector<float> fxwim;
+    if (n_pad <= 128) {
+        fxptr.assign((size_t)n_ant + 1, 0);
+        fxent.reserve(m.size());
+        fxwim.reserve(m.size());
+        for (int a = 0; a < n_ant; ++a) {
+            for (const MapEntry* e : by_ant[a]) {
+                fxent.push_back(pack_entry(e->w, ((e->cell / NG) << 16) | (e->cell % NG)));
+                fxwim.push_back(float(e->w.imag()));
+            }
+            fxptr[(size_t)a + 1] = (int)fxent.size();
+        }
+    }
     std::vector<float2> lag;
     int smem_optin_ac = 0;
     cudaDeviceGetAttribute(&smem_optin_ac, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -380,6 +400,8 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         (e = upload(&p->ant_ptr, aptr)) != cudaSuccess || (e = upload(&p->ant_ent, aent)) != cudaSuccess ||
         (e = upload(&p->twiddle, tw)) != cudaSuccess || (e = upload(&p->lag_tab, lag)) != cudaSuccess ||
         (complex_w && ((e = upload(&p->cell_wim, cwim)) != cudaSuccess || (e = upload(&p->ant_wim, awim)) != cudaSuccess)) ||
+        (n_pad <= 128 && ((e = upload(&p->fx_ptr, fxptr)) != cudaSuccess || (e = upload(&p->fx_ent, fxent)) != cudaSuccess ||
+                          (complex_w && (e = upload(&p->fx_wim, fxwim)) != cudaSuccess))) ||
         (SL > 0 && ((e = upload(&p->wlane, wlane)) != cudaSuccess || (e = upload(&p->wbase, wbase)) != cudaSuccess ||
                     (e = upload(&p->went, went)) != cudaSuccess ||
                     (complex_w && (e = upload(&p->wwim, wwim)) != cudaSuccess)))) {
@@ -637,6 +659,26 @@ epic_status epic_correlate(const epic_plan* plan, const void* volt, int n_time, 
     a.vis = reinterpret_cast<float2*>(vis);
     const cudaError_t e = epic::launch_xeng(plan->vdt, a, plan->n_sm, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "correlator kernel launch");
+}
+
+epic_status epic_fx_image(const epic_plan* plan, const float* vis, float* image, void* stream) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (!vis || !image) return epic_fail(EPIC_EINVAL, "NULL device array");
+    if (plan->n_pad > 128 || !plan->fx_ptr)
+        return epic_fail(EPIC_EUNSUPPORTED, "the FX imaging kernel holds the lag plane in shared memory: n_pad <= 128");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    epic::FxArgs a;
+    a.vis = reinterpret_cast<const float2*>(vis);
+    a.n_cp = plan->n_chan * plan->n_pol;
+    a.n_ant = plan->n_ant;
+    a.ptr = plan->fx_ptr;
+    a.ent = plan->fx_ent;
+    a.wim = plan->fx_wim;
+    a.image = image;
+    const cudaError_t e = epic::launch_fx_image(plan->n_pad, a, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "FX imaging kernel launch");
 }
 
 epic_status epic_grid(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* grid,

@@ -85,6 +85,16 @@ struct XengArgs {
     float2* vis;               // [CP][A][A]
 };
 size_t xeng_smem_bytes();
+// FX route's imaging of visibilities (xeng.cu), N_p <= 128
+struct FxArgs {
+    const float2* vis;         // [CP][A][A]
+    int n_cp, n_ant;
+    const int* ptr;            // antenna-major mapping [A+1]
+    const int2* ent;           // {weight re bits, (gy << 16) | gx}
+    const float* wim;          // or nullptr
+    float* image;              // [CP][N_p][N_p]
+};
+cudaError_t launch_fx_image(int n_pad, const FxArgs& a, cudaStream_t st);
 cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st);
 
 // Standalone gridder (grid.cu): E_t(g) for every sample of a call, written to device memory.

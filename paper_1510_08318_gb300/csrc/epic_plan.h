@@ -18,6 +18,9 @@ struct epic_plan {
     int* wbase = nullptr;
     int2* went = nullptr;
     float* wwim = nullptr;
+    int* fx_ptr = nullptr;       // antenna-major mapping for the FX route's visibility gridding (N_p <= 128):
+    int2* fx_ent = nullptr;      // [A+1] row pointers, {weight re bits, (gy << 16) | gx}
+    float* fx_wim = nullptr;     // weight imaginary parts, or nullptr
     int* ant_ptr = nullptr;
     int2* ant_ent = nullptr;
     float* ant_wim = nullptr;

@@ -247,9 +247,127 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256) : "memory");
 }
 
+// ---- the FX route's imaging of an integration's visibilities (Eq. "dirty-image-FX") ----
+//   U(d) = sum_{a, b} V_ab B_ab(d),  B_ab(d) = sum_g M[g, a] conj(M[g - d, b]),
+//   I(k) = Re sum_d U(d) exp(+2 pi i d.k / N_p)  (image pixel order, k = 0 at the centre).
+// One CTA per (channel, pol).  The lag plane U (N_p x N_p, lags wrapped mod N_p; with
+// N_p >= 2 N_g - 1 none alias) is accumulated in shared memory: thread per antenna pair
+// (a, b), every pair of mapping entries (e of a, f of b) adds w_e conj(w_f) V_ab at the lag
+// g_e - g_f (shared-memory atomics).  Then a separable DFT in place: rows (each thread a
+// strided set of one row's outputs), columns straight to the image.
+constexpr int FX_NT = 512;
+
+template <int NP>
+__global__ void __launch_bounds__(FX_NT) fx_image_kernel(const FxArgs a) {
+    constexpr int NPIX = NP * NP, MSK = NP - 1, LG = NP == 32 ? 5 : NP == 64 ? 6 : 7, PER = NPIX / FX_NT;
+    static_assert(PER * FX_NT == NPIX && NP <= 128, "sizes");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* U = reinterpret_cast<float2*>(smem_raw);       // [NP][NP]
+    float2* TW = U + NPIX;                                 // [NP] exp(+2 pi i j / NP)
+    const int tid = threadIdx.x, cp = blockIdx.x, A = a.n_ant;
+    for (int j = tid; j < NP; j += FX_NT) {
+        double s, c;
+        sincospi(2.0 * j / NP, &s, &c);
+        TW[j] = make_float2(float(c), float(s));
+    }
+    for (int i = tid; i < NPIX; i += FX_NT) U[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const float2* V = a.vis + (size_t)cp * A * A;
+    const long long n_pairs = (long long)A * A;
+    for (long long pr = tid; pr < n_pairs; pr += FX_NT) {
+        const int aa = (int)(pr / A), b = (int)(pr - (long long)aa * A);
+        const float2 v = __ldg(V + pr);
+        const int e0 = __ldg(a.ptr + aa), e1 = __ldg(a.ptr + aa + 1);
+        const int f0 = __ldg(a.ptr + b), f1 = __ldg(a.ptr + b + 1);
+        for (int e = e0; e < e1; ++e) {
+            const int2 ee = __ldg(a.ent + e);
+            const float2 we = make_float2(__int_as_float(ee.x), a.wim ? __ldg(a.wim + e) : 0.f);
+            const float2 ve = cmul(we, v);
+            const int gye = ee.y >> 16, gxe = ee.y & 0xFFFF;
+            for (int f = f0; f < f1; ++f) {
+                const int2 ff = __ldg(a.ent + f);
+                float2 t;
+                if (a.wim) {
+                    t = cmulc(ve, make_float2(__int_as_float(ff.x), __ldg(a.wim + f)));
+                } else {
+                    const float wf = __int_as_float(ff.x);
+                    t = make_float2(ve.x * wf, ve.y * wf);
+                }
+                const int idx = (((gye - (ff.y >> 16)) & MSK) << LG) | ((gxe - (ff.y & 0xFFFF)) & MSK);
+                atomicAdd(&U[idx].x, t.x);
+                atomicAdd(&U[idx].y, t.y);
+            }
+        }
+    }
+    __syncthreads();
+    // rows: T(dy, ix) = sum_dx U(dy, dx) exp(+2 pi i dx (ix - NP/2) / NP); thread -> row dy,
+    // pixels ix = q + (FX_NT / NP) j
+    {
+        constexpr int TPR = FX_NT / NP;                    // threads per row
+        const int dy = tid / TPR, q = tid % TPR;
+        float2 acc[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int dx = 0; dx < NP; ++dx) {
+            const float2 u = U[dy * NP + dx];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int kx = q + TPR * j - NP / 2;
+                const float2 w = TW[(dx * kx) & MSK];
+                acc[j].x = fmaf(u.x, w.x, fmaf(-u.y, w.y, acc[j].x));
+                acc[j].y = fmaf(u.x, w.y, fmaf(u.y, w.x, acc[j].y));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PER; ++j) U[dy * NP + q + TPR * j] = acc[j];
+    }
+    __syncthreads();
+    // columns: I(iy, ix) = Re sum_dy T(dy, ix) exp(+2 pi i dy (iy - NP/2) / NP); thread ->
+    // column ix = tid % NP, rows iy = tid / NP + (FX_NT / NP) j
+    {
+        constexpr int RPT = FX_NT / NP;
+        const int ix = tid % NP, r0 = tid / NP;
+        float acc[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) acc[j] = 0.f;
+        for (int dy = 0; dy < NP; ++dy) {
+            const float2 t = U[dy * NP + ix];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int ky = r0 + RPT * j - NP / 2;
+                const float2 w = TW[(dy * ky) & MSK];
+                acc[j] = fmaf(t.x, w.x, fmaf(-t.y, w.y, acc[j]));
+            }
+        }
+        float* img = a.image + (size_t)cp * NPIX;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) img[(r0 + RPT * j) * NP + ix] = acc[j];
+    }
+}
+
+template <int NP>
+cudaError_t launch_fx_image_t(const FxArgs& a, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * ((size_t)NP * NP + NP);
+    cudaError_t e = ensure_smem<fx_image_kernel<NP>>(smem);
+    if (e != cudaSuccess) return e;
+    fx_image_kernel<NP><<<a.n_cp, FX_NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace xe
 
 size_t xeng_smem_bytes() { return xe::smem_bytes(); }
+
+cudaError_t launch_fx_image(int n_pad, const FxArgs& a, cudaStream_t st) {
+    if (a.n_cp == 0) return cudaSuccess;
+    switch (n_pad) {
+        case 32: return xe::launch_fx_image_t<32>(a, st);
+        case 64: return xe::launch_fx_image_t<64>(a, st);
+        case 128: return xe::launch_fx_image_t<128>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st) {
     const int nab = (a.n_ant + 127) / 128;

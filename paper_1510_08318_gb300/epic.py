@@ -1,7 +1,7 @@
 """Thin Python binding of the MOFF imaging C ABI (include/epic.h).
 
 The functions named like the C entry points (`epic_create`, `epic_image`,
-`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_weff`, `epic_isotropic`, `epic_fengine`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
+`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_weff`, `epic_isotropic`, `epic_fengine`, `epic_fx_image`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
 arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
 for torch tensors, and `MoffImage` is the autograd.Function whose backward is the
 library's adjoint kernel.  There is no CPU fallback: if the library has not been built
@@ -21,7 +21,7 @@ EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
-           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine")
+           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine", "epic_fx_image")
 XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
@@ -52,6 +52,8 @@ def load(path=LIB_PATH):
     lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.epic_image_xpol.restype = i32
     lib.epic_image_xpol.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp, vp]
+    lib.epic_fx_image.restype = i32
+    lib.epic_fx_image.argtypes = [vp, vp, vp, vp]
     lib.epic_fengine.restype = i32
     lib.epic_fengine.argtypes = [i32, i32, i32, i32, i32, vp, i32, vp, i32, vp]
     lib.epic_weff.restype = i32
@@ -161,6 +163,10 @@ def fengine(raw, n_chan, in_dtype, out_dtype="f16", stream=None):
     epic_fengine(A, P, n_chan, T, VOLT_DTYPES[in_dtype], raw.data_ptr(), VOLT_DTYPES[out_dtype], out.data_ptr(),
                  raw.device.index or 0, st.cuda_stream)
     return out
+
+
+def epic_fx_image(plan, vis, image, stream):
+    _check(load().epic_fx_image(plan, vis, image, stream))
 
 
 def epic_weff(plan, weff, stream):
@@ -334,6 +340,18 @@ class Plan:
         epic_image_xpol(self._h, vptr, T, self._gains_ptr(gains), accum4.data_ptr(), t_prev, img.data_ptr(),
                         cross.data_ptr(), st.cuda_stream)
         return {"image": img, "cross": cross, "accum4": accum4}
+
+    def fx_image(self, vis, stream=None):
+        """Run epic_fx_image: the FX-route image [C, P, N_p, N_p] of visibilities [C, P, A, A]."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        if (vis.dtype != torch.complex64 or tuple(vis.shape) != (self.n_chan, self.n_pol, self.n_ant, self.n_ant)
+                or not vis.is_cuda or not vis.is_contiguous()):
+            raise ValueError("vis must be a contiguous complex64 CUDA tensor [C, P, A, A]")
+        out = torch.empty((self.n_chan, self.n_pol, self.n_pad, self.n_pad), dtype=torch.float32, device=dev)
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        epic_fx_image(self._h, vis.data_ptr(), out.data_ptr(), st.cuda_stream)
+        return out
 
     def weff(self, stream=None):
         """Run epic_weff: the effective weighting W_eff [N_p, N_p] (float32 CUDA tensor)."""

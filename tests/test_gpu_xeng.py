@@ -121,3 +121,38 @@ def test_rejects_complex64(epic):
     plan = epic.Plan.from_workload(wl)
     with pytest.raises(epic.EpicError):
         plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())
+
+
+def test_gpu_fx_route_equals_moff(epic):
+    """Both routes of Sec. 2 entirely on the GPU: epic_correlate then epic_fx_image gives the
+    image epic_image gives (LWA slice, 4+4-bit, gains; N_p = 128), and matches the FP64 oracle."""
+    wl = synth.workload_lwa(n_chan=2, n_time=64, chan_index=[0, 127])
+    g = synth.random_gains(np.random.default_rng(4), (wl.n_chan, wl.n_pol, wl.n_ant))
+    gd = torch.from_numpy(np.ascontiguousarray(g.astype(np.complex64))).cuda()
+    plan = epic.Plan.from_workload(wl)
+    v = torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda()
+    fx_img = plan.fx_image(plan.correlate(v, gd)).cpu().numpy()
+    moff_img = plan.image(v, gd)["image"].cpu().numpy()
+    M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+    want = moff.moff_image(M, wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad)
+    for got in (fx_img, moff_img):
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-4
+        assert np.abs(got - want).max() < 1e-4 * want.max()
+
+
+@pytest.mark.parametrize("n_pad, n_grid, n_ant", [(32, 14, 20), (64, 30, 60)])
+def test_gpu_fx_image_small_sizes_complex_weights(epic, n_pad, n_grid, n_ant):
+    """FX imaging at N_p = 32 and 64 with complex footprint weights, against the oracle's FX route."""
+    rng = np.random.default_rng(n_pad)
+    pos = rng.uniform(2.0, n_grid - 3.0, (n_ant, 2))
+    kerns = [synth.kernel_square(rng.uniform(0.5, 2.5), 1 / 3) for _ in range(n_ant)]
+    ptr, dxdy, w = synth.pack_kernels(kerns)
+    w = w * np.exp(1j * rng.uniform(0, 2 * np.pi, w.shape))
+    wl = synth.Workload("fxs", pos, ptr, dxdy, w, 1.0, np.zeros(2), n_grid, n_pad, np.full(1, 1e8), 1, 24, "f16")
+    v = rng.standard_normal((24, 1, 1, n_ant)) + 1j * rng.standard_normal((24, 1, 1, n_ant))
+    wl = synth._finish(wl, v, "f16")
+    plan = epic.Plan.from_workload(wl)
+    img = plan.fx_image(plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())).cpu().numpy()
+    M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+    want = fx.fx_image(M, wl.volt, None, wl.n_grid, wl.n_pad).real
+    assert np.linalg.norm(img - want) / np.linalg.norm(want) < 1e-4
