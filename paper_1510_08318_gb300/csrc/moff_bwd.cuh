@@ -78,6 +78,20 @@ moff_bwd_kernel(const BwdArgs a) {
         }
     };
 
+    // raw voltages of an item, loaded one item ahead (owner threads aa = tid + NT i)
+    constexpr int VPT = G::VPT;
+    VT raw[VPT];
+    auto prefetch = [&](int item) {
+        const int cpn = item / T, tn = item - cpn * T;
+        const VT* base = V + ((long long)tn * a.n_cp + cpn) * (long long)A;
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) {
+            const int aa = tid + NT * i;
+            if (aa < A) raw[i] = __ldg(base + aa);
+        }
+    };
+    if (beg < end) prefetch(beg);
+
     int cur = -1;
     for (int item = beg; item < end; ++item) {
         const int cp = item / T;
@@ -102,14 +116,24 @@ moff_bwd_kernel(const BwdArgs a) {
             cur = cp;
         }
 
-        // ---- decode ----
+        // ---- decode (this item's voltages were loaded during the previous one), prefetch ----
         {
             const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
-            for (int aa = tid; aa < A; aa += NT) {
+#pragma unroll
+            for (int i = 0; i < VPT; ++i) {
+                const int aa = tid + NT * i;
+                if (aa < A) {
+                    const float2 v = Volt<VDT>::dec(raw[i]);
+                    VR[aa] = v;
+                    VB[aa] = cmul(GN[aa], v);
+                }
+            }
+            for (int aa = tid + NT * VPT; aa < A; aa += NT) {
                 const float2 v = Volt<VDT>::dec(__ldg(base + aa));
                 VR[aa] = v;
                 VB[aa] = cmul(GN[aa], v);
             }
+            if (item + 1 < end) prefetch(item + 1);
         }
         block_or_cluster_sync<Q>();
 
