@@ -13,7 +13,10 @@
 // bound (largest |g V| of the sample times the largest sum_a |M[g, a]| of the plan), so that
 // the FP16 operands stay in range; |F|^2 is scaled back exactly.
 //
-// One CTA (512 threads) per SM owns all 512 TMEM columns:
+// One CTA per SM (16 worker warps and one issuer warp) owns all 512 TMEM columns.  Only the
+// first thread of the issuer warp issues MMAs: issuing stalls while the tensor pipe's queue is
+// full, and a worker that issued would hold up its share of the CUDA-core work and, through the
+// CTA barriers, every other warp.  TMEM columns:
 //   [0, 128)    stage-1 accumulator X (re 0..63, im 64..127), FP32
 //   [128, 256)  stage-2 A operand: X re hi, re lo, im hi, im lo (FP16 pairs, 32 columns each)
 //   [256, 512)  stage-2 accumulator F (re 256..383, im 384..511), FP32
@@ -35,6 +38,8 @@ namespace dg {
 using namespace tc;
 
 constexpr int NP = 128, NG = 64, NT = 512;
+constexpr int NTH = NT + 32;      // 16 worker warps + one warp whose first thread issues the MMAs
+constexpr int ISSUER = NT;        // thread that issues every tcgen05.mma (never a worker)
 constexpr int WTAB = NP * NG;     // halves per W table
 constexpr int ETAB = NG * NG;     // halves per E^T table
 enum { WR_HI, WR_LO, WI_HI, WI_LO, NWI_HI, NWI_LO, N_WTAB };
@@ -57,7 +62,7 @@ constexpr size_t smem_fixed() {
 }
 
 template <int VDT>
-__global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab) {
+__global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab) {
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __half* sW = reinterpret_cast<__half*>(smem_raw);                  // [N_WTAB][WTAB]
@@ -70,12 +75,13 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
     float* PW = reinterpret_cast<float*>(GN + a.n_ant);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool worker = tid < NT;     // the issuer warp does no gridding, decoding or epilogue work
     const int A = a.n_ant, T = a.n_time;
     const VT* V = static_cast<const VT*>(a.volt);
 
-    for (int i = tid; i < N_WTAB * WTAB / 8; i += NT)
+    for (int i = tid; i < N_WTAB * WTAB / 8; i += NTH)
         reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wtab) + i);
-    for (int aa = tid; aa < A; aa += NT) PW[aa] = 0.f;
+    for (int aa = tid; aa < A; aa += NTH) PW[aa] = 0.f;
     const uint32_t mb1 = smem_u32(&mbar[0]), mb2 = smem_u32(&mbar[1]);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mb1), "r"(1) : "memory");
@@ -111,6 +117,7 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
     // decode + gain; the largest component magnitude goes to vmax[slot] (positive float bits
     // order like unsigned integers)
     auto decode = [&](int item, int slot) {
+        if (!worker) return;
         const int cp = item / T, t = item - cp * T;
         const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
         float m = 0.f;
@@ -125,16 +132,19 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
         if (lane == 0 && m > 0.f) atomicMax(vmax + slot, __float_as_uint(m));
     };
     auto load_gains = [&](int cp) {
+        if (!worker) return;
         for (int aa = tid; aa < A; aa += NT)
             GN[aa] = a.gains ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
     };
     auto flush_power = [&](int cp) {
+        if (!worker) return;
         for (int aa = tid; aa < A; aa += NT) {
             if (a.power != nullptr) atomicAdd(a.power + (size_t)cp * A + aa, (double)PW[aa]);
             PW[aa] = 0.f;
         }
     };
     auto flush_acc = [&](int cp) {
+        if (!worker) return;
         double* dst = a.accum + (size_t)cp * NP * NP;
         const int iy = (ky + NP / 2) & (NP - 1);
 #pragma unroll
@@ -169,6 +179,7 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
             }
             const float down = ldexpf(1.f, -ex);
             scale_cur = ldexpf(1.f, 2 * ex);
+            if (worker) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int cm = warp * 4 + j, xb = cm >> 3, yb = cm & 7;
@@ -204,11 +215,12 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
                 *reinterpret_cast<uint32_t*>(sE + EI_HI * ETAB + off) = ih;
                 *reinterpret_cast<uint32_t*>(sE + EI_LO * ETAB + off) = il;
             }
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) vmax[i & 1] = 0u;   // free for the sample after next
             // ---- stage 1 issue: X = W E (columns transformed) ----
-            if (tid == 0) {
+            if (tid == ISSUER) {
                 fence_after();
                 constexpr uint32_t id1 = idesc(64);
                 constexpr int tr[6][2] = {{WR_HI, ER_HI}, {WR_HI, ER_LO}, {WR_LO, ER_HI},
@@ -231,14 +243,16 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
         if (i >= 1) {
             if (!mbar_wait(mb2, (i - 1) & 1)) failed = true;
             fence_after();
+            if (worker) {
 #pragma unroll
-            for (int c = 0; c < 32; c += 16) {
-                float fr[16], fi[16];
-                tld<16>(tF + lane_base + 32 * qt + c, fr);
-                tld<16>(tF + 128 + lane_base + 32 * qt + c, fi);
-                tld_wait();
+                for (int c = 0; c < 32; c += 16) {
+                    float fr[16], fi[16];
+                    tld<16>(tF + lane_base + 32 * qt + c, fr);
+                    tld<16>(tF + 128 + lane_base + 32 * qt + c, fi);
+                    tld_wait();
 #pragma unroll
-                for (int u = 0; u < 16; ++u) acc[c + u] = fmaf(fmaf(fr[u], fr[u], fi[u] * fi[u]), scale_prev, acc[c + u]);
+                    for (int u = 0; u < 16; ++u) acc[c + u] = fmaf(fmaf(fr[u], fr[u], fi[u] * fi[u]), scale_prev, acc[c + u]);
+                }
             }
             ++since;
             const int prev = item - 1, cp_prev = prev / T;
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
             // ---- split X(i) into the stage-2 operands in TMEM ----
             if (!mbar_wait(mb1, i & 1)) failed = true;
             fence_after();
-            {
+            if (worker) {
                 // quarter qt: part (re / im) = qt >> 1, x range 32 * (qt & 1) .. + 32
                 const int part = qt >> 1, hx = qt & 1;
                 const uint32_t src = tX + lane_base + 64 * part + 32 * hx;
@@ -280,12 +294,12 @@ __global__ void __launch_bounds__(NT, 1) moff_dftgemm_kernel(const FwdArgs a, co
                     tst8(dhi + c / 2, ph);
                     tst8(dlo + c / 2, pl);
                 }
+                tst_wait();
             }
-            tst_wait();
             fence_before();
             failed = __syncthreads_or(failed) != 0;   // uniform across the CTA
             // ---- stage 2 issue: F = X W^T (rows transformed) ----
-            if (tid == 0 && !failed) {
+            if (tid == ISSUER && !failed) {
                 fence_after();
                 constexpr uint32_t id2 = idesc(128);
                 // A operand columns: X re hi/lo at +0/+32, X im hi/lo at +64/+96
@@ -353,7 +367,7 @@ cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm
     case V:                                                                                                  \
         e = ensure_smem<dg::moff_dftgemm_kernel<V>>(smem);                                              \
         if (e != cudaSuccess) return e;                                                                      \
-        if (grid > 0) dg::moff_dftgemm_kernel<V><<<(unsigned)grid, dg::NT, smem, st>>>(a, w);                \
+        if (grid > 0) dg::moff_dftgemm_kernel<V><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w);                \
         return cudaGetLastError();
         EPIC_DG_CASE(0)
         EPIC_DG_CASE(1)
