@@ -137,9 +137,23 @@ int fwd_interleave_lanes(int n_pad);  // S of the warp-interleaved mapping, 0 if
 int exchange_row_stride(int n_pad);   // row stride (float2) of the kernels' exchange buffer
 
 // Tensor-core DFT form of the forward kernel, N_p = 128 (moff_dftgemm.cu).
+// Its gridding walks the 2048 cell pairs (x, y), (x, y + 1), y even, of the 64 x 64 grid in 64
+// slots of 32 pairs ranked by entry count (most first), lanes of a slot in rank order; step k
+// of a slot holds the k-th entry of every lane whose pair has more than k entries (the entries
+// of cell y in cell-major order, then those of cell y + 1).
+struct DgGather {
+    const int2* lane;   // [64][32] {entries of cell y | (entries of the pair) << 16, E^T table offset of (x, y)}
+    const int* base;    // [64] first entry of each slot
+    const int2* ent;    // entries, {weight re bits, antenna}
+    const float* wim;   // weight imaginary parts, or nullptr when every weight is real
+};
 size_t dftgemm_smem_bytes(int n_ant);
 void dftgemm_tables(std::vector<uint16_t>& out);
-cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm, cudaStream_t st);
+// false if a pair has more than 65535 entries
+bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
+                           std::vector<int2>& lane, std::vector<int>& base, std::vector<int2>& ent,
+                           std::vector<float>& wim);
+cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st);
 
 // Standalone gridder: samples per work unit (8, or 4 when 8 do not fit shared memory) and launch.
 size_t grid_smem_bytes(int n_ant, int tb);

@@ -22,11 +22,16 @@
 //   [256, 512)  stage-2 accumulator F (re 256..383, im 384..511), FP32
 // Shared memory holds the six W operand tables (re hi/lo, im hi/lo, -im hi/lo) and the four
 // E^T operand tables (re/im, hi/lo), all K-major in 8 x 8 core matrices, no swizzle.
+// The gridding gathers cell pairs (x, y), (x, y + 1) from slot tables in which the 32 pairs of
+// a warp step have nearly equal entry counts (on the 256-antenna ellipse a cell-major walk
+// kept 40 % of the lanes busy, the ranked slots 96 %); each cell's entries are still summed
+// in cell-major order.
 // Pipeline per image i: grid(i) + stage 2(i-1) on the tensor cores, then stage 1(i) issue,
 // |F|^2 epilogue of i-1, decode of i+1, split of X(i) into TMEM, stage 2(i) issue.
 // Every wait on the tensor cores is bounded; on a timeout the CTA writes NaN into its
 // accumulator block and stops.
 #include <cuda_fp16.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -62,7 +67,8 @@ constexpr size_t smem_fixed() {
 }
 
 template <int VDT>
-__global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab) {
+__global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab,
+                                                              const DgGather g) {
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __half* sW = reinterpret_cast<__half*>(smem_raw);                  // [N_WTAB][WTAB]
@@ -180,36 +186,50 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
             const float down = ldexpf(1.f, -ex);
             scale_cur = ldexpf(1.f, 2 * ex);
             if (worker) {
+            // warp w gathers slots 4w .. 4w + 3, each 32 cell pairs of nearly equal entry count
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int cm = warp * 4 + j, xb = cm >> 3, yb = cm & 7;
-                const int x = 8 * xb + (lane & 7), y = 8 * yb + 2 * (lane >> 3);
-                float2 ev[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int cell = (y + u) * NG + x;
-                    const int e0 = __ldg(a.cell_ptr + cell), e1 = __ldg(a.cell_ptr + cell + 1);
-                    float2 s = make_float2(0.f, 0.f);
-                    if (a.cell_wim) {
-                        for (int e = e0; e < e1; ++e) {
-                            const int2 en = __ldg(a.cell_ent + e);
-                            cfma(s, make_float2(__int_as_float(en.x), __ldg(a.cell_wim + e)), VB[en.y]);
+                const int slot = warp * 4 + j;
+                const int2 lw = __ldg(g.lane + slot * 32 + lane);
+                const int c0 = lw.x & 0xffff, cnt = (int)((unsigned)lw.x >> 16);
+                const int kmax = __shfl_sync(0xffffffffu, cnt, 0);   // lane 0 has the longest list
+                int e = __ldg(g.base + slot) + lane;
+                float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+                if (g.wim) {
+                    for (int k = 0; k < kmax; ++k) {
+                        const bool on = k < cnt;
+                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                        if (on) {
+                            const int2 en = __ldg(g.ent + e);
+                            const float2 w = make_float2(__int_as_float(en.x), __ldg(g.wim + e));
+                            if (k < c0) cfma(s0, w, VB[en.y]);
+                            else cfma(s1, w, VB[en.y]);
                         }
-                    } else {
-                        for (int e = e0; e < e1; ++e) {
-                            const int2 en = __ldg(a.cell_ent + e);
+                        e += n_k;
+                    }
+                } else {
+                    for (int k = 0; k < kmax; ++k) {
+                        const bool on = k < cnt;
+                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                        if (on) {
+                            const int2 en = __ldg(g.ent + e);
                             const float w = __int_as_float(en.x);
                             const float2 v = VB[en.y];
-                            s.x = fmaf(w, v.x, s.x);
-                            s.y = fmaf(w, v.y, s.y);
+                            if (k < c0) {
+                                s0.x = fmaf(w, v.x, s0.x);
+                                s0.y = fmaf(w, v.y, s0.y);
+                            } else {
+                                s1.x = fmaf(w, v.x, s1.x);
+                                s1.y = fmaf(w, v.y, s1.y);
+                            }
                         }
+                        e += n_k;
                     }
-                    ev[u] = s;
                 }
                 uint32_t rh, rl, ih, il;
-                split2(ev[0].x * down, ev[1].x * down, rh, rl);
-                split2(ev[0].y * down, ev[1].y * down, ih, il);
-                const int off = koff(x, y, NG);
+                split2(s0.x * down, s1.x * down, rh, rl);
+                split2(s0.y * down, s1.y * down, ih, il);
+                const int off = lw.y;   // E^T element (x, y), y even: one 32-bit word holds y and y + 1
                 *reinterpret_cast<uint32_t*>(sE + ER_HI * ETAB + off) = rh;
                 *reinterpret_cast<uint32_t*>(sE + ER_LO * ETAB + off) = rl;
                 *reinterpret_cast<uint32_t*>(sE + EI_HI * ETAB + off) = ih;
@@ -356,7 +376,57 @@ void dftgemm_tables(std::vector<uint16_t>& out) {
         }
 }
 
-cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm, cudaStream_t st) {
+// Slot tables of the tensor-core form's gridding.  Pairs are ranked by entry count (most
+// first, ties by position) and the slot of ranks 32r .. 32r + 31 takes max(count) warp steps.
+// Slots go to warps heaviest first, each to the warp with the fewest steps so far among those
+// holding fewer than four (ties to the lowest warp), so the slowest warp's gridding is about
+// the heaviest slot or the mean, whichever is larger.
+bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
+                           std::vector<int2>& lane, std::vector<int>& base, std::vector<int2>& ent,
+                           std::vector<float>& wim) {
+    using namespace dg;
+    constexpr int NPAIR = NG * NG / 2, NSLOT = NPAIR / 32;
+    static_assert(NSLOT == 4 * (NT / 32), "four slots per worker warp");
+    struct Pair { int cell, c0, cnt, off; };
+    std::vector<Pair> pr(NPAIR);
+    for (int yp = 0; yp < NG / 2; ++yp)
+        for (int x = 0; x < NG; ++x) {
+            const int c = 2 * yp * NG + x;
+            const int n0 = cptr[c + 1] - cptr[c], n1 = cptr[c + NG + 1] - cptr[c + NG];
+            if (n0 + n1 > 0xffff) return false;
+            pr[yp * NG + x] = {c, n0, n0 + n1, koff(x, 2 * yp, NG)};
+        }
+    std::vector<int> order(NPAIR);
+    for (int i = 0; i < NPAIR; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return pr[u].cnt > pr[v].cnt; });
+    lane.assign((size_t)NSLOT * 32, int2{0, 0});
+    base.assign(NSLOT, 0);
+    ent.clear();
+    wim.clear();
+    constexpr int NW = NT / 32;
+    int held[NW] = {}, steps[NW] = {};
+    for (int r = 0; r < NSLOT; ++r) {
+        int w = -1;
+        for (int v = 0; v < NW; ++v)
+            if (held[v] < 4 && (w < 0 || steps[v] < steps[w])) w = v;
+        const int pos = 4 * w + held[w]++;
+        steps[w] += pr[order[32 * r]].cnt;
+        const Pair* P[32];
+        for (int i = 0; i < 32; ++i) P[i] = &pr[order[32 * r + i]];
+        base[pos] = (int)ent.size();
+        for (int i = 0; i < 32; ++i)
+            lane[(size_t)pos * 32 + i] = int2{(int)((unsigned)P[i]->c0 | ((unsigned)P[i]->cnt << 16)), P[i]->off};
+        for (int k = 0; k < P[0]->cnt; ++k)
+            for (int i = 0; i < 32 && P[i]->cnt > k; ++i) {
+                const int e = k < P[i]->c0 ? cptr[P[i]->cell] + k : cptr[P[i]->cell + NG] + (k - P[i]->c0);
+                ent.push_back(cent[e]);
+                wim.push_back(cwim[e]);
+            }
+    }
+    return true;
+}
+
+cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st) {
     const size_t smem = dftgemm_smem_bytes(a.n_ant);
     const __half* w = static_cast<const __half*>(wtab);
     cudaError_t e;
@@ -367,7 +437,7 @@ cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, int n_sm
     case V:                                                                                                  \
         e = ensure_smem<dg::moff_dftgemm_kernel<V>>(smem);                                              \
         if (e != cudaSuccess) return e;                                                                      \
-        if (grid > 0) dg::moff_dftgemm_kernel<V><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w);                \
+        if (grid > 0) dg::moff_dftgemm_kernel<V><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w, g);                \
         return cudaGetLastError();
         EPIC_DG_CASE(0)
         EPIC_DG_CASE(1)
