@@ -2,14 +2,19 @@
 // (Eq. "dirty-image-MOFF"; the transform of Sec. 3 "Spatial Fourier Transform" written as two
 // matrix products), N_p = 128 (N_g = 64):
 //
-//   X(ky, x)  = sum_y  W[ky][y] E(y, x)          stage 1, M = 128 (ky), N = 64 (x),   K = 64 (y)
-//   F(ky, kx) = sum_x  X(ky, x) W[kx][x]         stage 2, M = 128 (ky), N = 128 (kx), K = 64 (x)
+//   X(ky, x)  = sum_y  W[ky][y] E(y, x)          stage 1, M = 128 (ky), K = 64 (y)
+//   F(ky, kx) = sum_x  X(ky, x) W[kx][x]         stage 2, M = 128 (ky), K = 64 (x)
 //   I(ky, kx) += |F|^2
 //
 // with W[k][n] = exp(+2 pi i n k / N_p).  Complex products are four real products; every real
 // operand v is split as v = hi + lo (two FP16 numbers, hi = fp16(v), lo = fp16(v - hi)) and each
 // real product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory (about 22 bits of
-// operand precision).  Per image the gridded field is scaled by a power of two, chosen from a
+// operand precision).  The real and imaginary outputs of a stage come from one MMA whose B
+// operand stacks two tables along N: stage 1 takes A = Re W against B = [Re E ; Im E] and
+// A = Im W against [-Im E ; Re E] (N = 128: Re X | Im X); stage 2 takes A = Re X against
+// [Re W ; Im W] and A = Im X against [-Im W ; Re W] (N = 256: Re F | Im F).  Each stage is 24
+// MMAs; the wider N halves the A-operand reads per FLOP, which kept stage 1 waiting on shared
+// memory when it ran as 48 MMAs of N = 64.  Per image the gridded field is scaled by a power of two, chosen from a
 // bound (largest |g V| of the sample times the largest sum_a |M[g, a]| of the plan), so that
 // the FP16 operands stay in range; |F|^2 is scaled back exactly.
 //
@@ -20,8 +25,9 @@
 //   [0, 128)    stage-1 accumulator X (re 0..63, im 64..127), FP32
 //   [128, 256)  stage-2 A operand: X re hi, re lo, im hi, im lo (FP16 pairs, 32 columns each)
 //   [256, 512)  stage-2 accumulator F (re 256..383, im 384..511), FP32
-// Shared memory holds the six W operand tables (re hi/lo, im hi/lo, -im hi/lo) and the four
-// E^T operand tables (re/im, hi/lo), all K-major in 8 x 8 core matrices, no swizzle.
+// Shared memory holds the six W operand tables and the six E^T operand tables (-im, re, im of
+// the hi parts, then of the lo parts, so that every stacked B operand is two adjacent tables),
+// all K-major in 8 x 8 core matrices, no swizzle.
 // The gridding gathers cell pairs (x, y), (x, y + 1) from slot tables in which the 32 pairs of
 // a warp step have nearly equal entry counts (on the 256-antenna ellipse a cell-major walk
 // kept 40 % of the lanes busy, the ranked slots 96 %); each cell's entries are still summed
@@ -47,8 +53,9 @@ constexpr int NTH = NT + 32;      // 16 worker warps + one warp whose first thre
 constexpr int ISSUER = NT;        // thread that issues every tcgen05.mma (never a worker)
 constexpr int WTAB = NP * NG;     // halves per W table
 constexpr int ETAB = NG * NG;     // halves per E^T table
-enum { WR_HI, WR_LO, WI_HI, WI_LO, NWI_HI, NWI_LO, N_WTAB };
-enum { ER_HI, ER_LO, EI_HI, EI_LO, N_ETAB };
+// table order: a stacked B operand [T ; T'] is T followed by the next table in memory
+enum { NWI_HI, WR_HI, WI_HI, NWI_LO, WR_LO, WI_LO, N_WTAB };
+enum { NEI_HI, ER_HI, EI_HI, NEI_LO, ER_LO, EI_LO, N_ETAB };
 
 // (a, b) -> packed FP16 pairs hi = fp16(a, b), lo = fp16((a, b) - hi)
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
@@ -234,6 +241,9 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                 *reinterpret_cast<uint32_t*>(sE + ER_LO * ETAB + off) = rl;
                 *reinterpret_cast<uint32_t*>(sE + EI_HI * ETAB + off) = ih;
                 *reinterpret_cast<uint32_t*>(sE + EI_LO * ETAB + off) = il;
+                // split(-v) = -split(v) exactly: flip both halves' sign bits
+                *reinterpret_cast<uint32_t*>(sE + NEI_HI * ETAB + off) = ih ^ 0x80008000u;
+                *reinterpret_cast<uint32_t*>(sE + NEI_LO * ETAB + off) = il ^ 0x80008000u;
             }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -242,20 +252,16 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
             // ---- stage 1 issue: X = W E (columns transformed) ----
             if (tid == ISSUER) {
                 fence_after();
-                constexpr uint32_t id1 = idesc(64);
-                constexpr int tr[6][2] = {{WR_HI, ER_HI}, {WR_HI, ER_LO}, {WR_LO, ER_HI},
-                                          {NWI_HI, EI_HI}, {NWI_HI, EI_LO}, {NWI_LO, EI_HI}};
-                constexpr int ti[6][2] = {{WR_HI, EI_HI}, {WR_HI, EI_LO}, {WR_LO, EI_HI},
-                                          {WI_HI, ER_HI}, {WI_HI, ER_LO}, {WI_LO, ER_HI}};
+                constexpr uint32_t id1 = idesc(128);
+                // A = W table, B = [table ; next table]: Re W [Re E ; Im E], Im W [-Im E ; Re E]
+                constexpr int ta[6] = {WR_HI, WR_HI, WR_LO, WI_HI, WI_HI, WI_LO};
+                constexpr int tb[6] = {ER_HI, ER_LO, ER_HI, NEI_HI, NEI_LO, NEI_HI};
 #pragma unroll
                 for (int q = 0; q < 6; ++q)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        mma_ss(tX, dW0 + (uint64_t)(tr[q][0] * kWStep + 16 * j),
-                               dE0 + (uint64_t)(tr[q][1] * kEStep + 16 * j), id1, (q | j) != 0);
-                        mma_ss(tX + 64, dW0 + (uint64_t)(ti[q][0] * kWStep + 16 * j),
-                               dE0 + (uint64_t)(ti[q][1] * kEStep + 16 * j), id1, (q | j) != 0);
-                    }
+                    for (int j = 0; j < 4; ++j)
+                        mma_ss(tX, dW0 + (uint64_t)(ta[q] * kWStep + 16 * j), dE0 + (uint64_t)(tb[q] * kEStep + 16 * j),
+                               id1, (q | j) != 0);
                 commit(mb1);
             }
         }
@@ -321,19 +327,16 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
             // ---- stage 2 issue: F = X W^T (rows transformed) ----
             if (tid == ISSUER && !failed) {
                 fence_after();
-                constexpr uint32_t id2 = idesc(128);
-                // A operand columns: X re hi/lo at +0/+32, X im hi/lo at +64/+96
+                constexpr uint32_t id2 = idesc(256);
+                // A operand columns: X re hi/lo at +0/+32, X im hi/lo at +64/+96;
+                // B = [table ; next table]: Re X [Re W ; Im W], Im X [-Im W ; Re W]
                 constexpr int ar[6] = {0, 0, 32, 64, 64, 96};
                 constexpr int br[6] = {WR_HI, WR_LO, WR_HI, NWI_HI, NWI_LO, NWI_HI};
-                constexpr int bi[6] = {WI_HI, WI_LO, WI_HI, WR_HI, WR_LO, WR_HI};
 #pragma unroll
                 for (int q = 0; q < 6; ++q)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < 4; ++j)
                         mma_ts(tF, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(br[q] * kWStep + 16 * j), id2, (q | j) != 0);
-                        mma_ts(tF + 128, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(bi[q] * kWStep + 16 * j), id2,
-                               (q | j) != 0);
-                    }
                 commit(mb2);
             }
             if (!failed) ++issued2;
@@ -357,8 +360,8 @@ size_t dftgemm_smem_bytes(int n_ant) {
     return dg::smem_fixed() + (size_t)n_ant * (2 * sizeof(float2) + sizeof(float));
 }
 
-// W operand tables for N_p = 128: six [128][64] K-major FP16 tables (re hi/lo, im hi/lo,
-// -im hi/lo) of W[k][n] = exp(+2 pi i n k / 128), computed in float64.
+// W operand tables for N_p = 128: six [128][64] K-major FP16 tables (-im, re, im hi parts,
+// then the same lo parts) of W[k][n] = exp(+2 pi i n k / 128), computed in float64.
 void dftgemm_tables(std::vector<uint16_t>& out) {
     using namespace dg;
     out.assign((size_t)N_WTAB * WTAB, 0);
@@ -367,11 +370,12 @@ void dftgemm_tables(std::vector<uint16_t>& out) {
             const double ang = 2.0 * 3.14159265358979323846 * double((n * k) % NP) / double(NP);
             const double re = std::cos(ang), im = std::sin(ang);
             const double vals[3] = {re, im, -im};
+            const int thi[3] = {WR_HI, WI_HI, NWI_HI}, tlo[3] = {WR_LO, WI_LO, NWI_LO};
             for (int c = 0; c < 3; ++c) {
                 const __half hi = __double2half(vals[c]);
                 const __half lo = __double2half(vals[c] - (double)__half2float(hi));
-                out[(size_t)(2 * c) * WTAB + koff(k, n, NG)] = __half_as_ushort(hi);
-                out[(size_t)(2 * c + 1) * WTAB + koff(k, n, NG)] = __half_as_ushort(lo);
+                out[(size_t)thi[c] * WTAB + koff(k, n, NG)] = __half_as_ushort(hi);
+                out[(size_t)tlo[c] * WTAB + koff(k, n, NG)] = __half_as_ushort(lo);
             }
         }
 }
