@@ -500,7 +500,7 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
         epic_plan_fwd_args(plan, volt, n_time, reinterpret_cast<const float2*>(gains), accum, power);
     epic_status s;
     if (plan->xform == EPIC_XFORM_DFTGEMM) {
-        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_ent, plan->dg_wim};
+        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_ent, plan->dg_wim, (int)plan->nnz};
         e = epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st);
         s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core imaging kernel launch");
     } else {

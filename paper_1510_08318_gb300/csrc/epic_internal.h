@@ -146,8 +146,9 @@ struct DgGather {
     const int* base;    // [64] first entry of each slot
     const int2* ent;    // entries, {weight re bits, antenna}
     const float* wim;   // weight imaginary parts, or nullptr when every weight is real
+    int n_ent;          // number of entries
 };
-size_t dftgemm_smem_bytes(int n_ant);
+size_t dftgemm_smem_bytes(int n_ant);   // the least a launch needs (gather tables read through L1)
 void dftgemm_tables(std::vector<uint16_t>& out);
 // false if a pair has more than 65535 entries
 bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,

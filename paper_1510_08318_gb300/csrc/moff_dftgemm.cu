@@ -72,8 +72,23 @@ constexpr int kEStep = 2 * ETAB / 16;    // ... per E^T table
 constexpr size_t smem_fixed() {
     return sizeof(__half) * ((size_t)N_WTAB * WTAB + (size_t)N_ETAB * ETAB) + 64;
 }
+constexpr int NSLOT = NG * NG / 64;   // slots of 32 cell pairs
 
-template <int VDT>
+// Bytes of the gather tables when they are copied into shared memory (after the per-antenna
+// arrays, 16-byte aligned): slot words, slot bases, entries and imaginary weight parts.
+inline size_t table_smem_bytes(int n_ent, bool cw) {
+    return 16 + sizeof(int2) * NSLOT * 32 + sizeof(int) * NSLOT + sizeof(int2) * (size_t)n_ent +
+           (cw ? sizeof(float) * (size_t)n_ent : 0);
+}
+
+// Gather-table load: shared memory when the tables were copied there, else the read-only path.
+template <bool SMT, typename T>
+__device__ __forceinline__ T ldt(const T* p) {
+    if constexpr (SMT) return *p;
+    else return __ldg(p);
+}
+
+template <int VDT, bool SMT>
 __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab,
                                                               const DgGather g) {
     using VT = typename Volt<VDT>::T;
@@ -86,6 +101,16 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed());
     float2* GN = VB + a.n_ant;
     float* PW = reinterpret_cast<float*>(GN + a.n_ant);
+    // gather tables: copied into shared memory when they fit (SMT), else read through L1,
+    // whose share of the SM's 256 KB shrinks as the shared-memory request grows
+    int2* sLane = reinterpret_cast<int2*>(smem_raw + ((smem_fixed() + (size_t)a.n_ant * 20 + 15) & ~(size_t)15));
+    int* sBase = reinterpret_cast<int*>(sLane + NSLOT * 32);
+    int2* sEnt = reinterpret_cast<int2*>(sBase + NSLOT);
+    float* sWim = reinterpret_cast<float*>(sEnt + g.n_ent);
+    const int2* tLane = SMT ? sLane : g.lane;
+    const int* tBase = SMT ? sBase : g.base;
+    const int2* tEnt = SMT ? sEnt : g.ent;
+    const float* tWim = g.wim == nullptr ? nullptr : SMT ? sWim : g.wim;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = tid < NT;     // the issuer warp does no gridding, decoding or epilogue work
@@ -95,6 +120,13 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     for (int i = tid; i < N_WTAB * WTAB / 8; i += NTH)
         reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wtab) + i);
     for (int aa = tid; aa < A; aa += NTH) PW[aa] = 0.f;
+    if constexpr (SMT) {
+        for (int q = tid; q < NSLOT * 32; q += NTH) sLane[q] = __ldg(g.lane + q);
+        for (int q = tid; q < NSLOT; q += NTH) sBase[q] = __ldg(g.base + q);
+        for (int q = tid; q < g.n_ent; q += NTH) sEnt[q] = __ldg(g.ent + q);
+        if (g.wim)
+            for (int q = tid; q < g.n_ent; q += NTH) sWim[q] = __ldg(g.wim + q);
+    }
     const uint32_t mb1 = smem_u32(&mbar[0]), mb2 = smem_u32(&mbar[1]);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mb1), "r"(1) : "memory");
@@ -197,18 +229,18 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int slot = warp * 4 + j;
-                const int2 lw = __ldg(g.lane + slot * 32 + lane);
+                const int2 lw = ldt<SMT>(tLane + slot * 32 + lane);
                 const int c0 = lw.x & 0xffff, cnt = (int)((unsigned)lw.x >> 16);
                 const int kmax = __shfl_sync(0xffffffffu, cnt, 0);   // lane 0 has the longest list
-                int e = __ldg(g.base + slot) + lane;
+                int e = ldt<SMT>(tBase + slot) + lane;
                 float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-                if (g.wim) {
+                if (tWim) {
                     for (int k = 0; k < kmax; ++k) {
                         const bool on = k < cnt;
                         const int n_k = __popc(__ballot_sync(0xffffffffu, on));
                         if (on) {
-                            const int2 en = __ldg(g.ent + e);
-                            const float2 w = make_float2(__int_as_float(en.x), __ldg(g.wim + e));
+                            const int2 en = ldt<SMT>(tEnt + e);
+                            const float2 w = make_float2(__int_as_float(en.x), ldt<SMT>(tWim + e));
                             if (k < c0) cfma(s0, w, VB[en.y]);
                             else cfma(s1, w, VB[en.y]);
                         }
@@ -219,7 +251,7 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                         const bool on = k < cnt;
                         const int n_k = __popc(__ballot_sync(0xffffffffu, on));
                         if (on) {
-                            const int2 en = __ldg(g.ent + e);
+                            const int2 en = ldt<SMT>(tEnt + e);
                             const float w = __int_as_float(en.x);
                             const float2 v = VB[en.y];
                             if (k < c0) {
@@ -431,21 +463,31 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
 }
 
 cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st) {
-    const size_t smem = dftgemm_smem_bytes(a.n_ant);
     const __half* w = static_cast<const __half*>(wtab);
-    cudaError_t e;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    // the gather tables go into shared memory when the whole request still fits one block
+    const size_t base = (dftgemm_smem_bytes(a.n_ant) + 15) & ~(size_t)15;
+    const size_t with_tables = base + dg::table_smem_bytes(g.n_ent, g.wim != nullptr);
+    const bool smt = with_tables <= (size_t)optin;
+    const size_t smem = smt ? with_tables : dftgemm_smem_bytes(a.n_ant);
     long long grid = n_sm;
     if (grid > a.n_items) grid = a.n_items;
-    switch (vdt) {
-#define EPIC_DG_CASE(V)                                                                                      \
-    case V:                                                                                                  \
-        e = ensure_smem<dg::moff_dftgemm_kernel<V>>(smem);                                              \
+    switch (vdt * 2 + (smt ? 1 : 0)) {
+#define EPIC_DG_CASE(V, S)                                                                                   \
+    case V * 2 + S:                                                                                          \
+        e = ensure_smem<dg::moff_dftgemm_kernel<V, S>>(smem);                                                \
         if (e != cudaSuccess) return e;                                                                      \
-        if (grid > 0) dg::moff_dftgemm_kernel<V><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w, g);                \
+        if (grid > 0) dg::moff_dftgemm_kernel<V, S><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w, g);          \
         return cudaGetLastError();
-        EPIC_DG_CASE(0)
-        EPIC_DG_CASE(1)
-        EPIC_DG_CASE(2)
+        EPIC_DG_CASE(0, 0)
+        EPIC_DG_CASE(0, 1)
+        EPIC_DG_CASE(1, 0)
+        EPIC_DG_CASE(1, 1)
+        EPIC_DG_CASE(2, 0)
+        EPIC_DG_CASE(2, 1)
 #undef EPIC_DG_CASE
         default:
             return cudaErrorInvalidValue;

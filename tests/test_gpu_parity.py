@@ -279,6 +279,22 @@ def test_dftgemm_small(epic, n_grid, n_ant, n_time, n_chan, n_pol, vdtype):
     np.testing.assert_allclose(out["power"].cpu().numpy(), (np.abs(wl.volt * gg[None]) ** 2).sum(0), rtol=1e-5)
 
 
+def test_dftgemm_tables_beyond_shared_memory(epic):
+    """2000 antennas with complex weights: the gridding's slot tables (over 10,000 entries of
+    12 bytes) do not fit in shared memory beside the DFT operand tables, so the kernel reads
+    them through L1 instead of copying them; same oracle, same tolerance."""
+    wl = _small_workload(128, 64, 2000, 3, 1, 1, seed=2021, vdtype="c64")
+    M = oracle_map(wl)
+    assert M.nnz * 12 > 96 * 1024      # more than shared memory has left for the tables
+    rng = np.random.default_rng(5)
+    g = synth.random_gains(rng, (1, 1, wl.n_ant))
+    plan = epic.Plan.from_workload(wl).set_transform("dftgemm")
+    out = plan.image(to_dev(wl), gains_dev(g))
+    torch.cuda.synchronize()
+    check_close(out["image"].cpu().numpy(), moff.moff_image(M, wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad),
+                "image")
+
+
 def test_dftgemm_lwa_slice_matches_fft(epic):
     """LWA-like slice (4+4-bit, 2 channels, 2 pols, 48 samples): tensor-core form vs the oracle
     and vs the FP32 FFT form; the continuation rule holds for it too."""
