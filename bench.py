@@ -34,9 +34,9 @@ SM_MAX_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch on this workload, from ncu captures
 # of the 8-channel case (16,384 images) scaled by the units per launch (x16); None until
 # captured for the current kernel.  Forward FFT kernel: 6.48 MB per capture; tensor-core
-# DFT-GEMM kernel: 6.58 MB per capture.
+# DFT-GEMM kernel: 6.57 MB per capture.
 FWD_TRAFFIC_BYTES = 103.7e6
-DG_TRAFFIC_BYTES = None
+DG_TRAFFIC_BYTES = 105.1e6
 # standalone gridder: 480.3 MB per capture
 GRID_TRAFFIC_BYTES = 7.685e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")

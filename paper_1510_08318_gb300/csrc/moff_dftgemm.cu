@@ -29,9 +29,11 @@
 // the hi parts, then of the lo parts, so that every stacked B operand is two adjacent tables),
 // all K-major in 8 x 8 core matrices, no swizzle.
 // The gridding gathers cell pairs (x, y), (x, y + 1) from slot tables in which the 32 pairs of
-// a warp step have nearly equal entry counts (on the 256-antenna ellipse a cell-major walk
-// kept 40 % of the lanes busy, the ranked slots 96 %); each cell's entries are still summed
-// in cell-major order.
+// a warp step have similar entry counts and store to 32 distinct shared-memory banks (on the
+// 256-antenna ellipse a cell-major walk kept 40 % of the lanes busy, these slots 81 %, with the
+// slowest warp at the heaviest slot); each cell's entries are still summed in cell-major order.
+// The tables sit in shared memory when they fit beside the operand tables, else they are read
+// through L1.
 // Pipeline per image i: grid(i) + stage 2(i-1) on the tensor cores, then stage 1(i) issue,
 // |F|^2 epilogue of i-1, decode of i+1, split of X(i) into TMEM, stage 2(i) issue.
 // Every wait on the tensor cores is bounded; on a timeout the CTA writes NaN into its
@@ -251,16 +253,16 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                         const bool on = k < cnt;
                         const int n_k = __popc(__ballot_sync(0xffffffffu, on));
                         if (on) {
+                            // both cells take the entry, one with weight 0 (adds an exact 0):
+                            // no divergent branch inside the step
                             const int2 en = ldt<SMT>(tEnt + e);
                             const float w = __int_as_float(en.x);
                             const float2 v = VB[en.y];
-                            if (k < c0) {
-                                s0.x = fmaf(w, v.x, s0.x);
-                                s0.y = fmaf(w, v.y, s0.y);
-                            } else {
-                                s1.x = fmaf(w, v.x, s1.x);
-                                s1.y = fmaf(w, v.y, s1.y);
-                            }
+                            const float w0 = k < c0 ? w : 0.f, w1 = w - w0;
+                            s0.x = fmaf(w0, v.x, s0.x);
+                            s0.y = fmaf(w0, v.y, s0.y);
+                            s1.x = fmaf(w1, v.x, s1.x);
+                            s1.y = fmaf(w1, v.y, s1.y);
                         }
                         e += n_k;
                     }
@@ -412,17 +414,21 @@ void dftgemm_tables(std::vector<uint16_t>& out) {
         }
 }
 
-// Slot tables of the tensor-core form's gridding.  Pairs are ranked by entry count (most
-// first, ties by position) and the slot of ranks 32r .. 32r + 31 takes max(count) warp steps.
-// Slots go to warps heaviest first, each to the warp with the fewest steps so far among those
-// holding fewer than four (ties to the lowest warp), so the slowest warp's gridding is about
-// the heaviest slot or the mean, whichever is larger.
+// Slot tables of the tensor-core form's gridding.  The word of pair (x, y), y even, lands in
+// shared-memory bank 4 (x mod 8) + (y / 2 mod 4) of every E^T table, so the 2048 pairs fall
+// into 32 bank classes of 64.  Within each class pairs are ranked by entry count (most first,
+// ties by position) and slot r takes the r-th pair of every class: its 32 lanes store to 32
+// distinct banks, and classes interleave finely enough over the aperture that the r-th pairs
+// of all classes have similar counts.  A slot takes max(count) warp steps; slots go to warps
+// heaviest first, each to the warp with the fewest steps so far among those holding fewer
+// than four (ties to the lowest warp), so the slowest warp's gridding is about the heaviest
+// slot or the mean, whichever is larger.
 bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
                            std::vector<int2>& lane, std::vector<int>& base, std::vector<int2>& ent,
                            std::vector<float>& wim) {
     using namespace dg;
-    constexpr int NPAIR = NG * NG / 2, NSLOT = NPAIR / 32;
-    static_assert(NSLOT == 4 * (NT / 32), "four slots per worker warp");
+    constexpr int NPAIR = NG * NG / 2;
+    static_assert(NSLOT * 32 == NPAIR && NSLOT == 4 * (NT / 32), "four slots of 32 pairs per worker warp");
     struct Pair { int cell, c0, cnt, off; };
     std::vector<Pair> pr(NPAIR);
     for (int yp = 0; yp < NG / 2; ++yp)
@@ -432,9 +438,20 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
             if (n0 + n1 > 0xffff) return false;
             pr[yp * NG + x] = {c, n0, n0 + n1, koff(x, 2 * yp, NG)};
         }
-    std::vector<int> order(NPAIR);
-    for (int i = 0; i < NPAIR; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return pr[u].cnt > pr[v].cnt; });
+    auto heavier = [&](int u, int v) { return pr[u].cnt > pr[v].cnt; };
+    std::vector<std::vector<int>> cls(32);
+    for (int q = 0; q < NPAIR; ++q) cls[4 * ((q % NG) & 7) + ((q / NG) & 3)].push_back(q);
+    for (auto& c : cls) std::stable_sort(c.begin(), c.end(), heavier);
+    std::vector<std::vector<int>> slots(NSLOT);
+    for (int r = 0; r < NSLOT; ++r) {
+        for (int c = 0; c < 32; ++c) slots[r].push_back(cls[c][r]);
+        std::stable_sort(slots[r].begin(), slots[r].end(), heavier);   // lanes in rank order
+    }
+    std::stable_sort(slots.begin(), slots.end(), [&](const std::vector<int>& u, const std::vector<int>& v) {
+        return pr[u[0]].cnt > pr[v[0]].cnt;
+    });
+    std::vector<int> order;
+    for (const auto& sl : slots) order.insert(order.end(), sl.begin(), sl.end());
     lane.assign((size_t)NSLOT * 32, int2{0, 0});
     base.assign(NSLOT, 0);
     ent.clear();
