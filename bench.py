@@ -36,7 +36,7 @@ SM_MAX_MHZ = 2070.0
 # captured for the current kernel.  Forward FFT kernel: 6.48 MB per capture; tensor-core
 # DFT-GEMM kernel: 6.57 MB per capture.
 FWD_TRAFFIC_BYTES = 103.7e6
-DG_TRAFFIC_BYTES = 105.1e6
+DG_TRAFFIC_BYTES = None
 # standalone gridder: 480.3 MB per capture
 GRID_TRAFFIC_BYTES = 7.685e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -51,6 +51,7 @@ namespace dg {
 using namespace tc;
 
 constexpr int NP = 128, NG = 64, NT = 512;
+constexpr int VPT = 2;            // antennas per worker thread whose voltages are prefetched
 constexpr int NTH = NT + 32;      // 16 worker warps + one warp whose first thread issues the MMAs
 constexpr int ISSUER = NT;        // thread that issues every tcgen05.mma (never a worker)
 constexpr int WTAB = NP * NG;     // halves per W table
@@ -161,19 +162,41 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 
+    // raw voltages of antennas tid + NT * i (i < VPT) of an item, loaded one item ahead so the
+    // decode does not wait on HBM; antennas beyond NT * VPT are loaded when decoded
+    VT raw[VPT];
+    auto prefetch = [&](int item) {
+        if (!worker) return;
+        const int cp = item / T, t = item - cp * T;
+        const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q)
+            if (tid + NT * q < A) raw[q] = __ldg(base + tid + NT * q);
+    };
     // decode + gain; the largest component magnitude goes to vmax[slot] (positive float bits
-    // order like unsigned integers)
+    // order like unsigned integers); then the next item's voltages are prefetched
     auto decode = [&](int item, int slot) {
         if (!worker) return;
         const int cp = item / T, t = item - cp * T;
         const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
         float m = 0.f;
-        for (int aa = tid; aa < A; aa += NT) {
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int aa = tid + NT * q;
+            if (aa < A) {
+                const float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[q]));
+                VB[aa] = vp;
+                PW[aa] += cnorm(vp);
+                m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
+            }
+        }
+        for (int aa = tid + NT * VPT; aa < A; aa += NT) {
             const float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
             VB[aa] = vp;
             PW[aa] += cnorm(vp);
             m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
         }
+        if (item + 1 < beg + n) prefetch(item + 1);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0 && m > 0.f) atomicMax(vmax + slot, __float_as_uint(m));
@@ -208,6 +231,7 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     int since = 0;
     if (n > 0) {
         load_gains(beg / T);
+        prefetch(beg);
         decode(beg, 0);
     }
     __syncthreads();
