@@ -169,9 +169,10 @@ epic_status epic_image_backward(const epic_plan *plan, const void *volt, int n_t
  *
  * XY follows from the four sums by the polarisation identity, evaluated in float64:
  * Re XY = (S_{X+Y} - S_X - S_Y) / 2T, Im XY = (S_{X+iY} - S_X - S_Y) / 2T.  The forward
- * kernel therefore runs 4 C instead of 2 C (channel, pol) images.  The FFT form is used
- * whatever epic_set_transform chose; no auto-correlation term.  EPIC_EINVAL if the plan
- * does not have two pols.
+ * kernel therefore runs 4 C instead of 2 C (channel, pol) images, in the transform
+ * epic_set_transform chose (FP32 FFT or tensor-core DFT-GEMM); no auto-correlation term.
+ * EPIC_EINVAL if the plan does not have two pols; EPIC_EUNSUPPORTED if the antennas do not
+ * fit the chosen kernel's shared memory.
  */
 epic_status epic_image_xpol(const epic_plan *plan, const void *volt, int n_time, const float *gains,
                             double *accum4, int64_t t_prev, float *image, float *cross, void *stream);

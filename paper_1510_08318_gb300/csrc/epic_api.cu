@@ -569,9 +569,11 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
-    if (epic::fwd_xpol_smem_bytes(plan->n_pad, plan->n_ant) > (size_t)smem_optin)
-        return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the cross-polarisation kernel's shared memory",
-                         plan->n_ant);
+    const bool dg = plan->xform == EPIC_XFORM_DFTGEMM;
+    if ((dg ? epic::dftgemm_smem_bytes(plan->n_ant, true) : epic::fwd_xpol_smem_bytes(plan->n_pad, plan->n_ant)) >
+        (size_t)smem_optin)
+        return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the %s cross-polarisation kernel's shared memory",
+                         plan->n_ant, dg ? "tensor-core" : "FFT");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long npix = (long long)plan->n_pad * plan->n_pad;
     cudaError_t e;
@@ -580,7 +582,14 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     epic::FwdArgs a = epic_plan_fwd_args(plan, volt, n_time, reinterpret_cast<const float2*>(gains), accum4, nullptr);
     a.n_cp = plan->n_chan * 4;          // virtual pols X, Y, X + Y, X + iY per channel
     a.n_items = (long long)a.n_cp * n_time;
-    const epic_status s = launch_fwd(plan, a, st, true);
+    epic_status s;
+    if (dg) {
+        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_ent, plan->dg_wim, (int)plan->nnz};
+        e = epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st, true);
+        s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core cross-polarisation kernel launch");
+    } else {
+        s = launch_fwd(plan, a, st, true);
+    }
     if (s != EPIC_OK) return s;
     if ((e = epic::launch_finalize_xpol(accum4, image, reinterpret_cast<float2*>(cross), plan->n_chan, npix,
                                         1.0 / double(t_prev + n_time), st)) != cudaSuccess)

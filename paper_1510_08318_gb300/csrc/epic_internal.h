@@ -148,13 +148,15 @@ struct DgGather {
     const float* wim;   // weight imaginary parts, or nullptr when every weight is real
     int n_ent;          // number of entries
 };
-size_t dftgemm_smem_bytes(int n_ant);   // the least a launch needs (gather tables read through L1)
+size_t dftgemm_smem_bytes(int n_ant, bool xpol = false);   // the least a launch needs (tables read through L1)
 void dftgemm_tables(std::vector<uint16_t>& out);
 // false if a pair has more than 65535 entries
 bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
                            std::vector<int2>& lane, std::vector<int>& base, std::vector<int2>& ent,
                            std::vector<float>& wim);
-cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st);
+// xpol: the (channel, pol) items are the 4 C virtual pols of dual-pol data, as in the FFT form
+cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st,
+                           bool xpol = false);
 
 // Standalone gridder: samples per work unit (8, or 4 when 8 do not fit shared memory) and launch.
 size_t grid_smem_bytes(int n_ant, int tb);

@@ -77,6 +77,9 @@ constexpr size_t smem_fixed() {
 }
 constexpr int NSLOT = NG * NG / 64;   // slots of 32 cell pairs
 
+// Shared-memory bytes per antenna: voltages, gains, power (and the Y gains of XP).
+constexpr size_t ant_bytes(bool xp) { return xp ? 28 : 20; }
+
 // Bytes of the gather tables when they are copied into shared memory (after the per-antenna
 // arrays, 16-byte aligned): slot words, slot bases, entries and imaginary weight parts.
 inline size_t table_smem_bytes(int n_ent, bool cw) {
@@ -91,7 +94,7 @@ __device__ __forceinline__ T ldt(const T* p) {
     else return __ldg(p);
 }
 
-template <int VDT, bool SMT>
+template <int VDT, bool SMT, bool XP>
 __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab,
                                                               const DgGather g) {
     using VT = typename Volt<VDT>::T;
@@ -103,10 +106,11 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     unsigned int* vmax = reinterpret_cast<unsigned int*>(tslot + 2);  // [2] max |g V| (float bits) per parity
     float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed());
     float2* GN = VB + a.n_ant;
-    float* PW = reinterpret_cast<float*>(GN + a.n_ant);
+    float2* GY = GN + a.n_ant;                                         // XP only: phi_v g_Y
+    float* PW = reinterpret_cast<float*>(GN + (XP ? 2 : 1) * a.n_ant);
     // gather tables: copied into shared memory when they fit (SMT), else read through L1,
     // whose share of the SM's 256 KB shrinks as the shared-memory request grows
-    int2* sLane = reinterpret_cast<int2*>(smem_raw + ((smem_fixed() + (size_t)a.n_ant * 20 + 15) & ~(size_t)15));
+    int2* sLane = reinterpret_cast<int2*>(smem_raw + ((smem_fixed() + (size_t)a.n_ant * ant_bytes(XP) + 15) & ~(size_t)15));
     int* sBase = reinterpret_cast<int*>(sLane + NSLOT * 32);
     int2* sEnt = reinterpret_cast<int2*>(sBase + NSLOT);
     float* sWim = reinterpret_cast<float*>(sEnt + g.n_ent);
@@ -162,36 +166,63 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 
+    // voltage row of item (cp, t); for XP, cp = 4 c + v runs over the virtual pols of channel
+    // c and the row is pol X of channel c (pol Y for v = 1), the Y row following it
+    auto vrow = [&](int cp, int t) -> const VT* {
+        if constexpr (XP) {
+            const int c = cp >> 2, p = (cp & 3) == 1 ? 1 : 0;
+            return V + ((long long)t * (a.n_cp >> 1) + 2 * c + p) * (long long)A;
+        } else {
+            return V + ((long long)t * a.n_cp + cp) * (long long)A;
+        }
+    };
     // raw voltages of antennas tid + NT * i (i < VPT) of an item, loaded one item ahead so the
     // decode does not wait on HBM; antennas beyond NT * VPT are loaded when decoded
-    VT raw[VPT];
+    VT raw[VPT], rawy[XP ? VPT : 1];
     auto prefetch = [&](int item) {
         if (!worker) return;
         const int cp = item / T, t = item - cp * T;
-        const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
+        const VT* base = vrow(cp, t);
 #pragma unroll
-        for (int q = 0; q < VPT; ++q)
+        for (int q = 0; q < VPT; ++q) {
             if (tid + NT * q < A) raw[q] = __ldg(base + tid + NT * q);
+            if constexpr (XP) {
+                if (tid + NT * q < A && (cp & 3) >= 2) rawy[q] = __ldg(base + A + tid + NT * q);
+            }
+        }
     };
     // decode + gain; the largest component magnitude goes to vmax[slot] (positive float bits
     // order like unsigned integers); then the next item's voltages are prefetched
     auto decode = [&](int item, int slot) {
         if (!worker) return;
         const int cp = item / T, t = item - cp * T;
-        const VT* base = V + ((long long)t * a.n_cp + cp) * (long long)A;
+        const VT* base = vrow(cp, t);
+        const bool two = XP && (cp & 3) >= 2;     // virtual pol combining X and Y
         float m = 0.f;
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
             const int aa = tid + NT * q;
             if (aa < A) {
-                const float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[q]));
+                float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[q]));
+                if constexpr (XP) {
+                    if (two) {
+                        const float2 w = cmul(GY[aa], Volt<VDT>::dec(rawy[q]));
+                        vp.x += w.x;
+                        vp.y += w.y;
+                    }
+                }
                 VB[aa] = vp;
                 PW[aa] += cnorm(vp);
                 m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
             }
         }
         for (int aa = tid + NT * VPT; aa < A; aa += NT) {
-            const float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
+            float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
+            if (two) {
+                const float2 w = cmul(GY[aa], Volt<VDT>::dec(__ldg(base + A + aa)));
+                vp.x += w.x;
+                vp.y += w.y;
+            }
             VB[aa] = vp;
             PW[aa] += cnorm(vp);
             m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
@@ -203,8 +234,18 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     };
     auto load_gains = [&](int cp) {
         if (!worker) return;
-        for (int aa = tid; aa < A; aa += NT)
-            GN[aa] = a.gains ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
+        if constexpr (XP) {
+            // virtual pol v = cp & 3: X, Y, X + Y, X + iY; GY = phi_v g_Y (phi_2 = 1, phi_3 = i)
+            const int c = cp >> 2, v = cp & 3, p = v == 1 ? 1 : 0;
+            for (int aa = tid; aa < A; aa += NT) {
+                GN[aa] = a.gains ? a.gains[(size_t)(2 * c + p) * A + aa] : make_float2(1.f, 0.f);
+                const float2 gy = a.gains ? a.gains[(size_t)(2 * c + 1) * A + aa] : make_float2(1.f, 0.f);
+                GY[aa] = v == 3 ? make_float2(-gy.y, gy.x) : gy;
+            }
+        } else {
+            for (int aa = tid; aa < A; aa += NT)
+                GN[aa] = a.gains ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
+        }
     };
     auto flush_power = [&](int cp) {
         if (!worker) return;
@@ -414,8 +455,8 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
 
 }  // namespace dg
 
-size_t dftgemm_smem_bytes(int n_ant) {
-    return dg::smem_fixed() + (size_t)n_ant * (2 * sizeof(float2) + sizeof(float));
+size_t dftgemm_smem_bytes(int n_ant, bool xpol) {
+    return dg::smem_fixed() + (size_t)n_ant * dg::ant_bytes(xpol);
 }
 
 // W operand tables for N_p = 128: six [128][64] K-major FP16 tables (-im, re, im hi parts,
@@ -503,32 +544,39 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
     return true;
 }
 
-cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st) {
+cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st,
+                           bool xpol) {
     const __half* w = static_cast<const __half*>(wtab);
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
     // the gather tables go into shared memory when the whole request still fits one block
-    const size_t base = (dftgemm_smem_bytes(a.n_ant) + 15) & ~(size_t)15;
+    const size_t base = (dftgemm_smem_bytes(a.n_ant, xpol) + 15) & ~(size_t)15;
     const size_t with_tables = base + dg::table_smem_bytes(g.n_ent, g.wim != nullptr);
     const bool smt = with_tables <= (size_t)optin;
-    const size_t smem = smt ? with_tables : dftgemm_smem_bytes(a.n_ant);
+    const size_t smem = smt ? with_tables : dftgemm_smem_bytes(a.n_ant, xpol);
     long long grid = n_sm;
     if (grid > a.n_items) grid = a.n_items;
-    switch (vdt * 2 + (smt ? 1 : 0)) {
-#define EPIC_DG_CASE(V, S)                                                                                   \
-    case V * 2 + S:                                                                                          \
-        e = ensure_smem<dg::moff_dftgemm_kernel<V, S>>(smem);                                                \
+    switch (vdt * 4 + (smt ? 2 : 0) + (xpol ? 1 : 0)) {
+#define EPIC_DG_CASE(V, S, X)                                                                                \
+    case V * 4 + S * 2 + X:                                                                                  \
+        e = ensure_smem<dg::moff_dftgemm_kernel<V, S, X>>(smem);                                             \
         if (e != cudaSuccess) return e;                                                                      \
-        if (grid > 0) dg::moff_dftgemm_kernel<V, S><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w, g);          \
+        if (grid > 0) dg::moff_dftgemm_kernel<V, S, X><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w, g);       \
         return cudaGetLastError();
-        EPIC_DG_CASE(0, 0)
-        EPIC_DG_CASE(0, 1)
-        EPIC_DG_CASE(1, 0)
-        EPIC_DG_CASE(1, 1)
-        EPIC_DG_CASE(2, 0)
-        EPIC_DG_CASE(2, 1)
+        EPIC_DG_CASE(0, 0, 0)
+        EPIC_DG_CASE(0, 0, 1)
+        EPIC_DG_CASE(0, 1, 0)
+        EPIC_DG_CASE(0, 1, 1)
+        EPIC_DG_CASE(1, 0, 0)
+        EPIC_DG_CASE(1, 0, 1)
+        EPIC_DG_CASE(1, 1, 0)
+        EPIC_DG_CASE(1, 1, 1)
+        EPIC_DG_CASE(2, 0, 0)
+        EPIC_DG_CASE(2, 0, 1)
+        EPIC_DG_CASE(2, 1, 0)
+        EPIC_DG_CASE(2, 1, 1)
 #undef EPIC_DG_CASE
         default:
             return cudaErrorInvalidValue;

@@ -62,8 +62,8 @@ def _dual(n_pad, n_grid, n_ant, n_time, n_chan, vdtype, seed, alpha=0.6 - 0.5j):
     return synth._finish(wl, v, vdtype)
 
 
-def run(epic, wl, gains=None, t_split=None):
-    plan = epic.Plan.from_workload(wl)
+def run(epic, wl, gains=None, t_split=None, xform="fft"):
+    plan = epic.Plan.from_workload(wl).set_transform(xform)
     g = None if gains is None else torch.from_numpy(np.ascontiguousarray(gains.astype(np.complex64))).cuda()
     v = torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda()
     if t_split is None:
@@ -110,6 +110,42 @@ def test_continuation_and_single_pol_agreement(epic):
     img = plan.image(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())["image"].cpu().numpy()
     a = one["image"].cpu().numpy()
     assert np.linalg.norm(a - img) / np.linalg.norm(img) < 1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# the tensor-core DFT form (N_p = 128) runs the same virtual pols: same oracle, same bounds
+# ---------------------------------------------------------------------------------------------
+def test_dftgemm_lwa_slice_ci4_gains(epic):
+    wl = synth.workload_lwa(n_chan=2, n_time=40, chan_index=[0, 127])
+    g = synth.random_gains(np.random.default_rng(6), (wl.n_chan, 2, wl.n_ant))
+    out = run(epic, wl, g, xform="dftgemm")
+    check(out, moff.moff_cross_image(oracle_map(wl), wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad),
+          "lwa tensor-core")
+
+
+@pytest.mark.parametrize("n_grid, n_ant, n_time, n_chan, vdtype", [
+    (64, 700, 5, 1, "f16"),      # A beyond the prefetched antennas' first slot
+    (40, 60, 6, 2, "c64"),       # ragged grid, two channels
+    (64, 1500, 3, 1, "c64"),     # A beyond the prefetched antennas (tail loop)
+])
+def test_dftgemm_polarised(epic, n_grid, n_ant, n_time, n_chan, vdtype):
+    wl = _dual(128, n_grid, n_ant, n_time, n_chan, vdtype, seed=n_ant + 11)
+    g = synth.random_gains(np.random.default_rng(n_ant + 1), (n_chan, 2, n_ant))
+    out = run(epic, wl, g, xform="dftgemm")
+    want = moff.moff_cross_image(oracle_map(wl), wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad)
+    check(out, want, "tensor-core %d antennas" % n_ant, polarised=True)
+
+
+def test_dftgemm_continuation_matches_fft(epic):
+    """Two tensor-core calls (t_prev) equal one, and agree with the FFT form's four products."""
+    wl = _dual(128, 50, 80, 10, 2, "c64", seed=9)
+    one = run(epic, wl, xform="dftgemm")
+    two = run(epic, wl, t_split=4, xform="dftgemm")
+    ref = run(epic, wl)
+    for k in ("image", "cross"):
+        a, b, f = one[k].cpu().numpy(), two[k].cpu().numpy(), ref[k].cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-6
+        assert np.linalg.norm(a - f) / np.linalg.norm(f) < 1e-4
 
 
 def test_rejects_single_pol_plan(epic):
