@@ -56,8 +56,9 @@ void free_plan(epic_plan* p) {
     cudaFree(p->dg_tab);
     cudaFree(p->dg_lane);
     cudaFree(p->dg_base);
-    cudaFree(p->dg_ent);
+    cudaFree(p->dg_wre);
     cudaFree(p->dg_wim);
+    cudaFree(p->dg_ant);
     delete p;
 }
 
@@ -298,10 +299,11 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     }
 
     // gridding slot tables of the tensor-core form (N_p = 128 only)
-    std::vector<int2> dlane, dent;
+    std::vector<int2> dlane;
     std::vector<int> dbase;
-    std::vector<float> dwim;
-    const bool dg_ok = n_pad == 128 && epic::dftgemm_gather_tables(cptr, cent, cwim, dlane, dbase, dent, dwim);
+    std::vector<float> dwre, dwim;
+    std::vector<uint16_t> dant;
+    const bool dg_ok = n_pad == 128 && epic::dftgemm_gather_tables(cptr, cent, cwim, dlane, dbase, dwre, dwim, dant);
 
     // antenna-major CSR per row block (degridding side of the adjoint); cells are stored as
     // offsets into the adjoint kernel's shared-memory row buffer
@@ -416,7 +418,7 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
                     (e = upload(&p->went, went)) != cudaSuccess ||
                     (complex_w && (e = upload(&p->wwim, wwim)) != cudaSuccess))) ||
         (dg_ok && ((e = upload(&p->dg_lane, dlane)) != cudaSuccess || (e = upload(&p->dg_base, dbase)) != cudaSuccess ||
-                   (e = upload(&p->dg_ent, dent)) != cudaSuccess ||
+                   (e = upload(&p->dg_wre, dwre)) != cudaSuccess || (e = upload(&p->dg_ant, dant)) != cudaSuccess ||
                    (complex_w && (e = upload(&p->dg_wim, dwim)) != cudaSuccess)))) {
         free_plan(p);
         return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
@@ -435,7 +437,9 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
     }
     if (xform != EPIC_XFORM_DFTGEMM) return epic_fail(EPIC_EINVAL, "xform %d", xform);
     if (plan->n_pad != 128) return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad == 128 (plan: %d)", plan->n_pad);
-    if (!plan->dg_lane) return epic_fail(EPIC_EUNSUPPORTED, "a pair of grid cells has more than 65535 mapping entries");
+    if (!plan->dg_lane)
+        return epic_fail(EPIC_EUNSUPPORTED, "a pair of grid cells has more than 65535 mapping entries, or more than "
+                                            "65536 antennas");
     EpicDeviceGuard guard(plan->device);
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
@@ -500,7 +504,7 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
         epic_plan_fwd_args(plan, volt, n_time, reinterpret_cast<const float2*>(gains), accum, power);
     epic_status s;
     if (plan->xform == EPIC_XFORM_DFTGEMM) {
-        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_ent, plan->dg_wim, (int)plan->nnz};
+        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_wre, plan->dg_wim, plan->dg_ant, (int)plan->nnz};
         e = epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st);
         s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core imaging kernel launch");
     } else {
@@ -584,7 +588,7 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     a.n_items = (long long)a.n_cp * n_time;
     epic_status s;
     if (dg) {
-        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_ent, plan->dg_wim, (int)plan->nnz};
+        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_wre, plan->dg_wim, plan->dg_ant, (int)plan->nnz};
         e = epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st, true);
         s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core cross-polarisation kernel launch");
     } else {

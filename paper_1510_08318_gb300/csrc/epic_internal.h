@@ -142,18 +142,19 @@ int exchange_row_stride(int n_pad);   // row stride (float2) of the kernels' exc
 // of a slot holds the k-th entry of every lane whose pair has more than k entries (the entries
 // of cell y in cell-major order, then those of cell y + 1).
 struct DgGather {
-    const int2* lane;   // [64][32] {entries of cell y | (entries of the pair) << 16, E^T table offset of (x, y)}
-    const int* base;    // [64] first entry of each slot
-    const int2* ent;    // entries, {weight re bits, antenna}
-    const float* wim;   // weight imaginary parts, or nullptr when every weight is real
-    int n_ent;          // number of entries
+    const int2* lane;      // [64][32] {entries of cell y | (entries of the pair) << 16, E^T table offset of (x, y)}
+    const int* base;       // [64] first entry of each slot
+    const float* wre;      // entry weights, real parts
+    const float* wim;      // entry weights, imaginary parts, or nullptr when every weight is real
+    const uint16_t* ant;   // entry antennas
+    int n_ent;             // number of entries
 };
 size_t dftgemm_smem_bytes(int n_ant, bool xpol = false);   // the least a launch needs (tables read through L1)
 void dftgemm_tables(std::vector<uint16_t>& out);
-// false if a pair has more than 65535 entries
+// false if a pair has more than 65535 entries or an antenna index does not fit 16 bits
 bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
-                           std::vector<int2>& lane, std::vector<int>& base, std::vector<int2>& ent,
-                           std::vector<float>& wim);
+                           std::vector<int2>& lane, std::vector<int>& base, std::vector<float>& wre,
+                           std::vector<float>& wim, std::vector<uint16_t>& ant);
 // xpol: the (channel, pol) items are the 4 C virtual pols of dual-pol data, as in the FFT form
 cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st,
                            bool xpol = false);

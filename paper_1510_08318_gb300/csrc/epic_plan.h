@@ -30,8 +30,9 @@ struct epic_plan {
     uint16_t* dg_tab = nullptr;   // DFT operand tables of the tensor-core form
     int2* dg_lane = nullptr;      // gridding slot tables of the tensor-core form (N_p = 128)
     int* dg_base = nullptr;
-    int2* dg_ent = nullptr;
+    float* dg_wre = nullptr;
     float* dg_wim = nullptr;
+    uint16_t* dg_ant = nullptr;
     float wsum_max = 0.f;         // max over cells of sum_a |M[g, a]|
 };
 

@@ -9,14 +9,15 @@
 // with W[k][n] = exp(+2 pi i n k / N_p).  Complex products are four real products; every real
 // operand v is split as v = hi + lo (two FP16 numbers, hi = fp16(v), lo = fp16(v - hi)) and each
 // real product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory (about 22 bits of
-// operand precision).  The real and imaginary outputs of a stage come from one MMA whose B
-// operand stacks two tables along N: stage 1 takes A = Re W against B = [Re E ; Im E] and
-// A = Im W against [-Im E ; Re E] (N = 128: Re X | Im X); stage 2 takes A = Re X against
-// [Re W ; Im W] and A = Im X against [-Im W ; Re W] (N = 256: Re F | Im F).  Each stage is 24
-// MMAs; the wider N halves the A-operand reads per FLOP, which kept stage 1 waiting on shared
-// memory when it ran as 48 MMAs of N = 64.  Per image the gridded field is scaled by a power of two, chosen from a
-// bound (largest |g V| of the sample times the largest sum_a |M[g, a]| of the plan), so that
-// the FP16 operands stay in range; |F|^2 is scaled back exactly.
+// operand precision).  Stage 1 produces the real and imaginary parts of X in one MMA whose B
+// operand stacks two E tables along N: A = Re W against B = [Re E ; Im E] and A = Im W against
+// [-Im E ; Re E] (N = 128: Re X | Im X), 24 MMAs; as 48 MMAs of N = 64 it waited on shared
+// memory.  Stage 2 reads A = Re X, Im X from tensor memory against B = Re W, Im W (N = 128),
+// the minus sign of Re F = Re X Re W - Im X Im W taken by the instruction descriptor's negate-A
+// bit, so no negated W table is stored: 48 MMAs.  Per image the gridded field is scaled by a
+// power of two, chosen from a bound (largest |g V| of the sample times the largest
+// sum_a |M[g, a]| of the plan), so that the FP16 operands stay in range; |F|^2 is scaled back
+// exactly.
 //
 // One CTA per SM (16 worker warps and one issuer warp) owns all 512 TMEM columns.  Only the
 // first thread of the issuer warp issues MMAs: issuing stalls while the tensor pipe's queue is
@@ -25,23 +26,31 @@
 //   [0, 128)    stage-1 accumulator X (re 0..63, im 64..127), FP32
 //   [128, 256)  stage-2 A operand: X re hi, re lo, im hi, im lo (FP16 pairs, 32 columns each)
 //   [256, 512)  stage-2 accumulator F (re 256..383, im 384..511), FP32
-// Shared memory holds the six W operand tables and the six E^T operand tables (-im, re, im of
-// the hi parts, then of the lo parts, so that every stacked B operand is two adjacent tables),
-// all K-major in 8 x 8 core matrices, no swizzle.
+// Shared memory holds the four W operand tables (re, im; hi, lo) and two buffers of the six E^T
+// operand tables (-im, re, im of the hi parts, then of the lo parts, so that every stacked B
+// operand is two adjacent tables), all K-major in 8 x 8 core matrices, no swizzle, and two
+// buffers of decoded voltages.
+//
+// Pipeline (iteration i; stage 1 of image i is on the tensor pipe when it starts):
+//   workers: grid image i+1 into E buffer (i+1) mod 2  |  |F|^2 epilogue of image i-1
+//            (after stage 2 of i-1)  |  decode image i+2  |  split X(i) into the stage-2 A
+//            operand (after stage 1 of i)  |  barrier
+//   issuer:  after the barrier, stage 2 of image i, then stage 1 of image i+1
+// so the gridding of the next image runs under both stages of the current one.
+//
 // The gridding gathers cell pairs (x, y), (x, y + 1) from slot tables in which the 32 pairs of
 // a warp step have similar entry counts and store to 32 distinct shared-memory banks (on the
 // 256-antenna ellipse a cell-major walk kept 40 % of the lanes busy, these slots 81 %, with the
 // slowest warp at the heaviest slot); each cell's entries are still summed in cell-major order.
-// The tables sit in shared memory when they fit beside the operand tables, else they are read
-// through L1.
-// Pipeline per image i: grid(i) + stage 2(i-1) on the tensor cores, then stage 1(i) issue,
-// |F|^2 epilogue of i-1, decode of i+1, split of X(i) into TMEM, stage 2(i) issue.
+// Entries are an FP32 weight and a 16-bit antenna index; the tables sit in shared memory when
+// they fit beside the operand tables, else they are read through L1.
 // Every wait on the tensor cores is bounded; on a timeout the CTA writes NaN into its
 // accumulator block and stops.
 #include <cuda_fp16.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 #include "moff_common.cuh"
 #include "tcgen05.cuh"
@@ -56,9 +65,10 @@ constexpr int NTH = NT + 32;      // 16 worker warps + one warp whose first thre
 constexpr int ISSUER = NT;        // thread that issues every tcgen05.mma (never a worker)
 constexpr int WTAB = NP * NG;     // halves per W table
 constexpr int ETAB = NG * NG;     // halves per E^T table
-// table order: a stacked B operand [T ; T'] is T followed by the next table in memory
-enum { NWI_HI, WR_HI, WI_HI, NWI_LO, WR_LO, WI_LO, N_WTAB };
+enum { WR_HI, WI_HI, WR_LO, WI_LO, N_WTAB };
+// E^T table order: a stacked B operand [T ; T'] is T followed by the next table in memory
 enum { NEI_HI, ER_HI, EI_HI, NEI_LO, ER_LO, EI_LO, N_ETAB };
+constexpr uint32_t kNegA = 1u << 13;   // instruction descriptor: negate the A operand
 
 // (a, b) -> packed FP16 pairs hi = fp16(a, b), lo = fp16((a, b) - hi)
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
@@ -73,18 +83,18 @@ constexpr int kWStep = 2 * WTAB / 16;    // descriptor start-field step per W ta
 constexpr int kEStep = 2 * ETAB / 16;    // ... per E^T table
 
 constexpr size_t smem_fixed() {
-    return sizeof(__half) * ((size_t)N_WTAB * WTAB + (size_t)N_ETAB * ETAB) + 64;
+    return sizeof(__half) * ((size_t)N_WTAB * WTAB + 2 * (size_t)N_ETAB * ETAB) + 64;
 }
 constexpr int NSLOT = NG * NG / 64;   // slots of 32 cell pairs
 
-// Shared-memory bytes per antenna: voltages, gains, power (and the Y gains of XP).
-constexpr size_t ant_bytes(bool xp) { return xp ? 28 : 20; }
+// Shared-memory bytes per antenna: two voltage buffers, gains, power (and the Y gains of XP).
+constexpr size_t ant_bytes(bool xp) { return xp ? 36 : 28; }
 
 // Bytes of the gather tables when they are copied into shared memory (after the per-antenna
-// arrays, 16-byte aligned): slot words, slot bases, entries and imaginary weight parts.
+// arrays, 16-byte aligned): slot words, slot bases, weights (and imaginary parts), antennas.
 inline size_t table_smem_bytes(int n_ent, bool cw) {
-    return 16 + sizeof(int2) * NSLOT * 32 + sizeof(int) * NSLOT + sizeof(int2) * (size_t)n_ent +
-           (cw ? sizeof(float) * (size_t)n_ent : 0);
+    return 16 + sizeof(int2) * NSLOT * 32 + sizeof(int) * NSLOT + sizeof(float) * (size_t)n_ent * (cw ? 2 : 1) +
+           sizeof(uint16_t) * (size_t)n_ent;
 }
 
 // Gather-table load: shared memory when the tables were copied there, else the read-only path.
@@ -99,29 +109,31 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                                                               const DgGather g) {
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __half* sW = reinterpret_cast<__half*>(smem_raw);                  // [N_WTAB][WTAB]
-    __half* sE = sW + N_WTAB * WTAB;                                  // [N_ETAB][ETAB]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + N_ETAB * ETAB); // [2]
+    __half* sW = reinterpret_cast<__half*>(smem_raw);                      // [N_WTAB][WTAB]
+    __half* sE = sW + N_WTAB * WTAB;                                      // [2][N_ETAB][ETAB]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + 2 * N_ETAB * ETAB); // [2]
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
-    unsigned int* vmax = reinterpret_cast<unsigned int*>(tslot + 2);  // [2] max |g V| (float bits) per parity
-    float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed());
-    float2* GN = VB + a.n_ant;
-    float2* GY = GN + a.n_ant;                                         // XP only: phi_v g_Y
-    float* PW = reinterpret_cast<float*>(GN + (XP ? 2 : 1) * a.n_ant);
+    unsigned int* vmax = reinterpret_cast<unsigned int*>(tslot + 2);      // [4] max |g V| (float bits) per image mod 4
+    const int A = a.n_ant, T = a.n_time;
+    float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed());      // [2][A] decoded voltages
+    float2* GN = VB + 2 * A;
+    float2* GY = GN + A;                                                  // XP only: phi_v g_Y
+    float* PW = reinterpret_cast<float*>(GN + (XP ? 2 : 1) * A);
     // gather tables: copied into shared memory when they fit (SMT), else read through L1,
     // whose share of the SM's 256 KB shrinks as the shared-memory request grows
-    int2* sLane = reinterpret_cast<int2*>(smem_raw + ((smem_fixed() + (size_t)a.n_ant * ant_bytes(XP) + 15) & ~(size_t)15));
+    int2* sLane = reinterpret_cast<int2*>(smem_raw + ((smem_fixed() + (size_t)A * ant_bytes(XP) + 15) & ~(size_t)15));
     int* sBase = reinterpret_cast<int*>(sLane + NSLOT * 32);
-    int2* sEnt = reinterpret_cast<int2*>(sBase + NSLOT);
-    float* sWim = reinterpret_cast<float*>(sEnt + g.n_ent);
+    float* sWre = reinterpret_cast<float*>(sBase + NSLOT);
+    float* sWim = sWre + g.n_ent;
+    uint16_t* sAnt = reinterpret_cast<uint16_t*>(sWre + (g.wim ? 2 : 1) * g.n_ent);
     const int2* tLane = SMT ? sLane : g.lane;
     const int* tBase = SMT ? sBase : g.base;
-    const int2* tEnt = SMT ? sEnt : g.ent;
+    const float* tWre = SMT ? sWre : g.wre;
     const float* tWim = g.wim == nullptr ? nullptr : SMT ? sWim : g.wim;
+    const uint16_t* tAnt = SMT ? sAnt : g.ant;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = tid < NT;     // the issuer warp does no gridding, decoding or epilogue work
-    const int A = a.n_ant, T = a.n_time;
     const VT* V = static_cast<const VT*>(a.volt);
 
     for (int i = tid; i < N_WTAB * WTAB / 8; i += NTH)
@@ -130,7 +142,10 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     if constexpr (SMT) {
         for (int q = tid; q < NSLOT * 32; q += NTH) sLane[q] = __ldg(g.lane + q);
         for (int q = tid; q < NSLOT; q += NTH) sBase[q] = __ldg(g.base + q);
-        for (int q = tid; q < g.n_ent; q += NTH) sEnt[q] = __ldg(g.ent + q);
+        for (int q = tid; q < g.n_ent; q += NTH) {
+            sWre[q] = __ldg(g.wre + q);
+            sAnt[q] = __ldg(g.ant + q);
+        }
         if (g.wim)
             for (int q = tid; q < g.n_ent; q += NTH) sWim[q] = __ldg(g.wim + q);
     }
@@ -145,7 +160,7 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                      :: "r"(smem_u32(tslot)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid < 2) vmax[tid] = 0u;
+    if (tid < 4) vmax[tid] = 0u;
     fence_before();
     __syncthreads();
     fence_after();
@@ -180,7 +195,6 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     // decode does not wait on HBM; antennas beyond NT * VPT are loaded when decoded
     VT raw[VPT], rawy[XP ? VPT : 1];
     auto prefetch = [&](int item) {
-        if (!worker) return;
         const int cp = item / T, t = item - cp * T;
         const VT* base = vrow(cp, t);
 #pragma unroll
@@ -191,49 +205,7 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
             }
         }
     };
-    // decode + gain; the largest component magnitude goes to vmax[slot] (positive float bits
-    // order like unsigned integers); then the next item's voltages are prefetched
-    auto decode = [&](int item, int slot) {
-        if (!worker) return;
-        const int cp = item / T, t = item - cp * T;
-        const VT* base = vrow(cp, t);
-        const bool two = XP && (cp & 3) >= 2;     // virtual pol combining X and Y
-        float m = 0.f;
-#pragma unroll
-        for (int q = 0; q < VPT; ++q) {
-            const int aa = tid + NT * q;
-            if (aa < A) {
-                float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[q]));
-                if constexpr (XP) {
-                    if (two) {
-                        const float2 w = cmul(GY[aa], Volt<VDT>::dec(rawy[q]));
-                        vp.x += w.x;
-                        vp.y += w.y;
-                    }
-                }
-                VB[aa] = vp;
-                PW[aa] += cnorm(vp);
-                m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
-            }
-        }
-        for (int aa = tid + NT * VPT; aa < A; aa += NT) {
-            float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
-            if (two) {
-                const float2 w = cmul(GY[aa], Volt<VDT>::dec(__ldg(base + A + aa)));
-                vp.x += w.x;
-                vp.y += w.y;
-            }
-            VB[aa] = vp;
-            PW[aa] += cnorm(vp);
-            m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
-        }
-        if (item + 1 < beg + n) prefetch(item + 1);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0 && m > 0.f) atomicMax(vmax + slot, __float_as_uint(m));
-    };
     auto load_gains = [&](int cp) {
-        if (!worker) return;
         if constexpr (XP) {
             // virtual pol v = cp & 3: X, Y, X + Y, X + iY; GY = phi_v g_Y (phi_2 = 1, phi_3 = i)
             const int c = cp >> 2, v = cp & 3, p = v == 1 ? 1 : 0;
@@ -248,14 +220,125 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         }
     };
     auto flush_power = [&](int cp) {
-        if (!worker) return;
         for (int aa = tid; aa < A; aa += NT) {
             if (a.power != nullptr) atomicAdd(a.power + (size_t)cp * A + aa, (double)PW[aa]);
             PW[aa] = 0.f;
         }
     };
+    // decode + gain of local image j into voltage buffer j mod 2 (workers; every thread owns the
+    // same antennas in all arrays, so no barrier separates the gains, power and voltage updates);
+    // the largest component magnitude goes to vmax[j mod 4] (positive float bits order like
+    // unsigned integers); then the next image's voltages are prefetched
+    auto decode = [&](int j) {
+        const int item = beg + j, cp = item / T, t = item - cp * T;
+        if (j == 0 || (item - 1) / T != cp) {
+            if (j > 0) flush_power((item - 1) / T);
+            load_gains(cp);
+        }
+        const VT* base = vrow(cp, t);
+        float2* vb = VB + (j & 1) * A;
+        const bool two = XP && (cp & 3) >= 2;     // virtual pol combining X and Y
+        float m = 0.f;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int aa = tid + NT * q;
+            if (aa < A) {
+                float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[q]));
+                if constexpr (XP) {
+                    if (two) {
+                        const float2 w = cmul(GY[aa], Volt<VDT>::dec(rawy[q]));
+                        vp.x += w.x;
+                        vp.y += w.y;
+                    }
+                }
+                vb[aa] = vp;
+                PW[aa] += cnorm(vp);
+                m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
+            }
+        }
+        for (int aa = tid + NT * VPT; aa < A; aa += NT) {
+            float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
+            if (two) {
+                const float2 w = cmul(GY[aa], Volt<VDT>::dec(__ldg(base + A + aa)));
+                vp.x += w.x;
+                vp.y += w.y;
+            }
+            vb[aa] = vp;
+            PW[aa] += cnorm(vp);
+            m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
+        }
+        if (j + 1 < n) prefetch(item + 1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && m > 0.f) atomicMax(vmax + (j & 3), __float_as_uint(m));
+    };
+    // gridding of local image j into E buffer j mod 2 (workers); returns the image's scale 4^s
+    auto grid = [&](int j) -> float {
+        // |E| <= (largest sum_a |M[g, a]|) * sqrt(2) * (largest |g V| component)
+        const float bound = a.wsum_max * 1.5f * __uint_as_float(vmax[j & 3]);
+        int ex = 0;
+        if (bound > 0.f) {
+            frexpf(bound, &ex);
+            ex = max(-100, min(100, ex - 9));    // scaled bound in [256, 512)
+        }
+        const float down = ldexpf(1.f, -ex);
+        const float2* vb = VB + (j & 1) * A;
+        __half* sEj = sE + (j & 1) * N_ETAB * ETAB;
+        // warp w gathers slots 4w .. 4w + 3, each 32 cell pairs of nearly equal entry count
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int slot = warp * 4 + jj;
+            const int2 lw = ldt<SMT>(tLane + slot * 32 + lane);
+            const int c0 = lw.x & 0xffff, cnt = (int)((unsigned)lw.x >> 16);
+            const int kmax = __shfl_sync(0xffffffffu, cnt, 0);   // lane 0 has the longest list
+            int e = ldt<SMT>(tBase + slot) + lane;
+            float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+            if (tWim) {
+                for (int k = 0; k < kmax; ++k) {
+                    const bool on = k < cnt;
+                    const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                    if (on) {
+                        const float2 w = make_float2(ldt<SMT>(tWre + e), ldt<SMT>(tWim + e));
+                        const float2 v = vb[ldt<SMT>(tAnt + e)];
+                        if (k < c0) cfma(s0, w, v);
+                        else cfma(s1, w, v);
+                    }
+                    e += n_k;
+                }
+            } else {
+                for (int k = 0; k < kmax; ++k) {
+                    const bool on = k < cnt;
+                    const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                    if (on) {
+                        // both cells take the entry, one with weight 0 (adds an exact 0): no
+                        // divergent branch inside the step
+                        const float w = ldt<SMT>(tWre + e);
+                        const float2 v = vb[ldt<SMT>(tAnt + e)];
+                        const float w0 = k < c0 ? w : 0.f, w1 = w - w0;
+                        s0.x = fmaf(w0, v.x, s0.x);
+                        s0.y = fmaf(w0, v.y, s0.y);
+                        s1.x = fmaf(w1, v.x, s1.x);
+                        s1.y = fmaf(w1, v.y, s1.y);
+                    }
+                    e += n_k;
+                }
+            }
+            uint32_t rh, rl, ih, il;
+            split2(s0.x * down, s1.x * down, rh, rl);
+            split2(s0.y * down, s1.y * down, ih, il);
+            const int off = lw.y;   // E^T element (x, y), y even: one 32-bit word holds y and y + 1
+            *reinterpret_cast<uint32_t*>(sEj + ER_HI * ETAB + off) = rh;
+            *reinterpret_cast<uint32_t*>(sEj + ER_LO * ETAB + off) = rl;
+            *reinterpret_cast<uint32_t*>(sEj + EI_HI * ETAB + off) = ih;
+            *reinterpret_cast<uint32_t*>(sEj + EI_LO * ETAB + off) = il;
+            // split(-v) = -split(v) exactly: flip both halves' sign bits
+            *reinterpret_cast<uint32_t*>(sEj + NEI_HI * ETAB + off) = ih ^ 0x80008000u;
+            *reinterpret_cast<uint32_t*>(sEj + NEI_LO * ETAB + off) = il ^ 0x80008000u;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // E^T visible to the tensor cores
+        return ldexpf(1.f, 2 * ex);
+    };
     auto flush_acc = [&](int cp) {
-        if (!worker) return;
         double* dst = a.accum + (size_t)cp * NP * NP;
         const int iy = (ky + NP / 2) & (NP - 1);
 #pragma unroll
@@ -265,187 +348,138 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
             acc[j] = 0.f;
         }
     };
-
-    bool failed = false;
-    int issued2 = 0;            // stage-2 batches committed
-    float scale_prev = 1.f;     // 4^s of the image whose stage 2 is in flight
     int since = 0;
-    if (n > 0) {
-        load_gains(beg / T);
-        prefetch(beg);
-        decode(beg, 0);
-    }
-    __syncthreads();
-
-    for (int i = 0; i <= n && !failed; ++i) {
-        const int item = beg + i;
-        float scale_cur = 1.f;
-        if (i < n) {
-            // ---- gridding into the E^T operand tables (scaled, FP16 hi/lo) ----
-            // scale: |E| <= (largest sum_a |M[g, a]|) * sqrt(2) * (largest |g V| component)
-            const float bound = a.wsum_max * 1.5f * __uint_as_float(vmax[i & 1]);
-            int ex = 0;
-            if (bound > 0.f) {
-                frexpf(bound, &ex);
-                ex = max(-100, min(100, ex - 9));    // scaled bound in [256, 512)
-            }
-            const float down = ldexpf(1.f, -ex);
-            scale_cur = ldexpf(1.f, 2 * ex);
-            if (worker) {
-            // warp w gathers slots 4w .. 4w + 3, each 32 cell pairs of nearly equal entry count
+    // |F|^2 epilogue of local image j (workers, after its stage 2 has completed)
+    auto epilogue = [&](int j, float scale) {
+#pragma unroll
+        for (int c = 0; c < 32; c += 16) {
+            float fr[16], fi[16];
+            tld<16>(tF + lane_base + 32 * qt + c, fr);
+            tld<16>(tF + 128 + lane_base + 32 * qt + c, fi);
+            tld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[c + u] = fmaf(fmaf(fr[u], fr[u], fi[u] * fi[u]), scale, acc[c + u]);
+        }
+        ++since;
+        const int item = beg + j, cp = item / T;
+        if (j + 1 == n || (item + 1) / T != cp || since == a.flush_every) {
+            flush_acc(cp);
+            since = 0;
+        }
+    };
+    // split X into the stage-2 A operand in TMEM (workers, after its stage 1 has completed);
+    // quarter qt: part (re / im) = qt >> 1, x range 32 * (qt & 1) .. + 32
+    auto split = [&]() {
+        const int part = qt >> 1, hx = qt & 1;
+        const uint32_t src = tX + lane_base + 64 * part + 32 * hx;
+        const uint32_t dhi = tXop + lane_base + 64 * part + 16 * hx;
+        const uint32_t dlo = dhi + 32;
+#pragma unroll
+        for (int c = 0; c < 32; c += 16) {
+            float xv[16];
+            tld<16>(src + c, xv);
+            tld_wait();
+            uint32_t ph[8], pl[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) split2(xv[2 * u], xv[2 * u + 1], ph[u], pl[u]);
+            tst8(dhi + c / 2, ph);
+            tst8(dlo + c / 2, pl);
+        }
+        tst_wait();
+    };
+    // stage 1 of the image in E buffer b: X = W E (columns transformed)
+    auto issue_stage1 = [&](int b) {
+        constexpr uint32_t id1 = idesc(128);
+        // A = W table, B = [table ; next table]: Re W [Re E ; Im E], Im W [-Im E ; Re E]
+        constexpr int ta[6] = {WR_HI, WR_HI, WR_LO, WI_HI, WI_HI, WI_LO};
+        constexpr int tb[6] = {ER_HI, ER_LO, ER_HI, NEI_HI, NEI_LO, NEI_HI};
+        const uint64_t dE = dE0 + (uint64_t)(b * N_ETAB * kEStep);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                mma_ss(tX, dW0 + (uint64_t)(ta[q] * kWStep + 16 * j), dE + (uint64_t)(tb[q] * kEStep + 16 * j), id1,
+                       (q | j) != 0);
+        commit(mb1);
+    };
+    // stage 2: F = X W^T (rows transformed); A operand columns: X re hi/lo at +0/+32, X im
+    // hi/lo at +64/+96.  Re F = Re X Re W - Im X Im W, Im F = Re X Im W + Im X Re W.
+    auto issue_stage2 = [&]() {
+        constexpr uint32_t id2 = idesc(128);
+        constexpr int ar[6] = {0, 0, 32, 64, 64, 96};
+        constexpr int bre[6] = {WR_HI, WR_LO, WR_HI, WI_HI, WI_LO, WI_HI};
+        constexpr int bim[6] = {WI_HI, WI_LO, WI_HI, WR_HI, WR_LO, WR_HI};
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int slot = warp * 4 + j;
-                const int2 lw = ldt<SMT>(tLane + slot * 32 + lane);
-                const int c0 = lw.x & 0xffff, cnt = (int)((unsigned)lw.x >> 16);
-                const int kmax = __shfl_sync(0xffffffffu, cnt, 0);   // lane 0 has the longest list
-                int e = ldt<SMT>(tBase + slot) + lane;
-                float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-                if (tWim) {
-                    for (int k = 0; k < kmax; ++k) {
-                        const bool on = k < cnt;
-                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
-                        if (on) {
-                            const int2 en = ldt<SMT>(tEnt + e);
-                            const float2 w = make_float2(__int_as_float(en.x), ldt<SMT>(tWim + e));
-                            if (k < c0) cfma(s0, w, VB[en.y]);
-                            else cfma(s1, w, VB[en.y]);
-                        }
-                        e += n_k;
-                    }
-                } else {
-                    for (int k = 0; k < kmax; ++k) {
-                        const bool on = k < cnt;
-                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
-                        if (on) {
-                            // both cells take the entry, one with weight 0 (adds an exact 0):
-                            // no divergent branch inside the step
-                            const int2 en = ldt<SMT>(tEnt + e);
-                            const float w = __int_as_float(en.x);
-                            const float2 v = VB[en.y];
-                            const float w0 = k < c0 ? w : 0.f, w1 = w - w0;
-                            s0.x = fmaf(w0, v.x, s0.x);
-                            s0.y = fmaf(w0, v.y, s0.y);
-                            s1.x = fmaf(w1, v.x, s1.x);
-                            s1.y = fmaf(w1, v.y, s1.y);
-                        }
-                        e += n_k;
-                    }
-                }
-                uint32_t rh, rl, ih, il;
-                split2(s0.x * down, s1.x * down, rh, rl);
-                split2(s0.y * down, s1.y * down, ih, il);
-                const int off = lw.y;   // E^T element (x, y), y even: one 32-bit word holds y and y + 1
-                *reinterpret_cast<uint32_t*>(sE + ER_HI * ETAB + off) = rh;
-                *reinterpret_cast<uint32_t*>(sE + ER_LO * ETAB + off) = rl;
-                *reinterpret_cast<uint32_t*>(sE + EI_HI * ETAB + off) = ih;
-                *reinterpret_cast<uint32_t*>(sE + EI_LO * ETAB + off) = il;
-                // split(-v) = -split(v) exactly: flip both halves' sign bits
-                *reinterpret_cast<uint32_t*>(sE + NEI_HI * ETAB + off) = ih ^ 0x80008000u;
-                *reinterpret_cast<uint32_t*>(sE + NEI_LO * ETAB + off) = il ^ 0x80008000u;
+                mma_ts(tF, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(bre[q] * kWStep + 16 * j), q < 3 ? id2 : id2 | kNegA,
+                       (q | j) != 0);
+                mma_ts(tF + 128, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(bim[q] * kWStep + 16 * j), id2, (q | j) != 0);
             }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) vmax[i & 1] = 0u;   // free for the sample after next
-            // ---- stage 1 issue: X = W E (columns transformed) ----
-            if (tid == ISSUER) {
-                fence_after();
-                constexpr uint32_t id1 = idesc(128);
-                // A = W table, B = [table ; next table]: Re W [Re E ; Im E], Im W [-Im E ; Re E]
-                constexpr int ta[6] = {WR_HI, WR_HI, WR_LO, WI_HI, WI_HI, WI_LO};
-                constexpr int tb[6] = {ER_HI, ER_LO, ER_HI, NEI_HI, NEI_LO, NEI_HI};
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        mma_ss(tX, dW0 + (uint64_t)(ta[q] * kWStep + 16 * j), dE0 + (uint64_t)(tb[q] * kEStep + 16 * j),
-                               id1, (q | j) != 0);
-                commit(mb1);
-            }
+        commit(mb2);
+    };
+
+    bool failed = false;
+    int issued1 = 0, issued2 = 0;   // stage-1 / stage-2 batches committed
+    float sc_prev = 1.f, sc_cur = 1.f, sc_next = 1.f;   // 4^s of images i-1, i, i+1
+    if (n > 0) {
+        // prologue: decode images 0 and 1, grid image 0, stage 1 of image 0
+        if (worker) {
+            prefetch(beg);
+            decode(0);
         }
-        // ---- epilogue of image i-1: |F|^2 into the accumulators ----
-        if (i >= 1) {
-            if (!mbar_wait(mb2, (i - 1) & 1)) failed = true;
+        __syncthreads();
+        if (worker) {
+            sc_cur = grid(0);
+            if (n > 1) decode(1);
+        }
+        __syncthreads();
+        if (tid == ISSUER) {
             fence_after();
-            if (worker) {
-#pragma unroll
-                for (int c = 0; c < 32; c += 16) {
-                    float fr[16], fi[16];
-                    tld<16>(tF + lane_base + 32 * qt + c, fr);
-                    tld<16>(tF + 128 + lane_base + 32 * qt + c, fi);
-                    tld_wait();
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) acc[c + u] = fmaf(fmaf(fr[u], fr[u], fi[u] * fi[u]), scale_prev, acc[c + u]);
-                }
-            }
-            ++since;
-            const int prev = item - 1, cp_prev = prev / T;
-            const bool last = (i == n) || ((prev + 1) / T != cp_prev);
-            if (last || since == a.flush_every) {
-                flush_acc(cp_prev);
-                since = 0;
-            }
+            issue_stage1(0);
         }
-        if (i < n) {
-            // ---- decode of the next item (the gridding of this one has finished) ----
-            if (i + 1 < n) {
-                const int cp = item / T, cpn = (item + 1) / T;
-                if (cpn != cp) {
-                    flush_power(cp);
-                    load_gains(cpn);
-                }
-                decode(item + 1, (i + 1) & 1);
-            } else {
-                flush_power(item / T);
+        ++issued1;
+        if (tid == 0) vmax[0] = 0u;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (worker) {
+            if (i + 1 < n) sc_next = grid(i + 1);
+            if (i >= 1) {
+                if (!mbar_wait(mb2, (i - 1) & 1)) failed = true;
+                fence_after();
+                epilogue(i - 1, sc_prev);
             }
-            // ---- split X(i) into the stage-2 operands in TMEM ----
+            if (i + 2 < n) decode(i + 2);
             if (!mbar_wait(mb1, i & 1)) failed = true;
             fence_after();
-            if (worker) {
-                // quarter qt: part (re / im) = qt >> 1, x range 32 * (qt & 1) .. + 32
-                const int part = qt >> 1, hx = qt & 1;
-                const uint32_t src = tX + lane_base + 64 * part + 32 * hx;
-                const uint32_t dhi = tXop + lane_base + 64 * part + 16 * hx;
-                const uint32_t dlo = dhi + 32;
-#pragma unroll
-                for (int c = 0; c < 32; c += 16) {
-                    float xv[16];
-                    tld<16>(src + c, xv);
-                    tld_wait();
-                    uint32_t ph[8], pl[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) split2(xv[2 * u], xv[2 * u + 1], ph[u], pl[u]);
-                    tst8(dhi + c / 2, ph);
-                    tst8(dlo + c / 2, pl);
-                }
-                tst_wait();
-            }
-            fence_before();
-            failed = __syncthreads_or(failed) != 0;   // uniform across the CTA
-            // ---- stage 2 issue: F = X W^T (rows transformed) ----
-            if (tid == ISSUER && !failed) {
-                fence_after();
-                constexpr uint32_t id2 = idesc(256);
-                // A operand columns: X re hi/lo at +0/+32, X im hi/lo at +64/+96;
-                // B = [table ; next table]: Re X [Re W ; Im W], Im X [-Im W ; Re W]
-                constexpr int ar[6] = {0, 0, 32, 64, 64, 96};
-                constexpr int br[6] = {WR_HI, WR_LO, WR_HI, NWI_HI, NWI_LO, NWI_HI};
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        mma_ts(tF, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(br[q] * kWStep + 16 * j), id2, (q | j) != 0);
-                commit(mb2);
-            }
-            if (!failed) ++issued2;
-            scale_prev = scale_cur;
+            split();
         }
+        fence_before();
+        failed = __syncthreads_or(failed) != 0;   // uniform across the CTA
+        if (failed) break;
+        if (tid == ISSUER) {
+            fence_after();
+            issue_stage2();
+            if (i + 1 < n) issue_stage1((i + 1) & 1);
+        }
+        ++issued2;
+        if (i + 1 < n) ++issued1;
+        if (tid == 0) vmax[(i + 1) & 3] = 0u;   // read by the gridding of image i + 1, done
+        sc_prev = sc_cur;
+        sc_cur = sc_next;
+    }
+    if (!failed && n > 0 && worker) {
+        if (!mbar_wait(mb2, (n - 1) & 1)) failed = true;
+        fence_after();
+        if (!failed) epilogue(n - 1, sc_prev);
+        flush_power((beg + n - 1) / T);
     }
     if (failed) {
         // a tensor-core wait ran out: mark this CTA's first (channel, pol) block with NaN,
-        // wait (bounded) for the last stage-2 batch still in flight, and stop
+        // wait (bounded) for the last batches still in flight, and stop
         if (n > 0 && tid == 0) a.accum[(size_t)(beg / T) * NP * NP] = __longlong_as_double(0x7ff8000000000000LL);
+        if (issued1 > 0) mbar_wait(mb1, (issued1 - 1) & 1);
         if (issued2 > 0) mbar_wait(mb2, (issued2 - 1) & 1);
     }
     fence_before();
@@ -459,18 +493,17 @@ size_t dftgemm_smem_bytes(int n_ant, bool xpol) {
     return dg::smem_fixed() + (size_t)n_ant * dg::ant_bytes(xpol);
 }
 
-// W operand tables for N_p = 128: six [128][64] K-major FP16 tables (-im, re, im hi parts,
-// then the same lo parts) of W[k][n] = exp(+2 pi i n k / 128), computed in float64.
+// W operand tables for N_p = 128: four [128][64] K-major FP16 tables (re, im hi parts, then
+// the same lo parts) of W[k][n] = exp(+2 pi i n k / 128), computed in float64.
 void dftgemm_tables(std::vector<uint16_t>& out) {
     using namespace dg;
     out.assign((size_t)N_WTAB * WTAB, 0);
     for (int k = 0; k < NP; ++k)
         for (int n = 0; n < NG; ++n) {
             const double ang = 2.0 * 3.14159265358979323846 * double((n * k) % NP) / double(NP);
-            const double re = std::cos(ang), im = std::sin(ang);
-            const double vals[3] = {re, im, -im};
-            const int thi[3] = {WR_HI, WI_HI, NWI_HI}, tlo[3] = {WR_LO, WI_LO, NWI_LO};
-            for (int c = 0; c < 3; ++c) {
+            const double vals[2] = {std::cos(ang), std::sin(ang)};
+            const int thi[2] = {WR_HI, WI_HI}, tlo[2] = {WR_LO, WI_LO};
+            for (int c = 0; c < 2; ++c) {
                 const __half hi = __double2half(vals[c]);
                 const __half lo = __double2half(vals[c] - (double)__half2float(hi));
                 out[(size_t)thi[c] * WTAB + koff(k, n, NG)] = __half_as_ushort(hi);
@@ -489,11 +522,13 @@ void dftgemm_tables(std::vector<uint16_t>& out) {
 // than four (ties to the lowest warp), so the slowest warp's gridding is about the heaviest
 // slot or the mean, whichever is larger.
 bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
-                           std::vector<int2>& lane, std::vector<int>& base, std::vector<int2>& ent,
-                           std::vector<float>& wim) {
+                           std::vector<int2>& lane, std::vector<int>& base, std::vector<float>& wre,
+                           std::vector<float>& wim, std::vector<uint16_t>& ant) {
     using namespace dg;
     constexpr int NPAIR = NG * NG / 2;
     static_assert(NSLOT * 32 == NPAIR && NSLOT == 4 * (NT / 32), "four slots of 32 pairs per worker warp");
+    for (const int2& c : cent)
+        if (c.y < 0 || c.y > 0xffff) return false;
     struct Pair { int cell, c0, cnt, off; };
     std::vector<Pair> pr(NPAIR);
     for (int yp = 0; yp < NG / 2; ++yp)
@@ -519,8 +554,9 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
     for (const auto& sl : slots) order.insert(order.end(), sl.begin(), sl.end());
     lane.assign((size_t)NSLOT * 32, int2{0, 0});
     base.assign(NSLOT, 0);
-    ent.clear();
+    wre.clear();
     wim.clear();
+    ant.clear();
     constexpr int NW = NT / 32;
     int held[NW] = {}, steps[NW] = {};
     for (int r = 0; r < NSLOT; ++r) {
@@ -531,14 +567,17 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
         steps[w] += pr[order[32 * r]].cnt;
         const Pair* P[32];
         for (int i = 0; i < 32; ++i) P[i] = &pr[order[32 * r + i]];
-        base[pos] = (int)ent.size();
+        base[pos] = (int)wre.size();
         for (int i = 0; i < 32; ++i)
             lane[(size_t)pos * 32 + i] = int2{(int)((unsigned)P[i]->c0 | ((unsigned)P[i]->cnt << 16)), P[i]->off};
         for (int k = 0; k < P[0]->cnt; ++k)
             for (int i = 0; i < 32 && P[i]->cnt > k; ++i) {
                 const int e = k < P[i]->c0 ? cptr[P[i]->cell] + k : cptr[P[i]->cell + NG] + (k - P[i]->c0);
-                ent.push_back(cent[e]);
+                float w;
+                std::memcpy(&w, &cent[e].x, sizeof(float));
+                wre.push_back(w);
                 wim.push_back(cwim[e]);
+                ant.push_back((uint16_t)cent[e].y);
             }
     }
     return true;
