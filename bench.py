@@ -34,13 +34,13 @@ SM_MAX_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch on this workload, from ncu captures
 # of the 8-channel case (16,384 images) scaled by the units per launch (x16); None until
 # captured for the current kernel.  Forward FFT kernel: 6.48 MB per capture; tensor-core
-# DFT-GEMM kernel: 6.57 MB per capture.
+# DFT-GEMM kernel: 6.58 MB per capture.
 FWD_TRAFFIC_BYTES = 103.7e6
 # Executed tensor-core FLOP per image of the DFT-GEMM form: 12 real products per stage (4 per
 # complex product, 3 hi/lo terms each); stage 1 is 128 x 64 outputs over K = 64, stage 2
 # 128 x 128 over K = 64 (issued as 24 MMAs of N = 128, then 24 of N = 256: the same products).
 DG_FLOP_PER_IMAGE = 12 * 2.0 * 128 * 64 * 64 + 12 * 2.0 * 128 * 128 * 64
-DG_TRAFFIC_BYTES = None
+DG_TRAFFIC_BYTES = 105.2e6
 # standalone gridder: 480.3 MB per capture
 GRID_TRAFFIC_BYTES = 7.685e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -98,9 +98,10 @@ epic_status epic_create(epic_plan **plan, int n_ant, const double *pos_xy,
  * DFT matrix W[k][n] = exp(+2 pi i n k / N_p) on the tensor cores: every operand is split into
  * two FP16 numbers (hi + lo) and each real product is accumulated as hi*hi + hi*lo + lo*hi in
  * FP32 (per image the gridded field is scaled by a power of two to keep the operands in range).
- * It is available for n_pad == 128; otherwise EPIC_EUNSUPPORTED.  The first call with
- * EPIC_XFORM_DFTGEMM uploads the plan's DFT operand tables (96 KB).  epic_image_backward
- * always uses the FFT form.
+ * It is available for n_pad == 128 and up to about 2,400 antennas (the kernel keeps four
+ * per-antenna arrays in shared memory beside the operand tables; 1,900 for epic_image_xpol);
+ * otherwise EPIC_EUNSUPPORTED.  The first call with EPIC_XFORM_DFTGEMM uploads the plan's DFT
+ * operand tables (64 KB).  epic_image_backward always uses the FFT form.
  */
 epic_status epic_set_transform(epic_plan *plan, int xform);
 
