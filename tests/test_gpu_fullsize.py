@@ -25,12 +25,19 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def test_lwa_full_size_sampled(epic):
+@pytest.fixture(scope="module")
+def lwa_full():
+    return synth.workload_lwa()
+
+
+@pytest.mark.parametrize("xform", ["fft", "dftgemm"])
+def test_lwa_full_size_sampled(epic, lwa_full, xform):
     """256 antennas x 128 channels x 2 pols x 1024 samples, 4+4-bit, N_p = 128: the whole
-    integration in one epic_image call; three sampled (channel, pol) images and their
+    integration in one epic_image call, in both transform forms (the bench times both and
+    reports the tensor-core one); three sampled (channel, pol) images and their
     auto-correlation terms against the oracle over all 1024 samples."""
-    wl = synth.workload_lwa()
-    plan = epic.Plan.from_workload(wl)
+    wl = lwa_full
+    plan = epic.Plan.from_workload(wl).set_transform(xform)
     out = plan.image(torch.from_numpy(wl.volt_raw).cuda(), want_autocorr=True)
     torch.cuda.synchronize()
     img = out["image"].cpu().numpy()
@@ -47,6 +54,20 @@ def test_lwa_full_size_sampled(epic):
     # properties that hold for every image of the cube
     assert np.isfinite(img).all() and img.min() >= 0.0
     assert (img.sum(axis=(2, 3)) > 0).all()
+
+
+def test_lwa_full_size_forms_agree(epic, lwa_full):
+    """Every one of the 256 (channel, pol) images of the full LWA-like integration: the
+    tensor-core form within the FP32 bound (1e-4 relative L2, every pixel within 1e-4 of the
+    peak) of the FFT form, whose own images the oracle checks on samples."""
+    wl = lwa_full
+    v = torch.from_numpy(wl.volt_raw).cuda()
+    plan = epic.Plan.from_workload(wl)
+    ref = plan.image(v)["image"].cpu().numpy().astype(np.float64)
+    got = plan.set_transform("dftgemm").image(v)["image"].cpu().numpy().astype(np.float64)
+    d = np.linalg.norm((got - ref).reshape(-1, wl.n_pad ** 2), axis=1) / np.linalg.norm(ref.reshape(-1, wl.n_pad ** 2), axis=1)
+    assert d.max() < 1e-4, d.max()
+    assert (np.abs(got - ref).max(axis=(2, 3)) < 1e-4 * ref.max(axis=(2, 3))).all()
 
 
 def test_hera_full_layout_channel_slice(epic):

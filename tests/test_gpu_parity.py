@@ -279,6 +279,24 @@ def test_dftgemm_small(epic, n_grid, n_ant, n_time, n_chan, n_pol, vdtype):
     np.testing.assert_allclose(out["power"].cpu().numpy(), (np.abs(wl.volt * gg[None]) ** 2).sum(0), rtol=1e-5)
 
 
+def test_dftgemm_deep_pipeline_gains(epic):
+    """LWA-like slice, 2 channels x 2 pols x 1024 samples: every CTA images about 27
+    consecutive samples, so the double-buffered pipeline runs in its steady state (gridding of
+    sample i+1 under both DFT stages of sample i) and across (channel, pol) boundaries; random
+    gains, power and auto-correlation term against the oracle."""
+    wl = synth.workload_lwa(n_chan=2, n_time=1024, chan_index=[5, 100])
+    rng = np.random.default_rng(17)
+    g = synth.random_gains(rng, (wl.n_chan, wl.n_pol, wl.n_ant))
+    M = oracle_map(wl)
+    plan = epic.Plan.from_workload(wl).set_transform("dftgemm")
+    out = plan.image(to_dev(wl), gains_dev(g), want_autocorr=True)
+    torch.cuda.synchronize()
+    gg = g.astype(np.complex128)
+    check_close(out["image"].cpu().numpy(), moff.moff_image(M, wl.volt, gg, wl.n_grid, wl.n_pad), "image")
+    check_close(out["autocorr"].cpu().numpy(), moff.autocorr_term(M, wl.volt, gg, wl.n_grid, wl.n_pad), "autocorr")
+    np.testing.assert_allclose(out["power"].cpu().numpy(), (np.abs(wl.volt * gg[None]) ** 2).sum(0), rtol=1e-5)
+
+
 def test_dftgemm_tables_beyond_shared_memory(epic):
     """2000 antennas with complex weights: the gridding's slot tables (over 10,000 entries of
     12 bytes) do not fit in shared memory beside the DFT operand tables, so the kernel reads

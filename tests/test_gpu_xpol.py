@@ -116,7 +116,8 @@ def test_continuation_and_single_pol_agreement(epic):
 # the tensor-core DFT form (N_p = 128) runs the same virtual pols: same oracle, same bounds
 # ---------------------------------------------------------------------------------------------
 def test_dftgemm_lwa_slice_ci4_gains(epic):
-    wl = synth.workload_lwa(n_chan=2, n_time=40, chan_index=[0, 127])
+    """400 samples: every CTA images about 21 consecutive virtual-pol samples."""
+    wl = synth.workload_lwa(n_chan=2, n_time=400, chan_index=[0, 127])
     g = synth.random_gains(np.random.default_rng(6), (wl.n_chan, 2, wl.n_ant))
     out = run(epic, wl, g, xform="dftgemm")
     check(out, moff.moff_cross_image(oracle_map(wl), wl.volt, g.astype(np.complex128), wl.n_grid, wl.n_pad),
