@@ -4,13 +4,13 @@
 // an unnormalised forward DFT of each block of C consecutive samples (bins in FFT order:
 // c > C/2 are the negative frequencies), no window.
 //
-// One CTA per (block t, pol, tile of 32 antennas) at a time: the C x 32 samples are loaded
-// coalesced (antennas contiguous; the next unit's while this one is processed) into shared
-// memory, transformed along time with C = R1 R2
-// (Cooley-Tukey): thread (antenna, n1) does the R1-point DFT of samples n1 + R2 n2, twiddles
-// by exp(-2 pi i n1 k2 / C) and writes back in place; then each thread does R2-point DFTs of
-// (antenna, k2) and writes bins k2 + R1 k1 with coalesced stores.  HBM-bound: it reads the
-// raw samples once and writes the spectra once.
+// One CTA per (block t, pol, tile of 32 antennas) at a time, transformed along time with
+// C = R1 R2 (Cooley-Tukey): thread (antenna, n1) loads samples n1 + R2 n2 of its antenna into
+// registers (coalesced: antennas contiguous; the next unit's while this one is processed),
+// does their R1-point DFT there, twiddles by exp(-2 pi i n1 k2 / C) and writes the results to
+// shared memory; then each thread does R2-point DFTs of (antenna, k2) and writes bins
+// k2 + R1 k1 with coalesced stores.  HBM-bound: it reads the raw samples once and writes the
+// spectra once; shared memory sees one write and one read per value.
 #include <cuda_fp16.h>
 #include "moff_common.cuh"
 
@@ -40,7 +40,7 @@ template <> struct Out<1> {       // FP16 pair
 };
 
 template <int C, int VIN, int OUT>
-__global__ void __launch_bounds__(TA * Split<C>::R2) fengine_kernel(const FengArgs a) {
+__global__ void __launch_bounds__(TA * Split<C>::R2, (TA * Split<C>::R2 <= 256) ? 3 : 1) fengine_kernel(const FengArgs a) {
     constexpr int R2 = Split<C>::R2, R1 = C / R2, NT = TA * R2;
     static_assert(R1 >= R2 && R1 <= 64 && R1 % R2 == 0, "split");
     using VT = typename Volt<VIN>::T;
@@ -56,45 +56,36 @@ __global__ void __launch_bounds__(TA * Split<C>::R2) fengine_kernel(const FengAr
     }
     const int A = a.n_ant, P = a.n_pol;
     const int n_tiles = (A + TA - 1) / TA;
-    const long long n_units = (long long)a.n_time * P * n_tiles;
+    const int n_units = a.n_time * P * n_tiles;   // < 2^31 (checked by the caller)
     const VT* raw = static_cast<const VT*>(a.raw);
     OT* out = static_cast<OT*>(a.volt);
+    const long long row = (long long)P * A;       // elements from one sample (or bin) to the next
     // raw samples of a unit (rows n1 + R2 q of its block): the next unit's are loaded into
-    // registers while the current one is transformed and stored
+    // registers while the current one is transformed and stored.  Unit u = (t, p, tile) with
+    // the tile fastest; 32-bit coordinates, one running pointer per thread.
     VT nxt[R1];
-    auto load_unit = [&](long long u) {
-        const int tile = (int)(u % n_tiles);
-        const long long tp = u / n_tiles;
-        const int p = (int)(tp % P);
-        const long long t = tp / P;
+    auto load_unit = [&](int u) {
+        const int tile = u % n_tiles, tp = u / n_tiles, p = tp % P, t = tp / P;
         const int ant = tile * TA + al;
+        const VT* src = raw + ((long long)t * C + n1) * row + (long long)p * A + ant;
 #pragma unroll
-        for (int q = 0; q < R1; ++q) {
-            const int j = n1 + R2 * q;
-            nxt[q] = ant < A ? __ldg(raw + ((t * C + j) * P + p) * (long long)A + ant) : VT{};
-        }
+        for (int q = 0; q < R1; ++q) nxt[q] = ant < A ? __ldg(src + q * R2 * row) : VT{};
     };
     if (blockIdx.x < n_units) load_unit(blockIdx.x);
-    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int tile = (int)(u % n_tiles);
-        const long long tp = u / n_tiles;
-        const int p = (int)(tp % P);
-        const long long t = tp / P;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int tile = u % n_tiles, tp = u / n_tiles, p = tp % P, t = tp / P;
         const int ant = tile * TA + al;
-        __syncthreads();                                  // previous unit's X reads are done
-#pragma unroll
-        for (int q = 0; q < R1; ++q) X[(n1 + R2 * q) * TA + al] = Volt<VIN>::dec(nxt[q]);
-        if (u + gridDim.x < n_units) load_unit(u + gridDim.x);
-        __syncthreads();
-        // stage 1: R1-point DFT of samples n1 + R2 n2, then the twiddle exp(-2 pi i n1 k2 / C);
-        // every thread reads exactly the rows it loaded, so it can write back in place
+        // stage 1: R1-point DFT of samples n1 + R2 n2 (the rows this thread loaded, straight from
+        // registers), then the twiddle exp(-2 pi i n1 k2 / C) on the way into shared memory
         {
             float2 x[R1];
 #pragma unroll
-            for (int n2 = 0; n2 < R1; ++n2) x[n2] = X[(n1 + R2 * n2) * TA + al];
+            for (int q = 0; q < R1; ++q) x[q] = Volt<VIN>::dec(nxt[q]);
+            if (u + gridDim.x < n_units) load_unit(u + gridDim.x);
             dft<R1, -1>(x);
+            __syncthreads();                              // previous unit's stage-2 reads are done
 #pragma unroll
-            for (int k2 = 0; k2 < R1; ++k2) X[(n1 + R2 * k2) * TA + al] = cmul(x[k2], TW[(n1 * k2) % C]);
+            for (int k2 = 0; k2 < R1; ++k2) X[(n1 + R2 * k2) * TA + al] = cmul(x[k2], TW[n1 * k2]);   // n1 k2 < C
         }
         __syncthreads();
         // stage 2: for k2 = n1, n1 + R2, ...: R2-point DFT over n1' of the row n1' + R2 k2, bins
@@ -107,9 +98,9 @@ __global__ void __launch_bounds__(TA * Split<C>::R2) fengine_kernel(const FengAr
             for (int m = 0; m < R2; ++m) z[m] = X[(m + R2 * k2) * TA + al];
             dft<R2, -1>(z);
             if (ant < A) {
+                OT* dst = out + ((long long)t * C + k2) * row + (long long)p * A + ant;
 #pragma unroll
-                for (int k1 = 0; k1 < R2; ++k1)
-                    out[((t * C + (k2 + R1 * k1)) * P + p) * (long long)A + ant] = Out<OUT>::enc(z[k1]);
+                for (int k1 = 0; k1 < R2; ++k1) dst[k1 * R1 * row] = Out<OUT>::enc(z[k1]);
             }
         }
     }
@@ -126,6 +117,7 @@ cudaError_t launch_t(const FengArgs& a, int n_sm, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long n_units = (long long)a.n_time * a.n_pol * ((a.n_ant + TA - 1) / TA);
+    if (n_units > 2147483647LL) return cudaErrorInvalidValue;
     const long long grid = n_units < (long long)per_sm * n_sm ? n_units : (long long)per_sm * n_sm;
     if (grid == 0) return cudaSuccess;
     fengine_kernel<C, VIN, OUT><<<(unsigned)grid, NT, smem, st>>>(a);

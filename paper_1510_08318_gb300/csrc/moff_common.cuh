@@ -117,11 +117,12 @@ template <> struct Volt<1> {                   // complex half
 };
 template <> struct Volt<2> {                   // signed 4+4-bit
     using T = unsigned char;
+    // a two's-complement nibble n is (n ^ 8) - 8; (n ^ 8) goes into the mantissa of 2^23 and one
+    // exact FP32 subtraction of 2^23 + 8 leaves the value (no integer-to-float conversion)
     static __device__ __forceinline__ float2 dec(T v) {
-        const int b = v;
-        const int re = (b >> 4) - ((b & 0x80) >> 3);
-        const int im = (b & 0xF) - ((b & 0x8) << 1);
-        return make_float2(float(re), float(im));
+        const unsigned b = v;
+        return make_float2(__uint_as_float(0x4B000000u | ((b >> 4) ^ 8u)) - 8388616.0f,
+                           __uint_as_float(0x4B000000u | ((b & 0xFu) ^ 8u)) - 8388616.0f);
     }
 };
 
