@@ -60,11 +60,12 @@ __device__ __forceinline__ void operand_pairs(typename Volt<VDT>::T raw, uint32_
     w = __byte_perm(x, 0, 0x1032) ^ 0x8000u;     // swap the halves, negate the new low half
 }
 
-// unit -> (cp, row block, column block), column block >= row block
-__device__ __forceinline__ void unit_coords(long long u, int nab, int& cp, int& ab, int& bb) {
+// unit -> (cp, row block, column block), column block >= row block (32-bit: the launcher
+// checks that the units fit)
+__device__ __forceinline__ void unit_coords(int u, int nab, int& cp, int& ab, int& bb) {
     const int upc = nab * (nab + 1) / 2;
-    cp = (int)(u / upc);
-    int r = (int)(u - (long long)cp * upc);
+    cp = u / upc;
+    int r = u - cp * upc;
     ab = 0;
     while (r >= nab - ab) {
         r -= nab - ab;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int A = a.n_ant, T = a.n_time, CP = a.n_cp;
     const int nab = (A + 127) / 128;
-    const long long n_units = (long long)CP * (nab * (nab + 1) / 2);
+    const int n_units = CP * (nab * (nab + 1) / 2);
     const int n_chunks = (T + TC - 1) / TC;
     const VT* V = static_cast<const VT*>(a.volt);
 
@@ -108,8 +109,9 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     constexpr int kTileStep = 2 * TILE / 16;        // descriptor start-field step per tile
     constexpr uint32_t id = idesc(128);
 
-    long long beg, end;
-    work_range(n_units, blockIdx.x, gridDim.x, beg, end);
+    long long beg_l, end_l;
+    work_range(n_units, blockIdx.x, gridDim.x, beg_l, end_l);
+    const int beg = (int)beg_l, end = (int)end_l;
 
     // decode mapping: lane -> (row % 8, sample % 4), so that one warp's 4-byte stores cover 32
     // distinct banks of a core-matrix row block.  Thread (warp w, lane) owns rows
@@ -125,28 +127,45 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     const int sbase = 256 * warp + 4 * lr + lt;      // word offset of (r0, 2 lt) in a tile
     const long long RS = (long long)CP * A;          // sample stride of the voltages
     VT rb[2 * NJ], ra[2 * NJ];
-    auto load_chunk = [&](long long u, int kc) {
+    // per unit: this thread's voltage pointers at sample lt of chunk 0 and its row validity
+    struct UnitPtr {
+        const VT* pb;
+        const VT* pa;
+        bool vb0, vb1, va0, va1;
+    };
+    auto unit_ptr = [&](int u) {
         int cp, ab, bb;
         unit_coords(u, nab, cp, ab, bb);
+        UnitPtr p;
+        p.pb = V + (long long)cp * A + bb * 128 + r0 + lt * RS;
+        p.pa = V + (long long)cp * A + ab * 128 + r0 + lt * RS;
+        p.vb0 = bb * 128 + r0 < A;
+        p.vb1 = bb * 128 + r0 + 64 < A;
+        p.va0 = ab != bb && ab * 128 + r0 < A;
+        p.va1 = ab != bb && ab * 128 + r0 + 64 < A;
+        return p;
+    };
+    auto load_chunk = [&](const UnitPtr& p, int kc) {
         const int tq = kc * TC + lt;
-        const VT* pb = V + (long long)cp * A + bb * 128 + r0 + tq * RS;
-        const VT* pa = V + (long long)cp * A + ab * 128 + r0 + tq * RS;
-        const bool vb0 = bb * 128 + r0 < A, vb1 = bb * 128 + r0 + 64 < A;
-        const bool va0 = ab != bb && ab * 128 + r0 < A, va1 = ab != bb && ab * 128 + r0 + 64 < A;
+        const VT* pb = p.pb + (long long)(kc * TC) * RS;
+        const VT* pa = p.pa + (long long)(kc * TC) * RS;
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             const bool tin = tq + 4 * j < T;
-            rb[2 * j] = (tin && vb0) ? __ldg(pb + 4 * j * RS) : VT(0);
-            rb[2 * j + 1] = (tin && vb1) ? __ldg(pb + 4 * j * RS + 64) : VT(0);
-            ra[2 * j] = (tin && va0) ? __ldg(pa + 4 * j * RS) : VT(0);
-            ra[2 * j + 1] = (tin && va1) ? __ldg(pa + 4 * j * RS + 64) : VT(0);
+            rb[2 * j] = (tin && p.vb0) ? __ldg(pb) : VT(0);
+            rb[2 * j + 1] = (tin && p.vb1) ? __ldg(pb + 64) : VT(0);
+            ra[2 * j] = (tin && p.va0) ? __ldg(pa) : VT(0);
+            ra[2 * j + 1] = (tin && p.va1) ? __ldg(pa + 64) : VT(0);
+            pb += 4 * RS;
+            pa += 4 * RS;
         }
     };
     bool failed = false;
     int g = 0;            // chunks issued by this CTA
     int n_done = 0;       // units finished by this CTA
-    if (beg < end) load_chunk(beg, 0);
-    for (long long u = beg; u < end && !failed; ++u) {
+    UnitPtr up = beg < end ? unit_ptr(beg) : UnitPtr{};
+    if (beg < end) load_chunk(up, 0);
+    for (int u = beg; u < end && !failed; ++u) {
         int cp, ab, bb;
         unit_coords(u, nab, cp, ab, bb);
         const bool diag = ab == bb;
@@ -190,8 +209,12 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
                 if (kc == n_chunks - 1) commit(mb_acc);
             }
             // prefetch the next chunk (of this unit or of the next one)
-            if (kc + 1 < n_chunks) load_chunk(u, kc + 1);
-            else if (u + 1 < end) load_chunk(u + 1, 0);
+            if (kc + 1 < n_chunks) {
+                load_chunk(up, kc + 1);
+            } else if (u + 1 < end) {
+                up = unit_ptr(u + 1);
+                load_chunk(up, 0);
+            }
         }
         if (failed) break;
         // ---- epilogue: D -> V_ab = g_a conj(g_b) D / T (and the mirrored block) ----
@@ -373,6 +396,7 @@ cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st) {
     const int nab = (a.n_ant + 127) / 128;
     const long long n_units = (long long)a.n_cp * (nab * (nab + 1) / 2);
     if (n_units == 0) return cudaSuccess;
+    if (n_units > 2147483647LL) return cudaErrorInvalidValue;   // the kernel indexes units in 32 bits
     const long long grid = n_units < 2LL * n_sm ? n_units : 2LL * n_sm;
     const size_t smem = xe::smem_bytes();
     cudaError_t e;
