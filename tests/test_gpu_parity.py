@@ -313,6 +313,23 @@ def test_dftgemm_tables_beyond_shared_memory(epic):
                 "image")
 
 
+def test_dftgemm_antenna_limit(epic):
+    """The tensor-core form keeps four per-antenna arrays beside its operand tables in shared
+    memory: 2400 antennas fit (imaged against the oracle, gather tables read through L1),
+    2500 do not and the transform is refused with EPIC_EUNSUPPORTED."""
+    wl = _small_workload(128, 64, 2400, 2, 1, 1, seed=24, vdtype="ci4")
+    M = oracle_map(wl)
+    plan = epic.Plan.from_workload(wl).set_transform("dftgemm")
+    out = plan.image(to_dev(wl))
+    torch.cuda.synchronize()
+    check_close(out["image"].cpu().numpy(), moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad), "image")
+    big = _small_workload(128, 64, 2500, 1, 1, 1, seed=25, vdtype="ci4")
+    plan = epic.Plan.from_workload(big)
+    with pytest.raises(epic.EpicError) as e:
+        plan.set_transform("dftgemm")
+    assert e.value.status == epic.EPIC_EUNSUPPORTED
+
+
 def test_dftgemm_lwa_slice_matches_fft(epic):
     """LWA-like slice (4+4-bit, 2 channels, 2 pols, 48 samples): tensor-core form vs the oracle
     and vs the FP32 FFT form; the continuation rule holds for it too."""

@@ -149,6 +149,16 @@ def test_dftgemm_continuation_matches_fft(epic):
         assert np.linalg.norm(a - f) / np.linalg.norm(f) < 1e-4
 
 
+def test_dftgemm_xpol_antenna_limit(epic):
+    """The cross-polarisation form of the tensor-core kernel holds one more per-antenna array:
+    2000 antennas fit the single-pol form but not this one, which is refused."""
+    wl = _dual(128, 64, 2000, 1, 1, "ci4", seed=4)
+    plan = epic.Plan.from_workload(wl).set_transform("dftgemm")
+    with pytest.raises(epic.EpicError) as e:
+        plan.image_xpol(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())
+    assert e.value.status == epic.EPIC_EUNSUPPORTED
+
+
 def test_rejects_single_pol_plan(epic):
     wl = synth.workload_tiny(n_time=2)
     plan = epic.Plan.from_workload(wl)
