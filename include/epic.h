@@ -208,8 +208,8 @@ epic_status epic_fengine(int n_ant, int n_pol, int n_chan, int n_time, int in_dt
  *
  *   weff      device [N_p][N_p] float32, image pixel order (k = 0 at (N_p/2, N_p/2)).
  *
- * EPIC_EUNSUPPORTED for n_pad > 128 or footprints too wide for the lag tables; EPIC_EINVAL for
- * fewer than two antennas.  One CTA; meant to be called once per plan.
+ * All padded sizes; EPIC_EUNSUPPORTED for footprints too wide for the lag tables; EPIC_EINVAL
+ * for fewer than two antennas.  One CTA per 16 image rows; meant to be called once per plan.
  */
 epic_status epic_weff(const epic_plan *plan, float *weff, void *stream);
 

@@ -633,7 +633,6 @@ epic_status epic_weff(const epic_plan* plan, float* weff, void* stream) {
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (!weff) return epic_fail(EPIC_EINVAL, "weff is NULL");
     if (plan->n_ant < 2) return epic_fail(EPIC_EINVAL, "the effective weighting needs at least two antennas");
-    if (plan->n_pad > 128) return epic_fail(EPIC_EUNSUPPORTED, "effective weighting for n_pad <= 128 (plan: %d)", plan->n_pad);
     if (plan->lag_side == 0)
         return epic_fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
     EpicDeviceGuard guard(plan->device);

@@ -132,15 +132,19 @@ autocorr_kernel(const double* __restrict__ power, const float2* __restrict__ lag
 //   W_eff(k) = (1 / (A (A - 1))) sum_{a != b} |K_a(k)|^2 |K_b(k)|^2
 //            = ((sum_a P_a)^2 - sum_a P_a^2) / (A (A - 1)),  P_a(k) = |K_a(k)|^2,
 // with P_a the transform of the footprint auto-correlation R_a (the plan's lag tables),
-// evaluated antenna by antenna (separably: rows of the lag window, then the pixels) and
-// summed in shared memory by one CTA, image pixel order (k = 0 at the centre).
+// evaluated antenna by antenna (separably: rows of the lag window, then the pixels), image
+// pixel order (k = 0 at the centre).  CTA b owns image rows kWeffRows b .. + kWeffRows - 1 and
+// sums P_a and P_a^2 over the antennas in shared memory; every CTA redoes the row pass of each
+// antenna (L x N_p values), which is small beside its share of the pixels.
 constexpr int kWeffThreads = 512;
+constexpr int kWeffRows = 16;
 
 __global__ void __launch_bounds__(kWeffThreads)
 weff_kernel(const float2* __restrict__ lag_tab, int n_ant, int L, int n_pad, float* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int npix = n_pad * n_pad, LL = L * L, h = (L - 1) / 2, msk = n_pad - 1;
-    float* S2 = reinterpret_cast<float*>(smem_raw);
+    const int rows = min(kWeffRows, n_pad), r0 = blockIdx.x * rows;
+    const int npix = rows * n_pad, LL = L * L, h = (L - 1) / 2, msk = n_pad - 1;
+    float* S2 = reinterpret_cast<float*>(smem_raw);        // [rows][n_pad]
     float* S4 = S2 + npix;
     float2* T1 = reinterpret_cast<float2*>(S4 + npix);     // [L][n_pad]
     float2* TWs = T1 + L * n_pad;
@@ -166,7 +170,7 @@ weff_kernel(const float2* __restrict__ lag_tab, int n_ant, int L, int n_pad, flo
         }
         __syncthreads();
         for (int pix = threadIdx.x; pix < npix; pix += blockDim.x) {
-            const int iy = pix / n_pad, ix = pix % n_pad, ky = iy - n_pad / 2;
+            const int iy = r0 + pix / n_pad, ix = pix % n_pad, ky = iy - n_pad / 2;
             float p = 0.f;
             for (int dy = 0; dy < L; ++dy) {
                 const float2 w = TWs[((dy - h) * ky) & msk];
@@ -180,18 +184,20 @@ weff_kernel(const float2* __restrict__ lag_tab, int n_ant, int L, int n_pad, flo
     }
     const float norm = 1.f / (float(n_ant) * float(n_ant - 1));
     for (int pix = threadIdx.x; pix < npix; pix += blockDim.x)
-        out[pix] = fmaf(S2[pix], S2[pix], -S4[pix]) * norm;
+        out[(size_t)r0 * n_pad + pix] = fmaf(S2[pix], S2[pix], -S4[pix]) * norm;
 }
 
 size_t weff_smem_bytes(int lag_side, int n_pad) {
-    return sizeof(float) * 2 * (size_t)n_pad * n_pad + sizeof(float2) * ((size_t)lag_side * n_pad + n_pad);
+    const int rows = n_pad < kWeffRows ? n_pad : kWeffRows;
+    return sizeof(float) * 2 * (size_t)rows * n_pad + sizeof(float2) * ((size_t)lag_side * n_pad + n_pad);
 }
 
 cudaError_t launch_weff(const float2* lag_tab, int n_ant, int lag_side, int n_pad, float* out, cudaStream_t st) {
     const size_t smem = weff_smem_bytes(lag_side, n_pad);
     cudaError_t e = ensure_smem<weff_kernel>(smem);
     if (e != cudaSuccess) return e;
-    weff_kernel<<<1, kWeffThreads, smem, st>>>(lag_tab, n_ant, lag_side, n_pad, out);
+    const int rows = n_pad < kWeffRows ? n_pad : kWeffRows;
+    weff_kernel<<<n_pad / rows, kWeffThreads, smem, st>>>(lag_tab, n_ant, lag_side, n_pad, out);
     return cudaGetLastError();
 }
 

@@ -41,14 +41,16 @@ def _small_hetero(n_pad, n_grid, n_ant, seed):
     return synth._finish(wl, v, "c64")
 
 
-@pytest.mark.parametrize("case", ["twotype", "lwa", "np32", "np64"])
+@pytest.mark.parametrize("case", ["twotype", "lwa", "np32", "np64", "np256", "np512"])
 def test_weff_matches_oracle(epic, case):
     if case == "twotype":
         wl = synth.workload_twotype(n_time=4)
     elif case == "lwa":
         wl = synth.workload_lwa(n_chan=1, n_time=2, chan_index=[0])
     else:
-        wl = _small_hetero(32 if case == "np32" else 64, 14 if case == "np32" else 30, 40, seed=len(case))
+        n_pad = int(case[2:])
+        n_grid = {32: 14, 64: 30, 256: 90, 512: 60}[n_pad]
+        wl = _small_hetero(n_pad, n_grid, 40 if n_pad <= 256 else 12, seed=len(case) + n_pad)
     plan = epic.Plan.from_workload(wl)
     got = plan.weff().cpu().numpy()
     want = moff.weff_opt(oracle_map(wl), wl.n_grid, wl.n_pad)
