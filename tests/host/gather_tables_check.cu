@@ -1,0 +1,116 @@
+// Host-only check of the tensor-core kernel's gridding slot tables (no GPU): builds them with the
+// library's own builder from a cell-major mapping read from a text file, then walks them the
+// way the kernel's warps do (step k: lanes with more than k entries, contiguous run, start of
+// step k + 1 = start of step k + active lanes) and checks that
+//   every index stays inside the tables and every antenna inside the array,
+//   every cell pair (x, y), (x, y + 1) is stored exactly once, at an in-range even offset,
+//   the 32 lanes of a slot store to 32 distinct shared-memory banks,
+//   lanes are in decreasing entry count and each warp holds four slots,
+//   every cell's sum equals the cell-major sum of its entries bit for bit (same order).
+// Exit status 0 when every check holds.
+#include "../../paper_1510_08318_gb300/csrc/moff_dftgemm.cu"
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <random>
+#include <set>
+
+int main(int argc, char** argv) {
+    if (argc < 2) return 2;
+    std::ifstream f(argv[1]);
+    int ncell = 0, nnz = 0;
+    f >> ncell >> nnz;
+    if (ncell != 64 * 64) return 2;
+    std::vector<int> cptr(ncell + 1), ant(nnz);
+    std::vector<float> wr(nnz), wi(nnz);
+    for (auto& v : cptr) f >> v;
+    for (auto& v : ant) f >> v;
+    for (auto& v : wr) f >> v;
+    for (auto& v : wi) f >> v;
+    std::vector<int2> cent(nnz);
+    for (int i = 0; i < nnz; ++i) {
+        int b;
+        std::memcpy(&b, &wr[i], 4);
+        cent[i] = int2{b, ant[i]};
+    }
+    int A = 1;
+    for (int a : ant) A = std::max(A, a + 1);
+    std::vector<int2> lane;
+    std::vector<int> base;
+    std::vector<float> wre, wim;
+    std::vector<uint16_t> an;
+    if (!epic::dftgemm_gather_tables(cptr, cent, wi, lane, base, wre, wim, an)) {
+        std::printf("builder refused the mapping\n");
+        return 1;
+    }
+    const int NG = 64, ETAB = NG * NG, NSLOT = 64;
+    int bad = 0;
+    if ((int)lane.size() != NSLOT * 32 || (int)base.size() != NSLOT || (int)wre.size() != nnz ||
+        wim.size() != wre.size() || an.size() != wre.size()) {
+        std::printf("table sizes\n");
+        return 1;
+    }
+    std::mt19937 rng(7);
+    std::uniform_real_distribution<float> U(-1.f, 1.f);
+    std::vector<float2> VB(A);
+    for (auto& v : VB) v = make_float2(U(rng), U(rng));
+    std::vector<float2> E(ETAB, make_float2(0.f, 0.f));
+    std::vector<int> seen(ETAB, 0);
+    for (int slot = 0; slot < NSLOT; ++slot) {
+        int c0[32], cnt[32], e[32];
+        unsigned banks = 0;
+        for (int l = 0; l < 32; ++l) {
+            const unsigned x = (unsigned)lane[slot * 32 + l].x;
+            c0[l] = x & 0xffff;
+            cnt[l] = x >> 16;
+            if (c0[l] > cnt[l] || (l > 0 && cnt[l] > cnt[l - 1])) ++bad;
+            const int off = lane[slot * 32 + l].y;
+            if (off < 0 || off + 1 >= ETAB || (off & 1)) { ++bad; continue; }
+            banks |= 1u << ((off / 2) % 32);
+            e[l] = base[slot] + l;
+        }
+        if (banks != 0xffffffffu) ++bad;
+        float2 s0[32], s1[32];
+        for (int l = 0; l < 32; ++l) s0[l] = s1[l] = make_float2(0.f, 0.f);
+        for (int k = 0; k < cnt[0]; ++k) {
+            int nk = 0;
+            for (int l = 0; l < 32; ++l) nk += k < cnt[l];
+            for (int l = 0; l < nk; ++l) {
+                if (e[l] < 0 || e[l] >= (int)wre.size() || an[e[l]] >= A) { ++bad; continue; }
+                const float w0 = k < c0[l] ? wre[e[l]] : 0.f, w1 = wre[e[l]] - w0;   // as the kernel
+                const float wi0 = k < c0[l] ? wim[e[l]] : 0.f, wi1 = wim[e[l]] - wi0;
+                const float2 v = VB[an[e[l]]];
+                float2& s = k < c0[l] ? s0[l] : s1[l];
+                const float w = k < c0[l] ? w0 : w1, wq = k < c0[l] ? wi0 : wi1;
+                s.x = fmaf(w, v.x, fmaf(-wq, v.y, s.x));
+                s.y = fmaf(w, v.y, fmaf(wq, v.x, s.y));
+            }
+            for (int l = 0; l < 32; ++l) e[l] += nk;
+        }
+        for (int l = 0; l < 32; ++l) {
+            const int off = lane[slot * 32 + l].y;
+            if (off < 0 || off + 1 >= ETAB) continue;
+            E[off] = s0[l];
+            E[off + 1] = s1[l];
+            seen[off] += 1;
+            seen[off + 1] += 1;
+        }
+    }
+    // the reference: cell-major sums in the order of the CSR
+    int miss = 0;
+    double maxdiff = 0.0;
+    for (int y = 0; y < NG; ++y)
+        for (int x = 0; x < NG; ++x) {
+            const int c = y * NG + x, off = epic::tc::koff(x, y, NG);
+            if (seen[off] != 1) { ++miss; continue; }
+            float2 s = make_float2(0.f, 0.f);
+            for (int i = cptr[c]; i < cptr[c + 1]; ++i) {
+                const float2 v = VB[ant[i]];
+                s.x = fmaf(wr[i], v.x, fmaf(-wi[i], v.y, s.x));
+                s.y = fmaf(wr[i], v.y, fmaf(wi[i], v.x, s.y));
+            }
+            maxdiff = std::max(maxdiff, (double)std::max(std::fabs(E[off].x - s.x), std::fabs(E[off].y - s.y)));
+        }
+    std::printf("bad %d missing %d maxdiff %g\n", bad, miss, maxdiff);
+    return (bad || miss || maxdiff != 0.0) ? 1 : 0;
+}
