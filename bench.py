@@ -36,11 +36,12 @@ SM_MAX_MHZ = 2070.0
 # captured for the current kernel.  Forward FFT kernel: 6.48 MB per capture; tensor-core
 # DFT-GEMM kernel: 6.58 MB per capture.
 FWD_TRAFFIC_BYTES = 103.7e6
+DG_TRAFFIC_BYTES = 105.3e6
 # Executed tensor-core FLOP per image of the DFT-GEMM form: 12 real products per stage (4 per
 # complex product, 3 hi/lo terms each); stage 1 is 128 x 64 outputs over K = 64, stage 2
-# 128 x 128 over K = 64 (issued as 24 MMAs of N = 128, then 24 of N = 256: the same products).
+# 128 x 128 over K = 64 (issued as 24 MMAs of N = 128 with two stacked E tables, then 48 of
+# N = 128: the same products).
 DG_FLOP_PER_IMAGE = 12 * 2.0 * 128 * 64 * 64 + 12 * 2.0 * 128 * 128 * 64
-DG_TRAFFIC_BYTES = 105.3e6
 # standalone gridder: 480.3 MB per capture
 GRID_TRAFFIC_BYTES = 7.685e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
