@@ -62,8 +62,9 @@ def parse():
     p.add_argument("--channels", type=int, default=128,
                    help="image only the first C of the 128 channels (small profiling case)")
     p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid", "xpol", "fx",
-                                                          "crossover", "fengine"],
-                   help="lwa: the headline workload; batch: 64 heterogeneous sub-arrays, one graph launch; "
+                                                          "crossover", "fengine", "hera"],
+                   help="lwa: the headline workload; hera: the dense HERA-331-like layout (256^2 images); "
+                        "batch: 64 heterogeneous sub-arrays, one graph launch; "
                         "calib: forward + adjoint of the gain-calibration workload; "
                         "grid: the standalone gridder (epic_grid) on the headline workload; "
                         "xpol: all four cross-polarisation images (epic_image_xpol) of the headline workload; "
@@ -162,7 +163,7 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline_sample(wl_full, plan=None, torch=None, n_chan=1, n_time=256):
+def cpu_baseline_sample(wl_full, plan=None, torch=None, n_chan=1, n_time=256, forms=("fft", "dftgemm")):
     """Time the FP64 oracle on a bounded sample: the last n_chan channels, pol 1, the first
     n_time samples, image + auto-correlation term.  If a plan is given, the CUDA path images the
     same sample (both transform forms) and its relative L2 error against the oracle is returned."""
@@ -183,7 +184,7 @@ def cpu_baseline_sample(wl_full, plan=None, torch=None, n_chan=1, n_time=256):
         sub = epic.Plan(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid, wl.n_pad,
                         n_chan, 1, wl.vdtype, plan.device)
         raw = torch.from_numpy(np.ascontiguousarray(wl.volt_raw[:T, c0:, p:p + 1, :])).cuda(plan.device)
-        for xf in ("fft", "dftgemm"):
+        for xf in forms:
             got = sub.set_transform(xf).image(raw)["image"].cpu().numpy()
             err[xf] = float(np.linalg.norm(got - img) / np.linalg.norm(img))
         sub.close()
@@ -253,6 +254,94 @@ def run_reference(args):
                              "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_hera(args):
+    """The dense layout: a HERA-331-like hexagon (331 antennas of 14 m, 14 m spacing), 1 pol,
+    1024 channels x 256 samples of FP16 voltages, 256 x 256 images (FP32 FFT form, 4-CTA
+    clusters; the tensor-core form exists for N_p = 128 only).  Same metric and timing rules as
+    the headline: one epic_image call per step (image + auto-correlation term), L2 flushed before
+    each step, the oracle on a bounded sample beside it."""
+    import torch
+    from paper_1510_08318_gb300 import build, epic, synth
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = synth.workload_hera(n_chan=args.channels if args.channels != 128 else 1024)
+    plan = epic.Plan.from_workload(wl, device=local)
+    A, T, C, P, NP = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_pad
+    volt = torch.from_numpy(wl.volt_raw).to(dev)
+    accum = torch.empty((C, P, NP, NP), dtype=torch.float64, device=dev)
+    power = torch.empty((C, P, A), dtype=torch.float64, device=dev)
+    image = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
+    autoc = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
+    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
+    host_img = torch.empty((C, P, NP, NP), dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    h = plan._h
+
+    def step():
+        epic.epic_image(h, volt.data_ptr(), T, None, accum.data_ptr(), power.data_ptr(), 0,
+                        image.data_ptr(), autoc.data_ptr(), st.cuda_stream)
+
+    def kernel_only():
+        epic.epic_image(h, volt.data_ptr(), T, None, accum.data_ptr(), None, 0, None, None, st.cuda_stream)
+
+    def e2e_step():
+        volt.copy_(host_v, non_blocking=True)
+        step()
+        host_img.copy_(image, non_blocking=True)
+
+    def timed(fn, clocks=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ms, clk = timed(step, Clocks(local))
+    kern_ms, _ = timed(kernel_only)
+    e2e_ms, _ = timed(e2e_step)
+    units = A * T * C * P
+    flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * P
+    peak = n_sm * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": flops / (kern_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "traffic": None, "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, max clock)"
+                                          % (n_sm, SM_MAX_MHZ),
+            "flop_basis": "per image 5 N log2 N (N = N_p^2) + 8 nnz + 4 N, as the headline"}
+    roof["frac"] = roof["achieved"] / peak
+    cb, err = None, {}
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, err = cpu_baseline_sample(wl, plan, torch, n_chan=2, n_time=T, forms=("fft",))
+    line = {"metric": METRIC, "value": job_throughput(units, world, ms), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP16 voltages)", "data": "synthetic",
+            "config": {"workload": wl.name, "antennas": A, "time_samples": T, "channels": C, "pols": P,
+                       "grid": "%dx%d padded to %dx%d" % (wl.n_grid, wl.n_grid, NP, NP),
+                       "images_per_step": T * C * P, "l2": "flushed (256 MB write) before every timed step"},
+            "images_per_s": world * T * C * P / (ms / 1e3), "kernel_ms": kern_ms, "roofline": roof,
+            "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": UNIT,
+                    "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
+                    "d2h_bytes_per_step": int(host_img.numel() * host_img.element_size())},
+            "gpu_launches": 3 * args.steps, "clocks": clk}
+    if cb is not None:
+        line["cpu_baseline"] = cb
+        line["err_vs_oracle"] = {"relative_l2": err, "sample": "last 2 channels, all %d samples, image" % T}
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def run_batch(args):
@@ -857,6 +946,8 @@ def main():
         return run_crossover(args)
     if args.workload == "fengine":
         return run_fengine(args)
+    if args.workload == "hera":
+        return run_hera(args)
     import numpy as np
     import torch
     from paper_1510_08318_gb300 import build, epic, synth
