@@ -443,3 +443,29 @@ def test_fengine_brute_force_tone_parseval():
     tone = np.exp(2j * np.pi * c0 * np.arange(2 * C) / C)[:, None, None] * np.ones((1, 1, 2))
     Vt = moff.fengine(tone, C)
     assert np.allclose(Vt[:, c0], C) and np.abs(np.delete(Vt, c0, axis=1)).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------------
+# the X-engine of the FX route (Sec. 3, Eq. "cc-vis")
+# ----------------------------------------------------------------------------------
+def test_visibilities_closed_form():
+    """For antenna b carrying a scaled copy V_b = c V_a of antenna a's voltage,
+    V_ab = g_a conj(g_b) conj(c) <|V_a|^2> and V_ba = conj(V_ab): fixes which side carries
+    the conjugate and where the gains enter.  The diagonal is the antenna power, the matrix
+    is Hermitian, and the cross-polarised form with q = p is the single-pol form."""
+    rng = np.random.default_rng(21)
+    T, A = 40, 4
+    va = rng.standard_normal(T) + 1j * rng.standard_normal(T)
+    c = 0.3 - 1.2j
+    v = np.stack([va, c * va, rng.standard_normal(T) + 0j, 1j * va], axis=1)   # [T, A]
+    g = np.array([1.0 + 0.5j, -0.4 + 0.8j, 0.9 + 0j, 0.2 - 0.7j])
+    V = fx.visibilities(v, g)
+    pa = (np.abs(va) ** 2).sum() / T
+    assert abs(V[0, 1] - g[0] * np.conj(g[1]) * np.conj(c) * pa) < 1e-12 * pa
+    assert abs(V[1, 0] - np.conj(V[0, 1])) < 1e-12 * pa
+    assert abs(V[0, 3] - g[0] * np.conj(g[3]) * (-1j) * pa) < 1e-12 * pa
+    np.testing.assert_allclose(np.diag(V).real, moff.antenna_power(v, g), rtol=1e-12)
+    np.testing.assert_allclose(V, np.conj(V.T), rtol=0, atol=1e-12 * pa)
+    Vx = fx.visibilities(v, g, exclude_auto=True)
+    assert np.all(np.diag(Vx) == 0) and np.array_equal(Vx[0, 1:], V[0, 1:])
+    np.testing.assert_allclose(fx.cross_visibilities(v, g, v, g), V, rtol=0, atol=1e-15 * pa)
