@@ -42,8 +42,8 @@ DG_TRAFFIC_BYTES = 105.3e6
 # 128 x 128 over K = 64 (issued as 24 MMAs of N = 128 with two stacked E tables, then 48 of
 # N = 128: the same products).
 DG_FLOP_PER_IMAGE = 12 * 2.0 * 128 * 64 * 64 + 12 * 2.0 * 128 * 128 * 64
-# standalone gridder: 480.3 MB per capture
-GRID_TRAFFIC_BYTES = 7.685e9
+# standalone gridder: 479.8 MB per capture launch (1,024 of the 16,384 units), scaled x16
+GRID_TRAFFIC_BYTES = 7.677e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 try:
     with open(MEASURED_PEAKS) as _f:

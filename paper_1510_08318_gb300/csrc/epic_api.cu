@@ -733,6 +733,7 @@ epic_status epic_grid(const epic_plan* plan, const void* volt, int n_time, const
     a.cell_ptr = plan->cell_ptr;
     a.cell_ent = plan->cell_ent;
     a.cell_wim = plan->cell_wim;
+    a.nnz = (int)plan->nnz;
     a.csr_width = plan->n_pad / 2;
     a.n_grid = plan->n_grid;
     a.out = reinterpret_cast<float2*>(grid);

@@ -105,6 +105,7 @@ struct GridArgs {
     const int* cell_ptr;       // cell-major mapping CSR, rows csr_width cells wide
     const int2* cell_ent;
     const float* cell_wim;
+    int nnz;                   // mapping entries (length of cell_ent and cell_wim)
     int csr_width;             // N_p / 2
     int n_grid;                // N_g (output rows and columns)
     float2* out;               // [T][CP][N_g][N_g]
