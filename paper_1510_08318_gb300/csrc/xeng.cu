@@ -24,6 +24,11 @@
 // units.  Two 256-thread CTAs share an SM (256 TMEM columns each), so one CTA's decode and
 // loads overlap the other's MMAs.  Every wait on the tensor cores is bounded; on a timeout
 // the CTA writes NaN into its first output element and stops.
+//
+// WIDE (4+4-bit voltages, A a multiple of 16, 16-byte aligned input): a thread loads 16
+// consecutive antennas of one sample with one 16-byte load (a warp reads whole 128-byte
+// lines), and the raw bytes of the next two chunks are held in registers, so a chunk's loads
+// are issued two decode steps before they are used.
 #include <cuda_fp16.h>
 #include <cstdint>
 #include "moff_common.cuh"
@@ -60,6 +65,17 @@ __device__ __forceinline__ void operand_pairs(typename Volt<VDT>::T raw, uint32_
     w = __byte_perm(x, 0, 0x1032) ^ 0x8000u;     // swap the halves, negate the new low half
 }
 
+// Operand pair X = (re, im) of byte i of a word of 4+4-bit voltages, from the word's biased
+// high nibbles H and low nibbles L (each n ^ 8 in [0, 15], one per byte): the same exact
+// 1032 + n construction as operand_pairs.
+template <int I>
+__device__ __forceinline__ uint32_t ci4_pair(uint32_t H, uint32_t L) {
+    const uint32_t u = (__byte_perm(H, L, I | ((4 + I) << 8)) & 0x00FF00FFu) | 0x64006400u;
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&u), __halves2half2(__ushort_as_half(0x6408),
+                                                                                      __ushort_as_half(0x6408)));
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 // unit -> (cp, row block, column block), column block >= row block (32-bit: the launcher
 // checks that the units fit)
 __device__ __forceinline__ void unit_coords(int u, int nab, int& cp, int& ab, int& bb) {
@@ -74,8 +90,9 @@ __device__ __forceinline__ void unit_coords(int u, int nab, int& cp, int& ab, in
     bb = ab + r;
 }
 
-template <int VDT>
+template <int VDT, bool WIDE>
 __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
+    static_assert(!WIDE || VDT == 2, "the wide loads are for 4+4-bit voltages");
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __half* sT = reinterpret_cast<__half*>(smem_raw);                           // [NSTAGE][N_TILE][TILE]
@@ -126,13 +143,13 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     const int r0 = 8 * warp + lr;
     const int sbase = 256 * warp + 4 * lr + lt;      // word offset of (r0, 2 lt) in a tile
     const long long RS = (long long)CP * A;          // sample stride of the voltages
-    VT rb[2 * NJ], ra[2 * NJ];
     // per unit: this thread's voltage pointers at sample lt of chunk 0 and its row validity
     struct UnitPtr {
         const VT* pb;
         const VT* pa;
         bool vb0, vb1, va0, va1;
     };
+    VT rb[WIDE ? 1 : 2 * NJ], ra[WIDE ? 1 : 2 * NJ];
     auto unit_ptr = [&](int u) {
         int cp, ab, bb;
         unit_coords(u, nab, cp, ab, bb);
@@ -146,25 +163,100 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
         return p;
     };
     auto load_chunk = [&](const UnitPtr& p, int kc) {
-        const int tq = kc * TC + lt;
-        const VT* pb = p.pb + (long long)(kc * TC) * RS;
-        const VT* pa = p.pa + (long long)(kc * TC) * RS;
+        if constexpr (!WIDE) {
+            const int tq = kc * TC + lt;
+            const VT* pb = p.pb + (long long)(kc * TC) * RS;
+            const VT* pa = p.pa + (long long)(kc * TC) * RS;
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const bool tin = tq + 4 * j < T;
-            rb[2 * j] = (tin && p.vb0) ? __ldg(pb) : VT(0);
-            rb[2 * j + 1] = (tin && p.vb1) ? __ldg(pb + 64) : VT(0);
-            ra[2 * j] = (tin && p.va0) ? __ldg(pa) : VT(0);
-            ra[2 * j + 1] = (tin && p.va1) ? __ldg(pa + 64) : VT(0);
-            pb += 4 * RS;
-            pa += 4 * RS;
+            for (int j = 0; j < NJ; ++j) {
+                const bool tin = tq + 4 * j < T;
+                rb[2 * j] = (tin && p.vb0) ? __ldg(pb) : VT(0);
+                rb[2 * j + 1] = (tin && p.vb1) ? __ldg(pb + 64) : VT(0);
+                ra[2 * j] = (tin && p.va0) ? __ldg(pa) : VT(0);
+                ra[2 * j + 1] = (tin && p.va1) ? __ldg(pa + 64) : VT(0);
+                pb += 4 * RS;
+                pa += 4 * RS;
+            }
         }
     };
+
+    // WIDE mapping: thread (warp w, lane l) loads rows 16 p .. 16 p + 15, p = l % 8, of
+    // sample tw = 4 w + l / 8 of a chunk.  In a tile, row r and sample t sit at word
+    // 256 (r / 8) + 32 (t / 4) + 4 (r % 8) + t % 4 (bank 4 (r % 8) + t % 4).  Store instruction
+    // (s, i) of a lane writes row 16 p + 4 (s ^ si) + (i + ri) % 4 with ri = p % 4, si = p / 4:
+    // the 32 lanes then differ in (t % 4, ri, si) and hit 32 distinct banks.  One byte permute
+    // per word selects word s ^ si and rotates its bytes by ri.
+    const int wp = lane & 7, wri = lane & 3, wsi = (lane >> 2) & 1, wtw = 4 * warp + (lane >> 3);
+    const uint32_t wsel = (uint32_t)(((0 + wri) & 3) | (((1 + wri) & 3) << 4) | (((2 + wri) & 3) << 8) |
+                                     (((3 + wri) & 3) << 12)) + (wsi ? 0x4444u : 0u);
+    int woff[2][4];                                  // word offsets for s % 2 and i (+ 256 (s / 2))
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            woff[j][i] = 512 * wp + 32 * warp + (lane >> 3) + 16 * (j ^ wsi) + 4 * ((i + wri) & 3);
+    uint4 wb0 = make_uint4(0, 0, 0, 0), wa0 = wb0, wb1 = wb0, wa1 = wb0;   // chunks g (even / odd sets)
+    int lu = beg, lkc = 0, lcp = 0, lab = 0, lbb = 0;                       // load cursor
+    if (WIDE && beg < end) unit_coords(beg, nab, lcp, lab, lbb);
+    const unsigned char* VW = static_cast<const unsigned char*>(a.volt);
+    auto wide_load = [&](uint4& xb, uint4& xa) {
+        xb = make_uint4(0, 0, 0, 0);
+        xa = xb;
+        if (lu >= end) return;
+        const int t = lkc * TC + wtw;
+        if (t < T) {
+            const unsigned char* row = VW + (long long)t * RS + (long long)lcp * A + 16 * wp;
+            if (lbb * 128 + 16 * wp < A) xb = __ldg(reinterpret_cast<const uint4*>(row + lbb * 128));
+            if (lab != lbb && lab * 128 + 16 * wp < A) xa = __ldg(reinterpret_cast<const uint4*>(row + lab * 128));
+        }
+        if (++lkc == n_chunks) {
+            lkc = 0;
+            if (++lu < end) unit_coords(lu, nab, lcp, lab, lbb);
+        }
+    };
+    auto wide_word = [&](uint32_t* tile, uint32_t* wtile, uint32_t R, int s) {
+        const uint32_t H = ((R >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+        const uint32_t L = (R & 0x0F0F0F0Fu) ^ 0x08080808u;
+        const uint32_t x0 = ci4_pair<0>(H, L), x1 = ci4_pair<1>(H, L), x2 = ci4_pair<2>(H, L), x3 = ci4_pair<3>(H, L);
+        const int* o = woff[s & 1];
+        const int hi = 256 * (s >> 1);
+        tile[o[0] + hi] = x0;
+        tile[o[1] + hi] = x1;
+        tile[o[2] + hi] = x2;
+        tile[o[3] + hi] = x3;
+        if (wtile) {
+            wtile[o[0] + hi] = __byte_perm(x0, 0, 0x1032) ^ 0x8000u;
+            wtile[o[1] + hi] = __byte_perm(x1, 0, 0x1032) ^ 0x8000u;
+            wtile[o[2] + hi] = __byte_perm(x2, 0, 0x1032) ^ 0x8000u;
+            wtile[o[3] + hi] = __byte_perm(x3, 0, 0x1032) ^ 0x8000u;
+        }
+    };
+    auto wide_decode = [&](const uint4& xb, const uint4& xa, __half* st, bool diag) {
+        uint32_t* tX = reinterpret_cast<uint32_t*>(st + T_XB * TILE);
+        uint32_t* tW = reinterpret_cast<uint32_t*>(st + T_WB * TILE);
+        uint32_t* tA = reinterpret_cast<uint32_t*>(st + T_XA * TILE);
+        wide_word(tX, tW, __byte_perm(xb.x, xb.y, wsel), 0);
+        wide_word(tX, tW, __byte_perm(xb.y, xb.x, wsel), 1);
+        wide_word(tX, tW, __byte_perm(xb.z, xb.w, wsel), 2);
+        wide_word(tX, tW, __byte_perm(xb.w, xb.z, wsel), 3);
+        if (!diag) {
+            wide_word(tA, nullptr, __byte_perm(xa.x, xa.y, wsel), 0);
+            wide_word(tA, nullptr, __byte_perm(xa.y, xa.x, wsel), 1);
+            wide_word(tA, nullptr, __byte_perm(xa.z, xa.w, wsel), 2);
+            wide_word(tA, nullptr, __byte_perm(xa.w, xa.z, wsel), 3);
+        }
+    };
+
     bool failed = false;
     int g = 0;            // chunks issued by this CTA
     int n_done = 0;       // units finished by this CTA
-    UnitPtr up = beg < end ? unit_ptr(beg) : UnitPtr{};
-    if (beg < end) load_chunk(up, 0);
+    UnitPtr up = (!WIDE && beg < end) ? unit_ptr(beg) : UnitPtr{};
+    if constexpr (WIDE) {
+        wide_load(wb0, wa0);
+        wide_load(wb1, wa1);
+    } else if (beg < end) {
+        load_chunk(up, 0);
+    }
     for (int u = beg; u < end && !failed; ++u) {
         int cp, ab, bb;
         unit_coords(u, nab, cp, ab, bb);
@@ -176,22 +268,33 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
             failed = __syncthreads_or(failed) != 0;
             if (failed) break;
             __half* st = sT + s * N_TILE * TILE;
-            uint32_t* sxb = reinterpret_cast<uint32_t*>(st + T_XB * TILE) + sbase;
-            uint32_t* swb = reinterpret_cast<uint32_t*>(st + T_WB * TILE) + sbase;
-            uint32_t* sxa = reinterpret_cast<uint32_t*>(st + T_XA * TILE) + sbase;
-#pragma unroll
-            for (int j = 0; j < NJ; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t x, w;
-                    operand_pairs<VDT>(rb[2 * j + h], x, w);
-                    sxb[32 * j + 2048 * h] = x;
-                    swb[32 * j + 2048 * h] = w;
-                    if (!diag) {
-                        operand_pairs<VDT>(ra[2 * j + h], x, w);
-                        sxa[32 * j + 2048 * h] = x;
-                    }
+            if constexpr (WIDE) {
+                // decode chunk g, then load chunk g + 2 into the same register set
+                if (s == 0) {
+                    wide_decode(wb0, wa0, st, diag);
+                    wide_load(wb0, wa0);
+                } else {
+                    wide_decode(wb1, wa1, st, diag);
+                    wide_load(wb1, wa1);
                 }
+            } else {
+                uint32_t* sxb = reinterpret_cast<uint32_t*>(st + T_XB * TILE) + sbase;
+                uint32_t* swb = reinterpret_cast<uint32_t*>(st + T_WB * TILE) + sbase;
+                uint32_t* sxa = reinterpret_cast<uint32_t*>(st + T_XA * TILE) + sbase;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t x, w;
+                        operand_pairs<VDT>(rb[2 * j + h], x, w);
+                        sxb[32 * j + 2048 * h] = x;
+                        swb[32 * j + 2048 * h] = w;
+                        if (!diag) {
+                            operand_pairs<VDT>(ra[2 * j + h], x, w);
+                            sxa[32 * j + 2048 * h] = x;
+                        }
+                    }
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
@@ -209,11 +312,13 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
                 if (kc == n_chunks - 1) commit(mb_acc);
             }
             // prefetch the next chunk (of this unit or of the next one)
-            if (kc + 1 < n_chunks) {
-                load_chunk(up, kc + 1);
-            } else if (u + 1 < end) {
-                up = unit_ptr(u + 1);
-                load_chunk(up, 0);
+            if constexpr (!WIDE) {
+                if (kc + 1 < n_chunks) {
+                    load_chunk(up, kc + 1);
+                } else if (u + 1 < end) {
+                    up = unit_ptr(u + 1);
+                    load_chunk(up, 0);
+                }
             }
         }
         if (failed) break;
@@ -392,25 +497,31 @@ cudaError_t launch_fx_image(int n_pad, const FxArgs& a, cudaStream_t st) {
     }
 }
 
+namespace {
+template <int VDT, bool WIDE>
+cudaError_t launch_xeng_t(const XengArgs& a, long long grid, cudaStream_t st) {
+    const size_t smem = xe::smem_bytes();
+    const cudaError_t e = ensure_smem<xe::xeng_kernel<VDT, WIDE>>(smem);
+    if (e != cudaSuccess) return e;
+    xe::xeng_kernel<VDT, WIDE><<<(unsigned)grid, xe::NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st) {
     const int nab = (a.n_ant + 127) / 128;
     const long long n_units = (long long)a.n_cp * (nab * (nab + 1) / 2);
     if (n_units == 0) return cudaSuccess;
     if (n_units > 2147483647LL) return cudaErrorInvalidValue;   // the kernel indexes units in 32 bits
     const long long grid = n_units < 2LL * n_sm ? n_units : 2LL * n_sm;
-    const size_t smem = xe::smem_bytes();
-    cudaError_t e;
     switch (vdt) {
         case 1:
-            e = ensure_smem<xe::xeng_kernel<1>>(smem);
-            if (e != cudaSuccess) return e;
-            xe::xeng_kernel<1><<<(unsigned)grid, xe::NT, smem, st>>>(a);
-            return cudaGetLastError();
+            return launch_xeng_t<1, false>(a, grid, st);
         case 2:
-            e = ensure_smem<xe::xeng_kernel<2>>(smem);
-            if (e != cudaSuccess) return e;
-            xe::xeng_kernel<2><<<(unsigned)grid, xe::NT, smem, st>>>(a);
-            return cudaGetLastError();
+            // 16-byte loads of 16 antennas need every row of 16 to start on a 16-byte boundary
+            if (a.n_ant % 16 == 0 && reinterpret_cast<uintptr_t>(a.volt) % 16 == 0)
+                return launch_xeng_t<2, true>(a, grid, st);
+            return launch_xeng_t<2, false>(a, grid, st);
         default:
             return cudaErrorInvalidValue;
     }

@@ -70,6 +70,16 @@ def test_lwa_slice_ci4_gains(epic):
     check(vis, wl, g, "lwa")
 
 
+def test_lwa_units_beyond_one_per_cta(epic):
+    """384 units (64 channels x 2 pols x 3 blocks) on at most 304 CTAs: CTAs that own two
+    units load the next unit's first chunks while finishing the current one (4+4-bit voltages
+    on 16-byte loads; 40 samples, a ragged second chunk)."""
+    wl = synth.workload_lwa(n_chan=64, n_time=40, chan_index=list(range(0, 128, 2)))
+    g = synth.random_gains(np.random.default_rng(9), (wl.n_chan, wl.n_pol, wl.n_ant))
+    _, vis = run(epic, wl, g)
+    check(vis, wl, g, "lwa 384 units")
+
+
 def test_hera_slice_f16(epic):
     """331 antennas (3 x 3 blocks with a 75-antenna tail), FP16 voltages, 40 samples."""
     wl = synth.workload_hera(n_chan=2, n_time=40)
@@ -82,6 +92,7 @@ def test_hera_slice_f16(epic):
     (129, 31, 1, 2, "f16"),     # a one-antenna tail block, less than one chunk
     (300, 33, 2, 1, "ci4"),     # three blocks, one sample past a chunk
     (640, 64, 1, 1, "ci4"),     # five full blocks, two full chunks
+    (336, 45, 1, 2, "ci4"),     # 16-byte loads with an 80-antenna tail block, a ragged chunk
 ])
 def test_small_shapes(epic, n_ant, n_time, n_chan, n_pol, vdtype):
     wl = _small(n_ant, n_time, n_chan, n_pol, vdtype, seed=n_ant + n_time)
