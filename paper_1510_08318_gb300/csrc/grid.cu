@@ -7,7 +7,8 @@
 // scattered antennas of one plane spreads over the banks).  Each thread then owns grid cells:
 // it reads a cell's mapping entries once from the cell-major CSR (atomics-free) and applies
 // them to all TB samples, then streams the TB results out with coalesced evict-first stores.
-// Output bytes (8 N_g^2 per sample) dominate, so the kernel is bound by HBM writes.
+// Output bytes (8 N_g^2 per sample) dominate the traffic; the gather (shared-memory reads of the
+// planes and lanes whose cells have different entry counts) keeps it below the write bandwidth.
 //
 // SMAP: when the mapping CSR fits beside the planes with two CTAs per SM, each persistent CTA
 // copies it into shared memory once, so that the per-entry loads do not wait on L1/L2.  Either
