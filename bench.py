@@ -140,6 +140,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def alu_roofline(flops, kern_ms, n_sm, clocks=None, traffic=None, flop_basis=None):
+    """FP32-FMA roofline of a CUDA-core kernel: achieved FLOP/s against SMs x 128 lanes x 2 FLOP
+    x the maximum SM clock ("frac"), and also against the median SM clock sampled during the
+    timed region and the median clock recorded under the GEMM power cap, when those are known."""
+    def peak_at(mhz):
+        return n_sm * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_at(SM_MAX_MHZ), "unit": "TFLOP/s",
+            "traffic": traffic,
+            "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, max clock)" % (n_sm, SM_MAX_MHZ)}
+    if flop_basis:
+        roof["flop_basis"] = flop_basis
+    roof["frac"] = achieved / roof["peak"]
+    mhz = (clocks or {}).get("sm_mhz")
+    if mhz:
+        roof["sampled_sm_mhz"] = mhz
+        roof["frac_at_sampled_clock"] = achieved / peak_at(mhz)
+    load = MEASURED.get("clocks_under_load", {}).get("sm_mhz_median")
+    if load:
+        roof["gemm_load_sm_mhz"] = load
+        roof["frac_at_gemm_load_clock"] = achieved / peak_at(load)
+    return roof
+
+
 def max_over_ranks(values, world, device):
     """Element-wise maximum over ranks (each rank passes its own timings)."""
     if world <= 1:
@@ -317,12 +341,8 @@ def run_hera(args):
     e2e_ms, _ = timed(e2e_step)
     units = A * T * C * P
     flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * P
-    peak = n_sm * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "achieved": flops / (kern_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "traffic": None, "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, max clock)"
-                                          % (n_sm, SM_MAX_MHZ),
-            "flop_basis": "per image 5 N log2 N (N = N_p^2) + 8 nnz + 4 N, as the headline"}
-    roof["frac"] = roof["achieved"] / peak
+    roof = alu_roofline(flops, kern_ms, n_sm, clk,
+                        flop_basis="per image 5 N log2 N (N = N_p^2) + 8 nnz + 4 N, as the headline")
     cb, err = None, {}
     if rank == 0 and not args.no_cpu_baseline:
         cb, err = cpu_baseline_sample(wl, plan, torch, n_chan=2, n_time=T, forms=("fft",))
@@ -646,11 +666,9 @@ def run_xpol(args):
                 "flop_basis": "executed tensor FLOP per virtual-pol image as the headline, 4 per channel-sample"}
     else:
         flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * 4
-        peak = n_sm * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / (f["kernel_ms"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "traffic": None,
-                "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, max clock)" % (n_sm, SM_MAX_MHZ),
-                "flop_basis": "per virtual-pol image as the headline (5 N log2 N + 8 nnz + 4 N), 4 per channel-sample"}
+        roof = alu_roofline(flops, f["kernel_ms"], n_sm, f["clocks"],
+                            flop_basis="per virtual-pol image as the headline (5 N log2 N + 8 nnz + 4 N), "
+                                       "4 per channel-sample")
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": METRIC, "value": job_throughput(units, world, f["ms_per_step"]), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": f["ms_per_step"],
@@ -1072,6 +1090,7 @@ def main():
         cb, err = cpu_baseline_sample(wl, plan, torch, n_chan=32, n_time=1024)
         cfb = cpu_fft_sample(wl, n_chan=32, n_time=1024)
     # the chosen form: the fastest whose error against the oracle meets the FP32 bound (1e-4)
+    fft_flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * P
     ok = [k for k in forms if err.get(forms[k]["xform"], 0.0) < 1e-4]
     chosen = min(ok, key=lambda k: forms[k]["ms_per_step"])
     f = forms[chosen]
@@ -1082,13 +1101,11 @@ def main():
                 "unit": "TFLOP/s", "traffic": DG_TRAFFIC_BYTES,
                 "peak_basis": "measured dense bf16 burst GEMM (FP16 has the same nominal rate), of measured"}
     else:
-        flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * P
-        peak = n_sm * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / (f["kernel_ms"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "traffic": FWD_TRAFFIC_BYTES,
-                "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, max clock)"
-                              % (n_sm, SM_MAX_MHZ)}
+        roof = alu_roofline(fft_flops, f["kernel_ms"], n_sm, f["clocks"], traffic=FWD_TRAFFIC_BYTES)
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # the plain FP32 form's own roofline, whichever form is chosen
+    fft_roof = alu_roofline(fft_flops, forms["fp32_fft"]["kernel_ms"], n_sm, forms["fp32_fft"]["clocks"],
+                            traffic=FWD_TRAFFIC_BYTES)
     line = {
         "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -1110,7 +1127,8 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": f["clocks"],
         "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()},
-        "plain_fp32": {"value": forms["fp32_fft"]["value"], "ms_per_step": forms["fp32_fft"]["ms_per_step"]},
+        "plain_fp32": {"value": forms["fp32_fft"]["value"], "ms_per_step": forms["fp32_fft"]["ms_per_step"],
+                       "roofline": fft_roof},
     }
     if cb is not None:
         line["cpu_baseline"] = cb
