@@ -73,3 +73,43 @@ def test_calls_reject_null_plan(lib):
     assert lib.epic_grid(None, None, 1, None, None, None) == epic.EPIC_EINVAL
     assert lib.epic_plan_info(None, None, None, None) == epic.EPIC_EINVAL
     lib.epic_destroy(None)
+
+
+def test_every_plan_call_rejects_null_plan(lib):
+    """Every call that takes a plan or a batch checks it on the host before any CUDA call."""
+    plan_calls = {
+        "epic_image_xpol": (None, None, 1, None, None, 0, None, None, None),
+        "epic_correlate": (None, None, 1, None, None, None),
+        "epic_fx_image": (None, None, None, None),
+        "epic_weff": (None, None, None),
+        "epic_isotropic": (None, None, None, None, 0.05, None, None),
+        "epic_set_transform": (None, 0),
+    }
+    for name, args in plan_calls.items():
+        assert getattr(lib, name)(*args) == epic.EPIC_EINVAL, name
+        assert "plan" in epic.epic_last_error(), name
+    assert lib.epic_batch_image(None, None, None, None, None, None, None) == epic.EPIC_EINVAL
+    assert lib.epic_batch_autotune(None, None, None, None, None, None) == epic.EPIC_EINVAL
+    assert lib.epic_batch_info(None, None, None, None, 0) == epic.EPIC_EINVAL
+    assert "batch" in epic.epic_last_error()
+    assert lib.epic_batch_create(None, 1, None) == epic.EPIC_EINVAL
+    out = ctypes.c_void_p(1)
+    assert lib.epic_batch_create(ctypes.byref(out), 0, None) == epic.EPIC_EINVAL
+    assert out.value is None                       # the out-pointer is cleared on failure
+    lib.epic_batch_destroy(None)
+
+
+@pytest.mark.parametrize("args, status", [
+    ((0, 2, 128, 4, 2, None, 1, None, 0, None), epic.EPIC_EINVAL),           # no antennas
+    ((8, 2, 100, 4, 2, None, 1, None, 0, None), epic.EPIC_EUNSUPPORTED),     # 100 channels
+    ((8, 2, 128, 4, 5, None, 1, None, 0, None), epic.EPIC_EINVAL),           # unknown input format
+    ((8, 2, 128, 4, 2, None, 2, None, 0, None), epic.EPIC_EINVAL),           # 4+4-bit output
+    ((8, 2, 128, 4, 2, None, 1, None, 0, None), epic.EPIC_EINVAL),           # NULL arrays
+])
+def test_fengine_rejects_on_host(lib, args, status):
+    assert lib.epic_fengine(*args) == status
+    assert epic.epic_last_error()
+
+
+def test_fengine_zero_blocks_is_a_no_op(lib):
+    assert lib.epic_fengine(8, 2, 128, 0, 2, None, 1, None, 0, None) == epic.EPIC_OK
