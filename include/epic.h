@@ -240,7 +240,9 @@ epic_status epic_isotropic(const epic_plan *plan, const float *image, const floa
  * Computed on the tensor cores as two real products with FP16 operands (the voltages are exact
  * in FP16) and FP32 accumulation: for 4+4-bit voltages the sums over the call are exact; the
  * gains and 1/T are applied in FP32 afterwards.  Each call is one integration (no
- * continuation).  The plan's mapping is not used.
+ * continuation).  The plan's mapping is not used.  4+4-bit voltages with A a multiple of 16
+ * in a 16-byte-aligned array are read 16 antennas per load (faster); any other A or
+ * alignment takes byte loads, with the same results.
  */
 epic_status epic_correlate(const epic_plan *plan, const void *volt, int n_time, const float *gains,
                            float *vis, void *stream);
