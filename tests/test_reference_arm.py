@@ -23,8 +23,15 @@ def _check_line(line, n_gpus):
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"] is True
     assert line["n_gpus"] == n_gpus and line["steps"] == 1 and line["warmup"] == 3
     assert line["value"] > 0 and line["ms_per_step"] > 0
-    # the headline arm's workload (the full LWA-like configuration)
-    assert line["config"]["workload"] == "LWA-like: 256 ant, 128 chan, 2 pol, T=1024, 128x128 image, ci4"
+    # the headline arm's config (the full LWA-like configuration), key for key
+    cfg = line["config"]
+    assert cfg["workload"] == "LWA-like: 256 ant, 128 chan, 2 pol, T=1024, 128x128 image, ci4"
+    assert (cfg["antennas"], cfg["time_samples"], cfg["channels"], cfg["pols"]) == (256, 1024, 128, 2)
+    assert cfg["grid"] == "64x64 padded to 128x128" and cfg["images_per_step"] == 262144
+    assert cfg["parallelism"] == ("1 GPU" if n_gpus == 1 else "independent replicas per GPU")
+    # ms_per_step is the measured time of the bounded sample step, not an extrapolation: the
+    # timed steps fit well inside the run
+    assert line["ms_per_step"] < 60e3
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
