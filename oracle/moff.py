@@ -19,6 +19,10 @@ in numpy/scipy float64, with no blocking, fusion or reordering:
                  A(k) = sum_a P_a |K_a(k)|^2 with P_a the mean antenna power and K_a
                  the spatial transform of antenna a's sampled footprint (the
                  per-antenna form Sec. 4.3 proposes).
+  remove_autocorr_peak_scaled  Sec. 4.2 as the paper does it: the image taken back to the
+                 uv plane, an estimated auto-correlation kernel scaled to the zero-spacing
+                 value subtracted, and the result transformed back (uv_from_image and
+                 image_from_uv_plane are the two transforms).
   fengine        Sec. 3 "Temporal Fourier transform": per-antenna spectra of blocks of
                  time samples (numpy's FFT as the library step).
   weff_opt, isotropic_image  Sec. 5: the effective weighting of the image of a
@@ -46,11 +50,6 @@ import scipy.sparse as sp
 # ----------------------------------------------------------------------------------
 # antenna-to-grid mapping (Sec. 3)
 # ----------------------------------------------------------------------------------
-def cell_of(x, x0, dx):
-    """Nearest grid index along one axis (round half up), in float64."""
-    return np.floor((x - x0) / dx + 0.5).astype(np.int64)
-
-
 def map_antennas(pos, kern_ptr, kern_dxdy, kern_w, dx, origin, n_grid):
     """Sparse M (N_g^2 x A, complex128, CSR).  Raises ValueError if a footprint sample
     falls outside the grid."""
@@ -106,11 +105,6 @@ def spatial_transform(E, n_pad):
 def fftshift2(x):
     n = x.shape[-1]
     return np.roll(np.roll(x, n // 2, axis=-1), n // 2, axis=-2)
-
-
-def ifftshift2(x):
-    n = x.shape[-1]
-    return np.roll(np.roll(x, -(n // 2), axis=-1), -(n // 2), axis=-2)
 
 
 def moff_image_cp(M, volt_t, gain, n_grid, n_pad):
@@ -185,9 +179,37 @@ def autocorr_term(M, volt, gains, n_grid, n_pad):
     return out
 
 
-# ----------------------------------------------------------------------------------
-# gradient of a real image-domain loss with respect to the complex gains
-# ----------------------------------------------------------------------------------
+def uv_from_image(image, n_grid):
+    """The uv plane of an image of the +i transform (Sec. 4.2: the squared image transformed
+    back to the uv plane): image [N_p, N_p] shifted -> U(d) for lags d in (-N_g, N_g)^2,
+    [2 N_g - 1, 2 N_g - 1] with lag (dy, dx) at (dy + N_g - 1, dx + N_g - 1).  Exact for
+    N_p >= 2 N_g - 1 (no lag aliases); numpy's FFT is the library step."""
+    n_pad = image.shape[-1]
+    P = np.fft.fft2(np.fft.ifftshift(image)) / (n_pad * n_pad)
+    lag = np.arange(-(n_grid - 1), n_grid) % n_pad
+    return P[np.ix_(lag, lag)]
+
+
+def image_from_uv_plane(U, n_grid, n_pad):
+    """Inverse of uv_from_image: I(k) = sum_d U(d) exp(+2 pi i d.k / N_p), shifted."""
+    P = np.zeros((n_pad, n_pad), dtype=np.complex128)
+    lag = np.arange(-(n_grid - 1), n_grid) % n_pad
+    P[np.ix_(lag, lag)] = U
+    return np.fft.fftshift(np.fft.ifft2(P) * (n_pad * n_pad))
+
+
+def remove_autocorr_peak_scaled(image, kernel_uv, n_grid):
+    """The paper's removal of the antenna auto-correlations from a MOFF image (Sec. 4.2), in its
+    order: transform the squared image back to the uv plane, subtract the estimated
+    auto-correlation kernel (kernel_uv, on the lag plane of uv_from_image, peak at zero spacing)
+    scaled so that its peak equals the uv plane's value at the zero-spacing pixel, and transform
+    back.  Returns (image with the auto-correlations removed, its uv plane)."""
+    U = uv_from_image(image, n_grid)
+    z = n_grid - 1
+    U = U - (U[z, z] / kernel_uv[z, z]) * kernel_uv
+    return image_from_uv_plane(U, n_grid, image.shape[-1]).real, U
+
+
 # ----------------------------------------------------------------------------------
 # the F-engine (Sec. 3 "Temporal Fourier transform")
 # ----------------------------------------------------------------------------------
@@ -225,6 +247,9 @@ def isotropic_image(image, autocorr, weff, n_ant):
     return (image - autocorr) / (n_ant * (n_ant - 1)) / weff
 
 
+# ----------------------------------------------------------------------------------
+# gradient of a real image-domain loss with respect to the complex gains
+# ----------------------------------------------------------------------------------
 def grad_gains(M, volt, gains, n_grid, n_pad, grad_image):
     """grad[c, p, a] = dL/dRe g + i dL/dIm g for a real loss L whose derivative with
     respect to the integrated image I[c, p] (shifted pixel order) is grad_image.

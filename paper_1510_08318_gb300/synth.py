@@ -46,6 +46,17 @@ def layout_disk(rng, n_ant, diameter):
     return layout_ellipse(rng, n_ant, diameter, diameter)
 
 
+def layout_rect_min_sep(rng, n_ant, width, height, min_sep):
+    """Uniform in a width x height box, drawn one by one and rejected closer than min_sep to an
+    earlier antenna (tiles that do not overlap)."""
+    pts = []
+    while len(pts) < n_ant:
+        p = np.array([rng.uniform(-width / 2, width / 2), rng.uniform(-height / 2, height / 2)])
+        if all(math.hypot(p[0] - q[0], p[1] - q[1]) >= min_sep for q in pts):
+            pts.append(p)
+    return np.array(pts, dtype=np.float64)
+
+
 def layout_hex(n_side, spacing):
     """Hexagonal close-packed core with n_side antennas per side (3 n (n-1) + 1 total)."""
     pts = []
@@ -400,6 +411,29 @@ def workload_twotype(seed=6, n_time=256, n_ant=51):
                              for ll, mm in zip(l, m)]
     wl.extra["types"] = np.array([a % 2 for a in range(n_ant)])
     return _finish(wl, v, "c64")
+
+
+def workload_mwa_core(seed=7, dx=0.5):
+    """The simulation of the paper's verification (Sec. 4.1) with a synthetic layout in place of
+    the MWA's: 51 identical tiles uniform in a 150 m x 150 m box (at least 5 m apart, so that no
+    two 4.4 m tiles overlap), uniform 4.4 m square apertures sampled on a lattice of step dx / 4,
+    grid spacing dx (0.5 m by default, lambda / 4 at 150 MHz), N_g the least even side above
+    (150 m + 4.4 m) / dx + 8 cells (318), N_p = 2 N_g, one channel at 150 MHz, one pol and one
+    sample of unit voltages (the synthesised beam), complex64."""
+    rng = np.random.default_rng(seed)
+    freqs = np.array([150e6])
+    side = 4.4
+    pos = layout_rect_min_sep(rng, 51, 150.0, 150.0, 5.0)
+    kd, kw = kernel_square(side, dx / 4)
+    ptr, dxdy, w = pack_kernels([(kd, kw)] * 51)
+    n_grid = int(math.ceil((150.0 + side) / dx)) + 8
+    n_grid += n_grid % 2
+    n_pad = 2 * n_grid
+    origin = centred_origin(pos, side / 2, dx, n_grid)
+    wl = Workload("MWA-core-like: 51 tiles of 4.4 m in 150 m, unit voltages, %gx%g m grid" % (dx, dx),
+                  pos, ptr, dxdy, w, dx, origin, n_grid, n_pad, freqs, 1, 1, "c64")
+    wl.extra["tile_side"] = side
+    return _finish(wl, np.ones((1, 1, 1, 51), dtype=np.complex128), "c64")
 
 
 def workload_batch(seed=4, n_sub=64, n_time=128, max_chan=None, max_ant=None, n_src=20):

@@ -116,3 +116,18 @@ def test_batch_workload():
         assert 1 <= wl.n_chan <= 2 and 32 <= wl.n_ant <= 40 and wl.vdtype == "f16"
         assert 50e6 <= wl.freqs.min() and wl.freqs.max() <= 200e6
         _inside_grid(wl)
+
+
+def test_mwa_core_like_workload():
+    """The verification simulation's layout (Sec. 4.1): 51 tiles of 4.4 m in a 150 m box, no two
+    tiles overlapping, unit voltages, every footprint sample on the grid with 2x padding."""
+    wl = synth.workload_mwa_core()
+    assert wl.n_ant == 51 and wl.n_pad == 2 * wl.n_grid and wl.dx == 0.5
+    assert np.abs(wl.pos).max() <= 75.0
+    d = np.hypot(*(wl.pos[:, None, :] - wl.pos[None, :, :]).transpose(2, 0, 1))
+    assert d[~np.eye(51, dtype=bool)].min() >= 5.0
+    assert np.all(wl.volt == 1.0) and wl.volt.shape == (1, 1, 1, 51)
+    k = wl.kern_dxdy[wl.kern_ptr[0]:wl.kern_ptr[1]]
+    assert np.abs(k).max() < 2.2 and abs(wl.kern_w[wl.kern_ptr[0]:wl.kern_ptr[1]].sum() - 1.0) < 1e-12
+    x = (wl.pos[:, None, 0] + wl.kern_dxdy[None, :, 0] - wl.origin[0]) / wl.dx
+    assert x.min() > 0 and x.max() < wl.n_grid - 1
