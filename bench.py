@@ -1214,805 +1214,6 @@ def main():
     }
     if cb is not None:
         line["cpu_baseline"] = cb
-        line["err_vs_oracle"] = {"relative_l2": err, "sample": "last 2 channels, all %d samples, image" % T}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def run_batch(args):
-    """64 heterogeneous sub-arrays (N_p 32..512, mixed apertures, FP16, T = 128), imaged by the
-    batch executor (autotuned), captured once as a CUDA graph and replayed: one graph launch
-    per step.  Metric as the headline: antenna-samples/s over all sub-arrays."""
-    import torch
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    subs = synth.workload_batch(n_time=128)
-    plans = [epic.Plan.from_workload(w, device=local) for w in subs]
-    volts = [torch.from_numpy(w.volt_raw).to(dev) for w in subs]
-    batch = epic.Batch(plans)
-    acc, img = batch.alloc()
-    info = batch.autotune(volts, acc)
-    st = torch.cuda.Stream(dev)
-    st.wait_stream(torch.cuda.current_stream(dev))
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(st):
-        batch.image(volts, acc, img)
-        with torch.cuda.graph(g, stream=st):
-            batch.image(volts, acc, img)
-    torch.cuda.synchronize()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(max(args.warmup, 3)):
-        g.replay()
-    torch.cuda.synchronize()
-    cur = torch.cuda.current_stream(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(local)
-    clocks.start()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(cur)
-        g.replay()
-        ev[i][1].record(cur)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    units = sum(w.n_ant * w.n_time * w.n_chan * w.n_pol for w in subs)
-    images = sum(w.n_time * w.n_chan * w.n_pol for w in subs)
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch: 64 heterogeneous sub-arrays, N_p 32-512, FP16, T=128",
-                       "sub_arrays": len(subs), "images_per_step": images, "antenna_samples_per_step": units,
-                       "classes": info, "launch": "one CUDA graph replay per step",
-                       "l2": "flushed (256 MB write) before every timed step"},
-            "images_per_s": images / (ms / 1e3), "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def run_calib(args):
-    """Gain calibration workload (1024 antennas, 32 channels, 64 samples, N_p = 256, complex64):
-    one step = forward image + adjoint (gradient of the image loss with respect to the gains)."""
-    import numpy as np
-    import torch
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    wl = synth.workload_calib()
-    plan = epic.Plan.from_workload(wl, device=local)
-    volt = torch.from_numpy(wl.volt_raw).to(dev)
-    g = torch.from_numpy(np.ones((wl.n_chan, 1, wl.n_ant), np.complex64)).to(dev)
-    G = torch.ones((wl.n_chan, 1, wl.n_pad, wl.n_pad), dtype=torch.float32, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    cur = torch.cuda.current_stream(dev)
-
-    def fwd():
-        plan.image(volt, g)
-
-    def bwd():
-        plan.image_backward(volt, g, G)
-
-    res = {}
-    for name, fn in (("forward", fwd), ("adjoint", bwd)):
-        for _ in range(max(args.warmup, 3)):
-            fn()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(cur)
-            fn()
-            ev[i][1].record(cur)
-        torch.cuda.synchronize()
-        res[name] = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    units = wl.n_ant * wl.n_time * wl.n_chan * wl.n_pol
-    ms = res["forward"] + res["adjoint"]
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "step": "forward image + adjoint w.r.t. gains",
-                       "images_per_step": wl.n_time * wl.n_chan * wl.n_pol,
-                       "l2": "flushed (256 MB write) before every timed call"},
-            "forward_ms": res["forward"], "adjoint_ms": res["adjoint"]}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def measure_gridder(wl, plan, volt, dev, steps, warmup, world, rank, flush, with_oracle=True, with_cpu=False,
-                    e2e=False):
-    """Time the standalone gridder (epic_grid) on a workload whose voltages are resident: every
-    sample gridded onto its N_g x N_g grid and written to HBM as complex64.  Returns its kernel
-    time, its HBM roofline (algorithmic bytes = voltages and the mapping CSR read once + grids
-    written once, over the event-timed kernel duration, against the measured copy bandwidth), the
-    error of sampled grids of the timed output against the oracle, and optionally the oracle's rate
-    and the end-to-end time with host copies."""
-    import numpy as np
-    import torch
-    from oracle import moff
-    from paper_1510_08318_gb300 import epic
-    A, T, C, P, NG = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_grid
-    out = torch.empty((T, C, P, NG, NG), dtype=torch.complex64, device=dev)
-    st = torch.cuda.current_stream(dev)
-    h = plan._h
-    host_v = host_out = None
-    if e2e:
-        host_v = volt.cpu().pin_memory()
-        host_out = torch.empty(out.shape, dtype=torch.complex64).pin_memory()
-
-    def step():
-        epic.epic_grid(h, volt.data_ptr(), T, None, out.data_ptr(), st.cuda_stream)
-
-    def e2e_step():
-        volt.copy_(host_v, non_blocking=True)
-        step()
-        host_out.copy_(out, non_blocking=True)
-
-    def timed(fn, clocks=None):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        for i in range(steps):
-            flush.zero_()
-            ev[i][0].record(st)
-            fn()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        clk = clocks.stop() if clocks else None
-        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / steps], world, dev)[0], clk
-
-    for _ in range(max(warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    ms, clk = timed(step, Clocks(dev.index if dev.index is not None else 0))
-    res = {"ms": ms, "clocks": clk, "output_bytes": out.numel() * out.element_size()}
-    if e2e:
-        res["e2e_ms"], _ = timed(e2e_step)
-        res["h2d_bytes"] = int(host_v.numel() * host_v.element_size())
-        res["d2h_bytes"] = int(host_out.numel() * host_out.element_size())
-    nnz = plan.info["nnz"]
-    alg_bytes = (volt.numel() * volt.element_size() + out.numel() * out.element_size()
-                 + nnz * 8 + ((wl.n_pad // 2) ** 2 + 1) * 4)
-    peak = MEASURED["hbm_gbs"]
-    roof = {"bound": "hbm", "achieved": alg_bytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-            "traffic": GRID_TRAFFIC_BYTES if (A, T, C, P) == (256, 1024, 128, 2) else None,
-            "peak_basis": "measured STREAM-style copy (read + write bytes), of measured",
-            "algorithmic_bytes": alg_bytes}
-    roof["frac"] = roof["achieved"] / peak
-    res["roofline"] = roof
-    if rank == 0 and (with_oracle or with_cpu):
-        M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
-        c_s = list(range(max(C - 16, 0), C))
-        t0 = time.perf_counter()
-        want = [moff.grid_efields(M, wl.volt[:, c, 1 % P, :], np.ones(A), NG) for c in c_s]
-        dt = time.perf_counter() - t0
-        ts = [0, T // 2, T - 1]
-        got = out[ts][:, c_s, 1 % P].cpu().numpy()
-        ref = np.stack([w[ts] for w in want], 1)
-        res["err_vs_oracle"] = {"relative_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                                "sample": "3 samples x %d channels of the timed output" % len(c_s)}
-        if with_cpu:
-            res["cpu_baseline"] = {
-                "value": A * T * len(c_s) / dt, "unit": UNIT,
-                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
-                "sample": "channels %d-%d, pol %d, all %d samples (%d antenna-samples): FP64 sparse "
-                          "gridding; %.2f s" % (c_s[0], c_s[-1], 1 % P, T, A * T * len(c_s), dt)}
-    del out
-    return res
-
-
-def run_grid(args):
-    """The standalone gridder on the headline workload: every one of the 262,144 samples
-    gridded onto its 64 x 64 grid and written to HBM (8.6 GB of complex64 per step).  Bound by
-    HBM; roofline = algorithmic bytes (voltages + mapping tables read once, grids written
-    once) / kernel time against the measured copy bandwidth."""
-    import torch
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    wl = synth.workload_lwa(n_chan=args.channels)
-    plan = epic.Plan.from_workload(wl, device=local)
-    A, T, C, P, NG = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_grid
-    volt = torch.from_numpy(wl.volt_raw).to(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    g = measure_gridder(wl, plan, volt, dev, args.steps, args.warmup, world, rank, flush, with_oracle=True,
-                        with_cpu=not args.no_cpu_baseline, e2e=True)
-    units = A * T * C * P
-    line = {"metric": METRIC, "value": job_throughput(units, world, g["ms"]), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": g["ms"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name + ", standalone gridder (epic_grid)", "grids_per_step": T * C * P,
-                       "grid": "%dx%d complex64" % (NG, NG), "output_bytes": g["output_bytes"],
-                       "l2": "output (8.6 GB) larger than L2; 256 MB flush write before every timed step"},
-            "roofline": g["roofline"],
-            "e2e": {"value": job_throughput(units, world, g["e2e_ms"]), "unit": UNIT,
-                    "h2d_bytes_per_step": g["h2d_bytes"], "d2h_bytes_per_step": g["d2h_bytes"]},
-            "gpu_launches": args.steps, "clocks": g["clocks"]}
-    if "err_vs_oracle" in g:
-        line["err_vs_oracle"] = g["err_vs_oracle"]
-    if "cpu_baseline" in g:
-        line["cpu_baseline"] = g["cpu_baseline"]
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def run_xpol(args):
-    """All four cross-polarisation images of the headline workload (XX, YY, XY; YX = conj XY)
-    with epic_image_xpol: the forward kernel runs 4 virtual pols per channel (X, Y, X + Y,
-    X + iY) and the epilogue forms XY by the polarisation identity.  Same metric as the
-    headline (antenna-samples/s of the dual-pol data)."""
-    import numpy as np
-    import torch
-    from oracle import moff
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    wl = synth.workload_lwa(n_chan=args.channels)
-    plan = epic.Plan.from_workload(wl, device=local)
-    A, T, C, P, NP = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_pad
-    volt = torch.from_numpy(wl.volt_raw).to(dev)
-    acc4 = torch.empty((C, 4, NP, NP), dtype=torch.float64, device=dev)
-    img = torch.empty((C, 2, NP, NP), dtype=torch.float32, device=dev)
-    cross = torch.empty((C, NP, NP), dtype=torch.complex64, device=dev)
-    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
-    host_img = torch.empty(img.shape, dtype=torch.float32).pin_memory()
-    host_cross = torch.empty(cross.shape, dtype=torch.complex64).pin_memory()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream(dev)
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-
-    def step():
-        epic.epic_image_xpol(plan._h, volt.data_ptr(), T, None, acc4.data_ptr(), 0, img.data_ptr(),
-                             cross.data_ptr(), st.cuda_stream)
-
-    def kernel_only():
-        epic.epic_image_xpol(plan._h, volt.data_ptr(), T, None, acc4.data_ptr(), 0, None, None, st.cuda_stream)
-
-    def e2e_step():
-        volt.copy_(host_v, non_blocking=True)
-        step()
-        host_img.copy_(img, non_blocking=True)
-        host_cross.copy_(cross, non_blocking=True)
-
-    def timed(fn, clocks=None):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(st)
-            fn()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        clk = clocks.stop() if clocks else None
-        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
-
-    forms = {}
-    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm")):
-        plan.set_transform(xf)
-        for _ in range(max(args.warmup, 3)):
-            step()
-        torch.cuda.synchronize()
-        f_ms, f_clk = timed(step, Clocks(local))
-        f_kern, _ = timed(kernel_only)
-        f_e2e, _ = timed(e2e_step)
-        forms[name] = {"xform": xf, "ms_per_step": f_ms, "kernel_ms": f_kern, "e2e_ms": f_e2e, "clocks": f_clk}
-    units = A * T * C * P
-    cb, err = None, {}
-    if rank == 0:
-        # the oracle's four products on a bounded sample: the last 8 channels, all samples
-        n_s = min(C, 8)
-        c0, Ts = C - n_s, T
-        t0 = time.perf_counter()
-        M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
-        want = moff.moff_cross_image(M, wl.volt[:Ts, c0:], None, wl.n_grid, NP)
-        dt = time.perf_counter() - t0
-        sub = epic.Plan(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid, NP, n_s, 2,
-                        wl.vdtype, local)
-        xx, yy, xy = want[:, 0, 0].real, want[:, 1, 1].real, want[:, 0, 1]
-        for name, f in forms.items():
-            sub.set_transform(f["xform"])
-            got = sub.image_xpol(torch.from_numpy(np.ascontiguousarray(wl.volt_raw[:Ts, c0:])).to(dev))
-            gi, gc = got["image"].cpu().numpy(), got["cross"].cpu().numpy()
-            err[f["xform"]] = {
-                "XX": float(np.linalg.norm(gi[:, 0] - xx) / np.linalg.norm(xx)),
-                "YY": float(np.linalg.norm(gi[:, 1] - yy) / np.linalg.norm(yy)),
-                "XY_vs_sqrt_XX_YY": float(np.linalg.norm(gc - xy) / np.sqrt(np.linalg.norm(xx) * np.linalg.norm(yy)))}
-        sub.close()
-        if not args.no_cpu_baseline:
-            cb = {"value": A * Ts * 2 * n_s / dt, "unit": UNIT,
-                  "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
-                  "sample": "channels %d-%d, both pols, samples 0-%d (%d antenna-samples): FP64 gridding + "
-                            "separable DFT + the four products; %.2f s" % (c0, C - 1, Ts - 1, A * Ts * 2 * n_s, dt)}
-    # the chosen form: the fastest whose errors against the oracle meet the FP32 bound (1e-4)
-    ok = [k for k in forms if max(err.get(forms[k]["xform"], {"": 0.0}).values()) < 1e-4]
-    chosen = min(ok, key=lambda k: forms[k]["ms_per_step"])
-    f = forms[chosen]
-    if chosen == "fp16x3_dftgemm":
-        roof = tensor_roofline(DG_ALG_FLOP_PER_IMAGE * T * C * 4, DG_FLOP_PER_IMAGE * T * C * 4, f["kernel_ms"],
-                               f["clocks"], flop_basis="per virtual-pol image as the headline (pruned DFT as "
-                                                       "real products; executed: 3 FP16 products each), "
-                                                       "4 per channel-sample")
-    else:
-        flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * 4
-        roof = alu_roofline(flops, f["kernel_ms"], n_sm, f["clocks"],
-                            flop_basis="per virtual-pol image as the headline (5 N log2 N + 8 nnz + 4 N), "
-                                       "4 per channel-sample")
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    line = {"metric": METRIC, "value": job_throughput(units, world, f["ms_per_step"]), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": f["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16x3" if chosen == "fp16x3_dftgemm" else "f32", "data": "synthetic",
-            "config": {"workload": wl.name + ", four cross-polarisation products (epic_image_xpol)",
-                       "images_per_step": T * C * 4, "l2": "flushed (256 MB write) before every timed step",
-                       "chosen_transform": chosen},
-            "kernel_ms": f["kernel_ms"], "roofline": roof,
-            "e2e": {"value": job_throughput(units, world, f["e2e_ms"]), "unit": UNIT,
-                    "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
-                    "d2h_bytes_per_step": int(host_img.numel() * 4 + host_cross.numel() * 8)},
-            "gpu_launches": 2 * args.steps, "clocks": f["clocks"],
-            "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()},
-            "err_vs_oracle": {"relative_l2": err, "sample": "last 8 channels, all samples"}}
-    if cb is not None:
-        line["cpu_baseline"] = cb
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def _xeng_flops(n_ant, n_cp, n_time):
-    """Tensor-core FLOP the correlator executes: per (channel, pol) the upper triangle of
-    128 x 128 blocks, 2 real products (re, im) x 2 x 128 x 128 x (2 x 32 x chunks)."""
-    nab = (n_ant + 127) // 128
-    chunks = (n_time + 31) // 32
-    return n_cp * nab * (nab + 1) // 2 * 2 * 2.0 * 128 * 128 * 64 * chunks
-
-
-def run_fx(args):
-    """The FX route's X-engine on the headline workload: visibilities of all 256 x 256 antenna
-    pairs for 128 channels x 2 pols from 1024 samples (epic_correlate, tensor cores)."""
-    import numpy as np
-    import torch
-    from oracle import fx
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    wl = synth.workload_lwa(n_chan=args.channels)
-    plan = epic.Plan.from_workload(wl, device=local)
-    A, T, C, P = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol
-    volt = torch.from_numpy(wl.volt_raw).to(dev)
-    vis = torch.empty((C, P, A, A), dtype=torch.complex64, device=dev)
-    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
-    host_vis = torch.empty(vis.shape, dtype=torch.complex64).pin_memory()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream(dev)
-
-    def step():
-        epic.epic_correlate(plan._h, volt.data_ptr(), T, None, vis.data_ptr(), st.cuda_stream)
-
-    def e2e_step():
-        volt.copy_(host_v, non_blocking=True)
-        step()
-        host_vis.copy_(vis, non_blocking=True)
-
-    def timed(fn, clocks=None):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(st)
-            fn()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        clk = clocks.stop() if clocks else None
-        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
-
-    fx_img = torch.empty((C, P, wl.n_pad, wl.n_pad), dtype=torch.float32, device=dev)
-
-    def fx_imaging():
-        epic.epic_fx_image(plan._h, vis.data_ptr(), fx_img.data_ptr(), st.cuda_stream)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    ms, clk = timed(step, Clocks(local))
-    e2e_ms, _ = timed(e2e_step)
-    for _ in range(2):
-        fx_imaging()
-    img_ms, _ = timed(fx_imaging)
-    units = A * T * C * P
-    flop = _xeng_flops(A, C * P, T)
-    peak = MEASURED["bf16_tflops"]
-    roof = {"bound": "tensor", "achieved": flop / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "traffic": None, "executed_flop": flop,
-            "unique_flop": 4.0 * A * (A + 1) * T * C * P,
-            "peak_basis": "measured dense bf16 burst GEMM (FP16 has the same nominal rate), of measured"}
-    roof["frac"] = roof["achieved"] / peak
-    cb, err = None, None
-    if rank == 0:
-        n_s = min(C, 32)
-        one = np.ones(A, dtype=np.complex128)
-        t0 = time.perf_counter()
-        want = [fx.visibilities(wl.volt[:, c, p, :], one) for c in range(C - n_s, C) for p in range(P)]
-        dt = time.perf_counter() - t0
-        got = vis[C - n_s:].cpu().numpy().reshape(n_s * P, A, A)
-        err = float(max(np.linalg.norm(g - w) / np.linalg.norm(w) for g, w in zip(got, want)))
-        if not args.no_cpu_baseline:
-            cb = {"value": A * T * n_s * P / dt, "unit": UNIT,
-                  "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
-                  "sample": "channels %d-%d, both pols, all %d samples (%d antenna-samples): FP64 V^T conj(V) "
-                            "(BLAS); %.2f s" % (C - n_s, C - 1, T, A * T * n_s * P, dt)}
-    line = {"metric": "FX correlator antenna-samples/s (visibilities of all pairs)", "value":
-            job_throughput(units, world, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f16 operands, f32 accumulation", "data": "synthetic",
-            "config": {"workload": wl.name + ", FX-route correlator (epic_correlate)",
-                       "pairs_per_cp": A * A, "l2": "flushed (256 MB write) before every timed step"},
-            "roofline": roof,
-            "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": UNIT,
-                    "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
-                    "d2h_bytes_per_step": int(host_vis.numel() * 8)},
-            "gpu_launches": args.steps, "clocks": clk,
-            "fx_imaging_ms_per_integration": img_ms, "fx_route_ms": ms + img_ms,
-            "err_vs_oracle": {"relative_l2_max": err, "sample": "last 32 channels, both pols"}}
-    if cb is not None:
-        line["cpu_baseline"] = cb
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def run_crossover(args):
-    """MOFF imaging (epic_image, FP32 FFT form) against the FX route's correlator
-    (epic_correlate) per (channel, pol, sample), over antenna counts on the LWA-like grid
-    (N_p = 128, Gaussian apertures, the 100 m x 110 m ellipse filled ever more densely).
-    Voltages are seeded random 4+4-bit bytes (the kernels' work does not depend on values).
-    The FX route's once-per-integration gridding and transform are not included."""
-    import numpy as np
-    import torch
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    C, P, T = 16, 2, 1024
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream(dev)
-    rng = np.random.default_rng(6)
-
-    def timed(fn):
-        for _ in range(max(args.warmup, 3)):
-            fn()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(st)
-            fn()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
-
-    rows = []
-    for A in (32, 64, 128, 256, 512, 1024, 2048, 4096):
-        lay = np.random.default_rng(A)
-        pos = synth.layout_ellipse(lay, A, 100.0, 110.0)
-        dx = synth.C_LIGHT / 80e6 / 2
-        kd, kw = synth.kernel_gaussian(1.5, dx / 4)
-        ptr, dxdy, w = synth.pack_kernels([(kd, kw)] * A)
-        origin = synth.centred_origin(pos, 4.5, dx, 64)
-        plan = epic.Plan(pos, ptr, dxdy, w, dx, origin, 64, 128, C, P, "ci4", local)
-        raw = torch.from_numpy(rng.integers(0, 256, (T, C, P, A), dtype=np.uint8)).to(dev)
-        acc = torch.empty((C, P, 128, 128), dtype=torch.float64, device=dev)
-        vis = torch.empty((C, P, A, A), dtype=torch.complex64, device=dev)
-        t_moff = timed(lambda: epic.epic_image(plan._h, raw.data_ptr(), T, None, acc.data_ptr(), None, 0, None,
-                                               None, st.cuda_stream))
-        t_fx = timed(lambda: epic.epic_correlate(plan._h, raw.data_ptr(), T, None, vis.data_ptr(), st.cuda_stream))
-        img = torch.empty((C, P, 128, 128), dtype=torch.float32, device=dev)
-        t_img = timed(lambda: epic.epic_fx_image(plan._h, vis.data_ptr(), img.data_ptr(), st.cuda_stream)) \
-            if A <= 1024 else None
-        n = C * P * T
-        rows.append({"antennas": A, "nnz": plan.info["nnz"], "moff_ns_per_sample": 1e6 * t_moff / n,
-                     "fx_correlator_ns_per_sample": 1e6 * t_fx / n, "fx_over_moff": t_fx / t_moff,
-                     "fx_imaging_ms_per_integration": t_img,
-                     "fx_route_over_moff": None if t_img is None else (t_fx + t_img) / t_moff})
-        plan.close()
-        del raw, acc, vis, img
-    cross = None
-    for r0, r1 in zip(rows, rows[1:]):
-        if r0["fx_over_moff"] < 1.0 <= r1["fx_over_moff"]:
-            # log-log interpolation of the antenna count where the two costs are equal
-            f = math.log(r0["fx_over_moff"]) / (math.log(r0["fx_over_moff"]) - math.log(r1["fx_over_moff"]))
-            cross = r0["antennas"] * (r1["antennas"] / r0["antennas"]) ** f
-    line = {"metric": "MOFF vs FX-correlator time per (channel, pol, sample)", "value": cross,
-            "unit": "antennas at equal cost (N_p = 128 grid)", "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "higher_is_better": None, "data": "synthetic (random 4+4-bit bytes)",
-            "config": {"workload": "LWA-like ellipse 100 m x 110 m, Gaussian sigma 1.5 m apertures, N_g 64, "
-                                   "N_p 128, 16 channels x 2 pols x 1024 samples per call",
-                       "fx_scope": "value and fx_over_moff: correlator only; fx_route_over_moff adds the FX "
-                                   "imaging of the integration (1024 samples; measured up to 1024 antennas)"},
-            "fx_over_moff_at_largest": rows[-1]["fx_over_moff"], "table": rows}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def run_fengine(args):
-    """The F-engine on the headline shapes: 256 antennas x 2 pols x 1024 spectra of 128
-    channels from 4+4-bit time samples (seeded random bytes), written as FP16 spectra, then
-    imaged (epic_image, FP16 plan).  Roofline of the F-engine: HBM bytes (samples read once,
-    spectra written once) against the measured copy bandwidth."""
-    import numpy as np
-    import torch
-    from oracle import moff
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    wl = synth.workload_lwa(n_chan=1, n_time=2, chan_index=[0])
-    A, P, C, T = wl.n_ant, 2, 128, 1024
-    rng = np.random.default_rng(11)
-    raw_h = rng.integers(0, 256, (T * C, P, A), dtype=np.uint8)
-    raw = torch.from_numpy(raw_h).to(dev)
-    spec = torch.empty((T, C, P, A, 2), dtype=torch.float16, device=dev)
-    plan = epic.Plan(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid, wl.n_pad, C, P,
-                     "f16", local)
-    acc = torch.empty((C, P, wl.n_pad, wl.n_pad), dtype=torch.float64, device=dev)
-    img = torch.empty((C, P, wl.n_pad, wl.n_pad), dtype=torch.float32, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream(dev)
-
-    def feng():
-        epic.epic_fengine(A, P, C, T, 2, raw.data_ptr(), 1, spec.data_ptr(), local, st.cuda_stream)
-
-    def chain():
-        feng()
-        epic.epic_image(plan._h, spec.data_ptr(), T, None, acc.data_ptr(), None, 0, img.data_ptr(), None,
-                        st.cuda_stream)
-
-    def timed(fn, clocks=None):
-        for _ in range(max(args.warmup, 3)):
-            fn()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        if clocks:
-            clocks.start()
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(st)
-            fn()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        clk = clocks.stop() if clocks else None
-        return sum(a.elapsed_time(b) for a, b in ev) / args.steps, clk
-
-    f_ms, clk = timed(feng, Clocks(local))
-    c_ms, _ = timed(chain)
-    nbytes = raw.numel() + spec.numel() * 2
-    peak = MEASURED["hbm_gbs"]
-    roof = {"bound": "hbm", "achieved": nbytes / (f_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s", "traffic": None,
-            "algorithmic_bytes": nbytes, "peak_basis": "measured STREAM-style copy (read + write bytes), of measured"}
-    roof["frac"] = roof["achieved"] / peak
-    err = None
-    if rank == 0:
-        # oracle spectra of 2 spectra x all channels, pol 1, against the FP16 output
-        want = moff.fengine(synth.decode_ci4(raw_h[:2 * C]), C)[:, :, 1]
-        got = spec[:2, :, 1].float().cpu().numpy()
-        got = got[..., 0] + 1j * got[..., 1]
-        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
-    units = A * T * C * P
-    line = {"metric": METRIC, "value": units / (c_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": c_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (FP16 spectra)", "data": "synthetic (random 4+4-bit time samples)",
-            "config": {"workload": "F-engine + imaging: 256 antennas, 2 pols, 1024 spectra x 128 channels from "
-                                   "4+4-bit time samples, FP16 spectra, LWA-like layout, 128x128 image",
-                       "l2": "flushed (256 MB write) before every timed step"},
-            "fengine_ms": f_ms, "imaging_ms": c_ms - f_ms, "roofline": roof, "gpu_launches": 3 * args.steps,
-            "clocks": clk, "err_vs_oracle": {"fengine_fp16_relative_l2": err, "sample": "2 spectra, pol 1"}}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "batch":
-        return run_batch(args)
-    if args.workload == "calib":
-        return run_calib(args)
-    if args.workload == "grid":
-        return run_grid(args)
-    if args.workload == "xpol":
-        return run_xpol(args)
-    if args.workload == "fx":
-        return run_fx(args)
-    if args.workload == "crossover":
-        return run_crossover(args)
-    if args.workload == "fengine":
-        return run_fengine(args)
-    if args.workload == "hera":
-        return run_hera(args)
-    import numpy as np
-    import torch
-    from paper_1510_08318_gb300 import build, epic, synth
-
-    world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    epic.load()
-
-    wl = synth.workload_lwa(n_chan=args.channels)
-    plan = epic.Plan.from_workload(wl, device=local)
-    A, T, C, P, NP = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_pad
-    volt = torch.from_numpy(wl.volt_raw).to(dev)
-    accum = torch.empty((C, P, NP, NP), dtype=torch.float64, device=dev)
-    power = torch.empty((C, P, A), dtype=torch.float64, device=dev)
-    image = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
-    autoc = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
-    host_img = torch.empty((C, P, NP, NP), dtype=torch.float32).pin_memory()
-    st = torch.cuda.current_stream(dev)
-    h = plan._h
-    units = A * T * C * P
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-
-    def step():
-        epic.epic_image(h, volt.data_ptr(), T, None, accum.data_ptr(), power.data_ptr(), 0,
-                        image.data_ptr(), autoc.data_ptr(), st.cuda_stream)
-
-    def kernel_only():
-        epic.epic_image(h, volt.data_ptr(), T, None, accum.data_ptr(), None, 0, None, None, st.cuda_stream)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    volt2 = torch.empty_like(volt)
-    image2 = torch.empty_like(image)
-    host_img2 = torch.empty((C, P, NP, NP), dtype=torch.float32).pin_memory()
-    cs = torch.cuda.Stream(dev)     # host -> device copies
-    ds = torch.cuda.Stream(dev)     # device -> host reads
-
-    def timed_stream():
-        """End to end through the C ABI, as a stream of integrations: step k's voltages are
-        copied from pinned host memory into one of two device buffers while step k-1 images, and
-        its image is read back into pinned host memory (from one of two image buffers) while step
-        k+1 images.  Every copy of every step lies between the two events; L2 is flushed before
-        each imaging call.  Returns the mean ms per step."""
-        vin, img, hout = (volt, volt2), (image, image2), (host_img, host_img2)
-        ev_in = [torch.cuda.Event() for _ in range(2)]     # inputs of buffer b are on the device
-        ev_done = [torch.cuda.Event() for _ in range(2)]   # imaging from buffer b has finished
-        ev_read = [torch.cuda.Event() for _ in range(2)]   # image buffer b has been read back
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        torch.cuda.synchronize()
-        t0.record(st)
-        cs.wait_event(t0)
-        ds.wait_event(t0)
-        for k in range(args.steps):
-            b = k & 1
-            if k >= 2:
-                cs.wait_event(ev_done[b])
-            with torch.cuda.stream(cs):
-                vin[b].copy_(host_v, non_blocking=True)
-            ev_in[b].record(cs)
-            st.wait_event(ev_in[b])
-            if k >= 2:
-                st.wait_event(ev_read[b])
-            flush.zero_()
-            epic.epic_image(h, vin[b].data_ptr(), T, None, accum.data_ptr(), power.data_ptr(), 0,
-                            img[b].data_ptr(), autoc.data_ptr(), st.cuda_stream)
-            ev_done[b].record(st)
-            ds.wait_event(ev_done[b])
-            with torch.cuda.stream(ds):
-                hout[b].copy_(img[b], non_blocking=True)
-            ev_read[b].record(ds)
-        st.wait_stream(cs)
-        st.wait_stream(ds)
-        t1.record(st)
-        torch.cuda.synchronize()
-        barrier()
-        return max_over_ranks([t0.elapsed_time(t1) / args.steps], world, dev)[0]
-
-    def timed(fn, clocks=None):
-        """Mean device time (ms) of fn over the timed steps, L2 flushed before each."""
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        barrier()
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(st)
-            fn()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        barrier()
-        clk = clocks.stop() if clocks else None
-        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-        return max_over_ranks([ms], world, dev)[0], clk
-
-    forms = {}
-    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm")):
-        plan.set_transform(xf)
-        for _ in range(max(args.warmup, 3)):
-            step()
-        torch.cuda.synchronize()
-        step_ms, clk = timed(step, Clocks(local))
-        kern_ms, _ = timed(kernel_only)
-        e2e_ms = timed_stream()
-        forms[name] = {"xform": xf, "ms_per_step": step_ms, "kernel_ms": kern_ms, "e2e_ms": e2e_ms,
-                       "value": job_throughput(units, world, step_ms), "clocks": clk}
-
-    err = {}
-    cb = None
-    cfb = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.channels == 128:
-        cb, err = cpu_baseline_sample(wl, plan, torch, n_chan=32, n_time=1024)
-        cfb = cpu_fft_sample(wl, n_chan=32, n_time=1024)
-    # the chosen form: the fastest whose error against the oracle meets the FP32 bound (1e-4)
-    fft_flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * P
-    ok = [k for k in forms if err.get(forms[k]["xform"], 0.0) < 1e-4]
-    chosen = min(ok, key=lambda k: forms[k]["ms_per_step"])
-    f = forms[chosen]
-    if chosen == "fp16x3_dftgemm":
-        peak = MEASURED["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": DG_FLOP_PER_IMAGE * T * C * P / (f["kernel_ms"] / 1e3) / 1e12,
-                "peak": peak,
-                "unit": "TFLOP/s", "traffic": DG_TRAFFIC_BYTES,
-                "peak_basis": "measured dense bf16 burst GEMM (FP16 has the same nominal rate), of measured"}
-    else:
-        roof = alu_roofline(fft_flops, f["kernel_ms"], n_sm, f["clocks"], traffic=FWD_TRAFFIC_BYTES)
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    # the plain FP32 form's own roofline, whichever form is chosen
-    fft_roof = alu_roofline(fft_flops, forms["fp32_fft"]["kernel_ms"], n_sm, forms["fp32_fft"]["clocks"],
-                            traffic=FWD_TRAFFIC_BYTES)
-    line = {
-        "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f16x3" if chosen == "fp16x3_dftgemm" else "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "antennas": A, "time_samples": T, "channels": C, "pols": P,
-                   "grid": "%dx%d padded to %dx%d" % (wl.n_grid, wl.n_grid, NP, NP), "voltages": "ci4",
-                   "images_per_step": T * C * P, "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": "independent replicas per GPU" if world > 1 else "1 GPU",
-                   "chosen_transform": chosen},
-        "images_per_s": world * T * C * P / (f["ms_per_step"] / 1e3),
-        "kernel_ms": f["kernel_ms"],
-        "roofline": roof,
-        "e2e": {"value": job_throughput(units, world, f["e2e_ms"]), "unit": UNIT,
-                "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
-                "d2h_bytes_per_step": int(host_img.numel() * host_img.element_size()),
-                "mode": "stream of integrations: each step's host-to-device copy overlaps the previous "
-                        "step's imaging and its image read-back the next one's (two buffers each); "
-                        "all copies inside the timed region, L2 flushed per step"},
-        "gpu_launches": 3 * args.steps,
-        "clocks": f["clocks"],
-        "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()},
-        "plain_fp32": {"value": forms["fp32_fft"]["value"], "ms_per_step": forms["fp32_fft"]["ms_per_step"],
-                       "roofline": fft_roof},
-    }
-    if cb is not None:
-        line["cpu_baseline"] = cb
         line["err_vs_oracle"] = {"relative_l2": err, "sample": "channels 96-127, pol 1, all 1024 samples, image"}
     if cfb is not None:
         line["cpu_fft_baseline"] = cfb

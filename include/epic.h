@@ -23,8 +23,11 @@
  *     pixel (iy, ix) is direction (l, m) = ((ix - N_p/2), (iy - N_p/2)) * lambda / (N_p dx).
  *   - Every call returns an epic_status and never aborts; on failure epic_last_error()
  *     returns a thread-local message.  Arguments are validated on the host before any
- *     launch.  Calls are asynchronous on the caller's stream; a CUDA error raised by a
- *     launch is reported as EPIC_ECUDA.
+ *     launch, including the alignment of every device array to its element: voltages to
+ *     their sample size (8, 4 or 1 bytes), complex64 and float64 arrays to 8 bytes, float32
+ *     arrays to 4 (a misaligned array, e.g. a view at an odd offset, is EPIC_EINVAL).  Calls
+ *     are asynchronous on the caller's stream; a CUDA error raised by a launch is reported as
+ *     EPIC_ECUDA.
  */
 #ifndef EPIC_H
 #define EPIC_H
@@ -42,7 +45,10 @@ typedef enum {
     EPIC_EINVAL = 1,        /* invalid argument (message says which) */
     EPIC_ENOMEM = 2,        /* the plan's device tables could not be allocated */
     EPIC_ECUDA = 3,         /* a CUDA runtime call or launch failed */
-    EPIC_EUNSUPPORTED = 4   /* valid, but outside what this library implements */
+    EPIC_EUNSUPPORTED = 4,  /* valid, but outside what this library implements */
+    EPIC_ETIMEOUT = 5       /* a kernel's bounded wait on the tensor cores ran out (reported by
+                               epic_sync; the outputs of the calls since the last epic_sync are
+                               undefined) */
 } epic_status;
 
 typedef enum {
@@ -107,6 +113,28 @@ epic_status epic_set_transform(epic_plan *plan, int xform);
 
 /* Release the plan and its device tables.  NULL is accepted. */
 void epic_destroy(epic_plan *plan);
+
+/*
+ * epic_sync -- wait for the work enqueued on stream and report what the plan's kernels found on
+ * the device.  The kernels that hand operands to the tensor cores (epic_image and
+ * epic_image_xpol in the EPIC_XFORM_DFTGEMM form, epic_correlate) wait on the tensor pipe with
+ * bounded waits; a wait that runs out sets a bit in the plan's device status word (the kernel
+ * then waits, with its full limit, for the products still in flight, releases its tensor memory
+ * and returns, marking its first output block with NaN).  This call synchronises the stream,
+ * reads the word, clears it and returns EPIC_ETIMEOUT if any bit was set (the message names the
+ * kernel), EPIC_ECUDA if the stream reported an error, else EPIC_OK.  The imaging calls
+ * themselves stay asynchronous.  Not meant for use inside a stream capture.
+ */
+epic_status epic_sync(const epic_plan *plan, void *stream);
+
+/*
+ * epic_set_wait_limit -- tries of each bounded wait of the plan's tensor-core pipelines (each try
+ * suspends the waiting thread for up to about 1 ms; default 1000, so a wait gives up after about
+ * a second).  0 to 1000000; with 0 every such wait reports a timeout at its first check, which
+ * exercises the failure path above without a fault (the waits that drain the products in flight
+ * always use the full limit).  Applies to calls enqueued after it.
+ */
+epic_status epic_set_wait_limit(epic_plan *plan, int tries);
 
 /*
  * epic_image -- the MOFF imaging step (Eq. "dirty-image-MOFF") for one block of samples.

@@ -34,6 +34,15 @@ epic_status epic_cuda_fail(cudaError_t e, const char* what) {
     return epic_fail(EPIC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+epic_status epic_check_alignment(std::initializer_list<EpicAlign> arrays) {
+    for (const EpicAlign& x : arrays)
+        if (x.ptr && reinterpret_cast<uintptr_t>(x.ptr) % x.bytes != 0)
+            return epic_fail(EPIC_EINVAL, "%s must be %zu-byte aligned", x.name, x.bytes);
+    return EPIC_OK;
+}
+
+size_t epic_volt_bytes(int vdt) { return vdt == EPIC_VOLT_C64 ? 8 : vdt == EPIC_VOLT_F16 ? 4 : 1; }
+
 namespace {
 
 void free_plan(epic_plan* p) {
@@ -59,6 +68,7 @@ void free_plan(epic_plan* p) {
     cudaFree(p->dg_wre);
     cudaFree(p->dg_wim);
     cudaFree(p->dg_ant);
+    cudaFree(p->status);
     delete p;
 }
 
@@ -125,6 +135,8 @@ epic::FwdArgs epic_plan_fwd_args(const epic_plan* plan, const void* volt, int n_
     a.n_items = (long long)a.n_cp * n_time;
     a.flush_every = 1024;
     a.wsum_max = plan->wsum_max;
+    a.status = plan->status;
+    a.wait_tries = plan->wait_tries;
     return a;
 }
 
@@ -424,8 +436,39 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
                                               : epic_cuda_fail(e, "plan upload");
     }
+    if ((e = upload(&p->status, std::vector<int>(1, 0))) != cudaSuccess) {
+        free_plan(p);
+        return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "status word: %s", cudaGetErrorString(e))
+                                              : epic_cuda_fail(e, "status word");
+    }
     *plan = p;
     return EPIC_OK;
+}
+
+epic_status epic_set_wait_limit(epic_plan* plan, int tries) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    if (tries < 0 || tries > 1000000) return epic_fail(EPIC_EINVAL, "tries = %d outside 0..1000000", tries);
+    plan->wait_tries = tries;
+    return EPIC_OK;
+}
+
+epic_status epic_sync(const epic_plan* plan, void* stream) {
+    epic_clear_error();
+    if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
+    EpicDeviceGuard guard(plan->device);
+    if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return epic_cuda_fail(e, "stream synchronize");
+    int word = 0;
+    if ((e = cudaMemcpy(&word, plan->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return epic_cuda_fail(e, "status word read");
+    if (word == 0) return EPIC_OK;
+    if ((e = cudaMemset(plan->status, 0, sizeof(int))) != cudaSuccess) return epic_cuda_fail(e, "status word clear");
+    return epic_fail(EPIC_ETIMEOUT, "a bounded wait on the tensor cores ran out in the %s%s%s (its outputs are undefined)",
+                     (word & epic::kStatusImageTimeout) ? "tensor-core imaging kernel" : "",
+                     (word & epic::kStatusImageTimeout) && (word & epic::kStatusCorrelateTimeout) ? " and the " : "",
+                     (word & epic::kStatusCorrelateTimeout) ? "correlator" : "");
 }
 
 epic_status epic_set_transform(epic_plan* plan, int xform) {
@@ -487,6 +530,12 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
     if (autocorr && !power) return epic_fail(EPIC_EINVAL, "autocorr needs the power accumulator");
     if (autocorr && plan->lag_side == 0)
         return epic_fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
+    {
+        const epic_status al = epic_check_alignment({{"volt", volt, epic_volt_bytes(plan->vdt)}, {"gains", gains, 8},
+                                                     {"accum", accum, 8}, {"power", power, 8}, {"image", image, 4},
+                                                     {"autocorr", autocorr, 4}});
+        if (al != EPIC_OK) return al;
+    }
     if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
         return epic_fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
     EpicDeviceGuard guard(plan->device);
@@ -526,6 +575,11 @@ epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_t
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
     if (!volt || !grad_image || !grad_gains) return epic_fail(EPIC_EINVAL, "NULL device array");
+    {
+        const epic_status al = epic_check_alignment({{"volt", volt, epic_volt_bytes(plan->vdt)}, {"gains", gains, 8},
+                                                     {"grad_image", grad_image, 4}, {"grad_gains", grad_gains, 8}});
+        if (al != EPIC_OK) return al;
+    }
     if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
         return epic_fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
     EpicDeviceGuard guard(plan->device);
@@ -566,6 +620,11 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     if (plan->n_pol != 2) return epic_fail(EPIC_EINVAL, "cross-polarisation images need a plan with 2 pols (has %d)", plan->n_pol);
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
     if (!volt || !accum4) return epic_fail(EPIC_EINVAL, "NULL device array");
+    {
+        const epic_status al = epic_check_alignment({{"volt", volt, epic_volt_bytes(plan->vdt)}, {"gains", gains, 8},
+                                                     {"accum4", accum4, 8}, {"image", image, 4}, {"cross", cross, 8}});
+        if (al != EPIC_OK) return al;
+    }
     if (t_prev < 0) return epic_fail(EPIC_EINVAL, "t_prev must be >= 0");
     if ((long long)plan->n_chan * 4 * n_time > 2147483647LL)
         return epic_fail(EPIC_EUNSUPPORTED, "4 * C * T must stay below 2^31 per call");
@@ -612,6 +671,11 @@ epic_status epic_fengine(int n_ant, int n_pol, int n_chan, int n_time, int in_dt
         return epic_fail(EPIC_EINVAL, "out_dtype %d (complex64 or FP16 pairs)", out_dtype);
     if (n_time == 0) return EPIC_OK;
     if (!raw || !volt) return epic_fail(EPIC_EINVAL, "NULL device array");
+    {
+        const epic_status al = epic_check_alignment({{"raw", raw, epic_volt_bytes(in_dtype)},
+                                                     {"volt", volt, epic_volt_bytes(out_dtype)}});
+        if (al != EPIC_OK) return al;
+    }
     EpicDeviceGuard guard(device);
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", device);
     int n_sm = 0;
@@ -632,6 +696,7 @@ epic_status epic_weff(const epic_plan* plan, float* weff, void* stream) {
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (!weff) return epic_fail(EPIC_EINVAL, "weff is NULL");
+    if (epic_check_alignment({{"weff", weff, 4}}) != EPIC_OK) return EPIC_EINVAL;
     if (plan->n_ant < 2) return epic_fail(EPIC_EINVAL, "the effective weighting needs at least two antennas");
     if (plan->lag_side == 0)
         return epic_fail(EPIC_EUNSUPPORTED, "footprints too wide for the auto-correlation tables");
@@ -651,6 +716,11 @@ epic_status epic_isotropic(const epic_plan* plan, const float* image, const floa
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (!image || !autocorr || !weff || !iso) return epic_fail(EPIC_EINVAL, "NULL device array");
+    {
+        const epic_status al = epic_check_alignment({{"image", image, 4}, {"autocorr", autocorr, 4},
+                                                     {"weff", weff, 4}, {"iso", iso, 4}});
+        if (al != EPIC_OK) return al;
+    }
     if (plan->n_ant < 2) return epic_fail(EPIC_EINVAL, "the isotropic estimate needs at least two antennas");
     if (!(rel_floor >= 0.f) || !(rel_floor < 1.f)) return epic_fail(EPIC_EINVAL, "rel_floor must be in [0, 1)");
     EpicDeviceGuard guard(plan->device);
@@ -668,7 +738,11 @@ epic_status epic_correlate(const epic_plan* plan, const void* volt, int n_time, 
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
     if (!volt || !vis) return epic_fail(EPIC_EINVAL, "NULL device array");
-    if (reinterpret_cast<uintptr_t>(vis) % 8 != 0) return epic_fail(EPIC_EINVAL, "vis must be 8-byte aligned");
+    {
+        const epic_status al = epic_check_alignment({{"volt", volt, epic_volt_bytes(plan->vdt)}, {"gains", gains, 8},
+                                                     {"vis", vis, 8}});
+        if (al != EPIC_OK) return al;
+    }
     if (plan->vdt == EPIC_VOLT_C64)
         return epic_fail(EPIC_EUNSUPPORTED, "the correlator takes FP16 or 4+4-bit voltages (exact FP16 operands)");
     if (n_time > 131072) return epic_fail(EPIC_EUNSUPPORTED, "n_time = %d: at most 131072 samples per call", n_time);
@@ -684,6 +758,8 @@ epic_status epic_correlate(const epic_plan* plan, const void* volt, int n_time, 
     a.n_ant = plan->n_ant;
     a.gains = reinterpret_cast<const float2*>(gains);
     a.vis = reinterpret_cast<float2*>(vis);
+    a.status = plan->status;
+    a.wait_tries = plan->wait_tries;
     const cudaError_t e = epic::launch_xeng(plan->vdt, a, plan->n_sm, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "correlator kernel launch");
 }
@@ -692,6 +768,10 @@ epic_status epic_fx_image(const epic_plan* plan, const float* vis, float* image,
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (!vis || !image) return epic_fail(EPIC_EINVAL, "NULL device array");
+    {
+        const epic_status al = epic_check_alignment({{"vis", vis, 8}, {"image", image, 4}});
+        if (al != EPIC_OK) return al;
+    }
     if (plan->n_pad > 128 || !plan->fx_ptr)
         return epic_fail(EPIC_EUNSUPPORTED, "the FX imaging kernel holds the lag plane in shared memory: n_pad <= 128");
     EpicDeviceGuard guard(plan->device);
@@ -714,7 +794,11 @@ epic_status epic_grid(const epic_plan* plan, const void* volt, int n_time, const
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
     if (!volt || !grid) return epic_fail(EPIC_EINVAL, "NULL device array");
-    if (reinterpret_cast<uintptr_t>(grid) % 8 != 0) return epic_fail(EPIC_EINVAL, "grid must be 8-byte aligned");
+    {
+        const epic_status al = epic_check_alignment({{"volt", volt, epic_volt_bytes(plan->vdt)}, {"gains", gains, 8},
+                                                     {"grid", grid, 8}});
+        if (al != EPIC_OK) return al;
+    }
     if ((long long)plan->n_chan * plan->n_pol * n_time > 2147483647LL)
         return epic_fail(EPIC_EUNSUPPORTED, "C * P * T must stay below 2^31 per call");
     EpicDeviceGuard guard(plan->device);

@@ -44,11 +44,20 @@ void destroy_batch(epic_batch* b) {
     delete b;
 }
 
-epic_status check_call(const epic_batch* b, const void* const* volt, const int* n_time, double* const* accum) {
+epic_status check_call(const epic_batch* b, const void* const* volt, const int* n_time, const float* const* gains,
+                       double* const* accum, float* const* image) {
     if (!b) return epic_fail(EPIC_EINVAL, "batch is NULL");
     if (!volt || !n_time || !accum) return epic_fail(EPIC_EINVAL, "NULL argument array");
     for (size_t i = 0; i < b->plans.size(); ++i) {
         if (!volt[i] || !accum[i]) return epic_fail(EPIC_EINVAL, "NULL device array for plan %zu", i);
+        const epic_status al = epic_check_alignment({{"volt", volt[i], epic_volt_bytes(b->vdt)},
+                                                     {"gains", gains ? gains[i] : nullptr, 8},
+                                                     {"accum", accum[i], 8},
+                                                     {"image", image ? image[i] : nullptr, 4}});
+        if (al != EPIC_OK) {
+            const std::string why = epic_last_error();
+            return epic_fail(EPIC_EINVAL, "plan %zu: %s", i, why.c_str());
+        }
         if (n_time[i] < 1) return epic_fail(EPIC_EINVAL, "n_time[%zu] = %d must be >= 1", i, n_time[i]);
         const long long items = (long long)b->plans[i]->n_chan * b->plans[i]->n_pol * n_time[i];
         if (items > 2147483647LL) return epic_fail(EPIC_EUNSUPPORTED, "plan %zu: C * P * T must stay below 2^31", i);
@@ -111,14 +120,27 @@ epic_status enqueue(epic_batch* b, const void* const* volt, const int* n_time, c
     }
     cudaError_t e = cudaEventRecord(b->fork, st);
     if (e != cudaSuccess) return epic_cuda_fail(e, "fork event");
+    // every class stream that waited on the fork is joined back into st, also when a later step
+    // fails, so that a stream capture of this call never ends with a stream left unjoined
+    epic_status s = EPIC_OK;
     for (ClassRun& c : b->classes) {
-        if ((e = cudaStreamWaitEvent(c.stream, b->fork, 0)) != cudaSuccess) return epic_cuda_fail(e, "fork wait");
-        epic_status s = run_class(b, c, volt, n_time, gains, accum, image, c.stream, c.max_workers);
-        if (s != EPIC_OK) return s;
-        if ((e = cudaEventRecord(c.join, c.stream)) != cudaSuccess) return epic_cuda_fail(e, "join event");
-        if ((e = cudaStreamWaitEvent(st, c.join, 0)) != cudaSuccess) return epic_cuda_fail(e, "join wait");
+        if ((e = cudaStreamWaitEvent(c.stream, b->fork, 0)) != cudaSuccess) {
+            s = epic_cuda_fail(e, "fork wait");
+            break;
+        }
+        epic_status r = run_class(b, c, volt, n_time, gains, accum, image, c.stream, c.max_workers);
+        cudaError_t ej = cudaEventRecord(c.join, c.stream);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, c.join, 0);
+        if (r != EPIC_OK) {
+            s = r;
+            break;
+        }
+        if (ej != cudaSuccess) {
+            s = epic_cuda_fail(ej, "join");
+            break;
+        }
     }
-    return EPIC_OK;
+    return s;
 }
 
 }  // namespace
@@ -174,7 +196,7 @@ void epic_batch_destroy(epic_batch* batch) {
 epic_status epic_batch_image(epic_batch* batch, const void* const* volt, const int* n_time, const float* const* gains,
                              double* const* accum, float* const* image, void* stream) {
     epic_clear_error();
-    epic_status s = check_call(batch, volt, n_time, accum);
+    epic_status s = check_call(batch, volt, n_time, gains, accum, image);
     if (s != EPIC_OK) return s;
     EpicDeviceGuard guard(batch->device);
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", batch->device);
@@ -184,15 +206,23 @@ epic_status epic_batch_image(epic_batch* batch, const void* const* volt, const i
 epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, const int* n_time,
                                 const float* const* gains, double* const* accum, void* stream) {
     epic_clear_error();
-    epic_status s = check_call(batch, volt, n_time, accum);
+    epic_status s = check_call(batch, volt, n_time, gains, accum, nullptr);
     if (s != EPIC_OK) return s;
     EpicDeviceGuard guard(batch->device);
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", batch->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaEvent_t e0, e1;
-    cudaError_t e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // timing events, destroyed on every way out of this call
+    struct Events {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Events() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } ev;
+    cudaError_t e = cudaEventCreate(&ev.e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev.e1);
     if (e != cudaSuccess) return epic_cuda_fail(e, "autotune events");
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     auto time_it = [&](auto&& body, float& ms) -> epic_status {
         float best = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -240,8 +270,6 @@ epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, cons
         }
         if (s == EPIC_OK) batch->concurrent = t_con < t_seq;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return s;
 }
 

@@ -28,7 +28,15 @@ struct FwdArgs {
     long long n_items;         // CP * T
     int flush_every;           // samples per float32 partial before a float64 flush
     float wsum_max;            // max over cells of sum_a |M[g, a]| (scales the FP16 operands)
+    int* status;               // device status word of the plan (kernels with bounded waits OR in
+                               // kStatus* bits when a wait runs out), or nullptr
+    int wait_tries;            // tries of each bounded wait of the pipeline (about 1 ms each)
 };
+
+// Bits of a plan's device status word, set by a kernel whose bounded wait on the tensor cores
+// ran out (the call's outputs are then undefined); read and cleared by epic_sync.
+constexpr int kStatusImageTimeout = 1;       // tensor-core imaging kernel
+constexpr int kStatusCorrelateTimeout = 2;   // X-engine
 
 // Sub-array calls imaged by one persistent forward launch (same N_p and voltage format);
 // a single epic_image call is a one-entry list.  Passed by value as a kernel parameter.
@@ -83,6 +91,8 @@ struct XengArgs {
     int n_time, n_cp, n_ant;
     const float2* gains;       // [CP][A] or nullptr (unit gains)
     float2* vis;               // [CP][A][A]
+    int* status;               // the plan's device status word, or nullptr
+    int wait_tries;            // tries of each bounded wait of the pipeline
 };
 size_t xeng_smem_bytes();
 // FX route's imaging of visibilities (xeng.cu), N_p <= 128

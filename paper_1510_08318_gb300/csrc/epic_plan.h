@@ -1,6 +1,8 @@
 // The plan object and host helpers shared by the C ABI translation units.
 #pragma once
+#include <cstddef>
 #include <cstdint>
+#include <initializer_list>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -34,7 +36,20 @@ struct epic_plan {
     float* dg_wim = nullptr;
     uint16_t* dg_ant = nullptr;
     float wsum_max = 0.f;         // max over cells of sum_a |M[g, a]|
+    int* status = nullptr;        // device status word (epic::kStatus* bits), read by epic_sync
+    int wait_tries = 1000;        // tries of each bounded tensor-core wait (about 1 ms each)
 };
+
+// Alignment a device array needs for the kernels' element (or vector) accesses.
+struct EpicAlign {
+    const char* name;
+    const void* ptr;      // nullptr (an omitted optional array) passes
+    size_t bytes;
+};
+// EPIC_EINVAL naming the first misaligned array, else EPIC_OK (checked before any launch).
+epic_status epic_check_alignment(std::initializer_list<EpicAlign> arrays);
+// Bytes of one voltage sample of a format (complex64 8, FP16 pair 4, 4+4-bit 1).
+size_t epic_volt_bytes(int vdt);
 
 // Thread-local error message of the C ABI.
 void epic_clear_error();

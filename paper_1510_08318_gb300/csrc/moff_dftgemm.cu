@@ -44,8 +44,9 @@
 // slowest warp at the heaviest slot); each cell's entries are still summed in cell-major order.
 // Entries are an FP32 weight and a 16-bit antenna index; the tables sit in shared memory when
 // they fit beside the operand tables, else they are read through L1.
-// Every wait on the tensor cores is bounded; on a timeout the CTA writes NaN into its
-// accumulator block and stops.
+// Every wait on the tensor cores is bounded (the pipeline's waits by the plan's try count); on a
+// timeout the CTA sets the image-timeout bit of the plan's status word, writes NaN into its
+// accumulator block, waits with the full limit for the MMAs in flight and stops.
 #include <cuda_fp16.h>
 #include <algorithm>
 #include <cmath>
@@ -442,18 +443,20 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         ++issued1;
         if (tid == 0) vmax[0] = 0u;
     }
+    // a wait that runs out sets `failed` for the whole warp (the TMEM passes after it are
+    // warp-collective and are skipped), then for the whole CTA at the next barrier
     for (int i = 0; i < n; ++i) {
         if (worker) {
             if (i + 1 < n) sc_next = grid(i + 1);
             if (i >= 1) {
-                if (!mbar_wait(mb2, (i - 1) & 1)) failed = true;
+                failed = __any_sync(0xffffffffu, failed || !mbar_wait(mb2, (i - 1) & 1, a.wait_tries)) != 0;
                 fence_after();
-                epilogue(i - 1, sc_prev);
+                if (!failed) epilogue(i - 1, sc_prev);
             }
             if (i + 2 < n) decode(i + 2);
-            if (!mbar_wait(mb1, i & 1)) failed = true;
+            failed = __any_sync(0xffffffffu, failed || !mbar_wait(mb1, i & 1, a.wait_tries)) != 0;
             fence_after();
-            split();
+            if (!failed) split();
         }
         fence_before();
         failed = __syncthreads_or(failed) != 0;   // uniform across the CTA
@@ -470,15 +473,20 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         sc_cur = sc_next;
     }
     if (!failed && n > 0 && worker) {
-        if (!mbar_wait(mb2, (n - 1) & 1)) failed = true;
+        failed = __any_sync(0xffffffffu, !mbar_wait(mb2, (n - 1) & 1, a.wait_tries)) != 0;
         fence_after();
         if (!failed) epilogue(n - 1, sc_prev);
         flush_power((beg + n - 1) / T);
     }
+    failed = __syncthreads_or(failed) != 0;
     if (failed) {
-        // a tensor-core wait ran out: mark this CTA's first (channel, pol) block with NaN,
-        // wait (bounded) for the last batches still in flight, and stop
-        if (n > 0 && tid == 0) a.accum[(size_t)(beg / T) * NP * NP] = __longlong_as_double(0x7ff8000000000000LL);
+        // a tensor-core wait ran out: report it in the plan's status word, mark this CTA's first
+        // (channel, pol) block with NaN, wait (bounded, with the full limit) for the batches
+        // still in flight, so that no MMA writes the tensor memory after it is released, and stop
+        if (n > 0 && tid == 0) {
+            if (a.status) atomicOr(a.status, kStatusImageTimeout);
+            a.accum[(size_t)(beg / T) * NP * NP] = __longlong_as_double(0x7ff8000000000000LL);
+        }
         if (issued1 > 0) mbar_wait(mb1, (issued1 - 1) & 1);
         if (issued2 > 0) mbar_wait(mb2, (issued2 - 1) & 1);
     }

@@ -43,11 +43,14 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Tries of a bounded wait when the caller gives none (about one second at most).
+constexpr int kWaitTries = 1000;
+
 // Bounded wait for an mbarrier phase (false on timeout).  Each try suspends the thread for up
 // to 1 ms (hint) instead of spinning, so waiting warps leave the issue slots to the others;
-// at most 1000 tries.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    for (int i = 0; i < 1000; ++i) {
+// at most `tries` tries (0: report a timeout without waiting).
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, int tries = kWaitTries) {
+    for (int i = 0; i < tries; ++i) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(addr), "r"(parity), "r"(1000000u) : "memory");

@@ -22,8 +22,10 @@
 // chunk after next.  After a unit's last chunk its accumulators are read back (tcgen05.ld),
 // scaled by g_a conj(g_b) / T and written, with the mirrored conjugate block for off-diagonal
 // units.  Two 256-thread CTAs share an SM (256 TMEM columns each), so one CTA's decode and
-// loads overlap the other's MMAs.  Every wait on the tensor cores is bounded; on a timeout
-// the CTA writes NaN into its first output element and stops.
+// loads overlap the other's MMAs.  Every wait on the tensor cores is bounded (the pipeline's
+// waits by the plan's try count); on a timeout the CTA sets the correlator-timeout bit of the
+// plan's status word, writes NaN into its first output element, waits with the full limit for
+// the MMAs in flight and stops.
 //
 // WIDE (4+4-bit voltages, A a multiple of 16, 16-byte aligned input): a thread loads 16
 // consecutive antennas of one sample with one 16-byte load (a warp reads whole 128-byte
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
         const int a0 = ab * 128, b0 = bb * 128;
         for (int kc = 0; kc < n_chunks && !failed; ++kc, ++g) {
             const int s = g & 1;
-            if (g >= 2 && !mbar_wait(smem_u32(&mbar[s]), ((g - 2) >> 1) & 1)) failed = true;
+            if (g >= 2 && !mbar_wait(smem_u32(&mbar[s]), ((g - 2) >> 1) & 1, a.wait_tries)) failed = true;
             failed = __syncthreads_or(failed) != 0;
             if (failed) break;
             __half* st = sT + s * N_TILE * TILE;
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
         }
         if (failed) break;
         // ---- epilogue: D -> V_ab = g_a conj(g_b) D / T (and the mirrored block) ----
-        if (!mbar_wait(mb_acc, n_done & 1)) failed = true;
+        if (!mbar_wait(mb_acc, n_done & 1, a.wait_tries)) failed = true;
         failed = __syncthreads_or(failed) != 0;
         if (failed) break;
         fence_after();
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     }
     if (failed) {
         if (tid == 0 && beg < end) {
+            if (a.status) atomicOr(a.status, kStatusCorrelateTimeout);
             int cp, ab, bb;
             unit_coords(beg, nab, cp, ab, bb);
             a.vis[(size_t)cp * A * A + (size_t)(ab * 128) * A + bb * 128] =

@@ -1,8 +1,9 @@
 """Thin Python binding of the MOFF imaging C ABI (include/epic.h).
 
 The functions named like the C entry points (`epic_create`, `epic_image`,
-`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_weff`, `epic_isotropic`, `epic_fengine`, `epic_fx_image`, `epic_grid`, `epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal
-arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
+`epic_image_backward`, `epic_image_xpol`, `epic_correlate`, `epic_weff`, `epic_isotropic`,
+`epic_fengine`, `epic_fx_image`, `epic_grid`, `epic_sync`, `epic_set_wait_limit`,
+`epic_destroy`, `epic_plan_info`, `epic_last_error`) only marshal arguments; every step of the imaging path runs in the CUDA library.  `Plan` wraps them
 for torch tensors, and `MoffImage` is the autograd.Function whose backward is the
 library's adjoint kernel.  There is no CPU fallback: if the library has not been built
 (paper_1510_08318_gb300.build), loading raises.
@@ -17,11 +18,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libepic.so")
 
-EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED = range(5)
+EPIC_OK, EPIC_EINVAL, EPIC_ENOMEM, EPIC_ECUDA, EPIC_EUNSUPPORTED, EPIC_ETIMEOUT = range(6)
 VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
-           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine", "epic_fx_image")
+           "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine", "epic_fx_image",
+           "epic_sync", "epic_set_wait_limit")
 XFORM_FFT, XFORM_DFTGEMM = 0, 1
 
 _lib = None
@@ -68,6 +70,10 @@ def load(path=LIB_PATH):
     lib.epic_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
     lib.epic_set_transform.restype = i32
     lib.epic_set_transform.argtypes = [vp, i32]
+    lib.epic_sync.restype = i32
+    lib.epic_sync.argtypes = [vp, vp]
+    lib.epic_set_wait_limit.restype = i32
+    lib.epic_set_wait_limit.argtypes = [vp, i32]
     pp = ctypes.POINTER(vp)
     lib.epic_batch_create.restype = i32
     lib.epic_batch_create.argtypes = [pp, i32, pp]
@@ -189,6 +195,14 @@ def epic_set_transform(plan, xform):
     _check(load().epic_set_transform(plan, int(xform)))
 
 
+def epic_sync(plan, stream):
+    _check(load().epic_sync(plan, stream))
+
+
+def epic_set_wait_limit(plan, tries):
+    _check(load().epic_set_wait_limit(plan, int(tries)))
+
+
 def _ptr_array(xs):
     return (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
 
@@ -249,6 +263,18 @@ class Plan:
         """'fft' (FP32 shared-memory FFT) or 'dftgemm' (tensor-core DFT, FP16 hi+lo, N_p = 128)."""
         epic_set_transform(self._h, {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM}[xform])
         self.xform = xform
+        return self
+
+    def sync(self, stream=None):
+        """epic_sync: wait for the stream and raise EpicError (status EPIC_ETIMEOUT) if a bounded
+        tensor-core wait of this plan's kernels ran out since the last sync."""
+        import torch
+        st = torch.cuda.current_stream(torch.device("cuda", self.device)) if stream is None else stream
+        epic_sync(self._h, st.cuda_stream)
+
+    def set_wait_limit(self, tries):
+        """epic_set_wait_limit: tries (about 1 ms each) of the tensor-core pipelines' waits."""
+        epic_set_wait_limit(self._h, tries)
         return self
 
     @classmethod

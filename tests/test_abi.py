@@ -92,6 +92,9 @@ def test_every_plan_call_rejects_null_plan(lib):
     assert lib.epic_batch_autotune(None, None, None, None, None, None) == epic.EPIC_EINVAL
     assert lib.epic_batch_info(None, None, None, None, 0) == epic.EPIC_EINVAL
     assert "batch" in epic.epic_last_error()
+    assert lib.epic_sync(None, None) == epic.EPIC_EINVAL
+    assert "plan" in epic.epic_last_error()
+    assert lib.epic_set_wait_limit(None, 10) == epic.EPIC_EINVAL
     assert lib.epic_batch_create(None, 1, None) == epic.EPIC_EINVAL
     out = ctypes.c_void_p(1)
     assert lib.epic_batch_create(ctypes.byref(out), 0, None) == epic.EPIC_EINVAL
@@ -113,3 +116,15 @@ def test_fengine_rejects_on_host(lib, args, status):
 
 def test_fengine_zero_blocks_is_a_no_op(lib):
     assert lib.epic_fengine(8, 2, 128, 0, 2, None, 1, None, 0, None) == epic.EPIC_OK
+
+
+@pytest.mark.parametrize("in_dtype, raw, out_dtype, volt", [
+    (0, 0x1004, 1, 0x2000),       # complex64 samples at a 4-byte offset
+    (1, 0x1002, 1, 0x2000),       # FP16 pairs at a 2-byte offset
+    (2, 0x1001, 0, 0x2004),       # 4+4-bit samples anywhere, complex64 spectra at a 4-byte offset
+])
+def test_fengine_rejects_misaligned_arrays_on_host(lib, in_dtype, raw, out_dtype, volt):
+    """The alignment of every device array is checked on the host before any CUDA call (the
+    addresses here are never dereferenced)."""
+    assert lib.epic_fengine(8, 2, 128, 4, in_dtype, raw, out_dtype, volt, 0, None) == epic.EPIC_EINVAL
+    assert "aligned" in epic.epic_last_error()
