@@ -310,12 +310,15 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         }
     }
 
-    // gridding slot tables of the tensor-core form (N_p = 128 only)
+    // gridding slot tables of the tensor-core forms (N_p = 128 and 256)
     std::vector<int2> dlane;
     std::vector<int> dbase;
     std::vector<float> dwre, dwim;
     std::vector<uint16_t> dant;
-    const bool dg_ok = n_pad == 128 && epic::dftgemm_gather_tables(cptr, cent, cwim, dlane, dbase, dwre, dwim, dant);
+    const bool dg_ok = (n_pad == 128 && epic::dftgemm_gather_tables(cptr, cent, cwim, dlane, dbase, dwre, dwim, dant)) ||
+                       (n_pad == 256 &&
+                        epic::dftgemm_gather_tables_ng(128, epic::kDg256GridWarps, cptr, cent, cwim, dlane, dbase,
+                                                       dwre, dwim, dant));
 
     // antenna-major CSR per row block (degridding side of the adjoint); cells are stored as
     // offsets into the adjoint kernel's shared-memory row buffer
@@ -479,7 +482,8 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
         return EPIC_OK;
     }
     if (xform != EPIC_XFORM_DFTGEMM) return epic_fail(EPIC_EINVAL, "xform %d", xform);
-    if (plan->n_pad != 128) return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad == 128 (plan: %d)", plan->n_pad);
+    if (plan->n_pad != 128 && plan->n_pad != 256)
+        return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad 128 or 256 (plan: %d)", plan->n_pad);
     if (!plan->dg_lane)
         return epic_fail(EPIC_EUNSUPPORTED, "a pair of grid cells has more than 65535 mapping entries, or more than "
                                             "65536 antennas");
@@ -487,11 +491,16 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
-    if (epic::dftgemm_smem_bytes(plan->n_ant) > (size_t)smem_optin)
+    const size_t dg_need =
+        plan->n_pad == 128 ? epic::dftgemm_smem_bytes(plan->n_ant) : epic::dftgemm256_smem_bytes(plan->n_ant);
+    if (dg_need > (size_t)smem_optin)
         return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the tensor-core kernel's shared memory", plan->n_ant);
     if (!plan->dg_tab) {
         std::vector<uint16_t> tab;
-        epic::dftgemm_tables(tab);
+        if (plan->n_pad == 128)
+            epic::dftgemm_tables(tab);
+        else
+            epic::dftgemm256_tables(tab);
         cudaError_t e = upload(&plan->dg_tab, tab);
         if (e != cudaSuccess) {
             cudaFree(plan->dg_tab);
@@ -554,7 +563,8 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
     epic_status s;
     if (plan->xform == EPIC_XFORM_DFTGEMM) {
         const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_wre, plan->dg_wim, plan->dg_ant, (int)plan->nnz};
-        e = epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st);
+        e = plan->n_pad == 128 ? epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st)
+                               : epic::launch_dftgemm256(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st);
         s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core imaging kernel launch");
     } else {
         s = launch_fwd(plan, a, st);
@@ -633,6 +643,9 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
     const bool dg = plan->xform == EPIC_XFORM_DFTGEMM;
+    if (dg && plan->n_pad != 128)
+        return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core cross-polarisation form exists for n_pad 128 only; "
+                                            "use the FFT form (epic_set_transform) at n_pad %d", plan->n_pad);
     if ((dg ? epic::dftgemm_smem_bytes(plan->n_ant, true) : epic::fwd_xpol_smem_bytes(plan->n_pad, plan->n_ant)) >
         (size_t)smem_optin)
         return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the %s cross-polarisation kernel's shared memory",

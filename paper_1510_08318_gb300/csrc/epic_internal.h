@@ -166,9 +166,24 @@ void dftgemm_tables(std::vector<uint16_t>& out);
 bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
                            std::vector<int2>& lane, std::vector<int>& base, std::vector<float>& wre,
                            std::vector<float>& wim, std::vector<uint16_t>& ant);
+// The same slot tables for a grid of ng x ng cells (ng = 64 or 128; ng^2 / 64 slots) gridded by
+// n_warps warps, warp w walking the ceil(slots / n_warps) positions from w * that (positions no
+// slot took are empty).  false as above, or for another ng.
+bool dftgemm_gather_tables_ng(int ng, int n_warps, const std::vector<int>& cptr, const std::vector<int2>& cent,
+                              const std::vector<float>& cwim, std::vector<int2>& lane, std::vector<int>& base,
+                              std::vector<float>& wre, std::vector<float>& wim, std::vector<uint16_t>& ant);
 // xpol: the (channel, pol) items are the 4 C virtual pols of dual-pol data, as in the FFT form
 cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st,
                            bool xpol = false);
+
+// Tensor-core DFT form for N_p = 256 (moff_dftgemm256.cu): two CTAs per image (one per half of
+// the image rows), the W tables streamed from global memory in 16 KB chunks; gather tables from
+// dftgemm_gather_tables_ng(128, ...).  Single-pol images only.
+constexpr int kDg256GridWarps = 15;   // gridding warps of the N_p = 256 kernel (the 16th issues)
+size_t dftgemm256_smem_bytes(int n_ant);
+void dftgemm256_tables(std::vector<uint16_t>& out);
+cudaError_t launch_dftgemm256(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm,
+                              cudaStream_t st);
 
 // Standalone gridder: samples per work unit (8, or 4 when 8 do not fit shared memory) and launch.
 size_t grid_smem_bytes(int n_ant, int tb);

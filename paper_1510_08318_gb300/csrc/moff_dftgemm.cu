@@ -443,20 +443,20 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         ++issued1;
         if (tid == 0) vmax[0] = 0u;
     }
-    // a wait that runs out sets `failed` for the whole warp (the TMEM passes after it are
-    // warp-collective and are skipped), then for the whole CTA at the next barrier
+    // a wait that runs out sets `failed` (the warp-collective TMEM passes after it still run, on
+    // values that are then discarded), and the CTA stops at the next barrier
     for (int i = 0; i < n; ++i) {
         if (worker) {
             if (i + 1 < n) sc_next = grid(i + 1);
             if (i >= 1) {
-                failed = __any_sync(0xffffffffu, failed || !mbar_wait(mb2, (i - 1) & 1, a.wait_tries)) != 0;
+                if (!mbar_wait(mb2, (i - 1) & 1, a.wait_tries)) failed = true;
                 fence_after();
-                if (!failed) epilogue(i - 1, sc_prev);
+                epilogue(i - 1, sc_prev);
             }
             if (i + 2 < n) decode(i + 2);
-            failed = __any_sync(0xffffffffu, failed || !mbar_wait(mb1, i & 1, a.wait_tries)) != 0;
+            if (!mbar_wait(mb1, i & 1, a.wait_tries)) failed = true;
             fence_after();
-            if (!failed) split();
+            split();
         }
         fence_before();
         failed = __syncthreads_or(failed) != 0;   // uniform across the CTA
@@ -473,9 +473,9 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         sc_cur = sc_next;
     }
     if (!failed && n > 0 && worker) {
-        failed = __any_sync(0xffffffffu, !mbar_wait(mb2, (n - 1) & 1, a.wait_tries)) != 0;
+        if (!mbar_wait(mb2, (n - 1) & 1, a.wait_tries)) failed = true;
         fence_after();
-        if (!failed) epilogue(n - 1, sc_prev);
+        epilogue(n - 1, sc_prev);
         flush_power((beg + n - 1) / T);
     }
     failed = __syncthreads_or(failed) != 0;
@@ -520,38 +520,42 @@ void dftgemm_tables(std::vector<uint16_t>& out) {
         }
 }
 
-// Slot tables of the tensor-core form's gridding.  The word of pair (x, y), y even, lands in
-// shared-memory bank 4 (x mod 8) + (y / 2 mod 4) of every E^T table, so the 2048 pairs fall
-// into 32 bank classes of 64.  Within each class pairs are ranked by entry count (most first,
+// Slot tables of the tensor-core forms' gridding on an ng x ng grid (64 for N_p = 128, 128 for
+// N_p = 256).  The word of pair (x, y), y even, lands in shared-memory bank
+// 4 (x mod 8) + (y / 2 mod 4) of every E^T table, so the ng^2 / 2 pairs fall into 32 bank
+// classes.  Within each class pairs are ranked by entry count (most first,
 // ties by position) and slot r takes the r-th pair of every class: its 32 lanes store to 32
 // distinct banks, and classes interleave finely enough over the aperture that the r-th pairs
-// of all classes have similar counts.  A slot takes max(count) warp steps; slots go to warps
-// heaviest first, each to the warp with the fewest steps so far among those holding fewer
-// than four (ties to the lowest warp), so the slowest warp's gridding is about the heaviest
-// slot or the mean, whichever is larger.
-bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
-                           std::vector<int2>& lane, std::vector<int>& base, std::vector<float>& wre,
-                           std::vector<float>& wim, std::vector<uint16_t>& ant) {
-    using namespace dg;
-    constexpr int NPAIR = NG * NG / 2;
-    static_assert(NSLOT * 32 == NPAIR && NSLOT == 4 * (NT / 32), "four slots of 32 pairs per worker warp");
+// of all classes have similar counts.  A slot takes max(count) warp steps; slots go to the
+// n_warps gridding warps heaviest first, each to the warp with the fewest steps so far among
+// those holding fewer than ceil(slots / n_warps) (ties to the lowest warp), so the slowest
+// warp's gridding is about the heaviest slot or the mean, whichever is larger.  Warp w walks
+// positions w * ceil(slots / n_warps) ..; positions no slot took hold no entries.
+bool dftgemm_gather_tables_ng(int ng, int n_warps, const std::vector<int>& cptr, const std::vector<int2>& cent,
+                              const std::vector<float>& cwim, std::vector<int2>& lane, std::vector<int>& base,
+                              std::vector<float>& wre, std::vector<float>& wim, std::vector<uint16_t>& ant) {
+    using tc::koff;
+    const int NW = n_warps;
+    const int NPAIR = ng * ng / 2, nslot = NPAIR / 32;
+    if ((ng != 64 && ng != 128) || NW < 1 || NW > 32) return false;
+    const int per_warp = (nslot + NW - 1) / NW;   // positions per warp; those left over stay empty
     for (const int2& c : cent)
         if (c.y < 0 || c.y > 0xffff) return false;
     struct Pair { int cell, c0, cnt, off; };
     std::vector<Pair> pr(NPAIR);
-    for (int yp = 0; yp < NG / 2; ++yp)
-        for (int x = 0; x < NG; ++x) {
-            const int c = 2 * yp * NG + x;
-            const int n0 = cptr[c + 1] - cptr[c], n1 = cptr[c + NG + 1] - cptr[c + NG];
+    for (int yp = 0; yp < ng / 2; ++yp)
+        for (int x = 0; x < ng; ++x) {
+            const int c = 2 * yp * ng + x;
+            const int n0 = cptr[c + 1] - cptr[c], n1 = cptr[c + ng + 1] - cptr[c + ng];
             if (n0 + n1 > 0xffff) return false;
-            pr[yp * NG + x] = {c, n0, n0 + n1, koff(x, 2 * yp, NG)};
+            pr[yp * ng + x] = {c, n0, n0 + n1, koff(x, 2 * yp, ng)};
         }
     auto heavier = [&](int u, int v) { return pr[u].cnt > pr[v].cnt; };
     std::vector<std::vector<int>> cls(32);
-    for (int q = 0; q < NPAIR; ++q) cls[4 * ((q % NG) & 7) + ((q / NG) & 3)].push_back(q);
+    for (int q = 0; q < NPAIR; ++q) cls[4 * ((q % ng) & 7) + ((q / ng) & 3)].push_back(q);
     for (auto& c : cls) std::stable_sort(c.begin(), c.end(), heavier);
-    std::vector<std::vector<int>> slots(NSLOT);
-    for (int r = 0; r < NSLOT; ++r) {
+    std::vector<std::vector<int>> slots(nslot);
+    for (int r = 0; r < nslot; ++r) {
         for (int c = 0; c < 32; ++c) slots[r].push_back(cls[c][r]);
         std::stable_sort(slots[r].begin(), slots[r].end(), heavier);   // lanes in rank order
     }
@@ -560,18 +564,17 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
     });
     std::vector<int> order;
     for (const auto& sl : slots) order.insert(order.end(), sl.begin(), sl.end());
-    lane.assign((size_t)NSLOT * 32, int2{0, 0});
-    base.assign(NSLOT, 0);
+    lane.assign((size_t)NW * per_warp * 32, int2{0, 0});
+    base.assign((size_t)NW * per_warp, 0);
     wre.clear();
     wim.clear();
     ant.clear();
-    constexpr int NW = NT / 32;
-    int held[NW] = {}, steps[NW] = {};
-    for (int r = 0; r < NSLOT; ++r) {
+    std::vector<int> held(NW, 0), steps(NW, 0);
+    for (int r = 0; r < nslot; ++r) {
         int w = -1;
         for (int v = 0; v < NW; ++v)
-            if (held[v] < 4 && (w < 0 || steps[v] < steps[w])) w = v;
-        const int pos = 4 * w + held[w]++;
+            if (held[v] < per_warp && (w < 0 || steps[v] < steps[w])) w = v;
+        const int pos = per_warp * w + held[w]++;
         steps[w] += pr[order[32 * r]].cnt;
         const Pair* P[32];
         for (int i = 0; i < 32; ++i) P[i] = &pr[order[32 * r + i]];
@@ -580,15 +583,23 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
             lane[(size_t)pos * 32 + i] = int2{(int)((unsigned)P[i]->c0 | ((unsigned)P[i]->cnt << 16)), P[i]->off};
         for (int k = 0; k < P[0]->cnt; ++k)
             for (int i = 0; i < 32 && P[i]->cnt > k; ++i) {
-                const int e = k < P[i]->c0 ? cptr[P[i]->cell] + k : cptr[P[i]->cell + NG] + (k - P[i]->c0);
-                float w;
-                std::memcpy(&w, &cent[e].x, sizeof(float));
-                wre.push_back(w);
+                const int e = k < P[i]->c0 ? cptr[P[i]->cell] + k : cptr[P[i]->cell + ng] + (k - P[i]->c0);
+                float wv;
+                std::memcpy(&wv, &cent[e].x, sizeof(float));
+                wre.push_back(wv);
                 wim.push_back(cwim[e]);
                 ant.push_back((uint16_t)cent[e].y);
             }
     }
     return true;
+}
+
+bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
+                           std::vector<int2>& lane, std::vector<int>& base, std::vector<float>& wre,
+                           std::vector<float>& wim, std::vector<uint16_t>& ant) {
+    static_assert(dg::NSLOT * 32 == dg::NG * dg::NG / 2 && dg::NSLOT == 4 * (dg::NT / 32),
+                  "four slots of 32 pairs per worker warp");
+    return dftgemm_gather_tables_ng(dg::NG, dg::NT / 32, cptr, cent, cwim, lane, base, wre, wim, ant);
 }
 
 cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st,

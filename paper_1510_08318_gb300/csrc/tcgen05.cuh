@@ -1,7 +1,7 @@
 // Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) shared by the tensor-core
 // kernels: K-major shared-memory operands in 8 x 8 core matrices without swizzle,
 // kind::f16 MMAs with M = 128 and FP32 accumulators in tensor memory, commits to mbarriers,
-// bounded mbarrier waits, and tensor-memory loads and stores.
+// bounded mbarrier waits, bulk global -> shared copies, and tensor-memory loads and stores.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -59,8 +59,31 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, int tr
     return false;
 }
 
+// mbarrier setup and the bulk (non-tensor) copy engine: one thread announces the bytes an
+// mbarrier phase waits for, then a contiguous global -> shared copy completes them.  Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
 template <int NR>
 __device__ __forceinline__ void tld(uint32_t taddr, float (&v)[NR]);
+template <>
+__device__ __forceinline__ void tld<8>(uint32_t t, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(t));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 template <>
 __device__ __forceinline__ void tld<16>(uint32_t t, float (&v)[16]) {
     uint32_t r[16];

@@ -1,15 +1,19 @@
-// Host-only check of the tensor-core kernel's gridding slot tables (no GPU): builds them with the
-// library's own builder from a cell-major mapping read from a text file, then walks them the
+// Host-only check of the tensor-core kernels' gridding slot tables (no GPU): builds them with the
+// library's own builder from a cell-major mapping read from a text file (on the 64 x 64 grid of
+// N_p = 128 with 16 warps, or the 128 x 128 grid of N_p = 256 with the warp count given as the
+// second argument), then walks them the
 // way the kernel's warps do (step k: lanes with more than k entries, contiguous run, start of
 // step k + 1 = start of step k + active lanes) and checks that
 //   every index stays inside the tables and every antenna inside the array,
 //   every cell pair (x, y), (x, y + 1) is stored exactly once, at an in-range even offset,
 //   the 32 lanes of a slot store to 32 distinct shared-memory banks,
-//   lanes are in decreasing entry count and each warp holds four slots,
+//   lanes are in decreasing entry count, every slot is held by one position of some warp (a warp
+//   holds at most ceil(slots / warps) of them: positions per warp, the rest all zero),
 //   every cell's sum equals the cell-major sum of its entries bit for bit (same order).
 // Exit status 0 when every check holds.
 #include "../../paper_1510_08318_gb300/csrc/moff_dftgemm.cu"
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <random>
@@ -20,7 +24,9 @@ int main(int argc, char** argv) {
     std::ifstream f(argv[1]);
     int ncell = 0, nnz = 0;
     f >> ncell >> nnz;
-    if (ncell != 64 * 64) return 2;
+    const int NG = ncell == 64 * 64 ? 64 : ncell == 128 * 128 ? 128 : 0;   // the form's grid side
+    if (NG == 0) return 2;
+    const int NW = argc > 2 ? std::atoi(argv[2]) : 16;                       // gridding warps
     std::vector<int> cptr(ncell + 1), ant(nnz);
     std::vector<float> wr(nnz), wi(nnz);
     for (auto& v : cptr) f >> v;
@@ -39,13 +45,16 @@ int main(int argc, char** argv) {
     std::vector<int> base;
     std::vector<float> wre, wim;
     std::vector<uint16_t> an;
-    if (!epic::dftgemm_gather_tables(cptr, cent, wi, lane, base, wre, wim, an)) {
+    const bool ok = NG == 64 && NW == 16 ? epic::dftgemm_gather_tables(cptr, cent, wi, lane, base, wre, wim, an)
+                                         : epic::dftgemm_gather_tables_ng(NG, NW, cptr, cent, wi, lane, base, wre,
+                                                                          wim, an);
+    if (!ok) {
         std::printf("builder refused the mapping\n");
         return 1;
     }
-    const int NG = 64, ETAB = NG * NG, NSLOT = 64;
+    const int ETAB = NG * NG, NSLOT = NG * NG / 64, PER = (NSLOT + NW - 1) / NW, NPOS = NW * PER;
     int bad = 0;
-    if ((int)lane.size() != NSLOT * 32 || (int)base.size() != NSLOT || (int)wre.size() != nnz ||
+    if ((int)lane.size() != NPOS * 32 || (int)base.size() != NPOS || (int)wre.size() != nnz ||
         wim.size() != wre.size() || an.size() != wre.size()) {
         std::printf("table sizes\n");
         return 1;
@@ -56,7 +65,13 @@ int main(int argc, char** argv) {
     for (auto& v : VB) v = make_float2(U(rng), U(rng));
     std::vector<float2> E(ETAB, make_float2(0.f, 0.f));
     std::vector<int> seen(ETAB, 0);
-    for (int slot = 0; slot < NSLOT; ++slot) {
+    int used = 0;
+    for (int slot = 0; slot < NPOS; ++slot) {
+        // positions no slot took (when the slots do not divide evenly over the warps) are all zero
+        bool empty = true;
+        for (int l = 0; l < 32; ++l) empty = empty && lane[slot * 32 + l].x == 0 && lane[slot * 32 + l].y == 0;
+        if (empty) continue;
+        ++used;
         int c0[32], cnt[32], e[32];
         unsigned banks = 0;
         for (int l = 0; l < 32; ++l) {
@@ -96,6 +111,7 @@ int main(int argc, char** argv) {
             seen[off + 1] += 1;
         }
     }
+    if (used != NSLOT) ++bad;
     // the reference: cell-major sums in the order of the CSR
     int miss = 0;
     double maxdiff = 0.0;

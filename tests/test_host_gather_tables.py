@@ -27,18 +27,18 @@ def _layout(n_grid, n_ant, seed, complex_w):
     return moff.map_antennas(pos, ptr, dxdy, w, 1.0, np.zeros(2), n_grid)
 
 
-def _write_csr(M, n_grid, path):
-    """The mapping as the library holds it: cell-major over the 64 x 64 grid of N_p = 128."""
+def _write_csr(M, n_grid, path, side=64):
+    """The mapping as the library holds it: cell-major over the side x side grid of N_p = 2 side."""
     M = M.tocsr()
     M.sort_indices()
     rows = np.repeat(np.arange(M.shape[0]), np.diff(M.indptr))
-    cell = (rows // n_grid) * 64 + rows % n_grid
+    cell = (rows // n_grid) * side + rows % n_grid
     order = np.argsort(cell, kind="stable")
-    ptr = np.zeros(64 * 64 + 1, dtype=np.int64)
+    ptr = np.zeros(side * side + 1, dtype=np.int64)
     np.add.at(ptr, cell + 1, 1)
     ptr = np.cumsum(ptr)
     with open(path, "w") as f:
-        f.write("%d %d\n" % (64 * 64, M.nnz))
+        f.write("%d %d\n" % (side * side, M.nnz))
         f.write(" ".join(map(str, ptr)) + "\n")
         f.write(" ".join(map(str, M.indices[order])) + "\n")
         f.write(" ".join("%.9g" % v for v in np.float32(M.data.real[order])) + "\n")
@@ -75,4 +75,24 @@ def test_gather_tables(checker, tmp_path, case):
     path = str(tmp_path / "map.txt")
     _write_csr(M, n_grid, path)
     r = subprocess.run([checker, path], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("case", ["hera", "complex_ragged", "calib"])
+def test_gather_tables_np256(checker, tmp_path, case):
+    """The N_p = 256 form's tables: 128 x 128 grid, 256 slots over its 15 gridding warps."""
+    if case == "hera":
+        wl = synth.workload_hera(n_chan=1, n_time=1)
+        M, n_grid = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin,
+                                      wl.n_grid), wl.n_grid
+    elif case == "complex_ragged":
+        n_grid = 101
+        M = _layout(n_grid, 200, 14, True)
+    else:
+        wl = synth.workload_calib(n_chan=1, n_time=1)
+        M, n_grid = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin,
+                                      wl.n_grid), wl.n_grid
+    path = str(tmp_path / "map.txt")
+    _write_csr(M, n_grid, path, side=128)
+    r = subprocess.run([checker, path, "15"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
