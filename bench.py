@@ -222,7 +222,7 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline_sample(wl_full, plan=None, torch=None, n_chan=1, n_time=256, forms=("fft", "dftgemm")):
+def cpu_baseline_sample(wl_full, plan=None, torch=None, n_chan=1, n_time=256, forms=("fft", "dftgemm", "dftgemm_fp16")):
     """Time the FP64 oracle on a bounded sample: the last n_chan channels, pol 1, the first
     n_time samples, image + auto-correlation term.  If a plan is given, the CUDA path images the
     same sample (both transform forms) and its relative L2 error against the oracle is returned."""
@@ -1169,7 +1169,7 @@ def main():
         return max_over_ranks([ms], world, dev)[0], clk
 
     forms = {}
-    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm")):
+    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm"), ("fp16_dftgemm", "dftgemm_fp16")):
         plan.set_transform(xf)
         for _ in range(max(args.warmup, 3)):
             step()
@@ -1188,7 +1188,8 @@ def main():
         cfb = cpu_fft_sample(wl, n_chan=32, n_time=1024)
     # the chosen form: the fastest whose error against the oracle meets the FP32 bound (1e-4)
     fft_flops = workload_algorithmic_flops(wl, plan.info["nnz"]) * T * C * P
-    ok = [k for k in forms if err.get(forms[k]["xform"], 0.0) < 1e-4]
+    # (the reduced-precision form is reported beside, never chosen: its stated bound is 3e-3)
+    ok = [k for k in forms if k != "fp16_dftgemm" and err.get(forms[k]["xform"], 0.0) < 1e-4]
     chosen = min(ok, key=lambda k: forms[k]["ms_per_step"])
     f = forms[chosen]
     if chosen == "fp16x3_dftgemm":
@@ -1203,6 +1204,13 @@ def main():
     # the plain FP32 form's own roofline, whichever form is chosen
     fft_roof = alu_roofline(fft_flops, forms["fp32_fft"]["kernel_ms"], n_sm, forms["fp32_fft"]["clocks"],
                             traffic=FWD_TRAFFIC_BYTES)
+    # the reduced-precision tensor-core form: one FP16 product per real product (executed =
+    # algorithmic work), reported with its own error (its bound is 3e-3, not the FP32 path's)
+    lp = forms["fp16_dftgemm"]
+    lp["roofline"] = tensor_roofline(DG_ALG_FLOP_PER_IMAGE * T * C * P, DG_ALG_FLOP_PER_IMAGE * T * C * P,
+                                     lp["kernel_ms"], lp["clocks"],
+                                     flop_basis="the pruned 128 x 128 DFT as real products, 12.58 MFLOP per image, "
+                                                "each one FP16 product")
     # the standalone gridder (epic_grid) on the same resident voltages: the gridded fields of all
     # 262,144 samples written to HBM, against the measured copy bandwidth
     grid = measure_gridder(wl, plan, volt, dev, args.steps, args.warmup, world, rank, flush,
@@ -1230,6 +1238,10 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": f["clocks"],
         "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()},
+        "reduced_precision": {"form": "fp16_dftgemm: FP16 gridding operands (FP32 sums), one FP16 product per "
+                                      "real product of the DFT; stated bound 3e-3 relative L2",
+                              "value": lp["value"], "ms_per_step": lp["ms_per_step"], "kernel_ms": lp["kernel_ms"],
+                              "roofline": lp["roofline"]},
         "plain_fp32": {"value": forms["fp32_fft"]["value"], "ms_per_step": forms["fp32_fft"]["ms_per_step"],
                        "images_per_s": world * T * C * P / (forms["fp32_fft"]["ms_per_step"] / 1e3),
                        "roofline": fft_roof},

@@ -59,9 +59,12 @@ typedef enum {
 } epic_volt_dtype;
 
 typedef enum {
-    EPIC_XFORM_FFT = 0,     /* FP32 shared-memory FFT (all sizes; the default) */
-    EPIC_XFORM_DFTGEMM = 1  /* dense DFT on the tensor cores, FP16 hi+lo operands, FP32
-                               accumulation (N_p = 128 only) */
+    EPIC_XFORM_FFT = 0,         /* FP32 shared-memory FFT (all sizes; the default) */
+    EPIC_XFORM_DFTGEMM = 1,     /* dense DFT on the tensor cores, FP16 hi+lo operands, FP32
+                                   accumulation (N_p = 128 and 256) */
+    EPIC_XFORM_DFTGEMM_FP16 = 2 /* reduced precision: FP16 gridding operands (weights and gained
+                                   voltages rounded to FP16, products exact, FP32 sums) and one
+                                   FP16 product per real product of the DFT (N_p = 128) */
 } epic_xform;
 
 /*
@@ -104,10 +107,17 @@ epic_status epic_create(epic_plan **plan, int n_ant, const double *pos_xy,
  * DFT matrix W[k][n] = exp(+2 pi i n k / N_p) on the tensor cores: every operand is split into
  * two FP16 numbers (hi + lo) and each real product is accumulated as hi*hi + hi*lo + lo*hi in
  * FP32 (per image the gridded field is scaled by a power of two to keep the operands in range).
- * It is available for n_pad == 128 and up to about 2,400 antennas (the kernel keeps four
- * per-antenna arrays in shared memory beside the operand tables; 1,900 for epic_image_xpol);
- * otherwise EPIC_EUNSUPPORTED.  The first call with EPIC_XFORM_DFTGEMM uploads the plan's DFT
- * operand tables (64 KB).  epic_image_backward always uses the FFT form.
+ * It is available for n_pad == 128 (up to about 2,400 antennas: the kernel keeps four
+ * per-antenna arrays in shared memory beside the operand tables; 1,900 for epic_image_xpol) and
+ * for n_pad == 256 (up to about 1,860 antennas; two CTAs per image, each computing half of the
+ * image rows, the operand tables streamed from global memory; no cross-polarisation form);
+ * otherwise EPIC_EUNSUPPORTED.  EPIC_XFORM_DFTGEMM_FP16 (n_pad == 128, single polarisation
+ * products only) is the reduced-precision form: the gridding multiplies FP16-rounded weights by
+ * FP16-rounded calibrated voltages and sums in FP32, and each real product of the transform is
+ * one FP16 product with FP32 accumulation (no lo parts): about a third of the tensor work, with
+ * an error of about 1e-3 relative L2 against the exact image instead of about 1e-6.  The first
+ * call with a tensor-core form uploads the plan's DFT operand tables (64 KB for n_pad 128,
+ * 256 KB for 256).  epic_image_backward always uses the FFT form.
  */
 epic_status epic_set_transform(epic_plan *plan, int xform);
 

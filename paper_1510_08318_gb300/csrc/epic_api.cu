@@ -481,9 +481,12 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
         plan->xform = xform;
         return EPIC_OK;
     }
-    if (xform != EPIC_XFORM_DFTGEMM) return epic_fail(EPIC_EINVAL, "xform %d", xform);
+    if (xform != EPIC_XFORM_DFTGEMM && xform != EPIC_XFORM_DFTGEMM_FP16) return epic_fail(EPIC_EINVAL, "xform %d", xform);
     if (plan->n_pad != 128 && plan->n_pad != 256)
         return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad 128 or 256 (plan: %d)", plan->n_pad);
+    if (xform == EPIC_XFORM_DFTGEMM_FP16 && plan->n_pad != 128)
+        return epic_fail(EPIC_EUNSUPPORTED, "the reduced-precision tensor-core form exists for n_pad 128 only (plan: %d)",
+                         plan->n_pad);
     if (!plan->dg_lane)
         return epic_fail(EPIC_EUNSUPPORTED, "a pair of grid cells has more than 65535 mapping entries, or more than "
                                             "65536 antennas");
@@ -491,8 +494,9 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
-    const size_t dg_need =
-        plan->n_pad == 128 ? epic::dftgemm_smem_bytes(plan->n_ant) : epic::dftgemm256_smem_bytes(plan->n_ant);
+    const size_t dg_need = plan->n_pad == 128
+                               ? epic::dftgemm_smem_bytes(plan->n_ant, false, xform == EPIC_XFORM_DFTGEMM_FP16)
+                               : epic::dftgemm256_smem_bytes(plan->n_ant);
     if (dg_need > (size_t)smem_optin)
         return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the tensor-core kernel's shared memory", plan->n_ant);
     if (!plan->dg_tab) {
@@ -561,9 +565,10 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
     const epic::FwdArgs a =
         epic_plan_fwd_args(plan, volt, n_time, reinterpret_cast<const float2*>(gains), accum, power);
     epic_status s;
-    if (plan->xform == EPIC_XFORM_DFTGEMM) {
+    if (plan->xform == EPIC_XFORM_DFTGEMM || plan->xform == EPIC_XFORM_DFTGEMM_FP16) {
         const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_wre, plan->dg_wim, plan->dg_ant, (int)plan->nnz};
-        e = plan->n_pad == 128 ? epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st)
+        e = plan->n_pad == 128 ? epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st, false,
+                                                      plan->xform == EPIC_XFORM_DFTGEMM_FP16)
                                : epic::launch_dftgemm256(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st);
         s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core imaging kernel launch");
     } else {
@@ -642,6 +647,9 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    if (plan->xform == EPIC_XFORM_DFTGEMM_FP16)
+        return epic_fail(EPIC_EUNSUPPORTED, "the reduced-precision tensor-core form has no cross-polarisation variant; "
+                                            "use EPIC_XFORM_DFTGEMM or EPIC_XFORM_FFT");
     const bool dg = plan->xform == EPIC_XFORM_DFTGEMM;
     if (dg && plan->n_pad != 128)
         return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core cross-polarisation form exists for n_pad 128 only; "

@@ -160,7 +160,9 @@ struct DgGather {
     const uint16_t* ant;   // entry antennas
     int n_ent;             // number of entries
 };
-size_t dftgemm_smem_bytes(int n_ant, bool xpol = false);   // the least a launch needs (tables read through L1)
+// the least a launch needs (tables read through L1); lp: the reduced-precision form (FP16
+// operands and one product per real product)
+size_t dftgemm_smem_bytes(int n_ant, bool xpol = false, bool lp = false);
 void dftgemm_tables(std::vector<uint16_t>& out);
 // false if a pair has more than 65535 entries or an antenna index does not fit 16 bits
 bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>& cent, const std::vector<float>& cwim,
@@ -174,7 +176,7 @@ bool dftgemm_gather_tables_ng(int ng, int n_warps, const std::vector<int>& cptr,
                               std::vector<float>& wre, std::vector<float>& wim, std::vector<uint16_t>& ant);
 // xpol: the (channel, pol) items are the 4 C virtual pols of dual-pol data, as in the FFT form
 cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st,
-                           bool xpol = false);
+                           bool xpol = false, bool lp = false);
 
 // Tensor-core DFT form for N_p = 256 (moff_dftgemm256.cu): two CTAs per image (one per half of
 // the image rows), the W tables streamed from global memory in 16 KB chunks; gather tables from

@@ -83,13 +83,22 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
 constexpr int kWStep = 2 * WTAB / 16;    // descriptor start-field step per W table
 constexpr int kEStep = 2 * ETAB / 16;    // ... per E^T table
 
-constexpr size_t smem_fixed() {
-    return sizeof(__half) * ((size_t)N_WTAB * WTAB + 2 * (size_t)N_ETAB * ETAB) + 64;
+// W and E^T tables held in shared memory: the split form keeps hi and lo parts, the reduced-
+// precision form (LP) only the FP16 values (the hi tables: the first two W tables and the first
+// three E^T tables of each buffer)
+constexpr int n_wtab(bool lp) { return lp ? 2 : N_WTAB; }
+constexpr int n_etab(bool lp) { return lp ? 3 : N_ETAB; }
+constexpr size_t smem_fixed(bool lp = false) {
+    return sizeof(__half) * ((size_t)n_wtab(lp) * WTAB + 2 * (size_t)n_etab(lp) * ETAB) + 64;
 }
 constexpr int NSLOT = NG * NG / 64;   // slots of 32 cell pairs
 
-// Shared-memory bytes per antenna: two voltage buffers, gains, power (and the Y gains of XP).
-constexpr size_t ant_bytes(bool xp) { return xp ? 36 : 28; }
+// Shared-memory bytes per antenna: two voltage buffers (float2, or half2 in the LP form), gains,
+// power (and the Y gains of XP).
+constexpr size_t ant_bytes(bool xp, bool lp = false) { return (xp ? 36 : 28) - (lp ? 8 : 0); }
+
+// FP16 rounding of a float (the reduced-precision form's operands)
+__device__ __forceinline__ float round_h(float x) { return __half2float(__float2half_rn(x)); }
 
 // Bytes of the gather tables when they are copied into shared memory (after the per-antenna
 // arrays, 16-byte aligned): slot words, slot bases, weights (and imaginary parts), antennas.
@@ -105,24 +114,26 @@ __device__ __forceinline__ T ldt(const T* p) {
     else return __ldg(p);
 }
 
-template <int VDT, bool SMT, bool XP>
+template <int VDT, bool SMT, bool XP, bool LP>
 __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, const __half* __restrict__ wtab,
                                                               const DgGather g) {
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __half* sW = reinterpret_cast<__half*>(smem_raw);                      // [N_WTAB][WTAB]
-    __half* sE = sW + N_WTAB * WTAB;                                      // [2][N_ETAB][ETAB]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + 2 * N_ETAB * ETAB); // [2]
+    constexpr int NWT = n_wtab(LP), NET = n_etab(LP);
+    __half* sE = sW + NWT * WTAB;                                         // [2][NET][ETAB]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sE + 2 * NET * ETAB);    // [2]
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
     unsigned int* vmax = reinterpret_cast<unsigned int*>(tslot + 2);      // [4] max |g V| (float bits) per image mod 4
     const int A = a.n_ant, T = a.n_time;
-    float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed());      // [2][A] decoded voltages
-    float2* GN = VB + 2 * A;
+    float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed(LP));    // [2][A] decoded voltages
+    uint32_t* VBh = reinterpret_cast<uint32_t*>(VB);                     // LP: [2][A] half2
+    float2* GN = LP ? reinterpret_cast<float2*>(VBh + 2 * A) : VB + 2 * A;
     float2* GY = GN + A;                                                  // XP only: phi_v g_Y
     float* PW = reinterpret_cast<float*>(GN + (XP ? 2 : 1) * A);
     // gather tables: copied into shared memory when they fit (SMT), else read through L1,
     // whose share of the SM's 256 KB shrinks as the shared-memory request grows
-    int2* sLane = reinterpret_cast<int2*>(smem_raw + ((smem_fixed() + (size_t)A * ant_bytes(XP) + 15) & ~(size_t)15));
+    int2* sLane = reinterpret_cast<int2*>(smem_raw + ((smem_fixed(LP) + (size_t)A * ant_bytes(XP, LP) + 15) & ~(size_t)15));
     int* sBase = reinterpret_cast<int*>(sLane + NSLOT * 32);
     float* sWre = reinterpret_cast<float*>(sBase + NSLOT);
     float* sWim = sWre + g.n_ent;
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
     const bool worker = tid < NT;     // the issuer warp does no gridding, decoding or epilogue work
     const VT* V = static_cast<const VT*>(a.volt);
 
-    for (int i = tid; i < N_WTAB * WTAB / 8; i += NTH)
+    for (int i = tid; i < NWT * WTAB / 8; i += NTH)
         reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wtab) + i);
     for (int aa = tid; aa < A; aa += NTH) PW[aa] = 0.f;
     if constexpr (SMT) {
@@ -252,7 +263,12 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                         vp.y += w.y;
                     }
                 }
-                vb[aa] = vp;
+                if constexpr (LP) {
+                    const __half2 hv = __floats2half2_rn(vp.x, vp.y);
+                    VBh[(j & 1) * A + aa] = *reinterpret_cast<const uint32_t*>(&hv);
+                } else {
+                    vb[aa] = vp;
+                }
                 PW[aa] += cnorm(vp);
                 m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
             }
@@ -264,7 +280,12 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                 vp.x += w.x;
                 vp.y += w.y;
             }
-            vb[aa] = vp;
+            if constexpr (LP) {
+                const __half2 hv = __floats2half2_rn(vp.x, vp.y);
+                VBh[(j & 1) * A + aa] = *reinterpret_cast<const uint32_t*>(&hv);
+            } else {
+                vb[aa] = vp;
+            }
             PW[aa] += cnorm(vp);
             m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
         }
@@ -284,7 +305,23 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         }
         const float down = ldexpf(1.f, -ex);
         const float2* vb = VB + (j & 1) * A;
-        __half* sEj = sE + (j & 1) * N_ETAB * ETAB;
+        const uint32_t* vbh = VBh + (j & 1) * A;
+        // voltage of an entry's antenna: float2, or (LP) the FP16 pair widened exactly
+        auto volt_of = [&](int an) -> float2 {
+            if constexpr (LP) {
+                const uint32_t u = vbh[an];
+                return __half22float2(*reinterpret_cast<const __half2*>(&u));
+            } else {
+                return vb[an];
+            }
+        };
+        // weights: FP32, or (LP) rounded to FP16 (so every product is an FP16 x FP16 product,
+        // exact in FP32, and the sums accumulate in FP32)
+        auto wt = [&](float w) -> float {
+            if constexpr (LP) return round_h(w);
+            else return w;
+        };
+        __half* sEj = sE + (j & 1) * NET * ETAB;
         // warp w gathers slots 4w .. 4w + 3, each 32 cell pairs of nearly equal entry count
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
@@ -299,8 +336,8 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                     const bool on = k < cnt;
                     const int n_k = __popc(__ballot_sync(0xffffffffu, on));
                     if (on) {
-                        const float2 w = make_float2(ldt<SMT>(tWre + e), ldt<SMT>(tWim + e));
-                        const float2 v = vb[ldt<SMT>(tAnt + e)];
+                        const float2 w = make_float2(wt(ldt<SMT>(tWre + e)), wt(ldt<SMT>(tWim + e)));
+                        const float2 v = volt_of(ldt<SMT>(tAnt + e));
                         if (k < c0) cfma(s0, w, v);
                         else cfma(s1, w, v);
                     }
@@ -313,8 +350,8 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                     if (on) {
                         // both cells take the entry, one with weight 0 (adds an exact 0): no
                         // divergent branch inside the step
-                        const float w = ldt<SMT>(tWre + e);
-                        const float2 v = vb[ldt<SMT>(tAnt + e)];
+                        const float w = wt(ldt<SMT>(tWre + e));
+                        const float2 v = volt_of(ldt<SMT>(tAnt + e));
                         const float w0 = k < c0 ? w : 0.f, w1 = w - w0;
                         s0.x = fmaf(w0, v.x, s0.x);
                         s0.y = fmaf(w0, v.y, s0.y);
@@ -324,17 +361,27 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
                     e += n_k;
                 }
             }
-            uint32_t rh, rl, ih, il;
-            split2(s0.x * down, s1.x * down, rh, rl);
-            split2(s0.y * down, s1.y * down, ih, il);
             const int off = lw.y;   // E^T element (x, y), y even: one 32-bit word holds y and y + 1
-            *reinterpret_cast<uint32_t*>(sEj + ER_HI * ETAB + off) = rh;
-            *reinterpret_cast<uint32_t*>(sEj + ER_LO * ETAB + off) = rl;
-            *reinterpret_cast<uint32_t*>(sEj + EI_HI * ETAB + off) = ih;
-            *reinterpret_cast<uint32_t*>(sEj + EI_LO * ETAB + off) = il;
-            // split(-v) = -split(v) exactly: flip both halves' sign bits
-            *reinterpret_cast<uint32_t*>(sEj + NEI_HI * ETAB + off) = ih ^ 0x80008000u;
-            *reinterpret_cast<uint32_t*>(sEj + NEI_LO * ETAB + off) = il ^ 0x80008000u;
+            if constexpr (LP) {
+                const __half2 hr = __floats2half2_rn(s0.x * down, s1.x * down);
+                const __half2 hi2 = __floats2half2_rn(s0.y * down, s1.y * down);
+                const uint32_t rh = *reinterpret_cast<const uint32_t*>(&hr);
+                const uint32_t ih = *reinterpret_cast<const uint32_t*>(&hi2);
+                *reinterpret_cast<uint32_t*>(sEj + ER_HI * ETAB + off) = rh;
+                *reinterpret_cast<uint32_t*>(sEj + EI_HI * ETAB + off) = ih;
+                *reinterpret_cast<uint32_t*>(sEj + NEI_HI * ETAB + off) = ih ^ 0x80008000u;
+            } else {
+                uint32_t rh, rl, ih, il;
+                split2(s0.x * down, s1.x * down, rh, rl);
+                split2(s0.y * down, s1.y * down, ih, il);
+                *reinterpret_cast<uint32_t*>(sEj + ER_HI * ETAB + off) = rh;
+                *reinterpret_cast<uint32_t*>(sEj + ER_LO * ETAB + off) = rl;
+                *reinterpret_cast<uint32_t*>(sEj + EI_HI * ETAB + off) = ih;
+                *reinterpret_cast<uint32_t*>(sEj + EI_LO * ETAB + off) = il;
+                // split(-v) = -split(v) exactly: flip both halves' sign bits
+                *reinterpret_cast<uint32_t*>(sEj + NEI_HI * ETAB + off) = ih ^ 0x80008000u;
+                *reinterpret_cast<uint32_t*>(sEj + NEI_LO * ETAB + off) = il ^ 0x80008000u;
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // E^T visible to the tensor cores
         return ldexpf(1.f, 2 * ex);
@@ -382,9 +429,16 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
             tld_wait();
             uint32_t ph[8], pl[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) split2(xv[2 * u], xv[2 * u + 1], ph[u], pl[u]);
+            for (int u = 0; u < 8; ++u) {
+                if constexpr (LP) {
+                    const __half2 h = __floats2half2_rn(xv[2 * u], xv[2 * u + 1]);
+                    ph[u] = *reinterpret_cast<const uint32_t*>(&h);
+                } else {
+                    split2(xv[2 * u], xv[2 * u + 1], ph[u], pl[u]);
+                }
+            }
             tst8(dhi + c / 2, ph);
-            tst8(dlo + c / 2, pl);
+            if constexpr (!LP) tst8(dlo + c / 2, pl);
         }
         tst_wait();
     };
@@ -394,13 +448,15 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         // A = W table, B = [table ; next table]: Re W [Re E ; Im E], Im W [-Im E ; Re E]
         constexpr int ta[6] = {WR_HI, WR_HI, WR_LO, WI_HI, WI_HI, WI_LO};
         constexpr int tb[6] = {ER_HI, ER_LO, ER_HI, NEI_HI, NEI_LO, NEI_HI};
-        const uint64_t dE = dE0 + (uint64_t)(b * N_ETAB * kEStep);
+        const uint64_t dE = dE0 + (uint64_t)(b * NET * kEStep);
 #pragma unroll
-        for (int q = 0; q < 6; ++q)
+        for (int q = 0; q < 6; ++q) {
+            if (LP && q % 3 != 0) continue;     // LP: the hi*hi products only
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 mma_ss(tX, dW0 + (uint64_t)(ta[q] * kWStep + 16 * j), dE + (uint64_t)(tb[q] * kEStep + 16 * j), id1,
                        (q | j) != 0);
+        }
         commit(mb1);
     };
     // stage 2: F = X W^T (rows transformed); A operand columns: X re hi/lo at +0/+32, X im
@@ -411,13 +467,15 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
         constexpr int bre[6] = {WR_HI, WR_LO, WR_HI, WI_HI, WI_LO, WI_HI};
         constexpr int bim[6] = {WI_HI, WI_LO, WI_HI, WR_HI, WR_LO, WR_HI};
 #pragma unroll
-        for (int q = 0; q < 6; ++q)
+        for (int q = 0; q < 6; ++q) {
+            if (LP && q % 3 != 0) continue;     // LP: the hi*hi products only
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 mma_ts(tF, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(bre[q] * kWStep + 16 * j), q < 3 ? id2 : id2 | kNegA,
                        (q | j) != 0);
                 mma_ts(tF + 128, tXop + ar[q] + 8 * j, dW0 + (uint64_t)(bim[q] * kWStep + 16 * j), id2, (q | j) != 0);
             }
+        }
         commit(mb2);
     };
 
@@ -497,8 +555,8 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm_kernel(const FwdArgs a, c
 
 }  // namespace dg
 
-size_t dftgemm_smem_bytes(int n_ant, bool xpol) {
-    return dg::smem_fixed() + (size_t)n_ant * dg::ant_bytes(xpol);
+size_t dftgemm_smem_bytes(int n_ant, bool xpol, bool lp) {
+    return dg::smem_fixed(lp) + (size_t)n_ant * dg::ant_bytes(xpol, lp);
 }
 
 // W operand tables for N_p = 128: four [128][64] K-major FP16 tables (re, im hi parts, then
@@ -603,38 +661,45 @@ bool dftgemm_gather_tables(const std::vector<int>& cptr, const std::vector<int2>
 }
 
 cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm, cudaStream_t st,
-                           bool xpol) {
+                           bool xpol, bool lp) {
     const __half* w = static_cast<const __half*>(wtab);
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
     // the gather tables go into shared memory when the whole request still fits one block
-    const size_t base = (dftgemm_smem_bytes(a.n_ant, xpol) + 15) & ~(size_t)15;
+    if (lp && xpol) return cudaErrorInvalidValue;
+    const size_t base = (dftgemm_smem_bytes(a.n_ant, xpol, lp) + 15) & ~(size_t)15;
     const size_t with_tables = base + dg::table_smem_bytes(g.n_ent, g.wim != nullptr);
     const bool smt = with_tables <= (size_t)optin;
-    const size_t smem = smt ? with_tables : dftgemm_smem_bytes(a.n_ant, xpol);
+    const size_t smem = smt ? with_tables : dftgemm_smem_bytes(a.n_ant, xpol, lp);
     long long grid = n_sm;
     if (grid > a.n_items) grid = a.n_items;
-    switch (vdt * 4 + (smt ? 2 : 0) + (xpol ? 1 : 0)) {
-#define EPIC_DG_CASE(V, S, X)                                                                                \
-    case V * 4 + S * 2 + X:                                                                                  \
-        e = ensure_smem<dg::moff_dftgemm_kernel<V, S, X>>(smem);                                             \
+    switch (vdt * 8 + (smt ? 4 : 0) + (xpol ? 2 : 0) + (lp ? 1 : 0)) {
+#define EPIC_DG_CASE(V, S, X, L)                                                                             \
+    case V * 8 + S * 4 + X * 2 + L:                                                                          \
+        e = ensure_smem<dg::moff_dftgemm_kernel<V, S, X, L>>(smem);                                          \
         if (e != cudaSuccess) return e;                                                                      \
-        if (grid > 0) dg::moff_dftgemm_kernel<V, S, X><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w, g);       \
+        if (grid > 0) dg::moff_dftgemm_kernel<V, S, X, L><<<(unsigned)grid, dg::NTH, smem, st>>>(a, w, g);    \
         return cudaGetLastError();
-        EPIC_DG_CASE(0, 0, 0)
-        EPIC_DG_CASE(0, 0, 1)
-        EPIC_DG_CASE(0, 1, 0)
-        EPIC_DG_CASE(0, 1, 1)
-        EPIC_DG_CASE(1, 0, 0)
-        EPIC_DG_CASE(1, 0, 1)
-        EPIC_DG_CASE(1, 1, 0)
-        EPIC_DG_CASE(1, 1, 1)
-        EPIC_DG_CASE(2, 0, 0)
-        EPIC_DG_CASE(2, 0, 1)
-        EPIC_DG_CASE(2, 1, 0)
-        EPIC_DG_CASE(2, 1, 1)
+        EPIC_DG_CASE(0, 0, 0, 0)
+        EPIC_DG_CASE(0, 0, 1, 0)
+        EPIC_DG_CASE(0, 0, 0, 1)
+        EPIC_DG_CASE(0, 1, 0, 0)
+        EPIC_DG_CASE(0, 1, 1, 0)
+        EPIC_DG_CASE(0, 1, 0, 1)
+        EPIC_DG_CASE(1, 0, 0, 0)
+        EPIC_DG_CASE(1, 0, 1, 0)
+        EPIC_DG_CASE(1, 0, 0, 1)
+        EPIC_DG_CASE(1, 1, 0, 0)
+        EPIC_DG_CASE(1, 1, 1, 0)
+        EPIC_DG_CASE(1, 1, 0, 1)
+        EPIC_DG_CASE(2, 0, 0, 0)
+        EPIC_DG_CASE(2, 0, 1, 0)
+        EPIC_DG_CASE(2, 0, 0, 1)
+        EPIC_DG_CASE(2, 1, 0, 0)
+        EPIC_DG_CASE(2, 1, 1, 0)
+        EPIC_DG_CASE(2, 1, 0, 1)
 #undef EPIC_DG_CASE
         default:
             return cudaErrorInvalidValue;

@@ -24,7 +24,8 @@ SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
            "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine", "epic_fx_image",
            "epic_sync", "epic_set_wait_limit")
-XFORM_FFT, XFORM_DFTGEMM = 0, 1
+XFORM_FFT, XFORM_DFTGEMM, XFORM_DFTGEMM_FP16 = 0, 1, 2
+XFORMS = {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM, "dftgemm_fp16": XFORM_DFTGEMM_FP16}
 
 _lib = None
 
@@ -260,8 +261,10 @@ class Plan:
         self.info = epic_plan_info(self._h)
 
     def set_transform(self, xform):
-        """'fft' (FP32 shared-memory FFT) or 'dftgemm' (tensor-core DFT, FP16 hi+lo, N_p = 128)."""
-        epic_set_transform(self._h, {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM}[xform])
+        """'fft' (FP32 shared-memory FFT), 'dftgemm' (tensor-core DFT, FP16 hi+lo, N_p = 128 or
+        256) or 'dftgemm_fp16' (reduced precision: FP16 gridding operands and one FP16 product
+        per real product, N_p = 128)."""
+        epic_set_transform(self._h, XFORMS[xform])
         self.xform = xform
         return self
 
