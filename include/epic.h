@@ -62,9 +62,11 @@ typedef enum {
     EPIC_XFORM_FFT = 0,         /* FP32 shared-memory FFT (all sizes; the default) */
     EPIC_XFORM_DFTGEMM = 1,     /* dense DFT on the tensor cores, FP16 hi+lo operands, FP32
                                    accumulation (N_p = 128 and 256) */
-    EPIC_XFORM_DFTGEMM_FP16 = 2 /* reduced precision: FP16 gridding operands (weights and gained
+    EPIC_XFORM_DFTGEMM_FP16 = 2,/* reduced precision: FP16 gridding operands (weights and gained
                                    voltages rounded to FP16, products exact, FP32 sums) and one
                                    FP16 product per real product of the DFT (N_p = 128) */
+    EPIC_XFORM_FFT_TWOPASS = 3  /* FP32 FFT as a row pass and a column pass with the row-
+                                   transformed grid staged in device memory (N_p = 512) */
 } epic_xform;
 
 /*
@@ -117,7 +119,12 @@ epic_status epic_create(epic_plan **plan, int n_ant, const double *pos_xy,
  * one FP16 product with FP32 accumulation (no lo parts): about a third of the tensor work, with
  * an error of about 1e-3 relative L2 against the exact image instead of about 1e-6.  The first
  * call with a tensor-core form uploads the plan's DFT operand tables (64 KB for n_pad 128,
- * 256 KB for 256).  epic_image_backward always uses the FFT form.
+ * 256 KB for 256).  EPIC_XFORM_FFT_TWOPASS (n_pad == 512) computes the same FP32 transform as the
+ * default form in two passes over every SM instead of one 16-CTA cluster per image (only one
+ * such cluster fits a GPC): the row pass writes each sample's row-transformed grid (1 MB) to a
+ * scratch buffer the plan allocates on the first call (4 x SMs samples, about 608 MB on 152
+ * SMs), the column pass reads it back; no cross-polarisation variant.  epic_image_backward
+ * always uses the FFT form.
  */
 epic_status epic_set_transform(epic_plan *plan, int xform);
 
@@ -330,8 +337,9 @@ epic_status epic_plan_info(const epic_plan *plan, int64_t *nnz, int64_t *n_cells
  * Batches: many plans (e.g. heterogeneous sub-arrays, each with its own antennas, kernels,
  * grid and channels) imaged by one persistent launch per padded-size class, the classes
  * forked onto internal streams and joined back into the caller's stream.  The stacking of
- * data streams for array operations is App. A.3's; the batch object owns its streams and
- * events only, so epic_batch_image allocates nothing and can be captured in a CUDA graph.
+ * data streams for array operations is App. A.3's; the batch object owns its streams, events
+ * and (for N_p = 512 classes) the two-pass form's scratch buffers, all allocated by
+ * epic_batch_create, so epic_batch_image allocates nothing and can be captured in a CUDA graph.
  * Plans must share the device and the voltage format; at most 64 plans per size class are
  * walked by one launch (more are split into further launches).
  */
@@ -352,9 +360,11 @@ epic_status epic_batch_image(epic_batch *batch, const void *const *volt, const i
 
 /*
  * Autotune the batch on representative inputs (same arguments as epic_batch_image; accum is
- * overwritten): for each size class, the number of resident CTAs (all, 3/4 or 1/2) that runs it
- * fastest, then whether the classes run faster concurrently or back to back.  Synchronises the
- * stream; not capturable.  The choice is kept in the batch.
+ * overwritten): for each size class, the kernel form and worker count that run it fastest
+ * alone -- the persistent form with all, 3/4 or 1/2 of its resident CTAs (clusters), and for
+ * N_p = 512 classes also the two-pass form -- then whether the classes run faster concurrently
+ * or back to back.  Synchronises the stream; not capturable.  The choice is kept in the batch
+ * (epic_batch_class reports it).
  */
 epic_status epic_batch_autotune(epic_batch *batch, const void *const *volt, const int *n_time,
                                 const float *const *gains, double *const *accum, void *stream);
@@ -363,6 +373,14 @@ epic_status epic_batch_autotune(epic_batch *batch, const void *const *volt, cons
  * (0 = all resident; at most max_workers entries written).  Any pointer may be NULL. */
 epic_status epic_batch_info(const epic_batch *batch, int *n_classes, int *concurrent, int *workers,
                             int max_workers);
+
+/* Size class k of the batch (0 .. n_classes - 1): its padded size, its worker cap (0 = all
+ * resident) and its kernel form, 0 = persistent (one CTA or cluster per image in flight), 1 =
+ * two-pass (N_p = 512 classes: a row pass and a column pass over every SM with the row-
+ * transformed grids staged in a scratch buffer the batch allocates at creation, 4 x SMs samples
+ * of 1 MB for each such class).  The form is what epic_batch_autotune chose (persistent until
+ * then).  Any out-pointer may be NULL. */
+epic_status epic_batch_class(const epic_batch *batch, int k, int *n_pad, int *workers, int *form);
 
 /* Release the batch (not its plans).  NULL is accepted. */
 void epic_batch_destroy(epic_batch *batch);

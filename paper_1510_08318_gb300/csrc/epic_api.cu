@@ -69,6 +69,7 @@ void free_plan(epic_plan* p) {
     cudaFree(p->dg_wim);
     cudaFree(p->dg_ant);
     cudaFree(p->status);
+    cudaFree(p->tp_scratch);
     delete p;
 }
 
@@ -481,6 +482,29 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
         plan->xform = xform;
         return EPIC_OK;
     }
+    if (xform == EPIC_XFORM_FFT_TWOPASS) {
+        if (plan->n_pad != 512)
+            return epic_fail(EPIC_EUNSUPPORTED, "the two-pass FFT form exists for n_pad 512 only (plan: %d)", plan->n_pad);
+        EpicDeviceGuard guard(plan->device);
+        if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+        int smem_optin = 0;
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+        if (epic::twopass_rows_smem_bytes(plan->n_ant) > (size_t)smem_optin)
+            return epic_fail(EPIC_EUNSUPPORTED, "%d antennas do not fit the two-pass row kernel's shared memory",
+                             plan->n_ant);
+        if (!plan->tp_scratch) {
+            const int chunk = 4 * plan->n_sm;
+            cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&plan->tp_scratch), epic::twopass_scratch_bytes(chunk));
+            if (e != cudaSuccess) {
+                plan->tp_scratch = nullptr;
+                return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "two-pass scratch: %s", cudaGetErrorString(e))
+                                                      : epic_cuda_fail(e, "two-pass scratch");
+            }
+            plan->tp_chunk = chunk;
+        }
+        plan->xform = xform;
+        return EPIC_OK;
+    }
     if (xform != EPIC_XFORM_DFTGEMM && xform != EPIC_XFORM_DFTGEMM_FP16) return epic_fail(EPIC_EINVAL, "xform %d", xform);
     if (plan->n_pad != 128 && plan->n_pad != 256)
         return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad 128 or 256 (plan: %d)", plan->n_pad);
@@ -571,6 +595,19 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
                                                       plan->xform == EPIC_XFORM_DFTGEMM_FP16)
                                : epic::launch_dftgemm256(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st);
         s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core imaging kernel launch");
+    } else if (plan->xform == EPIC_XFORM_FFT_TWOPASS) {
+        epic::SegList L;
+        L.seg[0] = a;
+        L.first[0] = 0;
+        L.first[1] = (int)a.n_items;
+        L.weight[0] = 1;
+        L.cost[0] = 0;
+        L.cost[1] = a.n_items;
+        L.n_seg = 1;
+        L.max_ant = a.n_ant;
+        L.max_workers = 0;
+        e = epic::launch_fwd512_twopass(plan->vdt, L, plan->n_sm, st, plan->tp_scratch, plan->tp_chunk);
+        s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "two-pass imaging kernels launch");
     } else {
         s = launch_fwd(plan, a, st);
     }
@@ -647,9 +684,10 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
-    if (plan->xform == EPIC_XFORM_DFTGEMM_FP16)
-        return epic_fail(EPIC_EUNSUPPORTED, "the reduced-precision tensor-core form has no cross-polarisation variant; "
-                                            "use EPIC_XFORM_DFTGEMM or EPIC_XFORM_FFT");
+    if (plan->xform == EPIC_XFORM_DFTGEMM_FP16 || plan->xform == EPIC_XFORM_FFT_TWOPASS)
+        return epic_fail(EPIC_EUNSUPPORTED, "the %s form has no cross-polarisation variant; use EPIC_XFORM_FFT%s",
+                         plan->xform == EPIC_XFORM_FFT_TWOPASS ? "two-pass" : "reduced-precision tensor-core",
+                         plan->xform == EPIC_XFORM_FFT_TWOPASS ? "" : " or EPIC_XFORM_DFTGEMM");
     const bool dg = plan->xform == EPIC_XFORM_DFTGEMM;
     if (dg && plan->n_pad != 128)
         return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core cross-polarisation form exists for n_pad 128 only; "

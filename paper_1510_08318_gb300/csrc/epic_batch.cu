@@ -14,12 +14,20 @@
 
 namespace {
 
+// Kernel forms a size class can run in: the persistent one-launch form (one CTA, or one cluster
+// for N_p >= 256, per image in flight) and, for N_p = 512, the two-pass form (a row pass and a
+// column pass over every SM, the row-transformed grids staged in the class's scratch buffer).
+enum ClassForm { kFormPersistent = 0, kFormTwoPass = 1 };
+
 struct ClassRun {
     int n_pad = 0;
     std::vector<int> members;      // plan indices (at most epic::kMaxSeg)
     cudaStream_t stream = nullptr;
     cudaEvent_t join = nullptr;
     int max_workers = 0;           // 0 = every resident CTA (cluster)
+    int form = kFormPersistent;
+    float2* scratch = nullptr;     // N_p = 512: the two-pass form's scratch (tp_chunk items)
+    int tp_chunk = 0;
 };
 
 }  // namespace
@@ -39,6 +47,7 @@ void destroy_batch(epic_batch* b) {
     for (ClassRun& c : b->classes) {
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.join) cudaEventDestroy(c.join);
+        if (c.scratch) cudaFree(c.scratch);
     }
     if (b->fork) cudaEventDestroy(b->fork);
     delete b;
@@ -74,7 +83,7 @@ epic_status check_call(const epic_batch* b, const void* const* volt, const int* 
 // Enqueue one class on stream st: zero its accumulators, one persistent launch, epilogues.
 epic_status run_class(const epic_batch* b, const ClassRun& c, const void* const* volt, const int* n_time,
                       const float* const* gains, double* const* accum, float* const* image, cudaStream_t st,
-                      int max_workers) {
+                      int max_workers, int form) {
     epic::SegList L;
     L.n_seg = (int)c.members.size();
     L.max_ant = 0;
@@ -95,7 +104,9 @@ epic_status run_class(const epic_batch* b, const ClassRun& c, const void* const*
         L.cost[s + 1] = L.cost[s] + L.weight[s] * a.n_items;
         L.max_ant = std::max(L.max_ant, p->n_ant);
     }
-    cudaError_t e = epic_launch_fwd_list(c.n_pad, b->vdt, L, b->n_sm, st);
+    cudaError_t e = form == kFormTwoPass
+                        ? epic::launch_fwd512_twopass(b->vdt, L, b->n_sm, st, c.scratch, c.tp_chunk)
+                        : epic_launch_fwd_list(c.n_pad, b->vdt, L, b->n_sm, st);
     if (e != cudaSuccess) return epic_cuda_fail(e, "batched imaging kernel launch");
     if (image) {
         for (int i : c.members) {
@@ -113,7 +124,7 @@ epic_status enqueue(epic_batch* b, const void* const* volt, const int* n_time, c
                     double* const* accum, float* const* image, cudaStream_t st) {
     if (!b->concurrent) {
         for (const ClassRun& c : b->classes) {
-            epic_status s = run_class(b, c, volt, n_time, gains, accum, image, st, c.max_workers);
+            epic_status s = run_class(b, c, volt, n_time, gains, accum, image, st, c.max_workers, c.form);
             if (s != EPIC_OK) return s;
         }
         return EPIC_OK;
@@ -128,7 +139,7 @@ epic_status enqueue(epic_batch* b, const void* const* volt, const int* n_time, c
             s = epic_cuda_fail(e, "fork wait");
             break;
         }
-        epic_status r = run_class(b, c, volt, n_time, gains, accum, image, c.stream, c.max_workers);
+        epic_status r = run_class(b, c, volt, n_time, gains, accum, image, c.stream, c.max_workers, c.form);
         cudaError_t ej = cudaEventRecord(c.join, c.stream);
         if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, c.join, 0);
         if (r != EPIC_OK) {
@@ -178,6 +189,19 @@ epic_status epic_batch_create(epic_batch** batch, int n_plans, epic_plan* const*
     for (ClassRun& c : b->classes) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming);
+        // the two-pass form's scratch, so that the autotuner can choose it and a call allocates
+        // nothing (each N_p = 512 class its own: classes may run concurrently)
+        if (e == cudaSuccess && c.n_pad == 512) {
+            int max_ant = 0;
+            for (int i : c.members) max_ant = std::max(max_ant, plans[i]->n_ant);
+            int smem_optin = 0;
+            cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+            if (epic::twopass_rows_smem_bytes(max_ant) <= (size_t)smem_optin) {
+                c.tp_chunk = 4 * b->n_sm;
+                e = cudaMalloc(reinterpret_cast<void**>(&c.scratch), epic::twopass_scratch_bytes(c.tp_chunk));
+                if (e != cudaSuccess) c.scratch = nullptr;
+            }
+        }
     }
     if (e != cudaSuccess) {
         destroy_batch(b);
@@ -239,24 +263,37 @@ epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, cons
         ms = best;
         return EPIC_OK;
     };
-    // 1) per class: the worker count (all resident, 3/4, 1/2 of them) that runs it fastest alone
+    // 1) per class: the kernel form and worker count that run it fastest alone -- the persistent
+    //    form with all, 3/4 or 1/2 of its resident CTAs (clusters), and for N_p = 512 also the
+    //    two-pass form on every SM
     std::vector<float> alone(batch->classes.size(), 0.f);
     for (size_t k = 0; k < batch->classes.size() && s == EPIC_OK; ++k) {
         ClassRun& c = batch->classes[k];
         const int full = epic_resident_workers(c.n_pad, batch->vdt, batch->plans, c.members, batch->n_sm);
-        int best_w = 0;
+        int best_w = 0, best_f = kFormPersistent;
         float best_t = 1e30f;
         for (int frac4 : {4, 3, 2}) {
             const int w = frac4 == 4 ? 0 : std::max(1, full * frac4 / 4);
             float t = 0.f;
-            s = time_it([&] { return run_class(batch, c, volt, n_time, gains, accum, nullptr, st, w); }, t);
+            s = time_it([&] { return run_class(batch, c, volt, n_time, gains, accum, nullptr, st, w, kFormPersistent); },
+                        t);
             if (s != EPIC_OK) break;
             if (t < best_t) {
                 best_t = t;
                 best_w = w;
             }
         }
+        if (s == EPIC_OK && c.scratch) {
+            float t = 0.f;
+            s = time_it([&] { return run_class(batch, c, volt, n_time, gains, accum, nullptr, st, 0, kFormTwoPass); }, t);
+            if (s == EPIC_OK && t < best_t) {
+                best_t = t;
+                best_w = 0;
+                best_f = kFormTwoPass;
+            }
+        }
         c.max_workers = best_w;
+        c.form = best_f;
         alone[k] = best_t;
     }
     // 2) classes back to back vs concurrently (forked streams)
@@ -271,6 +308,18 @@ epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, cons
         if (s == EPIC_OK) batch->concurrent = t_con < t_seq;
     }
     return s;
+}
+
+epic_status epic_batch_class(const epic_batch* batch, int k, int* n_pad, int* workers, int* form) {
+    epic_clear_error();
+    if (!batch) return epic_fail(EPIC_EINVAL, "batch is NULL");
+    if (k < 0 || k >= (int)batch->classes.size())
+        return epic_fail(EPIC_EINVAL, "class %d of %d", k, (int)batch->classes.size());
+    const ClassRun& c = batch->classes[k];
+    if (n_pad) *n_pad = c.n_pad;
+    if (workers) *workers = c.max_workers;
+    if (form) *form = c.form;
+    return EPIC_OK;
 }
 
 epic_status epic_batch_info(const epic_batch* batch, int* n_classes, int* concurrent, int* workers, int max_workers) {

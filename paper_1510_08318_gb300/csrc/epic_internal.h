@@ -187,6 +187,14 @@ void dftgemm256_tables(std::vector<uint16_t>& out);
 cudaError_t launch_dftgemm256(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm,
                               cudaStream_t st);
 
+// Two-pass form for N_p = 512 (moff_np512x2.cu): a row pass writes each item's row-transformed
+// grid (256 x 512 complex64, 1 MB) to scratch, a column pass transforms, squares and accumulates;
+// items in chunks of chunk_items, scratch of twopass_scratch_bytes(chunk_items), caller-owned.
+size_t twopass_scratch_bytes(int chunk_items);
+size_t twopass_rows_smem_bytes(int max_ant);
+cudaError_t launch_fwd512_twopass(int vdt, const SegList& L, int n_sm, cudaStream_t st, float2* scratch,
+                                  int chunk_items);
+
 // Standalone gridder: samples per work unit (8, or 4 when 8 do not fit shared memory) and launch.
 size_t grid_smem_bytes(int n_ant, int tb);
 int grid_samples_per_unit(int n_ant, size_t smem_optin);

@@ -36,6 +36,8 @@ struct epic_plan {
     float* dg_wim = nullptr;
     uint16_t* dg_ant = nullptr;
     float wsum_max = 0.f;         // max over cells of sum_a |M[g, a]|
+    float2* tp_scratch = nullptr; // two-pass form (N_p = 512): row-transformed grids of one chunk
+    int tp_chunk = 0;             // items per chunk of the two-pass form
     int* status = nullptr;        // device status word (epic::kStatus* bits), read by epic_sync
     int wait_tries = 1000;        // tries of each bounded tensor-core wait (about 1 ms each)
 };

@@ -23,9 +23,10 @@ VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
            "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine", "epic_fx_image",
-           "epic_sync", "epic_set_wait_limit")
-XFORM_FFT, XFORM_DFTGEMM, XFORM_DFTGEMM_FP16 = 0, 1, 2
-XFORMS = {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM, "dftgemm_fp16": XFORM_DFTGEMM_FP16}
+           "epic_sync", "epic_set_wait_limit", "epic_batch_class")
+XFORM_FFT, XFORM_DFTGEMM, XFORM_DFTGEMM_FP16, XFORM_FFT_TWOPASS = 0, 1, 2, 3
+XFORMS = {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM, "dftgemm_fp16": XFORM_DFTGEMM_FP16,
+          "fft_twopass": XFORM_FFT_TWOPASS}
 
 _lib = None
 
@@ -82,6 +83,8 @@ def load(path=LIB_PATH):
     lib.epic_batch_image.argtypes = [vp, pp, ctypes.POINTER(i32), pp, pp, pp, vp]
     lib.epic_batch_autotune.restype = i32
     lib.epic_batch_autotune.argtypes = [vp, pp, ctypes.POINTER(i32), pp, pp, vp]
+    lib.epic_batch_class.restype = i32
+    lib.epic_batch_class.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.epic_batch_info.restype = i32
     lib.epic_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i32]
     lib.epic_batch_destroy.restype = None
@@ -229,11 +232,18 @@ def epic_batch_autotune(batch, volt, n_time, gains, accum, stream):
                                       _ptr_array(accum), stream))
 
 
+def epic_batch_class(batch, k):
+    npad, w, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().epic_batch_class(batch, int(k), ctypes.byref(npad), ctypes.byref(w), ctypes.byref(f)))
+    return {"n_pad": npad.value, "workers": w.value, "form": ("persistent", "two-pass")[f.value]}
+
+
 def epic_batch_info(batch, max_classes=16):
     nc, conc = ctypes.c_int(), ctypes.c_int()
     w = (ctypes.c_int * max_classes)()
     _check(load().epic_batch_info(batch, ctypes.byref(nc), ctypes.byref(conc), w, max_classes))
-    return {"n_classes": nc.value, "concurrent": bool(conc.value), "workers": list(w)[:nc.value]}
+    return {"n_classes": nc.value, "concurrent": bool(conc.value), "workers": list(w)[:nc.value],
+            "classes": [epic_batch_class(batch, k) for k in range(nc.value)]}
 
 
 def epic_batch_destroy(batch):
@@ -262,8 +272,9 @@ class Plan:
 
     def set_transform(self, xform):
         """'fft' (FP32 shared-memory FFT), 'dftgemm' (tensor-core DFT, FP16 hi+lo, N_p = 128 or
-        256) or 'dftgemm_fp16' (reduced precision: FP16 gridding operands and one FP16 product
-        per real product, N_p = 128)."""
+        256), 'dftgemm_fp16' (reduced precision: FP16 gridding operands and one FP16 product
+        per real product, N_p = 128) or 'fft_twopass' (FP32 FFT in a row and a column pass
+        through a scratch buffer, N_p = 512)."""
         epic_set_transform(self._h, XFORMS[xform])
         self.xform = xform
         return self

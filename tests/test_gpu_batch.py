@@ -25,7 +25,9 @@ def epic():
 
 @pytest.fixture(scope="module")
 def setup(epic):
-    subs = synth.workload_batch(n_time=6, max_chan=3)
+    # the batching configuration's 128 samples per sub-array (channels capped at 3 to keep the
+    # oracle checks short)
+    subs = synth.workload_batch(n_time=128, max_chan=3)
     plans = [epic.Plan.from_workload(w) for w in subs]
     volts = [torch.from_numpy(np.ascontiguousarray(w.volt_raw)).cuda() for w in subs]
     batch = epic.Batch(plans)
@@ -88,7 +90,9 @@ def test_batch_graph_capture_and_autotune(epic, setup):
     for a, b in zip(ref, img2):
         assert rel(b.cpu().numpy(), a) < 1e-6
     info = batch.autotune(volts, acc)
-    assert info["n_classes"] == len(info["workers"])
+    assert info["n_classes"] == len(info["workers"]) == len(info["classes"])
+    for c in info["classes"]:
+        assert c["form"] == "persistent" or (c["form"] == "two-pass" and c["n_pad"] == 512)
     batch.image(volts, acc, img)
     torch.cuda.synchronize()
     for a, b in zip(ref, img):
