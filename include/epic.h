@@ -385,6 +385,32 @@ epic_status epic_batch_class(const epic_batch *batch, int k, int *n_pad, int *wo
 /* Release the batch (not its plans).  NULL is accepted. */
 void epic_batch_destroy(epic_batch *batch);
 
+/*
+ * epic_image_noalloc -- epic_image for an n_pad == 512 plan, in the two-pass form, that allocates
+ * no device memory.  The paper has no counterpart: this call exists for callers that cannot call
+ * cudaMalloc while they image -- a pipeline whose device memory is all reserved up front by
+ * another allocator, or a real-time data path that may not stop on an allocation between
+ * samples.  The two-pass form stages each sample's row-transformed grid (1 MB) in scratch
+ * memory; instead of a buffer of the plan (EPIC_XFORM_FFT_TWOPASS allocates one), this call uses
+ * a device array built into the library: 64 MB, held by every GPU that loads the library until
+ * the process exits.
+ *
+ *   volt, n_time, gains, accum, power, t_prev, image, autocorr, stream
+ *               as for epic_image (the plan's transform setting is not used).
+ *   chunk_items samples staged per pass, 1 .. 64 (the array's capacity); a larger value is
+ *               EPIC_EINVAL before anything is launched.  Any number of samples is imaged, in
+ *               chunks of this size; more samples per chunk keep more SMs busy.
+ *
+ * The first call on a device looks up the array's device address (with that device current) and
+ * keeps it; make that first call before any stream capture that might include this call.  Every
+ * call on a device shares the array and leaves its last chunk's rows in it; nothing in it needs
+ * to start at zero.  Calls whose kernels overlap on the GPU (two streams, or two host threads)
+ * race on the array: order them.  The call performs no cudaMalloc, cudaFree or other allocation.
+ */
+epic_status epic_image_noalloc(const epic_plan *plan, const void *volt, int n_time, const float *gains,
+                               double *accum, double *power, int64_t t_prev, float *image, float *autocorr,
+                               int chunk_items, void *stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char *epic_last_error(void);
 

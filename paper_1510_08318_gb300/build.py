@@ -17,7 +17,7 @@ LIB = os.path.join(OUT, "libepic.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["epic_api.cu", "finalize.cu", "moff_np32.cu", "moff_np64.cu", "moff_np128.cu", "moff_np256.cu",
-           "moff_np512.cu", "moff_dftgemm.cu", "moff_dftgemm256.cu", "moff_np512x2.cu", "epic_batch.cu", "grid.cu", "xeng.cu", "fengine.cu"]
+           "moff_np512.cu", "moff_dftgemm.cu", "moff_dftgemm256.cu", "moff_np512x2.cu", "epic_noalloc.cu", "epic_batch.cu", "grid.cu", "xeng.cu", "fengine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]

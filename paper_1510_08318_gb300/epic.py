@@ -23,7 +23,7 @@ VOLT_DTYPES = {"c64": 0, "f16": 1, "ci4": 2}
 SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "epic_plan_info",
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
            "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine", "epic_fx_image",
-           "epic_sync", "epic_set_wait_limit", "epic_batch_class")
+           "epic_sync", "epic_set_wait_limit", "epic_batch_class", "epic_image_noalloc")
 XFORM_FFT, XFORM_DFTGEMM, XFORM_DFTGEMM_FP16, XFORM_FFT_TWOPASS = 0, 1, 2, 3
 XFORMS = {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM, "dftgemm_fp16": XFORM_DFTGEMM_FP16,
           "fft_twopass": XFORM_FFT_TWOPASS}
@@ -52,6 +52,8 @@ def load(path=LIB_PATH):
     lib.epic_destroy.argtypes = [vp]
     lib.epic_image.restype = i32
     lib.epic_image.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
+    lib.epic_image_noalloc.restype = i32
+    lib.epic_image_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, i32, vp]
     lib.epic_image_backward.restype = i32
     lib.epic_image_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.epic_image_xpol.restype = i32
@@ -140,6 +142,11 @@ def epic_destroy(plan):
 
 def epic_image(plan, volt, n_time, gains, accum, power, t_prev, image, autocorr, stream):
     _check(load().epic_image(plan, volt, int(n_time), gains, accum, power, int(t_prev), image, autocorr, stream))
+
+
+def epic_image_noalloc(plan, volt, n_time, gains, accum, power, t_prev, image, autocorr, chunk_items, stream):
+    _check(load().epic_image_noalloc(plan, volt, int(n_time), gains, accum, power, int(t_prev), image, autocorr,
+                                     int(chunk_items), stream))
 
 
 def epic_image_backward(plan, volt, n_time, gains, grad_image, grad_gains, stream):
