@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -70,6 +71,9 @@ void free_plan(epic_plan* p) {
     cudaFree(p->dg_ant);
     cudaFree(p->status);
     cudaFree(p->tp_scratch);
+    cudaFree(p->fx_lag_ptr);
+    cudaFree(p->fx_lag_pair);
+    cudaFree(p->fx_lag_w);
     delete p;
 }
 
@@ -440,6 +444,9 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
         return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
                                               : epic_cuda_fail(e, "plan upload");
     }
+    p->fx_ptr_h = fxptr;
+    p->fx_ent_h = fxent;
+    p->fx_wim_h = fxwim;
     if ((e = upload(&p->status, std::vector<int>(1, 0))) != cudaSuccess) {
         free_plan(p);
         return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "status word: %s", cudaGetErrorString(e))
@@ -448,6 +455,103 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
     *plan = p;
     return EPIC_OK;
 }
+
+namespace {
+
+std::mutex g_fx_lag_mu;
+constexpr int64_t kMaxFxLagEntries = 1LL << 27;   // 1.5 GB of device tables at most
+
+// The FX route's antenna-pair kernels of every ordered pair (autocorrelations included),
+// B_ab(d) = sum over mapping entries e of a and f of b with g_e - g_f = d of w_e conj(w_f)
+// (Eq. "e-field-conv": the cross-correlation of the two sampled footprints), summed per pair in
+// float64 and grouped by wrapped lag cell d into a CSR, uploaded to the plan.  Built once, by the
+// first epic_fx_image call.
+epic_status build_fx_lag_table(const epic_plan* p) {
+    const int A = p->n_ant, NP = p->n_pad, MSK = NP - 1;
+    int lg = 0;
+    while ((1 << lg) < NP) ++lg;
+    const std::vector<int>& ptr = p->fx_ptr_h;
+    const std::vector<int2>& ent = p->fx_ent_h;
+    const bool cw = p->fx_wim != nullptr;
+    std::vector<int> y0(A, 1 << 30), y1(A, -1), x0(A, 1 << 30), x1(A, -1);
+    for (int a = 0; a < A; ++a)
+        for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+            const int gy = ent[e].y >> 16, gx = ent[e].y & 0xFFFF;
+            y0[a] = std::min(y0[a], gy); y1[a] = std::max(y1[a], gy);
+            x0[a] = std::min(x0[a], gx); x1[a] = std::max(x1[a], gx);
+        }
+    int64_t bound = 0;
+    for (int a = 0; a < A; ++a)
+        for (int b = 0; b < A; ++b)
+            if (y1[a] >= 0 && y1[b] >= 0)
+                bound += (int64_t)(y1[a] - y0[a] + y1[b] - y0[b] + 1) * (x1[a] - x0[a] + x1[b] - x0[b] + 1);
+    if (bound > kMaxFxLagEntries)
+        return epic_fail(EPIC_EUNSUPPORTED, "the antenna-pair lag table would hold up to %lld entries (limit %lld)",
+                         (long long)bound, (long long)kMaxFxLagEntries);
+    std::vector<int> lag, pair;
+    std::vector<float2> w;
+    lag.reserve((size_t)bound);
+    pair.reserve((size_t)bound);
+    w.reserve((size_t)bound);
+    std::vector<std::complex<double>> win;
+    auto weight = [&](int e) {
+        float re;
+        std::memcpy(&re, &ent[e].x, sizeof(float));
+        return std::complex<double>(re, cw ? p->fx_wim_h[e] : 0.0);
+    };
+    for (int a = 0; a < A; ++a) {
+        if (y1[a] < 0) continue;
+        for (int b = 0; b < A; ++b) {
+            if (y1[b] < 0) continue;
+            const int dy0 = y0[a] - y1[b], dx0 = x0[a] - x1[b];
+            const int H = y1[a] - y0[a] + y1[b] - y0[b] + 1, W = x1[a] - x0[a] + x1[b] - x0[b] + 1;
+            win.assign((size_t)H * W, std::complex<double>(0.0, 0.0));
+            for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+                const std::complex<double> we = weight(e);
+                const int gye = ent[e].y >> 16, gxe = ent[e].y & 0xFFFF;
+                for (int f = ptr[b]; f < ptr[b + 1]; ++f) {
+                    const int dy = gye - (ent[f].y >> 16), dx = gxe - (ent[f].y & 0xFFFF);
+                    win[(size_t)(dy - dy0) * W + (dx - dx0)] += we * std::conj(weight(f));
+                }
+            }
+            for (int i = 0; i < H; ++i)
+                for (int j = 0; j < W; ++j) {
+                    const std::complex<double> v = win[(size_t)i * W + j];
+                    if (v == std::complex<double>(0.0, 0.0)) continue;
+                    lag.push_back((((dy0 + i) & MSK) << lg) | ((dx0 + j) & MSK));
+                    pair.push_back(a * A + b);
+                    w.push_back(make_float2(float(v.real()), float(v.imag())));
+                }
+        }
+    }
+    // counting sort by lag cell
+    std::vector<int> lptr((size_t)NP * NP + 1, 0);
+    for (int l : lag) lptr[(size_t)l + 1]++;
+    for (size_t i = 0; i + 1 < lptr.size(); ++i) lptr[i + 1] += lptr[i];
+    std::vector<int> spair(pair.size()), fill(lptr.begin(), lptr.end() - 1);
+    std::vector<float2> sw(w.size());
+    for (size_t i = 0; i < lag.size(); ++i) {
+        const int at = fill[lag[i]]++;
+        spair[at] = pair[i];
+        sw[at] = w[i];
+    }
+    cudaError_t e;
+    if ((e = upload(&p->fx_lag_ptr, lptr)) != cudaSuccess || (e = upload(&p->fx_lag_pair, spair)) != cudaSuccess ||
+        (e = upload(&p->fx_lag_w, sw)) != cudaSuccess) {
+        cudaFree(p->fx_lag_ptr);
+        cudaFree(p->fx_lag_pair);
+        cudaFree(p->fx_lag_w);
+        p->fx_lag_ptr = nullptr;
+        p->fx_lag_pair = nullptr;
+        p->fx_lag_w = nullptr;
+        return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "FX lag table: %s", cudaGetErrorString(e))
+                                              : epic_cuda_fail(e, "FX lag table upload");
+    }
+    p->fx_lag_n = (int64_t)spair.size();
+    return EPIC_OK;
+}
+
+}  // namespace
 
 epic_status epic_set_wait_limit(epic_plan* plan, int tries) {
     epic_clear_error();
@@ -835,13 +939,20 @@ epic_status epic_fx_image(const epic_plan* plan, const float* vis, float* image,
         return epic_fail(EPIC_EUNSUPPORTED, "the FX imaging kernel holds the lag plane in shared memory: n_pad <= 128");
     EpicDeviceGuard guard(plan->device);
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
+    {
+        std::lock_guard<std::mutex> lock(g_fx_lag_mu);
+        if (plan->fx_lag_n < 0) {
+            const epic_status st = build_fx_lag_table(plan);
+            if (st != EPIC_OK) return st;
+        }
+    }
     epic::FxArgs a;
     a.vis = reinterpret_cast<const float2*>(vis);
     a.n_cp = plan->n_chan * plan->n_pol;
     a.n_ant = plan->n_ant;
-    a.ptr = plan->fx_ptr;
-    a.ent = plan->fx_ent;
-    a.wim = plan->fx_wim;
+    a.lag_ptr = plan->fx_lag_ptr;
+    a.lag_pair = plan->fx_lag_pair;
+    a.lag_w = plan->fx_lag_w;
     a.image = image;
     const cudaError_t e = epic::launch_fx_image(plan->n_pad, a, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "FX imaging kernel launch");

@@ -99,9 +99,9 @@ size_t xeng_smem_bytes();
 struct FxArgs {
     const float2* vis;         // [CP][A][A]
     int n_cp, n_ant;
-    const int* ptr;            // antenna-major mapping [A+1]
-    const int2* ent;           // {weight re bits, (gy << 16) | gx}
-    const float* wim;          // or nullptr
+    const int* lag_ptr;        // [N_p^2 + 1] CSR of the antenna-pair kernels by wrapped lag cell
+    const int* lag_pair;       // pair index a * A + b of each entry
+    const float2* lag_w;       // B_ab(d) of each entry
     float* image;              // [CP][N_p][N_p]
 };
 cudaError_t launch_fx_image(int n_pad, const FxArgs& a, cudaStream_t st);

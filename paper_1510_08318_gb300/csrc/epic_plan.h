@@ -23,6 +23,15 @@ struct epic_plan {
     int* fx_ptr = nullptr;       // antenna-major mapping for the FX route's visibility gridding (N_p <= 128):
     int2* fx_ent = nullptr;      // [A+1] row pointers, {weight re bits, (gy << 16) | gx}
     float* fx_wim = nullptr;     // weight imaginary parts, or nullptr
+    std::vector<int> fx_ptr_h;   // the same antenna-major mapping on the host (for the lag table)
+    std::vector<int2> fx_ent_h;
+    std::vector<float> fx_wim_h;
+    // The FX route's antenna-pair kernels B_ab(d) grouped by lag cell d (CSR over the N_p^2 wrapped
+    // lags: pair index a * A + b and weight), built by the first epic_fx_image call
+    mutable int* fx_lag_ptr = nullptr;
+    mutable int* fx_lag_pair = nullptr;
+    mutable float2* fx_lag_w = nullptr;
+    mutable int64_t fx_lag_n = -1;   // entries; -1 until built
     int* ant_ptr = nullptr;
     int2* ant_ent = nullptr;
     float* ant_wim = nullptr;

@@ -382,10 +382,10 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
 //   U(d) = sum_{a, b} V_ab B_ab(d),  B_ab(d) = sum_g M[g, a] conj(M[g - d, b]),
 //   I(k) = Re sum_d U(d) exp(+2 pi i d.k / N_p)  (image pixel order, k = 0 at the centre).
 // One CTA per (channel, pol).  The lag plane U (N_p x N_p, lags wrapped mod N_p; with
-// N_p >= 2 N_g - 1 none alias) is accumulated in shared memory: thread per antenna pair
-// (a, b), every pair of mapping entries (e of a, f of b) adds w_e conj(w_f) V_ab at the lag
-// g_e - g_f (shared-memory atomics).  Then a separable DFT in place: rows (each thread a
-// strided set of one row's outputs), columns straight to the image.
+// N_p >= 2 N_g - 1 none alias) is gathered into shared memory from the plan's table of the
+// antenna-pair kernels grouped by lag cell (B_ab(d) summed over the mapping entries of a and b
+// once, on the host): one warp per lag cell, no atomics.  Then a separable DFT in place: rows
+// (each thread a strided set of one row's outputs), columns straight to the image.
 constexpr int FX_NT = 512;
 
 template <int NP>
@@ -401,34 +401,41 @@ __global__ void __launch_bounds__(FX_NT) fx_image_kernel(const FxArgs a) {
         sincospi(2.0 * j / NP, &s, &c);
         TW[j] = make_float2(float(c), float(s));
     }
-    for (int i = tid; i < NPIX; i += FX_NT) U[i] = make_float2(0.f, 0.f);
-    __syncthreads();
+    // U(d) = sum over the pairs of lag cell d of V_ab B_ab(d): one warp per lag cell, its lanes
+    // taking every 32nd entry of the cell's list, a shuffle sum (no atomics)
     const float2* V = a.vis + (size_t)cp * A * A;
-    const long long n_pairs = (long long)A * A;
-    for (long long pr = tid; pr < n_pairs; pr += FX_NT) {
-        const int aa = (int)(pr / A), b = (int)(pr - (long long)aa * A);
-        const float2 v = __ldg(V + pr);
-        const int e0 = __ldg(a.ptr + aa), e1 = __ldg(a.ptr + aa + 1);
-        const int f0 = __ldg(a.ptr + b), f1 = __ldg(a.ptr + b + 1);
-        for (int e = e0; e < e1; ++e) {
-            const int2 ee = __ldg(a.ent + e);
-            const float2 we = make_float2(__int_as_float(ee.x), a.wim ? __ldg(a.wim + e) : 0.f);
-            const float2 ve = cmul(we, v);
-            const int gye = ee.y >> 16, gxe = ee.y & 0xFFFF;
-            for (int f = f0; f < f1; ++f) {
-                const int2 ff = __ldg(a.ent + f);
-                float2 t;
-                if (a.wim) {
-                    t = cmulc(ve, make_float2(__int_as_float(ff.x), __ldg(a.wim + f)));
-                } else {
-                    const float wf = __int_as_float(ff.x);
-                    t = make_float2(ve.x * wf, ve.y * wf);
-                }
-                const int idx = (((gye - (ff.y >> 16)) & MSK) << LG) | ((gxe - (ff.y & 0xFFFF)) & MSK);
-                atomicAdd(&U[idx].x, t.x);
-                atomicAdd(&U[idx].y, t.y);
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int d = warp; d < NPIX; d += FX_NT / 32) {
+        const int p0 = __ldg(a.lag_ptr + d), p1 = __ldg(a.lag_ptr + d + 1);
+        // four entries per lane per step, independent loads and sums, so that the dependent
+        // visibility gathers of several entries are in flight together
+        float2 acc4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc4[u] = make_float2(0.f, 0.f);
+        for (int q0 = p0 + lane; q0 < p1; q0 += 128) {
+            int pr[4];
+            float2 w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + 32 * u;
+                pr[u] = q < p1 ? __ldg(a.lag_pair + q) : -1;
+                w[u] = q < p1 ? __ldg(a.lag_w + q) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 v = pr[u] >= 0 ? __ldg(V + pr[u]) : make_float2(0.f, 0.f);
+                acc4[u].x = fmaf(v.x, w[u].x, fmaf(-v.y, w[u].y, acc4[u].x));
+                acc4[u].y = fmaf(v.x, w[u].y, fmaf(v.y, w[u].x, acc4[u].y));
             }
         }
+        float2 acc = make_float2((acc4[0].x + acc4[1].x) + (acc4[2].x + acc4[3].x),
+                                 (acc4[0].y + acc4[1].y) + (acc4[2].y + acc4[3].y));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) U[d] = acc;
     }
     __syncthreads();
     // rows: T(dy, ix) = sum_dx U(dy, dx) exp(+2 pi i dx (ix - NP/2) / NP); thread -> row dy,
