@@ -304,12 +304,17 @@ epic_status epic_correlate(const epic_plan *plan, const void *volt, int n_time, 
  *   vis       device [C][P][A][A] complex64.
  *   image     device [C][P][N_p][N_p] float32, image pixel order; overwritten.
  *
- * n_pad <= 128 (the lag plane is held in shared memory), else EPIC_EUNSUPPORTED.  The first
- * call builds, on the host, the plan's table of the antenna-pair kernels grouped by lag cell
- * (B_ab(d) of every ordered pair summed over the two footprints' entries: work grows as the
- * square of the mapping entries, 16 bytes of device memory per (pair, lag) entry, at most 2^27
- * entries, else EPIC_EUNSUPPORTED) and uploads it (synchronously, once); every call then gathers
- * U(d) cell by cell from it, without atomics, and transforms once per (channel, pol).
+ * n_pad <= 128 (the lag plane is transformed in shared memory), else EPIC_EUNSUPPORTED;
+ * A^2 * C * P below 2^31.  The first call builds, on the host, the plan's table of the
+ * antenna-pair kernels grouped by lag cell (B_ab(d) of every ordered pair summed over the two
+ * footprints' entries: work grows as the square of the mapping entries, 16 bytes of device
+ * memory per (pair, lag) entry, at most 2^27 entries, else EPIC_EUNSUPPORTED), uploads it
+ * (synchronously, once) and allocates the plan's imaging scratch (A^2 * C * P * 8 bytes for the
+ * visibilities in pair-major order, C * P * n_pad^2 * 8 bytes for the lag planes; EPIC_ENOMEM
+ * if that fails).  Every call then transposes vis into the scratch, gathers each lag plane U(d)
+ * cell by cell from the table (no atomics) and transforms each once (three launches).  The
+ * scratch belongs to the plan: calls on one plan whose kernels may overlap (two streams) race
+ * on it, so the caller orders them.
  */
 epic_status epic_fx_image(const epic_plan *plan, const float *vis, float *image, void *stream);
 

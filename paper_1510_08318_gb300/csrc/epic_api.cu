@@ -72,8 +72,9 @@ void free_plan(epic_plan* p) {
     cudaFree(p->status);
     cudaFree(p->tp_scratch);
     cudaFree(p->fx_lag_ptr);
-    cudaFree(p->fx_lag_pair);
-    cudaFree(p->fx_lag_w);
+    cudaFree(p->fx_lag_ent);
+    cudaFree(p->fx_vis_t);
+    cudaFree(p->fx_u);
     delete p;
 }
 
@@ -459,7 +460,7 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
 namespace {
 
 std::mutex g_fx_lag_mu;
-constexpr int64_t kMaxFxLagEntries = 1LL << 27;   // 1.5 GB of device tables at most
+constexpr int64_t kMaxFxLagEntries = 1LL << 27;   // 2 GB of device tables at most
 
 // The FX route's antenna-pair kernels of every ordered pair (autocorrelations included),
 // B_ab(d) = sum over mapping entries e of a and f of b with g_e - g_f = d of w_e conj(w_f)
@@ -488,6 +489,9 @@ epic_status build_fx_lag_table(const epic_plan* p) {
     if (bound > kMaxFxLagEntries)
         return epic_fail(EPIC_EUNSUPPORTED, "the antenna-pair lag table would hold up to %lld entries (limit %lld)",
                          (long long)bound, (long long)kMaxFxLagEntries);
+    if ((int64_t)A * A * p->n_chan * p->n_pol > 2147483647LL)
+        return epic_fail(EPIC_EUNSUPPORTED, "A^2 * C * P = %lld visibilities: the FX imaging indexes them in 32 bits",
+                         (long long)A * A * p->n_chan * p->n_pol);
     std::vector<int> lag, pair;
     std::vector<float2> w;
     lag.reserve((size_t)bound);
@@ -528,26 +532,31 @@ epic_status build_fx_lag_table(const epic_plan* p) {
     std::vector<int> lptr((size_t)NP * NP + 1, 0);
     for (int l : lag) lptr[(size_t)l + 1]++;
     for (size_t i = 0; i + 1 < lptr.size(); ++i) lptr[i + 1] += lptr[i];
-    std::vector<int> spair(pair.size()), fill(lptr.begin(), lptr.end() - 1);
-    std::vector<float2> sw(w.size());
+    std::vector<int> fill(lptr.begin(), lptr.end() - 1);
+    const int cp = p->n_chan * p->n_pol;
+    std::vector<int4> sent(pair.size());
     for (size_t i = 0; i < lag.size(); ++i) {
-        const int at = fill[lag[i]]++;
-        spair[at] = pair[i];
-        sw[at] = w[i];
+        int wr, wi;
+        std::memcpy(&wr, &w[i].x, sizeof(float));
+        std::memcpy(&wi, &w[i].y, sizeof(float));
+        sent[fill[lag[i]]++] = make_int4(wr, wi, pair[i] * cp, 0);
     }
     cudaError_t e;
-    if ((e = upload(&p->fx_lag_ptr, lptr)) != cudaSuccess || (e = upload(&p->fx_lag_pair, spair)) != cudaSuccess ||
-        (e = upload(&p->fx_lag_w, sw)) != cudaSuccess) {
+    if ((e = upload(&p->fx_lag_ptr, lptr)) != cudaSuccess || (e = upload(&p->fx_lag_ent, sent)) != cudaSuccess ||
+        (e = cudaMalloc(&p->fx_vis_t, (size_t)A * A * cp * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&p->fx_u, (size_t)cp * NP * NP * sizeof(float2))) != cudaSuccess) {
         cudaFree(p->fx_lag_ptr);
-        cudaFree(p->fx_lag_pair);
-        cudaFree(p->fx_lag_w);
+        cudaFree(p->fx_lag_ent);
+        cudaFree(p->fx_vis_t);
+        cudaFree(p->fx_u);
         p->fx_lag_ptr = nullptr;
-        p->fx_lag_pair = nullptr;
-        p->fx_lag_w = nullptr;
-        return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "FX lag table: %s", cudaGetErrorString(e))
+        p->fx_lag_ent = nullptr;
+        p->fx_vis_t = nullptr;
+        p->fx_u = nullptr;
+        return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "FX lag table and scratch: %s", cudaGetErrorString(e))
                                               : epic_cuda_fail(e, "FX lag table upload");
     }
-    p->fx_lag_n = (int64_t)spair.size();
+    p->fx_lag_n = (int64_t)sent.size();
     return EPIC_OK;
 }
 
@@ -951,8 +960,9 @@ epic_status epic_fx_image(const epic_plan* plan, const float* vis, float* image,
     a.n_cp = plan->n_chan * plan->n_pol;
     a.n_ant = plan->n_ant;
     a.lag_ptr = plan->fx_lag_ptr;
-    a.lag_pair = plan->fx_lag_pair;
-    a.lag_w = plan->fx_lag_w;
+    a.lag_ent = plan->fx_lag_ent;
+    a.vis_t = plan->fx_vis_t;
+    a.u = plan->fx_u;
     a.image = image;
     const cudaError_t e = epic::launch_fx_image(plan->n_pad, a, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "FX imaging kernel launch");

@@ -100,8 +100,9 @@ struct FxArgs {
     const float2* vis;         // [CP][A][A]
     int n_cp, n_ant;
     const int* lag_ptr;        // [N_p^2 + 1] CSR of the antenna-pair kernels by wrapped lag cell
-    const int* lag_pair;       // pair index a * A + b of each entry
-    const float2* lag_w;       // B_ab(d) of each entry
+    const int4* lag_ent;       // {B_ab(d) re bits, im bits, (a * A + b) * CP, 0} of each entry
+    float2* vis_t;             // scratch [A * A][CP]: the visibilities pair-major
+    float2* u;                 // scratch [CP][N_p][N_p]: the lag planes
     float* image;              // [CP][N_p][N_p]
 };
 cudaError_t launch_fx_image(int n_pad, const FxArgs& a, cudaStream_t st);

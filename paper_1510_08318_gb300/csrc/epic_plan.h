@@ -27,10 +27,12 @@ struct epic_plan {
     std::vector<int2> fx_ent_h;
     std::vector<float> fx_wim_h;
     // The FX route's antenna-pair kernels B_ab(d) grouped by lag cell d (CSR over the N_p^2 wrapped
-    // lags: pair index a * A + b and weight), built by the first epic_fx_image call
+    // lags: {weight re bits, im bits, (a * A + b) * C * P, 0}) and the imaging scratch (the
+    // visibilities pair-major, the lag planes), built by the first epic_fx_image call
     mutable int* fx_lag_ptr = nullptr;
-    mutable int* fx_lag_pair = nullptr;
-    mutable float2* fx_lag_w = nullptr;
+    mutable int4* fx_lag_ent = nullptr;
+    mutable float2* fx_vis_t = nullptr;
+    mutable float2* fx_u = nullptr;
     mutable int64_t fx_lag_n = -1;   // entries; -1 until built
     int* ant_ptr = nullptr;
     int2* ant_ent = nullptr;

@@ -381,115 +381,273 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
 // ---- the FX route's imaging of an integration's visibilities (Eq. "dirty-image-FX") ----
 //   U(d) = sum_{a, b} V_ab B_ab(d),  B_ab(d) = sum_g M[g, a] conj(M[g - d, b]),
 //   I(k) = Re sum_d U(d) exp(+2 pi i d.k / N_p)  (image pixel order, k = 0 at the centre).
-// One CTA per (channel, pol).  The lag plane U (N_p x N_p, lags wrapped mod N_p; with
-// N_p >= 2 N_g - 1 none alias) is gathered into shared memory from the plan's table of the
-// antenna-pair kernels grouped by lag cell (B_ab(d) summed over the mapping entries of a and b
-// once, on the host): one warp per lag cell, no atomics.  Then a separable DFT in place: rows
-// (each thread a strided set of one row's outputs), columns straight to the image.
-constexpr int FX_NT = 512;
+// Three launches.  (1) The visibilities are transposed to pair-major order with the (channel,
+// pol) index innermost, so that the values of one pair for consecutive (channel, pol) are
+// contiguous.  (2) The lag planes are gathered from the plan's table of the antenna-pair kernels
+// grouped by lag cell (B_ab(d) summed over the mapping entries of a and b once, on the host): a
+// warp takes one lag cell for a group of G (channel, pol) planes, its lanes G planes x 32 / G
+// entries, so that each entry's visibilities are one coalesced load for the G planes (no
+// atomics; a shuffle sum over the entries).  The lag planes (wrapped mod N_p; with
+// N_p >= 2 N_g - 1 none alias) go to a scratch array.  (3) One CTA per (channel, pol) takes its
+// lag plane into shared memory and transforms it: N_p = S1 x S2 Cooley-Tukey per line (S2-point
+// register DFTs, a twiddle, S1-point register DFTs across the line's threads), rows then
+// columns, the real part written as the image.
+
+// (1) vis [CP][P2] -> vis_t [P2][CP] through 32 x 32 shared-memory tiles
+__global__ void __launch_bounds__(256) fx_transpose_kernel(const float2* __restrict__ vis, int n_cp, long long n_pair,
+                                                           float2* __restrict__ vis_t) {
+    __shared__ float2 tile[32][33];
+    const long long p0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const int c = c0 + ty + j;
+        const long long p = p0 + tx;
+        if (c < n_cp && p < n_pair) tile[ty + j][tx] = __ldg(vis + (size_t)c * n_pair + p);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const long long p = p0 + ty + j;
+        const int c = c0 + tx;
+        if (c < n_cp && p < n_pair) vis_t[(size_t)p * n_cp + c] = tile[tx][ty + j];
+    }
+}
+
+// (2) U[cp][d] = sum over the entries of lag cell d of vis_t[off / CP][cp] * B (each entry
+// holds the element offset off = pair * CP of its pair's row).  A CTA takes an 8 x 8 tile of lag
+// cells (neighbouring cells share most of their pairs, which then stay in L1) for one group of
+// G planes; the CTAs of one tile (all groups) are adjacent in launch order so that they share
+// the tile's table entries in L2.  A warp takes whole lag cells.  It reads the entries of a cell
+// 32 at a time with one coalesced load into its own shared-memory slots (slots past the cell's
+// end hold zero weights at offset 0; the next 32 entries are loaded while these are used).
+// V4 (an even number of planes, G = 64): lane c takes planes 2c, 2c + 1 of the group with one
+// 16-byte load per entry, every lane every entry, 8 entries in flight.  Otherwise lane =
+// e * G + c (plane c, G <= 32) takes entries e, e + E, ... of the 32 (E = 32 / G) with 8-byte
+// loads, up to 16 in flight, and the sum over a cell's entries ends with a shuffle over e.
+constexpr int FXG_NT = 256;
+
+template <int G, bool V4>
+__global__ void __launch_bounds__(FXG_NT, V4 ? 2 : 3) fx_gather_kernel(const FxArgs a, int np) {
+    static_assert(V4 ? G == 64 : G <= 32, "group width");
+    constexpr int E = V4 ? 1 : 32 / G;                                   // entry slots per step
+    constexpr int U = V4 ? 8 : ((16 * E <= 32) ? 16 : 32 / E);           // entries per lane in flight
+    static_assert(U * E <= 32 && 32 % (U * E) == 0, "steps");
+    __shared__ int4 sent[FXG_NT / 32][32];
+    const int CP = a.n_cp, n_groups = (CP + G - 1) / G;
+    const int tiles_x = np / 8;
+    const int tile = blockIdx.x / n_groups, gi = blockIdx.x - tile * n_groups;
+    const int ty0 = 8 * (tile / tiles_x), tx0 = 8 * (tile % tiles_x);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = V4 ? 0 : lane / G;
+    const int cp = V4 ? gi * G + 2 * lane : gi * G + lane % G;          // first plane of the lane
+    const bool valid = cp < CP;
+    const float2* Vt = a.vis_t + (valid ? cp : 0);
+    int4* sw = sent[warp];
+    for (int j = warp; j < 64; j += FXG_NT / 32) {
+        const int d = (ty0 + (j >> 3)) * np + tx0 + (j & 7);
+        const int p0 = __ldg(a.lag_ptr + d), p1 = __ldg(a.lag_ptr + d + 1);
+        float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+        int4 nxt = p0 + lane < p1 ? __ldg(a.lag_ent + p0 + lane) : make_int4(0, 0, 0, 0);
+        for (int q0 = p0; q0 < p1; q0 += 32) {
+            const int nb = min(32, p1 - q0);
+            __syncwarp();
+            sw[lane] = nxt;
+            __syncwarp();
+            nxt = q0 + 32 + lane < p1 ? __ldg(a.lag_ent + q0 + 32 + lane) : make_int4(0, 0, 0, 0);
+            for (int k = 0; k < nb; k += U * E) {
+                if constexpr (V4) {
+                    float4 v[U];
+                    float2 w[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int4 en = sw[k + u];
+                        w[u] = make_float2(__int_as_float(en.x), __int_as_float(en.y));
+                        v[u] = __ldg(reinterpret_cast<const float4*>(Vt + en.z));
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        acc.x = fmaf(v[u].x, w[u].x, fmaf(-v[u].y, w[u].y, acc.x));
+                        acc.y = fmaf(v[u].x, w[u].y, fmaf(v[u].y, w[u].x, acc.y));
+                        acc1.x = fmaf(v[u].z, w[u].x, fmaf(-v[u].w, w[u].y, acc1.x));
+                        acc1.y = fmaf(v[u].z, w[u].y, fmaf(v[u].w, w[u].x, acc1.y));
+                    }
+                } else {
+                    float2 v[U], w[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int4 en = sw[k + u * E + e];
+                        w[u] = make_float2(__int_as_float(en.x), __int_as_float(en.y));
+                        v[u] = __ldg(Vt + en.z);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        acc.x = fmaf(v[u].x, w[u].x, fmaf(-v[u].y, w[u].y, acc.x));
+                        acc.y = fmaf(v[u].x, w[u].y, fmaf(v[u].y, w[u].x, acc.y));
+                    }
+                }
+            }
+        }
+        const size_t npix = (size_t)np * np;
+        if constexpr (V4) {
+            if (valid) {
+                a.u[(size_t)cp * npix + d] = acc;
+                a.u[(size_t)(cp + 1) * npix + d] = acc1;
+            }
+        } else {
+#pragma unroll
+            for (int o = 16; o >= G; o >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (e == 0 && valid) a.u[(size_t)cp * npix + d] = acc;
+        }
+    }
+}
+
+// (3) the transform of one lag plane.  Line of length NP = S1 x S2, n = S1 m + r, k = k1 + S2 k2:
+//   X[k1 + S2 k2] = sum_r exp(2 pi i r k2 / S1) [exp(2 pi i r k1 / NP) Y_r[k1]],
+//   Y_r[k1] = sum_m x[S1 m + r] exp(2 pi i m k1 / S2).
+// Thread (line, r) computes Y_r in registers and stores Y_r[k1] at line position
+// r S2 + (k1 xor r) (the xor spreads the S1 threads of a line over distinct banks); thread
+// (line, r') then takes k1 = r' + S1 i and does the S1-point DFTs.  Rows are padded to NP + S1
+// elements so that the lines a warp touches fall into complementary halves of the banks.  The
+// centring (k measured from N_p / 2) is the sign (-1)^(dx + dy) applied to U on loading.
+template <int NP>
+struct FxDft {
+    static constexpr int S1 = NP == 32 ? 4 : 8, S2 = NP / S1, NT = 4 * NP, P = NP + S1;
+    static constexpr size_t smem = sizeof(float2) * ((size_t)NP * P + NP);
+};
 
 template <int NP>
-__global__ void __launch_bounds__(FX_NT) fx_image_kernel(const FxArgs a) {
-    constexpr int NPIX = NP * NP, MSK = NP - 1, LG = NP == 32 ? 5 : NP == 64 ? 6 : 7, PER = NPIX / FX_NT;
-    static_assert(PER * FX_NT == NPIX && NP <= 128, "sizes");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* U = reinterpret_cast<float2*>(smem_raw);       // [NP][NP]
-    float2* TW = U + NPIX;                                 // [NP] exp(+2 pi i j / NP)
-    const int tid = threadIdx.x, cp = blockIdx.x, A = a.n_ant;
-    for (int j = tid; j < NP; j += FX_NT) {
+__global__ void __launch_bounds__(FxDft<NP>::NT) fx_dft_kernel(const float2* __restrict__ u, float* __restrict__ image) {
+    using D = FxDft<NP>;
+    constexpr int S1 = D::S1, S2 = D::S2, NT = D::NT, P = D::P, MSK = NP - 1;
+    static_assert(S1 * S2 == NP && S2 >= S1 && NT % NP == 0, "factorisation");
+    extern __shared__ __align__(16) unsigned char fx_smem[];
+    float2* L = reinterpret_cast<float2*>(fx_smem);       // [NP][P]
+    float2* TW = L + NP * P;                               // [NP] exp(+2 pi i j / NP)
+    const int tid = threadIdx.x, cp = blockIdx.x;
+    for (int j = tid; j < NP; j += NT) {
         double s, c;
         sincospi(2.0 * j / NP, &s, &c);
         TW[j] = make_float2(float(c), float(s));
     }
-    // U(d) = sum over the pairs of lag cell d of V_ab B_ab(d): one warp per lag cell, its lanes
-    // taking every 32nd entry of the cell's list, a shuffle sum (no atomics)
-    const float2* V = a.vis + (size_t)cp * A * A;
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int d = warp; d < NPIX; d += FX_NT / 32) {
-        const int p0 = __ldg(a.lag_ptr + d), p1 = __ldg(a.lag_ptr + d + 1);
-        // four entries per lane per step, independent loads and sums, so that the dependent
-        // visibility gathers of several entries are in flight together
-        float2 acc4[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc4[u] = make_float2(0.f, 0.f);
-        for (int q0 = p0 + lane; q0 < p1; q0 += 128) {
-            int pr[4];
-            float2 w[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = q0 + 32 * u;
-                pr[u] = q < p1 ? __ldg(a.lag_pair + q) : -1;
-                w[u] = q < p1 ? __ldg(a.lag_w + q) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 v = pr[u] >= 0 ? __ldg(V + pr[u]) : make_float2(0.f, 0.f);
-                acc4[u].x = fmaf(v.x, w[u].x, fmaf(-v.y, w[u].y, acc4[u].x));
-                acc4[u].y = fmaf(v.x, w[u].y, fmaf(v.y, w[u].x, acc4[u].y));
-            }
-        }
-        float2 acc = make_float2((acc4[0].x + acc4[1].x) + (acc4[2].x + acc4[3].x),
-                                 (acc4[0].y + acc4[1].y) + (acc4[2].y + acc4[3].y));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        }
-        if (lane == 0) U[d] = acc;
+    const float2* U = u + (size_t)cp * NP * NP;
+    for (int i = tid; i < NP * NP; i += NT) {
+        const int dy = i / NP, dx = i % NP;
+        float2 v = __ldg(U + i);
+        if ((dx + dy) & 1) v = make_float2(-v.x, -v.y);
+        L[dy * P + dx] = v;
     }
     __syncthreads();
-    // rows: T(dy, ix) = sum_dx U(dy, dx) exp(+2 pi i dx (ix - NP/2) / NP); thread -> row dy,
-    // pixels ix = q + (FX_NT / NP) j
+    // rows: line dy, element dx at L[dy * P + dx]
     {
-        constexpr int TPR = FX_NT / NP;                    // threads per row
-        const int dy = tid / TPR, q = tid % TPR;
-        float2 acc[PER];
+        constexpr int LPI = NT / S1;                        // lines per iteration
+        const int r = tid % S1;
+#pragma unroll 1
+        for (int l0 = 0; l0 < NP; l0 += LPI) {
+            float2* row = L + (l0 + tid / S1) * P;
+            float2 x[S2];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) acc[j] = make_float2(0.f, 0.f);
-        for (int dx = 0; dx < NP; ++dx) {
-            const float2 u = U[dy * NP + dx];
+            for (int m = 0; m < S2; ++m) x[m] = row[S1 * m + r];
+            dft<S2, 1>(x);
 #pragma unroll
-            for (int j = 0; j < PER; ++j) {
-                const int kx = q + TPR * j - NP / 2;
-                const float2 w = TW[(dx * kx) & MSK];
-                acc[j].x = fmaf(u.x, w.x, fmaf(-u.y, w.y, acc[j].x));
-                acc[j].y = fmaf(u.x, w.y, fmaf(u.y, w.x, acc[j].y));
+            for (int k1 = 1; k1 < S2; ++k1) x[k1] = cmul(x[k1], TW[(r * k1) & MSK]);
+            __syncthreads();
+#pragma unroll
+            for (int k1 = 0; k1 < S2; ++k1) row[r * S2 + (k1 ^ r)] = x[k1];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int l0 = 0; l0 < NP; l0 += LPI) {
+            float2* row = L + (l0 + tid / S1) * P;
+            float2 y[S2 / S1][S1];
+#pragma unroll
+            for (int i = 0; i < S2 / S1; ++i) {
+                const int k1 = r + S1 * i;
+#pragma unroll
+                for (int q = 0; q < S1; ++q) y[i][q] = row[q * S2 + (k1 ^ q)];
+                dft<S1, 1>(y[i]);
             }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < S2 / S1; ++i)
+#pragma unroll
+                for (int k2 = 0; k2 < S1; ++k2) row[r + S1 * i + S2 * k2] = y[i][k2];
+        }
+    }
+    __syncthreads();
+    // columns: line ix, element dy at L[dy * P + ix]; thread -> (ix = tid % NP, r), a warp 32
+    // consecutive columns
+    {
+        constexpr int RPI = NT / NP, RIT = S1 / RPI;        // r values per iteration, iterations
+        static_assert(RPI * RIT == S1, "column split");
+        const int ix = tid % NP;
+        // every r of a column is read before any is overwritten (the iterations share columns)
+        float2 x[RIT][S2];
+#pragma unroll
+        for (int it = 0; it < RIT; ++it) {
+            const int r = RPI * it + tid / NP;
+#pragma unroll
+            for (int m = 0; m < S2; ++m) x[it][m] = L[(S1 * m + r) * P + ix];
+            dft<S2, 1>(x[it]);
+#pragma unroll
+            for (int k1 = 1; k1 < S2; ++k1) x[it][k1] = cmul(x[it][k1], TW[(r * k1) & MSK]);
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < PER; ++j) U[dy * NP + q + TPR * j] = acc[j];
-    }
-    __syncthreads();
-    // columns: I(iy, ix) = Re sum_dy T(dy, ix) exp(+2 pi i dy (iy - NP/2) / NP); thread ->
-    // column ix = tid % NP, rows iy = tid / NP + (FX_NT / NP) j
-    {
-        constexpr int RPT = FX_NT / NP;
-        const int ix = tid % NP, r0 = tid / NP;
-        float acc[PER];
+        for (int it = 0; it < RIT; ++it) {
+            const int r = RPI * it + tid / NP;
 #pragma unroll
-        for (int j = 0; j < PER; ++j) acc[j] = 0.f;
-        for (int dy = 0; dy < NP; ++dy) {
-            const float2 t = U[dy * NP + ix];
+            for (int k1 = 0; k1 < S2; ++k1) L[(r * S2 + (k1 ^ r)) * P + ix] = x[it][k1];
+        }
+        __syncthreads();
+        float* img = image + (size_t)cp * NP * NP;
+#pragma unroll 1
+        for (int r0 = 0; r0 < S1; r0 += RPI) {
+            const int r = r0 + tid / NP;
 #pragma unroll
-            for (int j = 0; j < PER; ++j) {
-                const int ky = r0 + RPT * j - NP / 2;
-                const float2 w = TW[(dy * ky) & MSK];
-                acc[j] = fmaf(t.x, w.x, fmaf(-t.y, w.y, acc[j]));
+            for (int i = 0; i < S2 / S1; ++i) {
+                const int k1 = r + S1 * i;
+                float2 y[S1];
+#pragma unroll
+                for (int q = 0; q < S1; ++q) y[q] = L[(q * S2 + (k1 ^ q)) * P + ix];
+                dft<S1, 1>(y);
+#pragma unroll
+                for (int k2 = 0; k2 < S1; ++k2) img[(size_t)(k1 + S2 * k2) * NP + ix] = y[k2].x;
             }
         }
-        float* img = a.image + (size_t)cp * NPIX;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) img[(r0 + RPT * j) * NP + ix] = acc[j];
     }
 }
 
 template <int NP>
 cudaError_t launch_fx_image_t(const FxArgs& a, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * ((size_t)NP * NP + NP);
-    cudaError_t e = ensure_smem<fx_image_kernel<NP>>(smem);
+    const long long n_pair = (long long)a.n_ant * a.n_ant;
+    fx_transpose_kernel<<<dim3((unsigned)((n_pair + 31) / 32), (unsigned)((a.n_cp + 31) / 32)), 256, 0, st>>>(
+        a.vis, a.n_cp, n_pair, a.vis_t);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    fx_image_kernel<NP><<<a.n_cp, FX_NT, smem, st>>>(a);
+    const long long tiles = (NP / 8) * (NP / 8);
+    if (a.n_cp >= 64 && a.n_cp % 2 == 0) {
+        fx_gather_kernel<64, true><<<(unsigned)(tiles * ((a.n_cp + 63) / 64)), FXG_NT, 0, st>>>(a, NP);
+    } else {
+        int g = 1;
+        while (g < 32 && g < a.n_cp) g *= 2;
+        const unsigned blocks = (unsigned)(tiles * ((a.n_cp + g - 1) / g));
+        switch (g) {
+            case 1: fx_gather_kernel<1, false><<<blocks, FXG_NT, 0, st>>>(a, NP); break;
+            case 2: fx_gather_kernel<2, false><<<blocks, FXG_NT, 0, st>>>(a, NP); break;
+            case 4: fx_gather_kernel<4, false><<<blocks, FXG_NT, 0, st>>>(a, NP); break;
+            case 8: fx_gather_kernel<8, false><<<blocks, FXG_NT, 0, st>>>(a, NP); break;
+            case 16: fx_gather_kernel<16, false><<<blocks, FXG_NT, 0, st>>>(a, NP); break;
+            default: fx_gather_kernel<32, false><<<blocks, FXG_NT, 0, st>>>(a, NP); break;
+        }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    using D = FxDft<NP>;
+    if ((e = ensure_smem<fx_dft_kernel<NP>>(D::smem)) != cudaSuccess) return e;
+    fx_dft_kernel<NP><<<a.n_cp, D::NT, D::smem, st>>>(a.u, a.image);
     return cudaGetLastError();
 }
 

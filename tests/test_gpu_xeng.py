@@ -167,3 +167,30 @@ def test_gpu_fx_image_small_sizes_complex_weights(epic, n_pad, n_grid, n_ant):
     M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
     want = fx.fx_image(M, wl.volt, None, wl.n_grid, wl.n_pad).real
     assert np.linalg.norm(img - want) / np.linalg.norm(want) < 1e-4
+
+
+@pytest.mark.parametrize("n_chan, n_pol", [(3, 1), (20, 2), (33, 2), (65, 1)])
+def test_gpu_fx_image_plane_groupings(epic, n_chan, n_pol):
+    """The lag-plane gather's groupings of (channel, pol) planes: 3 planes (one group of 4),
+    40 (two groups of 32, the second ragged), 66 (two groups of 64 read 16 bytes per lane, the
+    second ragged) and 65 (odd: three groups of 32).  Every plane against the oracle's FX route
+    (complex footprint weights, N_p = 32)."""
+    rng = np.random.default_rng(100 + n_chan * n_pol)
+    n_grid, n_pad, n_ant, n_time = 14, 32, 20, 16
+    pos = rng.uniform(2.0, n_grid - 3.0, (n_ant, 2))
+    kerns = [synth.kernel_square(rng.uniform(0.5, 2.5), 1 / 3) for _ in range(n_ant)]
+    ptr, dxdy, w = synth.pack_kernels(kerns)
+    w = w * np.exp(1j * rng.uniform(0, 2 * np.pi, w.shape))
+    wl = synth.Workload("fxg", pos, ptr, dxdy, w, 1.0, np.zeros(2), n_grid, n_pad, np.full(n_chan, 1e8), n_pol,
+                        n_time, "f16")
+    v = rng.standard_normal((n_time, n_chan, n_pol, n_ant)) + 1j * rng.standard_normal((n_time, n_chan, n_pol, n_ant))
+    wl = synth._finish(wl, v, "f16")
+    plan = epic.Plan.from_workload(wl)
+    img = plan.fx_image(plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())).cpu().numpy()
+    M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+    want = fx.fx_image(M, wl.volt, None, wl.n_grid, wl.n_pad).real
+    assert img.shape == want.shape == (n_chan, n_pol, n_pad, n_pad)
+    for c in range(n_chan):
+        for p in range(n_pol):
+            assert np.linalg.norm(img[c, p] - want[c, p]) / np.linalg.norm(want[c, p]) < 1e-4, (c, p)
+            assert np.abs(img[c, p] - want[c, p]).max() < 1e-4 * np.abs(want[c, p]).max(), (c, p)
