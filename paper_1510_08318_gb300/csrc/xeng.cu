@@ -13,19 +13,26 @@
 //
 // Work unit: a 128 x 128 block (antenna rows a in block ab, columns b in block bb, bb >= ab:
 // the upper block triangle, the lower one follows by Hermitian symmetry) of one (channel,
-// pol).  K is walked in chunks of 32 samples (K = 64): the CTA's threads decode the chunk's
-// voltages (loaded into registers during the previous chunk) into K-major FP16 tiles (X of
-// the row block, X and W of the column block; a diagonal block reuses X of the column block
-// for the rows) in one of two shared-memory stages, then one thread issues 2 x 4 MMAs
-// (M = N = 128, K = 16) into the unit's TMEM
-// accumulators and commits them to the stage's mbarrier, which releases the stage for the
-// chunk after next.  After a unit's last chunk its accumulators are read back (tcgen05.ld),
-// scaled by g_a conj(g_b) / T and written, with the mirrored conjugate block for off-diagonal
-// units.  Two 256-thread CTAs share an SM (256 TMEM columns each), so one CTA's decode and
-// loads overlap the other's MMAs.  Every wait on the tensor cores is bounded (the pipeline's
-// waits by the plan's try count); on a timeout the CTA sets the correlator-timeout bit of the
-// plan's status word, writes NaN into its first output element, waits with the full limit for
-// the MMAs in flight and stops.
+// pol); one persistent CTA per SM takes a contiguous range of units, K walked in chunks of 32
+// samples (K = 64).  The CTA's warps have three roles, handing work over through mbarriers
+// only (no CTA-wide barrier inside the loop):
+//   - 8 decode warps convert a chunk's voltages (loaded into registers ahead of use) into
+//     K-major FP16 tiles (X of the row block, X and W of the column block, stored adjacent so
+//     that [X_b ; W_b] is one N = 256 operand; a diagonal block reuses X_b for the rows) in one
+//     stage of a 4-stage ring; each warp fences its stores for the tensor cores and arrives on
+//     the stage's full barrier, and refills a stage after the MMAs that read it have completed
+//     (the stage's empty barrier, signalled by tcgen05.commit);
+//   - one thread of the MMA warp issues 4 MMAs (M = 128, N = 256, K = 16) per chunk,
+//     D = X_a [X_b ; W_b]^T, Re V in columns 0..127 and Im V in 128..255 of one of two TMEM
+//     accumulator buffers (all 512 columns), commits each chunk to its stage's empty barrier
+//     and a unit's last chunk to the buffer's full barrier;
+//   - 4 epilogue warps (one per TMEM lane quarter) read a finished buffer (tcgen05.ld), scale
+//     by g_a conj(g_b) / T, write the block and, off the diagonal, its mirrored conjugate, then
+//     release the buffer, while the MMAs of the next unit fill the other one.
+// Every wait is bounded by the plan's try count and taken by a whole warp; on a timeout the role
+// stops, the CTA sets the correlator-timeout bit of the plan's status word and writes NaN into
+// its first output element; the MMA warp waits (full limit) for the MMAs it issued before the
+// tensor memory is released.
 //
 // WIDE (4+4-bit voltages, A a multiple of 16, 16-byte aligned input): a thread loads 16
 // consecutive antennas of one sample with one 16-byte load (a warp reads whole 128-byte
@@ -40,14 +47,21 @@ namespace epic {
 namespace xe {
 using namespace tc;
 
-constexpr int NT = 256;             // two CTAs per SM, 256 TMEM columns each
-constexpr int TC = 32;              // samples per K chunk
-constexpr int KC = 2 * TC;          // K per chunk (re/im interleaved)
-constexpr int TILE = 128 * KC;      // halves per operand tile (16 KB)
-enum { T_XA, T_XB, T_WB, N_TILE };
-constexpr int NSTAGE = 2;
+constexpr int NDS = 2;                      // decode warp sets, taking alternate chunks
+constexpr int NDW = 8 * NDS;                // decode warps (a set's tile mappings take 256 threads)
+constexpr int NEW = 4;                      // epilogue warps, one per TMEM lane quarter
+constexpr int MMA_WARP = NDW;               // the warp whose first thread issues the MMAs
+constexpr int NT = 32 * (NDW + 1 + NEW);    // one CTA per SM
+constexpr int TC = 32;                      // samples per K chunk
+constexpr int KC = 2 * TC;                  // K per chunk (re/im interleaved)
+constexpr int TILE = 128 * KC;              // halves per operand tile (16 KB)
+enum { T_XA, T_XB, T_WB, N_TILE };          // X_b and W_b adjacent: one N = 256 operand
+constexpr int NSTAGE = 4;
+// mbarriers: stage full [NSTAGE], stage empty [NSTAGE], accumulator full [2], accumulator
+// empty [2], drain
+constexpr int N_MBAR = 2 * NSTAGE + 5;
 
-constexpr size_t smem_bytes() { return sizeof(__half) * (size_t)NSTAGE * N_TILE * TILE + 64; }
+constexpr size_t smem_bytes() { return sizeof(__half) * (size_t)NSTAGE * N_TILE * TILE + 8 * N_MBAR + 16; }
 
 // FP16 operand pairs of one voltage, as half2 bits: X = (re, im), W = (-im, re).  FP16 input
 // is already the pair.  A 4+4-bit byte holds two 4-bit two's-complement values; XOR with 8
@@ -93,13 +107,14 @@ __device__ __forceinline__ void unit_coords(int u, int nab, int& cp, int& ab, in
 }
 
 template <int VDT, bool WIDE>
-__global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
+__global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
     static_assert(!WIDE || VDT == 2, "the wide loads are for 4+4-bit voltages");
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __half* sT = reinterpret_cast<__half*>(smem_raw);                           // [NSTAGE][N_TILE][TILE]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sT + NSTAGE * N_TILE * TILE);   // [NSTAGE] stages, [1] accumulator
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + NSTAGE + 1);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sT + NSTAGE * N_TILE * TILE);   // [N_MBAR]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + N_MBAR);
+    int* s_fail = reinterpret_cast<int*>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int A = a.n_ant, T = a.n_time, CP = a.n_cp;
@@ -107,178 +122,205 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
     const int n_units = CP * (nab * (nab + 1) / 2);
     const int n_chunks = (T + TC - 1) / TC;
     const VT* V = static_cast<const VT*>(a.volt);
+    auto mb_full = [&](int s) { return smem_u32(&mbar[s]); };
+    auto mb_empty = [&](int s) { return smem_u32(&mbar[NSTAGE + s]); };
+    auto mb_accf = [&](int b) { return smem_u32(&mbar[2 * NSTAGE + b]); };
+    auto mb_acce = [&](int b) { return smem_u32(&mbar[2 * NSTAGE + 2 + b]); };
+    const uint32_t mb_drain = smem_u32(&mbar[2 * NSTAGE + 4]);
+    // a bounded wait taken by a whole warp: the warp goes on only if every lane saw the phase
+    auto warp_wait = [&](uint32_t mb, int parity) -> bool {
+        return __all_sync(0xffffffffu, mbar_wait(mb, (uint32_t)parity, a.wait_tries)) != 0;
+    };
 
     if (tid == 0) {
-        for (int s = 0; s <= NSTAGE; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[s])), "r"(1) : "memory");
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(mb_full(s), 8);
+            mbar_init(mb_empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(mb_accf(b), 1);
+            mbar_init(mb_acce(b), NEW);
+        }
+        mbar_init(mb_drain, 1);
+        *s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(256) : "memory");
+                     :: "r"(smem_u32(tslot)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t tRe = tmem, tIm = tmem + 128;
-    const uint32_t mb_acc = smem_u32(&mbar[NSTAGE]);
-    const uint64_t d0 = sdesc(smem_u32(sT), 1024);
-    constexpr int kTileStep = 2 * TILE / 16;        // descriptor start-field step per tile
-    constexpr uint32_t id = idesc(128);
+    const uint32_t tmem = *tslot;             // accumulator buffer b: columns 256 b (Re), 256 b + 128 (Im)
 
     long long beg_l, end_l;
     work_range(n_units, blockIdx.x, gridDim.x, beg_l, end_l);
     const int beg = (int)beg_l, end = (int)end_l;
 
-    // decode mapping: lane -> (row % 8, sample % 4), so that one warp's 4-byte stores cover 32
-    // distinct banks of a core-matrix row block.  Thread (warp w, lane) owns rows
-    // r0 = 8 w + lane % 8 and r0 + 64 of a tile and samples 4 j + lane / 8, j < TC / 4, of a
-    // chunk: its voltages are V[(t CP + cp) A + row] (one base pointer per tile and a sample
-    // stride), its tile words sit at a fixed offset + 32 j (+ 2048 for the second row).  The raw
-    // voltages of the next chunk are loaded into registers (all at once) while the current
-    // chunk is on the tensor cores.
-    static_assert(NT == 256, "two rows of a 128-row tile per thread");
-    constexpr int NJ = TC / 4;
-    const int lr = lane & 7, lt = lane >> 3;
-    const int r0 = 8 * warp + lr;
-    const int sbase = 256 * warp + 4 * lr + lt;      // word offset of (r0, 2 lt) in a tile
-    const long long RS = (long long)CP * A;          // sample stride of the voltages
-    // per unit: this thread's voltage pointers at sample lt of chunk 0 and its row validity
-    struct UnitPtr {
-        const VT* pb;
-        const VT* pa;
-        bool vb0, vb1, va0, va1;
-    };
-    VT rb[WIDE ? 1 : 2 * NJ], ra[WIDE ? 1 : 2 * NJ];
-    auto unit_ptr = [&](int u) {
-        int cp, ab, bb;
-        unit_coords(u, nab, cp, ab, bb);
-        UnitPtr p;
-        p.pb = V + (long long)cp * A + bb * 128 + r0 + lt * RS;
-        p.pa = V + (long long)cp * A + ab * 128 + r0 + lt * RS;
-        p.vb0 = bb * 128 + r0 < A;
-        p.vb1 = bb * 128 + r0 + 64 < A;
-        p.va0 = ab != bb && ab * 128 + r0 < A;
-        p.va1 = ab != bb && ab * 128 + r0 + 64 < A;
-        return p;
-    };
-    auto load_chunk = [&](const UnitPtr& p, int kc) {
-        if constexpr (!WIDE) {
-            const int tq = kc * TC + lt;
-            const VT* pb = p.pb + (long long)(kc * TC) * RS;
-            const VT* pa = p.pa + (long long)(kc * TC) * RS;
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const bool tin = tq + 4 * j < T;
-                rb[2 * j] = (tin && p.vb0) ? __ldg(pb) : VT(0);
-                rb[2 * j + 1] = (tin && p.vb1) ? __ldg(pb + 64) : VT(0);
-                ra[2 * j] = (tin && p.va0) ? __ldg(pa) : VT(0);
-                ra[2 * j + 1] = (tin && p.va1) ? __ldg(pa + 64) : VT(0);
-                pb += 4 * RS;
-                pa += 4 * RS;
+    if (warp < NDW) {
+        // ---------------- decode warps: raw voltages -> FP16 operand tiles of stage g % NSTAGE ----
+        // set dset decodes the CTA's chunks g = dset, dset + NDS, ...; within a set, warp dw
+        const int dw = warp & 7, dset = warp >> 3;
+        // (unit, chunk) cursors step NDS chunks at a time; true when the unit changed
+        auto advance = [&](int& uu, int& kk, int by) -> bool {
+            kk += by;
+            bool changed = false;
+            while (kk >= n_chunks && uu < end) {
+                kk -= n_chunks;
+                ++uu;
+                changed = true;
             }
-        }
-    };
-
-    // WIDE mapping: thread (warp w, lane l) loads rows 16 p .. 16 p + 15, p = l % 8, of
-    // sample tw = 4 w + l / 8 of a chunk.  In a tile, row r and sample t sit at word
-    // 256 (r / 8) + 32 (t / 4) + 4 (r % 8) + t % 4 (bank 4 (r % 8) + t % 4).  Store instruction
-    // (s, i) of a lane writes row 16 p + 4 (s ^ si) + (i + ri) % 4 with ri = p % 4, si = p / 4:
-    // the 32 lanes then differ in (t % 4, ri, si) and hit 32 distinct banks.  One byte permute
-    // per word selects word s ^ si and rotates its bytes by ri.
-    const int wp = lane & 7, wri = lane & 3, wsi = (lane >> 2) & 1, wtw = 4 * warp + (lane >> 3);
-    const uint32_t wsel = (uint32_t)(((0 + wri) & 3) | (((1 + wri) & 3) << 4) | (((2 + wri) & 3) << 8) |
-                                     (((3 + wri) & 3) << 12)) + (wsi ? 0x4444u : 0u);
-    int woff[2][4];                                  // word offsets for s % 2 and i (+ 256 (s / 2))
+            return changed;
+        };
+        // decode mapping: lane -> (row % 8, sample % 4), so that one warp's 4-byte stores cover 32
+        // distinct banks of a core-matrix row block.  Thread (warp w, lane) owns rows
+        // r0 = 8 w + lane % 8 and r0 + 64 of a tile and samples 4 j + lane / 8, j < TC / 4, of a
+        // chunk: its voltages are V[(t CP + cp) A + row] (one base pointer per tile and a sample
+        // stride), its tile words sit at a fixed offset + 32 j (+ 2048 for the second row).  The raw
+        // voltages of the next chunk are loaded into registers (all at once) while the current
+        // chunk is on the tensor cores.
+        static_assert(NDW % 8 == 0, "two rows of a 128-row tile per thread of a decode set");
+        constexpr int NJ = TC / 4;
+        const int lr = lane & 7, lt = lane >> 3;
+        const int r0 = 8 * dw + lr;
+        const int sbase = 256 * dw + 4 * lr + lt;      // word offset of (r0, 2 lt) in a tile
+        const long long RS = (long long)CP * A;          // sample stride of the voltages
+        // per unit: this thread's voltage pointers at sample lt of chunk 0 and its row validity
+        struct UnitPtr {
+            const VT* pb;
+            const VT* pa;
+            bool vb0, vb1, va0, va1;
+        };
+        VT rb[WIDE ? 1 : 2 * NJ], ra[WIDE ? 1 : 2 * NJ];
+        auto unit_ptr = [&](int u) {
+            int cp, ab, bb;
+            unit_coords(u, nab, cp, ab, bb);
+            UnitPtr p;
+            p.pb = V + (long long)cp * A + bb * 128 + r0 + lt * RS;
+            p.pa = V + (long long)cp * A + ab * 128 + r0 + lt * RS;
+            p.vb0 = bb * 128 + r0 < A;
+            p.vb1 = bb * 128 + r0 + 64 < A;
+            p.va0 = ab != bb && ab * 128 + r0 < A;
+            p.va1 = ab != bb && ab * 128 + r0 + 64 < A;
+            return p;
+        };
+        auto load_chunk = [&](const UnitPtr& p, int kc) {
+            if constexpr (!WIDE) {
+                const int tq = kc * TC + lt;
+                const VT* pb = p.pb + (long long)(kc * TC) * RS;
+                const VT* pa = p.pa + (long long)(kc * TC) * RS;
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            woff[j][i] = 512 * wp + 32 * warp + (lane >> 3) + 16 * (j ^ wsi) + 4 * ((i + wri) & 3);
-    uint4 wb0 = make_uint4(0, 0, 0, 0), wa0 = wb0, wb1 = wb0, wa1 = wb0;   // chunks g (even / odd sets)
-    int lu = beg, lkc = 0, lcp = 0, lab = 0, lbb = 0;                       // load cursor
-    if (WIDE && beg < end) unit_coords(beg, nab, lcp, lab, lbb);
-    const unsigned char* VW = static_cast<const unsigned char*>(a.volt);
-    auto wide_load = [&](uint4& xb, uint4& xa) {
-        xb = make_uint4(0, 0, 0, 0);
-        xa = xb;
-        if (lu >= end) return;
-        const int t = lkc * TC + wtw;
-        if (t < T) {
-            const unsigned char* row = VW + (long long)t * RS + (long long)lcp * A + 16 * wp;
-            if (lbb * 128 + 16 * wp < A) xb = __ldg(reinterpret_cast<const uint4*>(row + lbb * 128));
-            if (lab != lbb && lab * 128 + 16 * wp < A) xa = __ldg(reinterpret_cast<const uint4*>(row + lab * 128));
-        }
-        if (++lkc == n_chunks) {
-            lkc = 0;
-            if (++lu < end) unit_coords(lu, nab, lcp, lab, lbb);
-        }
-    };
-    auto wide_word = [&](uint32_t* tile, uint32_t* wtile, uint32_t R, int s) {
-        const uint32_t H = ((R >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-        const uint32_t L = (R & 0x0F0F0F0Fu) ^ 0x08080808u;
-        const uint32_t x0 = ci4_pair<0>(H, L), x1 = ci4_pair<1>(H, L), x2 = ci4_pair<2>(H, L), x3 = ci4_pair<3>(H, L);
-        const int* o = woff[s & 1];
-        const int hi = 256 * (s >> 1);
-        tile[o[0] + hi] = x0;
-        tile[o[1] + hi] = x1;
-        tile[o[2] + hi] = x2;
-        tile[o[3] + hi] = x3;
-        if (wtile) {
-            wtile[o[0] + hi] = __byte_perm(x0, 0, 0x1032) ^ 0x8000u;
-            wtile[o[1] + hi] = __byte_perm(x1, 0, 0x1032) ^ 0x8000u;
-            wtile[o[2] + hi] = __byte_perm(x2, 0, 0x1032) ^ 0x8000u;
-            wtile[o[3] + hi] = __byte_perm(x3, 0, 0x1032) ^ 0x8000u;
-        }
-    };
-    auto wide_decode = [&](const uint4& xb, const uint4& xa, __half* st, bool diag) {
-        uint32_t* tX = reinterpret_cast<uint32_t*>(st + T_XB * TILE);
-        uint32_t* tW = reinterpret_cast<uint32_t*>(st + T_WB * TILE);
-        uint32_t* tA = reinterpret_cast<uint32_t*>(st + T_XA * TILE);
-        wide_word(tX, tW, __byte_perm(xb.x, xb.y, wsel), 0);
-        wide_word(tX, tW, __byte_perm(xb.y, xb.x, wsel), 1);
-        wide_word(tX, tW, __byte_perm(xb.z, xb.w, wsel), 2);
-        wide_word(tX, tW, __byte_perm(xb.w, xb.z, wsel), 3);
-        if (!diag) {
-            wide_word(tA, nullptr, __byte_perm(xa.x, xa.y, wsel), 0);
-            wide_word(tA, nullptr, __byte_perm(xa.y, xa.x, wsel), 1);
-            wide_word(tA, nullptr, __byte_perm(xa.z, xa.w, wsel), 2);
-            wide_word(tA, nullptr, __byte_perm(xa.w, xa.z, wsel), 3);
-        }
-    };
+                for (int j = 0; j < NJ; ++j) {
+                    const bool tin = tq + 4 * j < T;
+                    rb[2 * j] = (tin && p.vb0) ? __ldg(pb) : VT(0);
+                    rb[2 * j + 1] = (tin && p.vb1) ? __ldg(pb + 64) : VT(0);
+                    ra[2 * j] = (tin && p.va0) ? __ldg(pa) : VT(0);
+                    ra[2 * j + 1] = (tin && p.va1) ? __ldg(pa + 64) : VT(0);
+                    pb += 4 * RS;
+                    pa += 4 * RS;
+                }
+            }
+        };
 
-    bool failed = false;
-    int g = 0;            // chunks issued by this CTA
-    int n_done = 0;       // units finished by this CTA
-    UnitPtr up = (!WIDE && beg < end) ? unit_ptr(beg) : UnitPtr{};
-    if constexpr (WIDE) {
-        wide_load(wb0, wa0);
-        wide_load(wb1, wa1);
-    } else if (beg < end) {
-        load_chunk(up, 0);
-    }
-    for (int u = beg; u < end && !failed; ++u) {
-        int cp, ab, bb;
-        unit_coords(u, nab, cp, ab, bb);
-        const bool diag = ab == bb;
-        const int a0 = ab * 128, b0 = bb * 128;
-        for (int kc = 0; kc < n_chunks && !failed; ++kc, ++g) {
-            const int s = g & 1;
-            if (g >= 2 && !mbar_wait(smem_u32(&mbar[s]), ((g - 2) >> 1) & 1, a.wait_tries)) failed = true;
-            failed = __syncthreads_or(failed) != 0;
-            if (failed) break;
+        // WIDE mapping: thread (warp w, lane l) loads rows 16 p .. 16 p + 15, p = l % 8, of
+        // sample tw = 4 w + l / 8 of a chunk.  In a tile, row r and sample t sit at word
+        // 256 (r / 8) + 32 (t / 4) + 4 (r % 8) + t % 4 (bank 4 (r % 8) + t % 4).  Store instruction
+        // (s, i) of a lane writes row 16 p + 4 (s ^ si) + (i + ri) % 4 with ri = p % 4, si = p / 4:
+        // the 32 lanes then differ in (t % 4, ri, si) and hit 32 distinct banks.  One byte permute
+        // per word selects word s ^ si and rotates its bytes by ri.
+        const int wp = lane & 7, wri = lane & 3, wsi = (lane >> 2) & 1, wtw = 4 * dw + (lane >> 3);
+        const uint32_t wsel = (uint32_t)(((0 + wri) & 3) | (((1 + wri) & 3) << 4) | (((2 + wri) & 3) << 8) |
+                                         (((3 + wri) & 3) << 12)) + (wsi ? 0x4444u : 0u);
+        int woff[2][4];                                  // word offsets for s % 2 and i (+ 256 (s / 2))
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                woff[j][i] = 512 * wp + 32 * dw + (lane >> 3) + 16 * (j ^ wsi) + 4 * ((i + wri) & 3);
+        uint4 wb0 = make_uint4(0, 0, 0, 0), wa0 = wb0, wb1 = wb0, wa1 = wb0;   // a set's even / odd chunks
+        int lu = beg, lkc = 0, lcp = 0, lab = 0, lbb = 0;                       // load cursor
+        advance(lu, lkc, dset);
+        if (lu < end) unit_coords(lu, nab, lcp, lab, lbb);
+        const unsigned char* VW = static_cast<const unsigned char*>(a.volt);
+        auto wide_load = [&](uint4& xb, uint4& xa) {
+            xb = make_uint4(0, 0, 0, 0);
+            xa = xb;
+            if (lu >= end) return;
+            const int t = lkc * TC + wtw;
+            if (t < T) {
+                const unsigned char* row = VW + (long long)t * RS + (long long)lcp * A + 16 * wp;
+                if (lbb * 128 + 16 * wp < A) xb = __ldg(reinterpret_cast<const uint4*>(row + lbb * 128));
+                if (lab != lbb && lab * 128 + 16 * wp < A) xa = __ldg(reinterpret_cast<const uint4*>(row + lab * 128));
+            }
+            if (advance(lu, lkc, NDS) && lu < end) unit_coords(lu, nab, lcp, lab, lbb);
+        };
+        auto wide_word = [&](uint32_t* tile, uint32_t* wtile, uint32_t R, int s) {
+            const uint32_t H = ((R >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+            const uint32_t L = (R & 0x0F0F0F0Fu) ^ 0x08080808u;
+            const uint32_t x0 = ci4_pair<0>(H, L), x1 = ci4_pair<1>(H, L), x2 = ci4_pair<2>(H, L), x3 = ci4_pair<3>(H, L);
+            const int* o = woff[s & 1];
+            const int hi = 256 * (s >> 1);
+            tile[o[0] + hi] = x0;
+            tile[o[1] + hi] = x1;
+            tile[o[2] + hi] = x2;
+            tile[o[3] + hi] = x3;
+            if (wtile) {
+                wtile[o[0] + hi] = __byte_perm(x0, 0, 0x1032) ^ 0x8000u;
+                wtile[o[1] + hi] = __byte_perm(x1, 0, 0x1032) ^ 0x8000u;
+                wtile[o[2] + hi] = __byte_perm(x2, 0, 0x1032) ^ 0x8000u;
+                wtile[o[3] + hi] = __byte_perm(x3, 0, 0x1032) ^ 0x8000u;
+            }
+        };
+        auto wide_decode = [&](const uint4& xb, const uint4& xa, __half* st, bool diag) {
+            uint32_t* tX = reinterpret_cast<uint32_t*>(st + T_XB * TILE);
+            uint32_t* tW = reinterpret_cast<uint32_t*>(st + T_WB * TILE);
+            uint32_t* tA = reinterpret_cast<uint32_t*>(st + T_XA * TILE);
+            wide_word(tX, tW, __byte_perm(xb.x, xb.y, wsel), 0);
+            wide_word(tX, tW, __byte_perm(xb.y, xb.x, wsel), 1);
+            wide_word(tX, tW, __byte_perm(xb.z, xb.w, wsel), 2);
+            wide_word(tX, tW, __byte_perm(xb.w, xb.z, wsel), 3);
+            if (!diag) {
+                wide_word(tA, nullptr, __byte_perm(xa.x, xa.y, wsel), 0);
+                wide_word(tA, nullptr, __byte_perm(xa.y, xa.x, wsel), 1);
+                wide_word(tA, nullptr, __byte_perm(xa.z, xa.w, wsel), 2);
+                wide_word(tA, nullptr, __byte_perm(xa.w, xa.z, wsel), 3);
+            }
+        };
+
+
+        // non-WIDE loads: the chunk at the load cursor into rb / ra
+        UnitPtr up = (!WIDE && lu < end) ? unit_ptr(lu) : UnitPtr{};
+        auto nw_load = [&]() {
+            if (lu < end) load_chunk(up, lkc);
+            if (advance(lu, lkc, NDS) && lu < end) up = unit_ptr(lu);
+        };
+        if constexpr (WIDE) {
+            wide_load(wb0, wa0);
+            wide_load(wb1, wa1);
+        } else {
+            nw_load();
+        }
+        bool failed = false;
+        int cu = beg, ckc = 0, ccp = 0, cab = 0, cbb = 0;                       // decode cursor
+        advance(cu, ckc, dset);
+        if (cu < end) unit_coords(cu, nab, ccp, cab, cbb);
+        for (int i = 0; cu < end; ++i) {
+            const int g = (cu - beg) * n_chunks + ckc;
+            const int s = g % NSTAGE;
+            // the stage is free once the MMAs of its previous chunk have completed
+            if (g >= NSTAGE && !warp_wait(mb_empty(s), (g / NSTAGE - 1) & 1)) {
+                failed = true;
+                break;
+            }
+            const bool diag = cab == cbb;
             __half* st = sT + s * N_TILE * TILE;
             if constexpr (WIDE) {
-                // decode chunk g, then load chunk g + 2 into the same register set
-                if (s == 0) {
+                if ((i & 1) == 0)
                     wide_decode(wb0, wa0, st, diag);
-                    wide_load(wb0, wa0);
-                } else {
+                else
                     wide_decode(wb1, wa1, st, diag);
-                    wide_load(wb1, wa1);
-                }
             } else {
                 uint32_t* sxb = reinterpret_cast<uint32_t*>(st + T_XB * TILE) + sbase;
                 uint32_t* swb = reinterpret_cast<uint32_t*>(st + T_WB * TILE) + sbase;
@@ -297,85 +339,147 @@ __global__ void __launch_bounds__(NT, 2) xeng_kernel(const XengArgs a) {
                         }
                     }
             }
+            // this warp's tile stores, visible to the tensor cores, then its arrival
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                fence_after();
-                const uint64_t dS = d0 + (uint64_t)(s * N_TILE * kTileStep);
-                const uint64_t dA = dS + (uint64_t)((diag ? T_XB : T_XA) * kTileStep);
-                const uint64_t dX = dS + (uint64_t)(T_XB * kTileStep), dW = dS + (uint64_t)(T_WB * kTileStep);
-#pragma unroll
-                for (int j = 0; j < KC / 16; ++j) {
-                    const uint32_t acc = (kc | j) != 0;
-                    mma_ss(tRe, dA + 16 * j, dX + 16 * j, id, acc);
-                    mma_ss(tIm, dA + 16 * j, dW + 16 * j, id, acc);
-                }
-                commit(smem_u32(&mbar[s]));
-                if (kc == n_chunks - 1) commit(mb_acc);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(mb_full(s));
+            // the set's chunk after next into the register set just decoded (WIDE), or its
+            // next chunk
+            if constexpr (WIDE) {
+                if ((i & 1) == 0)
+                    wide_load(wb0, wa0);
+                else
+                    wide_load(wb1, wa1);
+            } else {
+                nw_load();
             }
-            // prefetch the next chunk (of this unit or of the next one)
-            if constexpr (!WIDE) {
-                if (kc + 1 < n_chunks) {
-                    load_chunk(up, kc + 1);
-                } else if (u + 1 < end) {
-                    up = unit_ptr(u + 1);
-                    load_chunk(up, 0);
+            if (advance(cu, ckc, NDS) && cu < end) unit_coords(cu, nab, ccp, cab, cbb);
+        }
+        if (failed) *s_fail = 1;
+    } else if (warp == MMA_WARP) {
+        // ---------------- MMA warp: per chunk 4 MMAs D[128 x 256] += X_a [X_b ; W_b]^T ----
+        bool failed = false;
+        int g = 0;                                // chunks whose MMAs this warp issued
+        int n = 0;                                // units started
+        const uint64_t d0 = sdesc(smem_u32(sT), 1024);
+        constexpr int kTileStep = 2 * TILE / 16;  // descriptor start-field step per tile
+        constexpr uint32_t id = idesc(256);
+        for (int u = beg; u < end && !failed; ++u, ++n) {
+            int cp, ab, bb;
+            unit_coords(u, nab, cp, ab, bb);
+            const bool diag = ab == bb;
+            const int b = n & 1;
+            // accumulator buffer b is free once the epilogue has read the unit before last
+            if (n >= 2 && !warp_wait(mb_acce(b), ((n >> 1) - 1) & 1)) {
+                failed = true;
+                break;
+            }
+            fence_after();
+            const uint32_t tacc = tmem + 256 * b;
+            for (int kc = 0; kc < n_chunks; ++kc) {
+                const int s = g % NSTAGE;
+                if (!warp_wait(mb_full(s), (g / NSTAGE) & 1)) {
+                    failed = true;
+                    break;
                 }
+                fence_after();
+                if (lane == 0) {
+                    const uint64_t dS = d0 + (uint64_t)(s * N_TILE * kTileStep);
+                    const uint64_t dA = dS + (uint64_t)((diag ? T_XB : T_XA) * kTileStep);
+                    const uint64_t dB = dS + (uint64_t)(T_XB * kTileStep);
+#pragma unroll
+                    for (int j = 0; j < KC / 16; ++j) mma_ss(tacc, dA + 16 * j, dB + 16 * j, id, (kc | j) != 0);
+                    commit(mb_empty(s));
+                    if (kc == n_chunks - 1) commit(mb_accf(b));
+                }
+                __syncwarp();
+                ++g;
             }
         }
-        if (failed) break;
-        // ---- epilogue: D -> V_ab = g_a conj(g_b) D / T (and the mirrored block) ----
-        if (!mbar_wait(mb_acc, n_done & 1, a.wait_tries)) failed = true;
-        failed = __syncthreads_or(failed) != 0;
-        if (failed) break;
-        fence_after();
-        {
-            constexpr int NPART = NT / 128, PW = 128 / NPART;    // column parts per lane quarter, width
-            const int q = warp & 3, part = warp >> 2;            // TMEM lane quarter, column part
-            const int r = 32 * q + lane, aa = a0 + r;
-            const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-            const float inv_t = 1.f / float(T);
+        // every MMA this warp issued has completed before the tensor memory is released
+        if (g > 0) {
+            if (lane == 0) commit(mb_drain);
+            __syncwarp();
+            mbar_wait(mb_drain, 0);
+        }
+        if (failed) *s_fail = 1;
+    } else {
+        // ---------------- epilogue warps: D -> V_ab = g_a conj(g_b) D / T (and the mirrored block) ----
+        bool failed = false;
+        const int q = warp & 3;                   // TMEM lane quarter this warp may read
+        const float inv_t = 1.f / float(T);
+        // 16-byte row stores when every row starts on a 16-byte boundary
+        const bool vec = (A % 2 == 0) && ((reinterpret_cast<uintptr_t>(a.vis) & 15) == 0);
+        int n = 0;
+        for (int u = beg; u < end; ++u, ++n) {
+            const int b = n & 1;
+            if (!warp_wait(mb_accf(b), (n >> 1) & 1)) {
+                failed = true;
+                break;
+            }
+            fence_after();
+            int cp, ab, bb;
+            unit_coords(u, nab, cp, ab, bb);
+            const bool diag = ab == bb;
+            const int a0 = ab * 128, b0 = bb * 128;
+            const int aa = a0 + 32 * q + lane;
+            const uint32_t tacc = tmem + 256 * b + ((uint32_t)(32 * q) << 16);
             const float2 ga = (aa < A && a.gains) ? a.gains[(size_t)cp * A + aa] : make_float2(1.f, 0.f);
             float2* out = a.vis + (size_t)cp * A * A;
 #pragma unroll 1
-            for (int c = 0; c < PW; c += 16) {
-                float dr[16], di[16];
-                tld<16>(tRe + lane_base + PW * part + c, dr);
-                tld<16>(tIm + lane_base + PW * part + c, di);
+            for (int c = 0; c < 128; c += 8) {
+                float dr[8], di[8];
+                tld<8>(tacc + c, dr);
+                tld<8>(tacc + 128 + c, di);
                 tld_wait();
                 if (aa < A) {
+                    float2 v[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int b = b0 + PW * part + c + j;
-                        if (b < A) {
-                            const float2 gb = a.gains ? __ldg(a.gains + (size_t)cp * A + b) : make_float2(1.f, 0.f);
-                            const float2 w = cmul(ga, make_float2(gb.x, -gb.y));
-                            const float2 v = cmul(w, make_float2(dr[j] * inv_t, di[j] * inv_t));
-                            out[(size_t)aa * A + b] = v;
-                            if (!diag) out[(size_t)b * A + aa] = make_float2(v.x, -v.y);
-                        }
+                    for (int j = 0; j < 8; ++j) {
+                        const int bcol = b0 + c + j;
+                        const float2 gb = (a.gains && bcol < A) ? __ldg(a.gains + (size_t)cp * A + bcol)
+                                                                : make_float2(1.f, 0.f);
+                        const float2 w = cmul(ga, make_float2(gb.x, -gb.y));
+                        v[j] = cmul(w, make_float2(dr[j] * inv_t, di[j] * inv_t));
+                    }
+                    float2* row = out + (size_t)aa * A + b0 + c;
+                    if (vec && b0 + c + 8 <= A) {
+                        float4* r4 = reinterpret_cast<float4*>(row);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) r4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (b0 + c + j < A) row[j] = v[j];
+                    }
+                    if (!diag) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (b0 + c + j < A) out[(size_t)(b0 + c + j) * A + aa] = make_float2(v[j].x, -v[j].y);
                     }
                 }
             }
+            // this warp's reads of buffer b are complete: the MMA warp may overwrite it
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(mb_acce(b));
         }
-        fence_before();
-        __syncthreads();     // accumulators read before the next unit's first MMA overwrites them
-        ++n_done;
+        if (failed) *s_fail = 1;
     }
-    if (failed) {
-        if (tid == 0 && beg < end) {
-            if (a.status) atomicOr(a.status, kStatusCorrelateTimeout);
-            int cp, ab, bb;
-            unit_coords(beg, nab, cp, ab, bb);
-            a.vis[(size_t)cp * A * A + (size_t)(ab * 128) * A + bb * 128] =
-                make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
-        }
-        // wait (bounded) for the MMAs still in flight: each stage's last commit
-        for (int k = g - 1; k >= 0 && k >= g - 2; --k) mbar_wait(smem_u32(&mbar[k & 1]), (k >> 1) & 1);
-    }
+
     fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256) : "memory");
+    if (tid == 0 && *s_fail && beg < end) {
+        if (a.status) atomicOr(a.status, kStatusCorrelateTimeout);
+        int cp, ab, bb;
+        unit_coords(beg, nab, cp, ab, bb);
+        a.vis[(size_t)cp * A * A + (size_t)(ab * 128) * A + bb * 128] =
+            make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+    }
+    if (warp == MMA_WARP) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512) : "memory");
+    }
 }
 
 // ---- the FX route's imaging of an integration's visibilities (Eq. "dirty-image-FX") ----
@@ -681,7 +785,7 @@ cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st) {
     const long long n_units = (long long)a.n_cp * (nab * (nab + 1) / 2);
     if (n_units == 0) return cudaSuccess;
     if (n_units > 2147483647LL) return cudaErrorInvalidValue;   // the kernel indexes units in 32 bits
-    const long long grid = n_units < 2LL * n_sm ? n_units : 2LL * n_sm;
+    const long long grid = n_units < n_sm ? n_units : n_sm;
     switch (vdt) {
         case 1:
             return launch_xeng_t<1, false>(a, grid, st);
