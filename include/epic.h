@@ -282,12 +282,13 @@ epic_status epic_isotropic(const epic_plan *plan, const float *image, const floa
  *             (EPIC_EUNSUPPORTED for complex64).  n_time <= 131072.
  *   vis       device [C][P][A][A] complex64, row-major (a, b); overwritten; 8-byte aligned.
  *
- * Computed on the tensor cores as two real products with FP16 operands (the voltages are exact
- * in FP16) and FP32 accumulation: for 4+4-bit voltages the sums over the call are exact; the
- * gains and 1/T are applied in FP32 afterwards.  Each call is one integration (no
- * continuation).  The plan's mapping is not used.  4+4-bit voltages with A a multiple of 16
- * in a 16-byte-aligned array are read 16 antennas per load (faster); any other A or
- * alignment takes byte loads, with the same results.
+ * Computed on the tensor cores as real products of the real and imaginary parts with FP16
+ * operands (the voltages are exact in FP16) and FP32 accumulation: for 4+4-bit voltages the
+ * sums over the call are exact; the gains and 1/T are applied in FP32 afterwards.  Each call is
+ * one integration (no continuation).  The plan's mapping is not used.  4+4-bit voltages with A
+ * a multiple of 4 in a 4-byte-aligned array are read 4 antennas per load (faster); any other A
+ * or alignment, and FP16 voltages, are read voltage by voltage, with the same results.  Uses
+ * about 200 KB of shared memory and all 512 tensor-memory columns of each SM it runs on.
  */
 epic_status epic_correlate(const epic_plan *plan, const void *volt, int n_time, const float *gains,
                            float *vis, void *stream);

@@ -3,41 +3,40 @@
 // of every antenna pair of every (channel, pol), as a Hermitian product E E^H on the
 // 5th-generation tensor cores.
 //
-// Per (channel, pol) the voltages form E [A x T] complex.  With the K index interleaving real
-// and imaginary parts, k = 2t + {0, 1}:
-//   X_a = (Re E_a(t), Im E_a(t))_t,    W_b = (-Im E_b(t), Re E_b(t))_t,
-//   Re V_ab = sum_k X_a[k] X_b[k],     Im V_ab = sum_k X_a[k] W_b[k],
-// two real matrix products D_re = X X^T and D_im = X W^T with K = 2T.  4+4-bit and FP16
-// voltages are exact in FP16, and each product (at most 64 in magnitude for 4+4-bit) is
-// accumulated in FP32 exactly while the sums stay below 2^24, so the raw sums are exact.
+// Per (channel, pol) the voltages form E [A x T] complex; with R = Re E and I = Im E
+//   Re V = R_a R_b^T + I_a I_b^T,   Im V = I_a R_b^T - R_a I_b^T   (summed over t),
+// four real products with K = T.  4+4-bit and FP16 voltages are exact in FP16, and each product
+// (at most 64 in magnitude for 4+4-bit) is accumulated in FP32 exactly while the sums stay below
+// 2^24, so the raw sums are exact.
 //
 // Work unit: a 128 x 128 block (antenna rows a in block ab, columns b in block bb, bb >= ab:
 // the upper block triangle, the lower one follows by Hermitian symmetry) of one (channel,
 // pol); one persistent CTA per SM takes a contiguous range of units, K walked in chunks of 32
-// samples (K = 64).  The CTA's warps have three roles, handing work over through mbarriers
-// only (no CTA-wide barrier inside the loop):
-//   - 8 decode warps convert a chunk's voltages (loaded into registers ahead of use) into
-//     K-major FP16 tiles (X of the row block, X and W of the column block, stored adjacent so
-//     that [X_b ; W_b] is one N = 256 operand; a diagonal block reuses X_b for the rows) in one
-//     stage of a 4-stage ring; each warp fences its stores for the tensor cores and arrives on
-//     the stage's full barrier, and refills a stage after the MMAs that read it have completed
-//     (the stage's empty barrier, signalled by tcgen05.commit);
-//   - one thread of the MMA warp issues 4 MMAs (M = 128, N = 256, K = 16) per chunk,
-//     D = X_a [X_b ; W_b]^T, Re V in columns 0..127 and Im V in 128..255 of one of two TMEM
-//     accumulator buffers (all 512 columns), commits each chunk to its stage's empty barrier
-//     and a unit's last chunk to the buffer's full barrier;
+// samples.  A chunk's operands are K-major FP16 planes: the B tile [R_b; I_b; -R_b] (384 rows)
+// and the A tile [R_a; I_a] (a diagonal unit takes its A planes from the B tile), so that two
+// MMAs with N = 256 per 16 samples give D = R_a [R_b; I_b]^T + I_a [I_b; -R_b]^T:
+// Re V in columns 0..127 and -Im V in 128..255.  The CTA's warps have three roles, handing work
+// over through mbarriers only (no CTA-wide barrier inside the loop):
+//   - two sets of 8 decode warps take alternate chunks and convert their voltages (loaded into
+//     registers two of the set's chunks ahead) into one stage of a 5-stage ring; each warp fences
+//     its stores for the tensor cores and arrives on the stage's full barrier, and refills a
+//     stage after the MMAs that read it have completed (the stage's empty barrier, signalled by
+//     tcgen05.commit);
+//   - one thread of the MMA warp issues the 4 MMAs (M = 128, N = 256, K = 16) of a chunk into one
+//     of two TMEM accumulator buffers (all 512 columns), commits each chunk to its stage's empty
+//     barrier and a unit's last chunk to the buffer's full barrier;
 //   - 4 epilogue warps (one per TMEM lane quarter) read a finished buffer (tcgen05.ld), scale
-//     by g_a conj(g_b) / T, write the block and, off the diagonal, its mirrored conjugate, then
-//     release the buffer, while the MMAs of the next unit fill the other one.
+//     by g_a conj(g_b) / T, write the block (16-byte stores along rows) and, off the diagonal,
+//     its mirrored conjugate, then release the buffer, while the next unit fills the other one.
 // Every wait is bounded by the plan's try count and taken by a whole warp; on a timeout the role
 // stops, the CTA sets the correlator-timeout bit of the plan's status word and writes NaN into
 // its first output element; the MMA warp waits (full limit) for the MMAs it issued before the
 // tensor memory is released.
 //
-// WIDE (4+4-bit voltages, A a multiple of 16, 16-byte aligned input): a thread loads 16
-// consecutive antennas of one sample with one 16-byte load (a warp reads whole 128-byte
-// lines), and the raw bytes of the next two chunks are held in registers, so a chunk's loads
-// are issued two decode steps before they are used.
+// WIDE (4+4-bit voltages, A a multiple of 4, 4-byte aligned input): a thread loads 4 antennas
+// of each of its 8 samples with 4-byte loads (a warp reads whole 128-byte rows), transposes the
+// 4 x 4 byte blocks with byte permutes and converts each 4 samples of an antenna with two
+// permute + packed-subtraction pairs per plane.  Other voltages are read one by one.
 #include <cuda_fp16.h>
 #include <cstdint>
 #include "moff_common.cuh"
@@ -47,49 +46,41 @@ namespace epic {
 namespace xe {
 using namespace tc;
 
-constexpr int NDS = 2;                      // decode warp sets, taking alternate chunks
+constexpr int NDS = 3;                      // decode warp sets, taking alternate chunks
 constexpr int NDW = 8 * NDS;                // decode warps (a set's tile mappings take 256 threads)
 constexpr int NEW = 4;                      // epilogue warps, one per TMEM lane quarter
 constexpr int MMA_WARP = NDW;               // the warp whose first thread issues the MMAs
 constexpr int NT = 32 * (NDW + 1 + NEW);    // one CTA per SM
-constexpr int TC = 32;                      // samples per K chunk
-constexpr int KC = 2 * TC;                  // K per chunk (re/im interleaved)
-constexpr int TILE = 128 * KC;              // halves per operand tile (16 KB)
-enum { T_XA, T_XB, T_WB, N_TILE };          // X_b and W_b adjacent: one N = 256 operand
-constexpr int NSTAGE = 4;
+constexpr int TC = 32;                      // samples per K chunk (K = 32: one real plane per operand row)
+// K-major FP16 planes without swizzle: 8 x 8 core matrices of 128 bytes, a row group of 8 rows
+// holding the chunk's 4 core matrices along K
+constexpr int kRowGroupBytes = 4 * 128;
+constexpr int kPlaneBytes = 16 * kRowGroupBytes;       // 128 rows x 32 samples (8 KB)
+constexpr int kBTileBytes = 3 * kPlaneBytes;           // [Re_b; Im_b; -Re_b]: 384 rows
+constexpr int kATileBytes = 2 * kPlaneBytes;           // [Re_a; Im_a]
+constexpr int kStageBytes = kBTileBytes + kATileBytes; // 40 KB
+constexpr int NSTAGE = 5;
 // mbarriers: stage full [NSTAGE], stage empty [NSTAGE], accumulator full [2], accumulator
 // empty [2], drain
 constexpr int N_MBAR = 2 * NSTAGE + 5;
 
-constexpr size_t smem_bytes() { return sizeof(__half) * (size_t)NSTAGE * N_TILE * TILE + 8 * N_MBAR + 16; }
+constexpr size_t smem_bytes() { return (size_t)NSTAGE * kStageBytes + 8 * N_MBAR + 16; }
 
-// FP16 operand pairs of one voltage, as half2 bits: X = (re, im), W = (-im, re).  FP16 input
-// is already the pair.  A 4+4-bit byte holds two 4-bit two's-complement values; XOR with 8
-// biases each to n + 8 in [0, 15], which placed in the mantissa of 1024 (bits 0x6400 | (n + 8))
-// is exactly 1032 + n, so one packed subtraction of 1032 yields both components exactly.
+// One voltage as an FP16 (re, im) pair (half2 bits).  FP16 input is already the pair.  A
+// 4+4-bit byte holds two 4-bit two's-complement values (re in the high nibble); XOR with 8 biases
+// each to n + 8 in [0, 15], which placed in the mantissa of 1024 (bits 0x6400 | (n + 8)) is
+// exactly 1032 + n, so one packed subtraction of 1032 yields both components exactly.
 template <int VDT>
-__device__ __forceinline__ void operand_pairs(typename Volt<VDT>::T raw, uint32_t& x, uint32_t& w) {
+__device__ __forceinline__ uint32_t voltage_pair(typename Volt<VDT>::T raw) {
     if constexpr (VDT == 1) {
-        x = raw;
+        return raw;
     } else {
         const uint32_t t = (uint32_t)raw ^ 0x88u;
         const uint32_t u = ((t >> 4) & 0xFu) | ((t & 0xFu) << 16) | 0x64006400u;
         const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&u), __halves2half2(__ushort_as_half(0x6408),
                                                                                           __ushort_as_half(0x6408)));
-        x = *reinterpret_cast<const uint32_t*>(&h);
+        return *reinterpret_cast<const uint32_t*>(&h);
     }
-    w = __byte_perm(x, 0, 0x1032) ^ 0x8000u;     // swap the halves, negate the new low half
-}
-
-// Operand pair X = (re, im) of byte i of a word of 4+4-bit voltages, from the word's biased
-// high nibbles H and low nibbles L (each n ^ 8 in [0, 15], one per byte): the same exact
-// 1032 + n construction as operand_pairs.
-template <int I>
-__device__ __forceinline__ uint32_t ci4_pair(uint32_t H, uint32_t L) {
-    const uint32_t u = (__byte_perm(H, L, I | ((4 + I) << 8)) & 0x00FF00FFu) | 0x64006400u;
-    const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&u), __halves2half2(__ushort_as_half(0x6408),
-                                                                                      __ushort_as_half(0x6408)));
-    return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 // unit -> (cp, row block, column block), column block >= row block (32-bit: the launcher
@@ -111,8 +102,8 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
     static_assert(!WIDE || VDT == 2, "the wide loads are for 4+4-bit voltages");
     using VT = typename Volt<VDT>::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __half* sT = reinterpret_cast<__half*>(smem_raw);                           // [NSTAGE][N_TILE][TILE]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sT + NSTAGE * N_TILE * TILE);   // [N_MBAR]
+    unsigned char* sT = smem_raw;                                               // [NSTAGE] stages
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sT + (size_t)NSTAGE * kStageBytes);   // [N_MBAR]
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + N_MBAR);
     int* s_fail = reinterpret_cast<int*>(tslot + 1);
 
@@ -160,9 +151,22 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
     const int beg = (int)beg_l, end = (int)end_l;
 
     if (warp < NDW) {
-        // ---------------- decode warps: raw voltages -> FP16 operand tiles of stage g % NSTAGE ----
-        // set dset decodes the CTA's chunks g = dset, dset + NDS, ...; within a set, warp dw
+        // ---------------- decode warps: raw voltages -> FP16 operand planes of stage g % NSTAGE ----
+        // Set dset decodes the CTA's chunks g = dset, dset + NDS, ...  Within a set, warps 0-3 fill
+        // the B tile ([Re; Im; -Re] of the column block) and warps 4-7 the A tile ([Re; Im] of the
+        // row block; nothing on a diagonal unit), warp dw taking samples 8 (dw % 4) .. + 7 of the
+        // chunk and lane l antennas 4 l .. 4 l + 3 of the block.  The thread's slot i holds antenna
+        // 4 l + (i + rot) % 4, rot = (l / 2) % 4, so that the 8 lanes of a quarter-warp write the
+        // 16-byte rows of 8 distinct rows mod 8 (all 32 banks) with each 16-byte store.
         const int dw = warp & 7, dset = warp >> 3;
+        const bool bside = dw < 4;
+        const int so = dw & 3, rot = (lane >> 1) & 3;
+        int soff[4];                                   // byte offset in a plane of slot i's row
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * lane + ((i + rot) & 3);
+            soff[i] = (r >> 3) * kRowGroupBytes + so * 128 + (r & 7) * 16;
+        }
         // (unit, chunk) cursors step NDS chunks at a time; true when the unit changed
         auto advance = [&](int& uu, int& kk, int by) -> bool {
             kk += by;
@@ -174,133 +178,102 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
             }
             return changed;
         };
-        // decode mapping: lane -> (row % 8, sample % 4), so that one warp's 4-byte stores cover 32
-        // distinct banks of a core-matrix row block.  Thread (warp w, lane) owns rows
-        // r0 = 8 w + lane % 8 and r0 + 64 of a tile and samples 4 j + lane / 8, j < TC / 4, of a
-        // chunk: its voltages are V[(t CP + cp) A + row] (one base pointer per tile and a sample
-        // stride), its tile words sit at a fixed offset + 32 j (+ 2048 for the second row).  The raw
-        // voltages of the next chunk are loaded into registers (all at once) while the current
-        // chunk is on the tensor cores.
-        static_assert(NDW % 8 == 0, "two rows of a 128-row tile per thread of a decode set");
-        constexpr int NJ = TC / 4;
-        const int lr = lane & 7, lt = lane >> 3;
-        const int r0 = 8 * dw + lr;
-        const int sbase = 256 * dw + 4 * lr + lt;      // word offset of (r0, 2 lt) in a tile
-        const long long RS = (long long)CP * A;          // sample stride of the voltages
-        // per unit: this thread's voltage pointers at sample lt of chunk 0 and its row validity
-        struct UnitPtr {
-            const VT* pb;
-            const VT* pa;
-            bool vb0, vb1, va0, va1;
+        const long long RS = (long long)CP * A;       // sample stride of the voltages
+        // slot i's row of the Re, Im (and, B tile, -Re) planes: 8 samples each
+        auto put_planes = [&](unsigned char* tile, int i, const uint4& re, const uint4& im, bool neg) {
+            *reinterpret_cast<uint4*>(tile + soff[i]) = re;
+            *reinterpret_cast<uint4*>(tile + kPlaneBytes + soff[i]) = im;
+            if (neg)
+                *reinterpret_cast<uint4*>(tile + 2 * kPlaneBytes + soff[i]) =
+                    make_uint4(re.x ^ 0x80008000u, re.y ^ 0x80008000u, re.z ^ 0x80008000u, re.w ^ 0x80008000u);
         };
-        VT rb[WIDE ? 1 : 2 * NJ], ra[WIDE ? 1 : 2 * NJ];
-        auto unit_ptr = [&](int u) {
-            int cp, ab, bb;
-            unit_coords(u, nab, cp, ab, bb);
-            UnitPtr p;
-            p.pb = V + (long long)cp * A + bb * 128 + r0 + lt * RS;
-            p.pa = V + (long long)cp * A + ab * 128 + r0 + lt * RS;
-            p.vb0 = bb * 128 + r0 < A;
-            p.vb1 = bb * 128 + r0 + 64 < A;
-            p.va0 = ab != bb && ab * 128 + r0 < A;
-            p.va1 = ab != bb && ab * 128 + r0 + 64 < A;
-            return p;
+        // the same from the slot's 8 samples as (re, im) FP16 pairs x[s]
+        auto put_pairs = [&](unsigned char* tile, int i, const uint32_t (&x)[8], bool neg) {
+            const uint4 re = make_uint4(__byte_perm(x[0], x[1], 0x5410), __byte_perm(x[2], x[3], 0x5410),
+                                        __byte_perm(x[4], x[5], 0x5410), __byte_perm(x[6], x[7], 0x5410));
+            const uint4 im = make_uint4(__byte_perm(x[0], x[1], 0x7632), __byte_perm(x[2], x[3], 0x7632),
+                                        __byte_perm(x[4], x[5], 0x7632), __byte_perm(x[6], x[7], 0x7632));
+            put_planes(tile, i, re, im, neg);
         };
-        auto load_chunk = [&](const UnitPtr& p, int kc) {
-            if constexpr (!WIDE) {
-                const int tq = kc * TC + lt;
-                const VT* pb = p.pb + (long long)(kc * TC) * RS;
-                const VT* pa = p.pa + (long long)(kc * TC) * RS;
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) {
-                    const bool tin = tq + 4 * j < T;
-                    rb[2 * j] = (tin && p.vb0) ? __ldg(pb) : VT(0);
-                    rb[2 * j + 1] = (tin && p.vb1) ? __ldg(pb + 64) : VT(0);
-                    ra[2 * j] = (tin && p.va0) ? __ldg(pa) : VT(0);
-                    ra[2 * j + 1] = (tin && p.va1) ? __ldg(pa + 64) : VT(0);
-                    pb += 4 * RS;
-                    pa += 4 * RS;
-                }
-            }
-        };
-
-        // WIDE mapping: thread (warp w, lane l) loads rows 16 p .. 16 p + 15, p = l % 8, of
-        // sample tw = 4 w + l / 8 of a chunk.  In a tile, row r and sample t sit at word
-        // 256 (r / 8) + 32 (t / 4) + 4 (r % 8) + t % 4 (bank 4 (r % 8) + t % 4).  Store instruction
-        // (s, i) of a lane writes row 16 p + 4 (s ^ si) + (i + ri) % 4 with ri = p % 4, si = p / 4:
-        // the 32 lanes then differ in (t % 4, ri, si) and hit 32 distinct banks.  One byte permute
-        // per word selects word s ^ si and rotates its bytes by ri.
-        const int wp = lane & 7, wri = lane & 3, wsi = (lane >> 2) & 1, wtw = 4 * dw + (lane >> 3);
-        const uint32_t wsel = (uint32_t)(((0 + wri) & 3) | (((1 + wri) & 3) << 4) | (((2 + wri) & 3) << 8) |
-                                         (((3 + wri) & 3) << 12)) + (wsi ? 0x4444u : 0u);
-        int woff[2][4];                                  // word offsets for s % 2 and i (+ 256 (s / 2))
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                woff[j][i] = 512 * wp + 32 * dw + (lane >> 3) + 16 * (j ^ wsi) + 4 * ((i + wri) & 3);
-        uint4 wb0 = make_uint4(0, 0, 0, 0), wa0 = wb0, wb1 = wb0, wa1 = wb0;   // a set's even / odd chunks
+        // raw words of this thread's 8 samples (fast path: byte i = antenna 4 l + i), two chunks
+        uint32_t rw0[8], rw1[8];
         int lu = beg, lkc = 0, lcp = 0, lab = 0, lbb = 0;                       // load cursor
         advance(lu, lkc, dset);
         if (lu < end) unit_coords(lu, nab, lcp, lab, lbb);
-        const unsigned char* VW = static_cast<const unsigned char*>(a.volt);
-        auto wide_load = [&](uint4& xb, uint4& xa) {
-            xb = make_uint4(0, 0, 0, 0);
-            xa = xb;
-            if (lu >= end) return;
-            const int t = lkc * TC + wtw;
-            if (t < T) {
-                const unsigned char* row = VW + (long long)t * RS + (long long)lcp * A + 16 * wp;
-                if (lbb * 128 + 16 * wp < A) xb = __ldg(reinterpret_cast<const uint4*>(row + lbb * 128));
-                if (lab != lbb && lab * 128 + 16 * wp < A) xa = __ldg(reinterpret_cast<const uint4*>(row + lab * 128));
+        const unsigned char* VB = static_cast<const unsigned char*>(a.volt);
+        auto fast_load = [&](uint32_t (&w)[8]) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s) w[s] = 0;
+            if (lu < end && (bside || lab != lbb)) {
+                const int col = (bside ? lbb : lab) * 128 + 4 * lane;
+                if (col < A) {
+                    const unsigned char* base = VB + (long long)lcp * A + col;
+                    const int t0 = lkc * TC + 8 * so;
+#pragma unroll
+                    for (int s = 0; s < 8; ++s)
+                        if (t0 + s < T) w[s] = __ldg(reinterpret_cast<const uint32_t*>(base + (long long)(t0 + s) * RS));
+                }
             }
             if (advance(lu, lkc, NDS) && lu < end) unit_coords(lu, nab, lcp, lab, lbb);
         };
-        auto wide_word = [&](uint32_t* tile, uint32_t* wtile, uint32_t R, int s) {
-            const uint32_t H = ((R >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-            const uint32_t L = (R & 0x0F0F0F0Fu) ^ 0x08080808u;
-            const uint32_t x0 = ci4_pair<0>(H, L), x1 = ci4_pair<1>(H, L), x2 = ci4_pair<2>(H, L), x3 = ci4_pair<3>(H, L);
-            const int* o = woff[s & 1];
-            const int hi = 256 * (s >> 1);
-            tile[o[0] + hi] = x0;
-            tile[o[1] + hi] = x1;
-            tile[o[2] + hi] = x2;
-            tile[o[3] + hi] = x3;
-            if (wtile) {
-                wtile[o[0] + hi] = __byte_perm(x0, 0, 0x1032) ^ 0x8000u;
-                wtile[o[1] + hi] = __byte_perm(x1, 0, 0x1032) ^ 0x8000u;
-                wtile[o[2] + hi] = __byte_perm(x2, 0, 0x1032) ^ 0x8000u;
-                wtile[o[3] + hi] = __byte_perm(x3, 0, 0x1032) ^ 0x8000u;
+        // 4+4-bit words (4 samples of one slot) -> FP16 pairs: the biased nibble h = n ^ 8 in
+        // [0, 15] placed under the exponent byte 0x64 is exactly 1024 + h, and 1024 + h - 1032 = n
+        auto nib_pairs = [](uint32_t N, uint32_t& p01, uint32_t& p23) {
+            const __half2 bias = __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));
+            uint32_t u0 = __byte_perm(N, 0x64646464u, 0x4140), u1 = __byte_perm(N, 0x64646464u, 0x4342);
+            const __half2 h0 = __hsub2(*reinterpret_cast<const __half2*>(&u0), bias);
+            const __half2 h1 = __hsub2(*reinterpret_cast<const __half2*>(&u1), bias);
+            p01 = *reinterpret_cast<const uint32_t*>(&h0);
+            p23 = *reinterpret_cast<const uint32_t*>(&h1);
+        };
+        auto fast_decode = [&](const uint32_t (&w)[8], unsigned char* tile) {
+            // rotate each sample's word so that byte i is slot i's antenna, then transpose the two
+            // 4 x 4 byte blocks: q[i][h] = samples 4 h .. 4 h + 3 of slot i
+            uint32_t x[8], q[4][2];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) x[s] = __funnelshift_r(w[s], w[s], 8 * rot);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t lo01 = __byte_perm(x[4 * h], x[4 * h + 1], 0x5140);
+                const uint32_t hi01 = __byte_perm(x[4 * h], x[4 * h + 1], 0x7362);
+                const uint32_t lo23 = __byte_perm(x[4 * h + 2], x[4 * h + 3], 0x5140);
+                const uint32_t hi23 = __byte_perm(x[4 * h + 2], x[4 * h + 3], 0x7362);
+                q[0][h] = __byte_perm(lo01, lo23, 0x5410);
+                q[1][h] = __byte_perm(lo01, lo23, 0x7632);
+                q[2][h] = __byte_perm(hi01, hi23, 0x5410);
+                q[3][h] = __byte_perm(hi01, hi23, 0x7632);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint4 re, im;
+                // re = high nibbles, im = low nibbles, each biased by 8
+                const uint32_t H0 = ((q[i][0] >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u, L0 = (q[i][0] & 0x0F0F0F0Fu) ^ 0x08080808u;
+                const uint32_t H1 = ((q[i][1] >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u, L1 = (q[i][1] & 0x0F0F0F0Fu) ^ 0x08080808u;
+                nib_pairs(H0, re.x, re.y);
+                nib_pairs(H1, re.z, re.w);
+                nib_pairs(L0, im.x, im.y);
+                nib_pairs(L1, im.z, im.w);
+                put_planes(tile, i, re, im, bside);
             }
         };
-        auto wide_decode = [&](const uint4& xb, const uint4& xa, __half* st, bool diag) {
-            uint32_t* tX = reinterpret_cast<uint32_t*>(st + T_XB * TILE);
-            uint32_t* tW = reinterpret_cast<uint32_t*>(st + T_WB * TILE);
-            uint32_t* tA = reinterpret_cast<uint32_t*>(st + T_XA * TILE);
-            wide_word(tX, tW, __byte_perm(xb.x, xb.y, wsel), 0);
-            wide_word(tX, tW, __byte_perm(xb.y, xb.x, wsel), 1);
-            wide_word(tX, tW, __byte_perm(xb.z, xb.w, wsel), 2);
-            wide_word(tX, tW, __byte_perm(xb.w, xb.z, wsel), 3);
-            if (!diag) {
-                wide_word(tA, nullptr, __byte_perm(xa.x, xa.y, wsel), 0);
-                wide_word(tA, nullptr, __byte_perm(xa.y, xa.x, wsel), 1);
-                wide_word(tA, nullptr, __byte_perm(xa.z, xa.w, wsel), 2);
-                wide_word(tA, nullptr, __byte_perm(xa.w, xa.z, wsel), 3);
+        // any voltage type, any A: slot by slot, voltage by voltage
+        auto slow_decode = [&](int cp, int blk, int kc, unsigned char* tile) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int ant = blk * 128 + 4 * lane + ((i + rot) & 3);
+                uint32_t x[8];
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const int t = kc * TC + 8 * so + s;
+                    const VT raw = (ant < A && t < T) ? __ldg(V + (long long)t * RS + (long long)cp * A + ant) : VT(0);
+                    x[s] = voltage_pair<VDT>(raw);
+                }
+                put_pairs(tile, i, x, bside);
             }
-        };
-
-
-        // non-WIDE loads: the chunk at the load cursor into rb / ra
-        UnitPtr up = (!WIDE && lu < end) ? unit_ptr(lu) : UnitPtr{};
-        auto nw_load = [&]() {
-            if (lu < end) load_chunk(up, lkc);
-            if (advance(lu, lkc, NDS) && lu < end) up = unit_ptr(lu);
         };
         if constexpr (WIDE) {
-            wide_load(wb0, wa0);
-            wide_load(wb1, wa1);
-        } else {
-            nw_load();
+            fast_load(rw0);
+            fast_load(rw1);
         }
         bool failed = false;
         int cu = beg, ckc = 0, ccp = 0, cab = 0, cbb = 0;                       // decode cursor
@@ -315,54 +288,41 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
                 break;
             }
             const bool diag = cab == cbb;
-            __half* st = sT + s * N_TILE * TILE;
-            if constexpr (WIDE) {
-                if ((i & 1) == 0)
-                    wide_decode(wb0, wa0, st, diag);
-                else
-                    wide_decode(wb1, wa1, st, diag);
-            } else {
-                uint32_t* sxb = reinterpret_cast<uint32_t*>(st + T_XB * TILE) + sbase;
-                uint32_t* swb = reinterpret_cast<uint32_t*>(st + T_WB * TILE) + sbase;
-                uint32_t* sxa = reinterpret_cast<uint32_t*>(st + T_XA * TILE) + sbase;
-#pragma unroll
-                for (int j = 0; j < NJ; ++j)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        uint32_t x, w;
-                        operand_pairs<VDT>(rb[2 * j + h], x, w);
-                        sxb[32 * j + 2048 * h] = x;
-                        swb[32 * j + 2048 * h] = w;
-                        if (!diag) {
-                            operand_pairs<VDT>(ra[2 * j + h], x, w);
-                            sxa[32 * j + 2048 * h] = x;
-                        }
-                    }
+            unsigned char* st = sT + (size_t)s * kStageBytes;
+            if (bside || !diag) {
+                unsigned char* tile = bside ? st : st + kBTileBytes;
+                if constexpr (WIDE) {
+                    if ((i & 1) == 0)
+                        fast_decode(rw0, tile);
+                    else
+                        fast_decode(rw1, tile);
+                } else {
+                    slow_decode(ccp, bside ? cbb : cab, ckc, tile);
+                }
             }
-            // this warp's tile stores, visible to the tensor cores, then its arrival
+            // this warp's stores, visible to the tensor cores, then its arrival
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(mb_full(s));
-            // the set's chunk after next into the register set just decoded (WIDE), or its
-            // next chunk
+            // the set's chunk after next into the register set just decoded
             if constexpr (WIDE) {
                 if ((i & 1) == 0)
-                    wide_load(wb0, wa0);
+                    fast_load(rw0);
                 else
-                    wide_load(wb1, wa1);
-            } else {
-                nw_load();
+                    fast_load(rw1);
             }
             if (advance(cu, ckc, NDS) && cu < end) unit_coords(cu, nab, ccp, cab, cbb);
         }
         if (failed) *s_fail = 1;
     } else if (warp == MMA_WARP) {
-        // ---------------- MMA warp: per chunk 4 MMAs D[128 x 256] += X_a [X_b ; W_b]^T ----
+        // ---------------- MMA warp: per K step of 16 samples two MMAs (M = 128, N = 256) ----
+        //   D += Re_a [Re_b; Im_b]^T,  D += Im_a [Im_b; -Re_b]^T
+        // so that D[:, 0:128] = Re_a Re_b + Im_a Im_b = Re V and D[:, 128:256] = Re_a Im_b - Im_a Re_b
+        // = -Im V (summed over the samples); on a diagonal unit the A planes are the B tile's.
         bool failed = false;
         int g = 0;                                // chunks whose MMAs this warp issued
         int n = 0;                                // units started
-        const uint64_t d0 = sdesc(smem_u32(sT), 1024);
-        constexpr int kTileStep = 2 * TILE / 16;  // descriptor start-field step per tile
+        const uint64_t d0 = sdesc(smem_u32(sT), kRowGroupBytes);
         constexpr uint32_t id = idesc(256);
         for (int u = beg; u < end && !failed; ++u, ++n) {
             int cp, ab, bb;
@@ -384,11 +344,16 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
                 }
                 fence_after();
                 if (lane == 0) {
-                    const uint64_t dS = d0 + (uint64_t)(s * N_TILE * kTileStep);
-                    const uint64_t dA = dS + (uint64_t)((diag ? T_XB : T_XA) * kTileStep);
-                    const uint64_t dB = dS + (uint64_t)(T_XB * kTileStep);
+                    // descriptor start fields count 16 bytes
+                    const uint64_t dB1 = d0 + (uint64_t)(s * kStageBytes / 16);
+                    const uint64_t dB2 = dB1 + kPlaneBytes / 16;
+                    const uint64_t dA1 = diag ? dB1 : dB1 + kBTileBytes / 16;
+                    const uint64_t dA2 = dA1 + kPlaneBytes / 16;
 #pragma unroll
-                    for (int j = 0; j < KC / 16; ++j) mma_ss(tacc, dA + 16 * j, dB + 16 * j, id, (kc | j) != 0);
+                    for (int j = 0; j < TC / 16; ++j) {
+                        mma_ss(tacc, dA1 + 16 * j, dB1 + 16 * j, id, (kc | j) != 0);
+                        mma_ss(tacc, dA2 + 16 * j, dB2 + 16 * j, id, 1);
+                    }
                     commit(mb_empty(s));
                     if (kc == n_chunks - 1) commit(mb_accf(b));
                 }
@@ -440,7 +405,7 @@ __global__ void __launch_bounds__(NT, 1) xeng_kernel(const XengArgs a) {
                         const float2 gb = (a.gains && bcol < A) ? __ldg(a.gains + (size_t)cp * A + bcol)
                                                                 : make_float2(1.f, 0.f);
                         const float2 w = cmul(ga, make_float2(gb.x, -gb.y));
-                        v[j] = cmul(w, make_float2(dr[j] * inv_t, di[j] * inv_t));
+                        v[j] = cmul(w, make_float2(dr[j] * inv_t, -di[j] * inv_t));   // D holds -Im V
                     }
                     float2* row = out + (size_t)aa * A + b0 + c;
                     if (vec && b0 + c + 8 <= A) {
@@ -790,8 +755,8 @@ cudaError_t launch_xeng(int vdt, const XengArgs& a, int n_sm, cudaStream_t st) {
         case 1:
             return launch_xeng_t<1, false>(a, grid, st);
         case 2:
-            // 16-byte loads of 16 antennas need every row of 16 to start on a 16-byte boundary
-            if (a.n_ant % 16 == 0 && reinterpret_cast<uintptr_t>(a.volt) % 16 == 0)
+            // 4-byte loads of 4 antennas need every group of 4 to start on a 4-byte boundary
+            if (a.n_ant % 4 == 0 && reinterpret_cast<uintptr_t>(a.volt) % 4 == 0)
                 return launch_xeng_t<2, true>(a, grid, st);
             return launch_xeng_t<2, false>(a, grid, st);
         default:

@@ -71,9 +71,10 @@ def test_lwa_slice_ci4_gains(epic):
 
 
 def test_lwa_units_beyond_one_per_cta(epic):
-    """384 units (64 channels x 2 pols x 3 blocks) on at most 304 CTAs: CTAs that own two
-    units load the next unit's first chunks while finishing the current one (4+4-bit voltages
-    on 16-byte loads; 40 samples, a ragged second chunk)."""
+    """384 units (64 channels x 2 pols x 3 blocks) on at most one CTA per SM: CTAs that own
+    several units load the next unit's first chunks while finishing the current one and drain
+    one accumulator buffer while filling the other (4+4-bit voltages on 4-byte loads; 40
+    samples, a ragged second chunk)."""
     wl = synth.workload_lwa(n_chan=64, n_time=40, chan_index=list(range(0, 128, 2)))
     g = synth.random_gains(np.random.default_rng(9), (wl.n_chan, wl.n_pol, wl.n_ant))
     _, vis = run(epic, wl, g)
@@ -92,7 +93,8 @@ def test_hera_slice_f16(epic):
     (129, 31, 1, 2, "f16"),     # a one-antenna tail block, less than one chunk
     (300, 33, 2, 1, "ci4"),     # three blocks, one sample past a chunk
     (640, 64, 1, 1, "ci4"),     # five full blocks, two full chunks
-    (336, 45, 1, 2, "ci4"),     # 16-byte loads with an 80-antenna tail block, a ragged chunk
+    (336, 45, 1, 2, "ci4"),     # 4-byte loads with an 80-antenna tail block, a ragged chunk
+    (130, 70, 1, 1, "ci4"),     # A not a multiple of 4: byte loads, a two-antenna tail block
 ])
 def test_small_shapes(epic, n_ant, n_time, n_chan, n_pol, vdtype):
     wl = _small(n_ant, n_time, n_chan, n_pol, vdtype, seed=n_ant + n_time)
