@@ -196,3 +196,20 @@ def test_gpu_fx_image_plane_groupings(epic, n_chan, n_pol):
         for p in range(n_pol):
             assert np.linalg.norm(img[c, p] - want[c, p]) / np.linalg.norm(want[c, p]) < 1e-4, (c, p)
             assert np.abs(img[c, p] - want[c, p]).max() < 1e-4 * np.abs(want[c, p]).max(), (c, p)
+
+
+@pytest.mark.parametrize("n_ant, n_time, n_chan, n_pol", [
+    (256, 40, 52, 2),     # 312 units: two per SM and 8 left over (two chunks)
+    (200, 70, 51, 1),     # 153 units: one left over, a ragged 70-sample K, a 72-antenna tail block
+])
+def test_units_not_dividing_over_the_sms(epic, n_ant, n_time, n_chan, n_pol):
+    """Unit counts that leave some SMs one unit more than others, 4+4-bit voltages with gains:
+    every matrix against the oracle, and a second call on the same plan gives the same bits."""
+    wl = _small(n_ant, n_time, n_chan, n_pol, "ci4", seed=n_ant + n_chan)
+    g = synth.random_gains(np.random.default_rng(n_time), (n_chan, n_pol, n_ant))
+    plan, vis = run(epic, wl, g)
+    check(vis, wl, g, "A=%d C=%d" % (n_ant, n_chan))
+    g2 = torch.from_numpy(np.ascontiguousarray(g.astype(np.complex64))).cuda()
+    vis2 = plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda(), g2)
+    torch.cuda.synchronize()
+    assert np.array_equal(vis2.cpu().numpy(), vis)
