@@ -13,6 +13,7 @@
 #include "../../include/epic.h"
 #include "epic_internal.h"
 #include "epic_plan.h"
+#include "epic_trace.h"
 
 namespace {
 thread_local std::string g_err;
@@ -187,6 +188,7 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
                         const double* kern_dxdy, const double* kern_w, double dx,
                         const double* origin_xy, int n_grid, int n_pad, int n_chan, int n_pol,
                         int volt_dtype, int device) {
+    EpicRange range("epic_create");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan out-pointer is NULL");
     *plan = nullptr;
@@ -571,6 +573,7 @@ epic_status epic_set_wait_limit(epic_plan* plan, int tries) {
 }
 
 epic_status epic_sync(const epic_plan* plan, void* stream) {
+    EpicRange range("epic_sync");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     EpicDeviceGuard guard(plan->device);
@@ -671,6 +674,7 @@ epic_status epic_plan_info(const epic_plan* plan, int64_t* nnz, int64_t* n_cells
 epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, const float* gains,
                        double* accum, double* power, int64_t t_prev, float* image, float* autocorr,
                        void* stream) {
+    EpicRange range("epic_image");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
@@ -736,6 +740,7 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
 
 epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_time, const float* gains,
                                 const float* grad_image, float* grad_gains, void* stream) {
+    EpicRange range("epic_image_backward");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
@@ -780,6 +785,7 @@ epic_status epic_image_backward(const epic_plan* plan, const void* volt, int n_t
 
 epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time, const float* gains,
                             double* accum4, int64_t t_prev, float* image, float* cross, void* stream) {
+    EpicRange range("epic_image_xpol");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (plan->n_pol != 2) return epic_fail(EPIC_EINVAL, "cross-polarisation images need a plan with 2 pols (has %d)", plan->n_pol);
@@ -834,6 +840,7 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
 
 epic_status epic_fengine(int n_ant, int n_pol, int n_chan, int n_time, int in_dtype, const void* raw, int out_dtype,
                          void* volt, int device, void* stream) {
+    EpicRange range("epic_fengine");
     epic_clear_error();
     if (n_ant < 1 || n_pol < 1 || n_time < 0) return epic_fail(EPIC_EINVAL, "bad sizes");
     if (n_chan != 32 && n_chan != 64 && n_chan != 128 && n_chan != 256 && n_chan != 512)
@@ -865,6 +872,7 @@ epic_status epic_fengine(int n_ant, int n_pol, int n_chan, int n_time, int in_dt
 }
 
 epic_status epic_weff(const epic_plan* plan, float* weff, void* stream) {
+    EpicRange range("epic_weff");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (!weff) return epic_fail(EPIC_EINVAL, "weff is NULL");
@@ -885,6 +893,7 @@ epic_status epic_weff(const epic_plan* plan, float* weff, void* stream) {
 
 epic_status epic_isotropic(const epic_plan* plan, const float* image, const float* autocorr, const float* weff,
                            float rel_floor, float* iso, void* stream) {
+    EpicRange range("epic_isotropic");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (!image || !autocorr || !weff || !iso) return epic_fail(EPIC_EINVAL, "NULL device array");
@@ -906,6 +915,7 @@ epic_status epic_isotropic(const epic_plan* plan, const float* image, const floa
 
 epic_status epic_correlate(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* vis,
                            void* stream) {
+    EpicRange range("epic_correlate");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);
@@ -937,6 +947,7 @@ epic_status epic_correlate(const epic_plan* plan, const void* volt, int n_time, 
 }
 
 epic_status epic_fx_image(const epic_plan* plan, const float* vis, float* image, void* stream) {
+    EpicRange range("epic_fx_image");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (!vis || !image) return epic_fail(EPIC_EINVAL, "NULL device array");
@@ -970,6 +981,7 @@ epic_status epic_fx_image(const epic_plan* plan, const float* vis, float* image,
 
 epic_status epic_grid(const epic_plan* plan, const void* volt, int n_time, const float* gains, float* grid,
                       void* stream) {
+    EpicRange range("epic_grid");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (n_time < 1) return epic_fail(EPIC_EINVAL, "n_time = %d must be >= 1", n_time);

@@ -11,6 +11,7 @@
 #include "../../include/epic.h"
 #include "epic_internal.h"
 #include "epic_plan.h"
+#include "epic_trace.h"
 
 namespace {
 
@@ -159,6 +160,7 @@ epic_status enqueue(epic_batch* b, const void* const* volt, const int* n_time, c
 extern "C" {
 
 epic_status epic_batch_create(epic_batch** batch, int n_plans, epic_plan* const* plans) {
+    EpicRange range("epic_batch_create");
     epic_clear_error();
     if (!batch) return epic_fail(EPIC_EINVAL, "batch out-pointer is NULL");
     *batch = nullptr;
@@ -219,6 +221,7 @@ void epic_batch_destroy(epic_batch* batch) {
 
 epic_status epic_batch_image(epic_batch* batch, const void* const* volt, const int* n_time, const float* const* gains,
                              double* const* accum, float* const* image, void* stream) {
+    EpicRange range("epic_batch_image");
     epic_clear_error();
     epic_status s = check_call(batch, volt, n_time, gains, accum, image);
     if (s != EPIC_OK) return s;
@@ -229,6 +232,7 @@ epic_status epic_batch_image(epic_batch* batch, const void* const* volt, const i
 
 epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, const int* n_time,
                                 const float* const* gains, double* const* accum, void* stream) {
+    EpicRange range("epic_batch_autotune");
     epic_clear_error();
     epic_status s = check_call(batch, volt, n_time, gains, accum, nullptr);
     if (s != EPIC_OK) return s;

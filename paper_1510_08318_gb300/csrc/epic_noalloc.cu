@@ -16,6 +16,7 @@
 #include "../../include/epic.h"
 #include "epic_internal.h"
 #include "epic_plan.h"
+#include "epic_trace.h"
 
 namespace {
 
@@ -50,6 +51,7 @@ epic_status noalloc_scratch(int device, float2** out) {
 extern "C" epic_status epic_image_noalloc(const epic_plan* plan, const void* volt, int n_time, const float* gains,
                                           double* accum, double* power, int64_t t_prev, float* image,
                                           float* autocorr, int chunk_items, void* stream) {
+    EpicRange range("epic_image_noalloc");
     epic_clear_error();
     if (!plan) return epic_fail(EPIC_EINVAL, "plan is NULL");
     if (plan->n_pad != 512)
