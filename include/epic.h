@@ -373,8 +373,10 @@ epic_status epic_batch_image(epic_batch *batch, const void *const *volt, const i
  * overwritten): for each size class, the kernel form and worker count that run it fastest
  * alone -- the persistent form with all, 3/4 or 1/2 of its resident CTAs (clusters), and for
  * N_p = 512 classes also the two-pass form -- then whether the classes run faster concurrently
- * or back to back.  Synchronises the stream; not capturable.  The choice is kept in the batch
- * (epic_batch_class reports it).
+ * or back to back (timed alternately; concurrent unless back to back is more than 2 % faster,
+ * the stream fork and join per class that eager timing adds and a captured graph does not).
+ * Synchronises the stream; not capturable.  The choice is kept in the batch (epic_batch_class
+ * reports it).
  */
 epic_status epic_batch_autotune(epic_batch *batch, const void *const *volt, const int *n_time,
                                 const float *const *gains, double *const *accum, void *stream);
