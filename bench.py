@@ -789,10 +789,72 @@ def run_xpol(args):
 
 def _xeng_flops(n_ant, n_cp, n_time):
     """Tensor-core FLOP the correlator executes: per (channel, pol) the upper triangle of
-    128 x 128 blocks, 2 real products (re, im) x 2 x 128 x 128 x (2 x 32 x chunks)."""
+    128 x 128 blocks, per 32-sample chunk 4 real products (Re Re, Im Im, Re Im, Im Re) of
+    2 x 128 x 128 x 32 FLOP each."""
     nab = (n_ant + 127) // 128
     chunks = (n_time + 31) // 32
     return n_cp * nab * (nab + 1) // 2 * 2 * 2.0 * 128 * 128 * 64 * chunks
+
+
+def measure_fx(wl, plan, volt, dev, steps, warmup, world, rank, flush):
+    """The FX route on a workload whose 4+4-bit or FP16 voltages are resident: the correlator
+    (epic_correlate, the tensor cores' visibilities of all antenna pairs) and the FX imaging of
+    the integration (epic_fx_image; its first call builds the plan's lag table on the host,
+    outside the timed region), each timed like the imaging step; the visibilities of the last
+    (channel, pol) of the timed output against the oracle."""
+    import numpy as np
+    import torch
+    from oracle import fx
+    from paper_1510_08318_gb300 import epic
+    A, T, C, P = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol
+    st = torch.cuda.current_stream(dev)
+    vis = torch.empty((C, P, A, A), dtype=torch.complex64, device=dev)
+    img = torch.empty((C, P, wl.n_pad, wl.n_pad), dtype=torch.float32, device=dev)
+
+    def correlate():
+        epic.epic_correlate(plan._h, volt.data_ptr(), T, None, vis.data_ptr(), st.cuda_stream)
+
+    def fx_imaging():
+        epic.epic_fx_image(plan._h, vis.data_ptr(), img.data_ptr(), st.cuda_stream)
+
+    def timed(fn, clocks=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / steps], world, dev)[0], clk
+
+    for _ in range(max(warmup, 3)):
+        correlate()
+    for _ in range(2):
+        fx_imaging()
+    torch.cuda.synchronize()
+    c_ms, clk = timed(correlate, Clocks(dev.index if dev.index is not None else 0))
+    i_ms, _ = timed(fx_imaging)
+    flop = _xeng_flops(A, C * P, T)
+    peak = MEASURED["bf16_tflops"]
+    roof = {"bound": "tensor", "achieved": flop / (c_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "traffic": None, "executed_flop": flop, "unique_flop": 4.0 * A * (A + 1) * T * C * P,
+            "peak_basis": "measured dense bf16 burst GEMM (FP16 has the same nominal rate), of measured"}
+    roof["frac"] = roof["achieved"] / peak
+    res = {"call": "epic_correlate, then epic_fx_image of the integration, on the same resident voltages",
+           "correlator_ms": c_ms, "roofline": roof, "fx_imaging_ms": i_ms, "fx_route_ms": c_ms + i_ms,
+           "clocks": clk}
+    if rank == 0:
+        want = fx.visibilities(wl.volt[:, C - 1, P - 1, :], np.ones(A, dtype=np.complex128))
+        got = vis[C - 1, P - 1].cpu().numpy()
+        res["err_vs_oracle"] = {"relative_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                                "sample": "visibilities of the last (channel, pol)"}
+    return res
 
 
 def run_fx(args):
@@ -1215,6 +1277,9 @@ def main():
     # 262,144 samples written to HBM, against the measured copy bandwidth
     grid = measure_gridder(wl, plan, volt, dev, args.steps, args.warmup, world, rank, flush,
                            with_oracle=(rank == 0 and not args.no_cpu_baseline))
+    # the FX route (correlator on the tensor cores, then the integration's FX imaging) on the same
+    # resident voltages
+    fxr = measure_fx(wl, plan, volt, dev, args.steps, args.warmup, world, rank, flush)
     config = headline_config(wl, world)
     line = {
         "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1249,6 +1314,7 @@ def main():
                             "as complex64 (%.2f GB)" % (T * C * P, grid["output_bytes"] / 1e9),
                     "kernel_ms": grid["ms"], "roofline": grid["roofline"], "clocks": grid["clocks"],
                     "err_vs_oracle": grid.get("err_vs_oracle")},
+        "fx_route": fxr,
     }
     if cb is not None:
         line["cpu_baseline"] = cb
