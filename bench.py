@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="headline workload only: skip the dense-layout and batch measurements of the default line")
     p.add_argument("--channels", type=int, default=128,
                    help="image only the first C of the 128 channels (small profiling case)")
     p.add_argument("--workload", default="lwa", choices=["lwa", "batch", "calib", "grid", "xpol", "fx",
@@ -325,21 +327,16 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_hera(args):
+def measure_hera(steps, warmup, world, rank, local, dev, with_oracle=True, with_e2e=True, n_chan=1024):
     """The dense layout: a HERA-331-like hexagon (331 antennas of 14 m, 14 m spacing), 1 pol,
-    1024 channels x 256 samples of FP16 voltages, 256 x 256 images, in both transform forms: the
+    n_chan channels x 256 samples of FP16 voltages, 256 x 256 images, in both transform forms: the
     FP32 FFT (4-CTA clusters) and the tensor-core DFT-GEMM with FP16 hi + lo operands (two CTAs
-    per image, one per half of the rows).  Same metric and timing rules as the headline: one
-    epic_image call per step (image + auto-correlation term), L2 flushed before each step, the
-    oracle on a bounded sample beside it; the line's value is the chosen form (the faster one
-    within the FP32 bound)."""
+    per image, one per half of the rows).  Same timing rules as the headline: one epic_image call
+    per step (image + auto-correlation term), L2 flushed before each step, the oracle on a bounded
+    sample (its error per form decides the chosen form: the faster one within the FP32 bound)."""
     import torch
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    wl = synth.workload_hera(n_chan=args.channels if args.channels != 128 else 1024)
+    from paper_1510_08318_gb300 import epic, synth
+    wl = synth.workload_hera(n_chan=n_chan)
     plan = epic.Plan.from_workload(wl, device=local)
     A, T, C, P, NP = wl.n_ant, wl.n_time, wl.n_chan, wl.n_pol, wl.n_pad
     volt = torch.from_numpy(wl.volt_raw).to(dev)
@@ -347,8 +344,8 @@ def run_hera(args):
     power = torch.empty((C, P, A), dtype=torch.float64, device=dev)
     image = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
     autoc = torch.empty((C, P, NP, NP), dtype=torch.float32, device=dev)
-    host_v = torch.from_numpy(wl.volt_raw).pin_memory()
-    host_img = torch.empty((C, P, NP, NP), dtype=torch.float32).pin_memory()
+    host_v = torch.from_numpy(wl.volt_raw).pin_memory() if with_e2e else None
+    host_img = torch.empty((C, P, NP, NP), dtype=torch.float32).pin_memory() if with_e2e else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream(dev)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -367,29 +364,29 @@ def run_hera(args):
         host_img.copy_(image, non_blocking=True)
 
     def timed(fn, clocks=None):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             ev[i][0].record(st)
             fn()
             ev[i][1].record(st)
         torch.cuda.synchronize()
         clk = clocks.stop() if clocks else None
-        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
+        return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / steps], world, dev)[0], clk
 
     units = A * T * C * P
     forms = {}
     for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm")):
         plan.set_transform(xf)
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             step()
         torch.cuda.synchronize()
         ms, clk = timed(step, Clocks(local))
         kern_ms, _ = timed(kernel_only)
-        e2e_ms, _ = timed(e2e_step)
+        e2e_ms = timed(e2e_step)[0] if with_e2e else None
         plan.sync()
         forms[name] = {"xform": xf, "ms_per_step": ms, "kernel_ms": kern_ms, "e2e_ms": e2e_ms, "clocks": clk,
                        "value": job_throughput(units, world, ms)}
@@ -407,44 +404,58 @@ def run_hera(args):
         flop_basis="algorithmic: the pruned 256 x 256 DFT of each image as real products, 100.7 MFLOP; "
                    "executed: 3 FP16 products per real product, 302.0 MFLOP")
     cb, err = None, {}
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and with_oracle:
         cb, err = cpu_baseline_sample(wl, plan, torch, n_chan=2, n_time=T, forms=("fft", "dftgemm"))
     ok = [k for k in forms if err.get(forms[k]["xform"], 0.0) < 1e-4]
     chosen = min(ok, key=lambda k: forms[k]["ms_per_step"])
-    f = forms[chosen]
-    line = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": f["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16x3" if chosen == "fp16x3_dftgemm" else "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "antennas": A, "time_samples": T, "channels": C, "pols": P,
-                       "grid": "%dx%d padded to %dx%d" % (wl.n_grid, wl.n_grid, NP, NP), "voltages": "f16",
-                       "images_per_step": T * C * P, "l2": "flushed (256 MB write) before every timed step"},
-            "chosen_form": {"name": chosen, "rule": "the faster form whose relative L2 error against the FP64 "
-                                                    "oracle (err_vs_oracle sample) is below 1e-4"},
-            "images_per_s": world * T * C * P / (f["ms_per_step"] / 1e3), "kernel_ms": f["kernel_ms"],
-            "roofline": f["roofline"],
-            "e2e": {"value": job_throughput(units, world, f["e2e_ms"]), "unit": UNIT,
-                    "h2d_bytes_per_step": int(host_v.numel() * host_v.element_size()),
-                    "d2h_bytes_per_step": int(host_img.numel() * host_img.element_size())},
-            "gpu_launches": 3 * args.steps, "clocks": f["clocks"],
-            "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()}}
-    if cb is not None:
-        line["cpu_baseline"] = cb
-        line["err_vs_oracle"] = {"relative_l2": err, "sample": "last 2 channels, all %d samples, image" % T}
-    if rank == 0:
-        print(json.dumps(line))
+    config = {"workload": wl.name, "antennas": A, "time_samples": T, "channels": C, "pols": P,
+              "grid": "%dx%d padded to %dx%d" % (wl.n_grid, wl.n_grid, NP, NP), "voltages": "f16",
+              "images_per_step": T * C * P, "l2": "flushed (256 MB write) before every timed step"}
+    return {"wl": wl, "forms": forms, "chosen": chosen, "cb": cb, "err": err, "config": config, "units": units,
+            "h2d": int(host_v.numel() * host_v.element_size()) if with_e2e else 0,
+            "d2h": int(host_img.numel() * host_img.element_size()) if with_e2e else 0}
 
 
-def run_batch(args):
-    """64 heterogeneous sub-arrays (N_p 32..512, mixed apertures, FP16, T = 128), imaged by the
-    batch executor (autotuned), captured once as a CUDA graph and replayed: one graph launch
-    per step.  Metric as the headline: antenna-samples/s over all sub-arrays."""
+def run_hera(args):
+    """The dense HERA-331-like layout at full size (1024 channels x 256 samples, 256 x 256
+    images) in both transform forms; the line's value is the chosen form."""
     import torch
-    from paper_1510_08318_gb300 import build, epic, synth
+    from paper_1510_08318_gb300 import build
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
+    r = measure_hera(args.steps, args.warmup, world, rank, local, dev, with_oracle=not args.no_cpu_baseline,
+                     n_chan=args.channels if args.channels != 128 else 1024)
+    forms, chosen, T = r["forms"], r["chosen"], r["wl"].n_time
+    f = forms[chosen]
+    C, P = r["wl"].n_chan, r["wl"].n_pol
+    line = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": f["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x3" if chosen == "fp16x3_dftgemm" else "f32", "data": "synthetic",
+            "config": r["config"],
+            "chosen_form": {"name": chosen, "rule": "the faster form whose relative L2 error against the FP64 "
+                                                    "oracle (err_vs_oracle sample) is below 1e-4"},
+            "images_per_s": world * T * C * P / (f["ms_per_step"] / 1e3), "kernel_ms": f["kernel_ms"],
+            "roofline": f["roofline"],
+            "e2e": {"value": job_throughput(r["units"], world, f["e2e_ms"]), "unit": UNIT,
+                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+            "gpu_launches": 3 * args.steps, "clocks": f["clocks"],
+            "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()}}
+    if r["cb"] is not None:
+        line["cpu_baseline"] = r["cb"]
+        line["err_vs_oracle"] = {"relative_l2": r["err"], "sample": "last 2 channels, all %d samples, image" % T}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def measure_batch(steps, warmup, local, dev):
+    """64 heterogeneous sub-arrays (N_p 32..512, mixed apertures, FP16, T = 128), imaged by the
+    batch executor (autotuned), captured once as a CUDA graph and replayed: one graph launch
+    per step, L2 flushed before each."""
+    import torch
+    from paper_1510_08318_gb300 import epic, synth
     subs = synth.workload_batch(n_time=128)
     plans = [epic.Plan.from_workload(w, device=local) for w in subs]
     volts = [torch.from_numpy(w.volt_raw).to(dev) for w in subs]
@@ -460,31 +471,43 @@ def run_batch(args):
             batch.image(volts, acc, img)
     torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         g.replay()
     torch.cuda.synchronize()
     cur = torch.cuda.current_stream(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     clocks = Clocks(local)
     clocks.start()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()
         ev[i][0].record(cur)
         g.replay()
         ev[i][1].record(cur)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     units = sum(w.n_ant * w.n_time * w.n_chan * w.n_pol for w in subs)
     images = sum(w.n_time * w.n_chan * w.n_pol for w in subs)
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {"ms_per_step": ms, "value": units / (ms / 1e3), "images_per_s": images / (ms / 1e3), "clocks": clk,
             "config": {"workload": "batch: 64 heterogeneous sub-arrays, N_p 32-512, FP16, T=128",
                        "sub_arrays": len(subs), "images_per_step": images, "antenna_samples_per_step": units,
                        "classes": info, "launch": "one CUDA graph replay per step",
-                       "l2": "flushed (256 MB write) before every timed step"},
-            "images_per_s": images / (ms / 1e3), "clocks": clk}
+                       "l2": "flushed (256 MB write) before every timed step"}}
+
+
+def run_batch(args):
+    """The batch workload; metric as the headline: antenna-samples/s over all sub-arrays."""
+    import torch
+    from paper_1510_08318_gb300 import build
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    r = measure_batch(args.steps, args.warmup, local, dev)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": r["config"],
+            "images_per_s": r["images_per_s"], "clocks": r["clocks"]}
     if rank == 0:
         print(json.dumps(line))
 
@@ -1280,6 +1303,28 @@ def main():
     # the FX route (correlator on the tensor cores, then the integration's FX imaging) on the same
     # resident voltages
     fxr = measure_fx(wl, plan, volt, dev, args.steps, args.warmup, world, rank, flush)
+    # the two other full-size configurations, timed in the same run (at most 5 steps each, one GPU
+    # only): the dense layout at 256 x 256 in both transform forms with their errors, and the
+    # batch of heterogeneous sub-arrays; a failure there is recorded, not fatal to the line
+    extra = {}
+    if world == 1 and not args.no_extra:
+        n_x = min(args.steps, 5)
+        for key, fn in (("precision_256", lambda: measure_hera(n_x, args.warmup, world, rank, local, dev,
+                                                               with_oracle=not args.no_cpu_baseline,
+                                                               with_e2e=False)),
+                        ("batch", lambda: measure_batch(n_x, args.warmup, local, dev))):
+            try:
+                r = fn()
+                if key == "precision_256":
+                    r = {"config": r["config"], "steps": n_x, "chosen_form": r["chosen"],
+                         "err_vs_oracle": {"relative_l2": r["err"], "sample": "last 2 channels, image"},
+                         "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks", "e2e_ms")}
+                                   for k, v in r["forms"].items()}}
+                else:
+                    r["steps"] = n_x
+                extra[key] = r
+            except Exception as exc:           # recorded in the line; the headline stands
+                extra[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     config = headline_config(wl, world)
     line = {
         "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1316,6 +1361,7 @@ def main():
                     "err_vs_oracle": grid.get("err_vs_oracle")},
         "fx_route": fxr,
     }
+    line.update(extra)
     if cb is not None:
         line["cpu_baseline"] = cb
         line["err_vs_oracle"] = {"relative_l2": err, "sample": "channels 96-127, pol 1, all 1024 samples, image"}
