@@ -512,16 +512,13 @@ def run_batch(args):
         print(json.dumps(line))
 
 
-def run_calib(args):
+def measure_calib(steps, warmup, local, dev):
     """Gain calibration workload (1024 antennas, 32 channels, 64 samples, N_p = 256, complex64):
-    one step = forward image + adjoint (gradient of the image loss with respect to the gains)."""
+    one step = forward image + adjoint (gradient of the image loss with respect to the gains),
+    each call timed with the L2 flushed before it."""
     import numpy as np
     import torch
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
+    from paper_1510_08318_gb300 import epic, synth
     wl = synth.workload_calib()
     plan = epic.Plan.from_workload(wl, device=local)
     volt = torch.from_numpy(wl.volt_raw).to(dev)
@@ -538,26 +535,39 @@ def run_calib(args):
 
     res = {}
     for name, fn in (("forward", fwd), ("adjoint", bwd)):
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             fn()
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for i in range(args.steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
             flush.zero_()
             ev[i][0].record(cur)
             fn()
             ev[i][1].record(cur)
         torch.cuda.synchronize()
-        res[name] = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        res[name] = sum(a.elapsed_time(b) for a, b in ev) / steps
     units = wl.n_ant * wl.n_time * wl.n_chan * wl.n_pol
     ms = res["forward"] + res["adjoint"]
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {"ms_per_step": ms, "value": units / (ms / 1e3), "forward_ms": res["forward"],
+            "adjoint_ms": res["adjoint"],
             "config": {"workload": wl.name, "step": "forward image + adjoint w.r.t. gains",
                        "images_per_step": wl.n_time * wl.n_chan * wl.n_pol,
-                       "l2": "flushed (256 MB write) before every timed call"},
-            "forward_ms": res["forward"], "adjoint_ms": res["adjoint"]}
+                       "l2": "flushed (256 MB write) before every timed call"}}
+
+
+def run_calib(args):
+    """The gain calibration workload: forward image + adjoint per step."""
+    import torch
+    from paper_1510_08318_gb300 import build
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    r = measure_calib(args.steps, args.warmup, local, dev)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": r["config"],
+            "forward_ms": r["forward_ms"], "adjoint_ms": r["adjoint_ms"]}
     if rank == 0:
         print(json.dumps(line))
 
@@ -1303,16 +1313,18 @@ def main():
     # the FX route (correlator on the tensor cores, then the integration's FX imaging) on the same
     # resident voltages
     fxr = measure_fx(wl, plan, volt, dev, args.steps, args.warmup, world, rank, flush)
-    # the two other full-size configurations, timed in the same run (at most 5 steps each, one GPU
-    # only): the dense layout at 256 x 256 in both transform forms with their errors, and the
-    # batch of heterogeneous sub-arrays; a failure there is recorded, not fatal to the line
+    # the other full-size configurations, timed in the same run (at most 5 steps each, one GPU
+    # only): the dense layout at 256 x 256 in both transform forms with their errors, the batch of
+    # heterogeneous sub-arrays and the gain calibration step; a failure there is recorded, not
+    # fatal to the line
     extra = {}
     if world == 1 and not args.no_extra:
         n_x = min(args.steps, 5)
         for key, fn in (("precision_256", lambda: measure_hera(n_x, args.warmup, world, rank, local, dev,
                                                                with_oracle=not args.no_cpu_baseline,
                                                                with_e2e=False)),
-                        ("batch", lambda: measure_batch(n_x, args.warmup, local, dev))):
+                        ("batch", lambda: measure_batch(n_x, args.warmup, local, dev)),
+                        ("calibration", lambda: measure_calib(n_x, args.warmup, local, dev))):
             try:
                 r = fn()
                 if key == "precision_256":
