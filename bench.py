@@ -102,7 +102,7 @@ class Clocks:
 
     def start(self):
         """Start sampling and return once the first sample is written, so that nvidia-smi's own
-        start-up (which can hold the driver for a while) stays outside the timed region."""
+        start-up (which can hold the NVIDIA kernel driver for a while) stays outside the timed region."""
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "100"],
