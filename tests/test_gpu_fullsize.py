@@ -70,6 +70,51 @@ def test_lwa_full_size_forms_agree(epic, lwa_full):
     assert (np.abs(got - ref).max(axis=(2, 3)) < 1e-4 * ref.max(axis=(2, 3))).all()
 
 
+def test_lwa_full_size_fx_route(epic, lwa_full):
+    """The FX route on the full LWA-like integration, in the launches the bench times
+    (epic_correlate of all 256 (channel, pol) planes, then epic_fx_image: 64 planes per warp
+    with 16-byte visibility loads): every plane's FX image equals the MOFF image of the same
+    data (Sec. 2: the two routes are equivalent with the autocorrelations included) within the
+    FP32 bound, and two sampled planes equal the oracle's FX route."""
+    from oracle import fx
+    wl = lwa_full
+    v = torch.from_numpy(wl.volt_raw).cuda()
+    plan = epic.Plan.from_workload(wl)
+    moff_img = plan.image(v)["image"].cpu().numpy().astype(np.float64)
+    fx_img = plan.fx_image(plan.correlate(v)).cpu().numpy().astype(np.float64)
+    n = wl.n_pad ** 2
+    d = np.linalg.norm((fx_img - moff_img).reshape(-1, n), axis=1) / np.linalg.norm(moff_img.reshape(-1, n), axis=1)
+    assert d.max() < 1e-4, d.max()
+    assert (np.abs(fx_img - moff_img).max(axis=(2, 3)) < 1e-4 * moff_img.max(axis=(2, 3))).all()
+    M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+    for c, p in [(5, 0), (127, 1)]:
+        want = fx.fx_image(M, wl.volt[:, c:c + 1, p:p + 1, :], None, wl.n_grid, wl.n_pad).real[0, 0]
+        assert rel_l2(fx_img[c, p], want) < 1e-4
+        assert np.abs(fx_img[c, p] - want).max() < 1e-4 * np.abs(want).max()
+
+
+def test_hera_full_size_both_forms(epic):
+    """The dense layout at its full 1024 channels x 256 samples, FP16 voltages, N_p = 256, in the
+    launches the bench times: the tensor-core split form's 1024 images within the FP32 bound of
+    the FFT form's, and the first and last channel of both against the oracle."""
+    wl = synth.workload_hera()
+    v = torch.from_numpy(wl.volt_raw).cuda()
+    plan = epic.Plan.from_workload(wl)
+    ref = plan.image(v)["image"].cpu().numpy()
+    got = plan.set_transform("dftgemm").image(v)["image"].cpu().numpy()
+    plan.sync()
+    n = wl.n_pad ** 2
+    r64, g64 = ref.reshape(-1, n).astype(np.float64), got.reshape(-1, n).astype(np.float64)
+    d = np.linalg.norm(g64 - r64, axis=1) / np.linalg.norm(r64, axis=1)
+    assert d.max() < 1e-4, d.max()
+    M = moff.map_antennas(wl.pos, wl.kern_ptr, wl.kern_dxdy, wl.kern_w, wl.dx, wl.origin, wl.n_grid)
+    for c in (0, wl.n_chan - 1):
+        want = moff.moff_image(M, wl.volt[:, c:c + 1], None, wl.n_grid, wl.n_pad)[0, 0]
+        for img in (ref, got):
+            assert rel_l2(img[c, 0], want) < 1e-4
+            assert np.abs(img[c, 0] - want).max() < 1e-4 * want.max()
+
+
 def test_hera_full_layout_channel_slice(epic):
     """331-antenna hexagon, FP16 voltages, N_p = 256 clusters, 16 channels x 256 samples;
     the first and last channel against the oracle over all samples."""
