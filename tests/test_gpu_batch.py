@@ -105,3 +105,41 @@ def test_batch_rejects_mixed_formats(epic):
     pa, pb = epic.Plan.from_workload(a), epic.Plan.from_workload(b)
     with pytest.raises(epic.EpicError):
         epic.Batch([pa, pb])
+
+
+def test_batch_full_configuration(epic):
+    """The batching configuration at full size, as the bench runs it (64 sub-arrays with their
+    full channel counts, 8 to 256, T = 128): autotuned and replayed as one CUDA graph, every
+    sub-array's images equal its per-plan call (1e-6), and one channel of the smallest sub-array
+    of each size class against the oracle."""
+    subs = synth.workload_batch(n_time=128)
+    plans = [epic.Plan.from_workload(w) for w in subs]
+    volts = [torch.from_numpy(np.ascontiguousarray(w.volt_raw)).cuda() for w in subs]
+    batch = epic.Batch(plans)
+    acc, img = batch.alloc()
+    batch.autotune(volts, acc)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            batch.image(volts, acc, img)
+    g.replay()
+    torch.cuda.synchronize()
+    for p, v, got in zip(plans, volts, img):
+        ref = p.image(v)["image"]
+        torch.cuda.synchronize()
+        assert rel(got.cpu().numpy(), ref.cpu().numpy()) < 1e-6
+    checked = set()
+    for i in np.argsort([w.n_ant * w.kern_dxdy.shape[0] for w in subs]):
+        w = subs[i]
+        if w.n_pad in checked:
+            continue
+        checked.add(w.n_pad)
+        c = w.n_chan - 1
+        M = moff.map_antennas(w.pos, w.kern_ptr, w.kern_dxdy, w.kern_w, w.dx, w.origin, w.n_grid)
+        want = moff.moff_image(M, w.volt[:, c:c + 1, :1], None, w.n_grid, w.n_pad)[0, 0]
+        got = img[i][c, 0].cpu().numpy()
+        assert rel(got, want) < 1e-4, (w.name, rel(got, want))
+        assert np.abs(got - want).max() < 1e-4 * want.max()
+    assert checked == {32, 64, 128, 256, 512}
