@@ -95,6 +95,7 @@ def test_hera_slice_f16(epic):
     (640, 64, 1, 1, "ci4"),     # five full blocks, two full chunks
     (336, 45, 1, 2, "ci4"),     # 4-byte loads with an 80-antenna tail block, a ragged chunk
     (130, 70, 1, 1, "ci4"),     # A not a multiple of 4: byte loads, a two-antenna tail block
+    (4, 3, 3, 2, "ci4"),        # the smallest 4-byte-load case: one lane's antennas, 3 samples
 ])
 def test_small_shapes(epic, n_ant, n_time, n_chan, n_pol, vdtype):
     wl = _small(n_ant, n_time, n_chan, n_pol, vdtype, seed=n_ant + n_time)
@@ -213,3 +214,19 @@ def test_units_not_dividing_over_the_sms(epic, n_ant, n_time, n_chan, n_pol):
     vis2 = plan.correlate(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda(), g2)
     torch.cuda.synchronize()
     assert np.array_equal(vis2.cpu().numpy(), vis)
+
+
+def test_longest_integration_reaches_2_to_24(epic):
+    """n_time = 131072, the most a call accepts: with every 4+4-bit voltage at -8 - 8i each
+    sample adds (-8 - 8i)(-8 + 8i) = 128 to every pair's sum, which reaches 128 x 131072 = 2^24,
+    the top of the exact FP32 integer range; every visibility must be exactly 128 + 0i (2^24
+    scaled by 1/T = 2^-17 is exact).  One sample more is refused before any launch."""
+    wl = _small(16, 4, 1, 1, "ci4", seed=3)
+    plan = epic.Plan.from_workload(wl)
+    T = 131072
+    raw = torch.full((T, 1, 1, 16), 0x88, dtype=torch.uint8, device="cuda")
+    vis = plan.correlate(raw).cpu().numpy()
+    assert np.array_equal(vis, np.full((1, 1, 16, 16), 128 + 0j, dtype=np.complex64))
+    with pytest.raises(epic.EpicError) as e:
+        plan.correlate(torch.full((T + 1, 1, 1, 16), 0x88, dtype=torch.uint8, device="cuda"))
+    assert e.value.status == epic.EPIC_EUNSUPPORTED
