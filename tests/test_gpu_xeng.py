@@ -172,9 +172,10 @@ def test_gpu_fx_image_small_sizes_complex_weights(epic, n_pad, n_grid, n_ant):
     assert np.linalg.norm(img - want) / np.linalg.norm(want) < 1e-4
 
 
-@pytest.mark.parametrize("n_chan, n_pol", [(3, 1), (20, 2), (33, 2), (65, 1)])
+@pytest.mark.parametrize("n_chan, n_pol", [(1, 1), (2, 1), (3, 1), (20, 2), (33, 2), (65, 1)])
 def test_gpu_fx_image_plane_groupings(epic, n_chan, n_pol):
-    """The lag-plane gather's groupings of (channel, pol) planes: 3 planes (one group of 4),
+    """The lag-plane gather's groupings of (channel, pol) planes: 1 and 2 planes (32 and 16
+    entries side by side per warp), 3 planes (one group of 4),
     40 (two groups of 32, the second ragged), 66 (two groups of 64 read 16 bytes per lane, the
     second ragged) and 65 (odd: three groups of 32).  Every plane against the oracle's FX route
     (complex footprint weights, N_p = 32)."""
