@@ -46,9 +46,9 @@ typedef enum {
     EPIC_ENOMEM = 2,        /* the plan's device tables could not be allocated */
     EPIC_ECUDA = 3,         /* a CUDA runtime call or launch failed */
     EPIC_EUNSUPPORTED = 4,  /* valid, but outside what this library implements */
-    EPIC_ETIMEOUT = 5       /* a kernel's bounded wait on the tensor cores ran out (reported by
-                               epic_sync; the outputs of the calls since the last epic_sync are
-                               undefined) */
+    EPIC_ETIMEOUT = 5       /* a kernel's bounded wait (on the tensor cores, or on a cluster
+                               exchange) ran out (reported by epic_sync; the outputs of the
+                               calls since the last epic_sync are undefined) */
 } epic_status;
 
 typedef enum {
@@ -137,7 +137,9 @@ void epic_destroy(epic_plan *plan);
  * epic_image_xpol in the EPIC_XFORM_DFTGEMM form, epic_correlate) wait on the tensor pipe with
  * bounded waits; a wait that runs out sets a bit in the plan's device status word (the kernel
  * then waits, with its full limit, for the products still in flight, releases its tensor memory
- * and returns, marking its first output block with NaN).  This call synchronises the stream,
+ * and returns, marking its first output block with NaN).  The FFT form at N_p = 256 and 512 waits,
+ * with a fixed bound of about a second, for the row-pass data its cluster peers send it; a wait
+ * that runs out sets another bit.  This call synchronises the stream,
  * reads the word, clears it and returns EPIC_ETIMEOUT if any bit was set (the message names the
  * kernel), EPIC_ECUDA if the stream reported an error, else EPIC_OK.  The imaging calls
  * themselves stay asynchronous.  Not meant for use inside a stream capture.

@@ -585,10 +585,12 @@ epic_status epic_sync(const epic_plan* plan, void* stream) {
         return epic_cuda_fail(e, "status word read");
     if (word == 0) return EPIC_OK;
     if ((e = cudaMemset(plan->status, 0, sizeof(int))) != cudaSuccess) return epic_cuda_fail(e, "status word clear");
-    return epic_fail(EPIC_ETIMEOUT, "a bounded wait on the tensor cores ran out in the %s%s%s (its outputs are undefined)",
-                     (word & epic::kStatusImageTimeout) ? "tensor-core imaging kernel" : "",
-                     (word & epic::kStatusImageTimeout) && (word & epic::kStatusCorrelateTimeout) ? " and the " : "",
-                     (word & epic::kStatusCorrelateTimeout) ? "correlator" : "");
+    std::string where;
+    if (word & epic::kStatusImageTimeout) where += "tensor-core imaging kernel";
+    if (word & epic::kStatusCorrelateTimeout) where += std::string(where.empty() ? "" : " and the ") + "correlator";
+    if (word & epic::kStatusClusterTimeout)
+        where += std::string(where.empty() ? "" : " and the ") + "cluster exchange of the FFT imaging kernel";
+    return epic_fail(EPIC_ETIMEOUT, "a bounded wait ran out in the %s (its outputs are undefined)", where.c_str());
 }
 
 epic_status epic_set_transform(epic_plan* plan, int xform) {

@@ -33,10 +33,11 @@ struct FwdArgs {
     int wait_tries;            // tries of each bounded wait of the pipeline (about 1 ms each)
 };
 
-// Bits of a plan's device status word, set by a kernel whose bounded wait on the tensor cores
-// ran out (the call's outputs are then undefined); read and cleared by epic_sync.
+// Bits of a plan's device status word, set by a kernel whose bounded wait ran out (the call's
+// outputs are then undefined); read and cleared by epic_sync.
 constexpr int kStatusImageTimeout = 1;       // tensor-core imaging kernel
 constexpr int kStatusCorrelateTimeout = 2;   // X-engine
+constexpr int kStatusClusterTimeout = 4;     // FFT imaging kernel's cluster exchange (N_p >= 256)
 
 // Sub-array calls imaged by one persistent forward launch (same N_p and voltage format);
 // a single epic_image call is a one-entry list.  Passed by value as a kernel parameter.

@@ -16,11 +16,13 @@ template <int NP> struct Cfg;
 // S, Q, minimum CTAs per SM, and the shared-memory row strides (in float2) chosen so that
 // every warp-wide exchange access is free of bank conflicts.
 // RR: gather the cells round-robin (measured faster for the cluster sizes) or cell by cell.
-template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8, RXS = 40,  RBS = 34; static constexpr bool RR = false; };
-template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2, RXS = 72,  RBS = 66; static constexpr bool RR = false; };
-template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1, RXS = 136, RBS = 129; static constexpr bool RR = false; };
-template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1, RXS = 264, RBS = 65; static constexpr bool RR = true; };
-template <> struct Cfg<512> { static constexpr int S = 16, Q = 16, MINB = 1, RXS = 520, RBS = 33; static constexpr bool RR = true; };
+// NB: most row-pass output buffers of the forward kernel (2: alternate items between two, so
+// that a cluster needs no barrier per item, used where the shared memory allows).
+template <> struct Cfg<32>  { static constexpr int S = 4,  Q = 1, MINB = 8, RXS = 40,  RBS = 34, NB = 1; static constexpr bool RR = false; };
+template <> struct Cfg<64>  { static constexpr int S = 8,  Q = 1, MINB = 2, RXS = 72,  RBS = 66, NB = 1; static constexpr bool RR = false; };
+template <> struct Cfg<128> { static constexpr int S = 8,  Q = 1, MINB = 1, RXS = 136, RBS = 129, NB = 1; static constexpr bool RR = false; };
+template <> struct Cfg<256> { static constexpr int S = 16, Q = 4, MINB = 1, RXS = 264, RBS = 65, NB = 2; static constexpr bool RR = true; };
+template <> struct Cfg<512> { static constexpr int S = 16, Q = 16, MINB = 1, RXS = 520, RBS = 33, NB = 1; static constexpr bool RR = true; };
 
 template <int NP> struct Geo {
     static constexpr int NG = NP / 2;          // unpadded grid side (2x padding, Sec. 3)
@@ -59,12 +61,19 @@ template <int NP> struct Geo {
     static constexpr int TWN = S * TWS;        // twiddle table entries
     static_assert((ROWS * RXS + NG * RBS) % 2 == 0, "twiddle table must stay 16-byte aligned");
 
-    static constexpr size_t smem_bytes(int n_ant) {
-        return sizeof(float2) * (size_t(ROWS) * RXS + size_t(NG) * RBS + TWN)
+    // the forward kernel's exchange mbarriers (two 8-byte words, cluster forms only), in float2
+    static constexpr int MBF = Q > 1 ? 2 : 0;
+
+    // forward kernel: exchange rows, nb row-pass output buffers, twiddles, mbarriers, then
+    // per antenna g V, gain and partial power
+    static constexpr size_t smem_bytes(int n_ant, int nb = 1) {
+        return sizeof(float2) * (size_t(ROWS) * RXS + size_t(nb) * NG * RBS + TWN + MBF)
              + size_t(n_ant) * (2 * sizeof(float2) + sizeof(float));
     }
     // the cross-polarisation form adds a table of phi_v g_Y per antenna (8-byte aligned)
-    static constexpr size_t smem_bytes_xpol(int n_ant) { return smem_bytes(n_ant) + size_t(n_ant + 2) * sizeof(float2); }
+    static constexpr size_t smem_bytes_xpol(int n_ant, int nb = 1) {
+        return smem_bytes(n_ant, nb) + size_t(n_ant + 2) * sizeof(float2);
+    }
 
     // Fill the twiddle table from the plan's exp(+2 pi i j / NP) table.
     static __device__ __forceinline__ void load_twiddles(float2* TW, const float2* tw, int tid, int nt) {

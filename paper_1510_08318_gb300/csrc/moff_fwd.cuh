@@ -19,7 +19,14 @@
 //                    grid (to the owning CTA of the cluster for Q > 1);
 //   column pass      thread (column, n1) reads the N_g non-zero rows of its column, does
 //                    the same two stages along y, squares and accumulates.
-// Two CTA (cluster) barriers per item; everything else is warp-synchronous.
+// One CTA: two CTA barriers per item; everything else is warp-synchronous.
+// Cluster (Q > 1): the row pass sends its outputs with `st.async`, whose bytes complete a
+// transaction count on the receiving CTA's mbarrier, so each CTA waits for its own column data
+// only (a bounded wait) instead of a cluster barrier.  With two row-pass output buffers (used
+// alternately by consecutive items) the item needs no cluster barrier at all: a CTA writes a
+// peer's buffer for item i + 2 only after it has received that peer's item-(i + 1) data, which
+// the peer sends after its column pass of item i has read the buffer.  With one buffer a
+// cluster barrier after the decode keeps the peers' column pass ahead of the next writes.
 //
 // Cross-polarisation variant (XP): the sub-array has two pols and its (channel, pol) index
 // runs over 4 C virtual pols v = 0..3 per channel, v = 0: X, 1: Y, 2: X + Y, 3: X + iY, whose
@@ -28,8 +35,36 @@
 // identity (Re = (S_2 - S_0 - S_1) / 2, Im = (S_3 - S_0 - S_1) / 2), evaluated in the epilogue.
 #pragma once
 #include "moff_common.cuh"
+#include "tcgen05.cuh"
 
 namespace epic {
+
+// Address in the shared memory of cluster rank q of this CTA's shared address p (volatile: it is
+// recomputed at each use instead of being held in registers across the row pass).
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t p, int q) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(p), "r"(q));
+    return r;
+}
+
+// Asynchronous 8-byte store into (possibly another CTA's) shared memory; its bytes complete
+// the transaction count of the mbarrier at mbar (in the destination CTA).
+__device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+                 :: "r"(addr), "f"(v.x), "f"(v.y), "r"(mbar) : "memory");
+}
+
+// Bounded wait for an mbarrier phase completed by stores of other CTAs of the cluster
+// (acquire at cluster scope); false on timeout.  Each try suspends the thread for up to 1 ms.
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t addr, uint32_t parity, int tries) {
+    for (int i = 0; i < tries; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(addr), "r"(parity), "r"(1000000u) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // First item whose cost position is >= c: items of sub-array s occupy the cost interval
 // [cost[s] + i w_s, cost[s] + (i + 1) w_s); consecutive workers' ranges tile the items exactly.
@@ -42,7 +77,7 @@ __device__ __forceinline__ int item_at_cost(const SegList& L, long long c) {
     return L.first[s] + (int)(i < n_s ? i : n_s);
 }
 
-template <int NP, int VDT, bool XP>
+template <int NP, int VDT, bool XP, int NB>
 __global__ void __launch_bounds__(Geo<NP>::NT, Geo<NP>::MINB)
 moff_fwd_kernel(const __grid_constant__ SegList L) {
     using G = Geo<NP>;
@@ -52,9 +87,10 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* RX = reinterpret_cast<float2*>(smem_raw);        // [ROWS][RXS] exchange
-    float2* RB = RX + G::ROWS * G::RXS;                      // [NG][RBS] row-pass output
-    float2* TW = RB + NG * G::RBS;                           // [S][TWS] exp(+2 pi i n1 k2 / NP)
-    float2* VB = TW + G::TWN;                                    // [A] g_a V_a
+    float2* RB0 = RX + G::ROWS * G::RXS;                     // [NB][NG][RBS] row-pass output
+    float2* TW = RB0 + NB * NG * G::RBS;                     // [S][TWS] exp(+2 pi i n1 k2 / NP)
+    uint64_t* MB = reinterpret_cast<uint64_t*>(TW + G::TWN); // [2] exchange mbarriers (Q > 1)
+    float2* VB = TW + G::TWN + G::MBF;                       // [A] g_a V_a
     float2* GN = VB + L.max_ant;                             // [A] gains
     float* PW = reinterpret_cast<float*>(GN + L.max_ant);    // [A] partial sum |g V|^2
     float2* GY = reinterpret_cast<float2*>(PW + ((L.max_ant + 1) & ~1));   // XP: [A] phi_v g_Y
@@ -71,8 +107,18 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
     }
     const int y = rank * G::ROWS + r;
 
+    static_assert(NB == 1 || (NB == 2 && Q > 1), "two row-pass buffers serve the cluster forms");
     G::load_twiddles(TW, L.seg[0].twiddle, tid, NT);
     for (int aa = tid; aa < L.max_ant; aa += NT) PW[aa] = 0.f;   // owner-thread entries
+    bool lost = false;          // a bounded exchange wait of this thread ran out
+    if constexpr (Q > 1) {
+        if (tid == 0) {
+            tc::mbar_init(tc::smem_u32(MB), 1);
+            tc::mbar_init(tc::smem_u32(MB + 1), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        cg::this_cluster().sync();      // every CTA's mbarriers exist before the first exchange
+    }
 
     // global items [0, first[n_seg]) of all sub-arrays, split over the workers in equal shares of
     // estimated cost (equal item counts for a single sub-array)
@@ -214,7 +260,18 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
             }
             if (g + 1 < end) prefetch(g + 1);
         }
-        block_or_cluster_sync<Q>();
+        // this worker's item j uses row-pass buffer j % NB, whose mbarrier phase has parity (j / NB) & 1
+        const int jb = NB == 2 ? (g - beg) & 1 : 0;
+        const uint32_t par = (uint32_t)(((g - beg) / NB) & 1);
+        float2* RB = RB0 + jb * (NG * G::RBS);
+        if constexpr (NB == 2) {
+            __syncthreads();
+        } else {
+            block_or_cluster_sync<Q>();
+        }
+        if constexpr (Q > 1) {      // this CTA receives N_g rows x COLS columns of the row pass
+            if (tid == 0 && !lost) tc::mbar_expect_tx(tc::smem_u32(MB + jb), NG * G::COLS * (int)sizeof(float2));
+        }
 
         // ---- row pass: gridding + 1-D transform along x of row y ----
         {
@@ -230,6 +287,7 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
             float2* rx = RX + r * G::RXS;
             G::twiddle_store(rx, Y, TW, n1);
             __syncwarp();
+            const uint32_t rb_s = tc::smem_u32(RB), mb_s = tc::smem_u32(MB + jb);
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
                 const int k2 = n1 * KP + q;
@@ -241,14 +299,26 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
                 for (int k1 = 0; k1 < S; ++k1) {
                     const int kx = k2 + R1 * k1;
                     if constexpr (Q > 1) {
-                        cluster_ptr(RB, (R1 * k1) / G::COLS)[y * G::RBS + (kx % G::COLS)] = z[k1];
+                        // after a timeout this thread stops sending: its peers' waits then run
+                        // out too (bounded), and no transaction count grows without end
+                        const int dst = (R1 * k1) / G::COLS;     // CTA owning column kx
+                        if (!lost)
+                            st_async_f2(mapa_u32(rb_s + (uint32_t)(y * G::RBS + kx % G::COLS) * (uint32_t)sizeof(float2), dst),
+                                        z[k1], mapa_u32(mb_s, dst));
                     } else {
                         RB[y * G::RBS + kx] = z[k1];
                     }
                 }
             }
         }
-        block_or_cluster_sync<Q>();
+        if constexpr (Q > 1) {      // wait for this CTA's columns from every CTA of the cluster
+            if (!lost && !mbar_wait_cluster(tc::smem_u32(MB + jb), par, tc::kWaitTries)) {
+                lost = true;
+                if (a.status) atomicOr(a.status, kStatusClusterTimeout);
+            }
+        } else {
+            __syncthreads();
+        }
 
         // ---- column pass: 1-D transform along y of two columns, |.|^2, accumulate ----
 #pragma unroll
@@ -276,15 +346,34 @@ moff_fwd_kernel(const __grid_constant__ SegList L) {
         }
     }
     if (cur >= 0) flush(cur, true);
+    // no CTA leaves while a peer may still store into its shared memory (after a timeout)
+    if constexpr (Q > 1) cg::this_cluster().sync();
 #undef a
 }
 
-template <int NP, int VDT, bool XP = false>
-cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
+// Row-pass output buffers of the forward kernel for sub-arrays of up to max_ant antennas: two
+// where the form has them and they fit this device's shared memory, else one.
+template <int NP, bool XP>
+int fwd_buffers(int max_ant) {
     using G = Geo<NP>;
-    auto kern = moff_fwd_kernel<NP, VDT, XP>;
-    const size_t smem = XP ? G::smem_bytes_xpol(L.max_ant) : G::smem_bytes(L.max_ant);
-    cudaError_t e = ensure_smem<moff_fwd_kernel<NP, VDT, XP>>(smem);
+    if constexpr (Cfg<NP>::NB < 2) {
+        return 1;
+    } else {
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return 1;
+        const size_t need = XP ? G::smem_bytes_xpol(max_ant, 2) : G::smem_bytes(max_ant, 2);
+        return need <= (size_t)optin ? 2 : 1;
+    }
+}
+
+template <int NP, int VDT, bool XP, int NB>
+cudaError_t launch_fwd_nb(const SegList& L, int n_sm, cudaStream_t st) {
+    using G = Geo<NP>;
+    auto kern = moff_fwd_kernel<NP, VDT, XP, NB>;
+    const size_t smem = XP ? G::smem_bytes_xpol(L.max_ant, NB) : G::smem_bytes(L.max_ant, NB);
+    cudaError_t e = ensure_smem<moff_fwd_kernel<NP, VDT, XP, NB>>(smem);
     if (e != cudaSuccess) return e;
     const long long n_items = L.first[L.n_seg];
     if (n_items == 0) return cudaSuccess;
@@ -329,12 +418,20 @@ cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
     }
 }
 
-template <int NP, int VDT>
-int resident_fwd_workers_t(int max_ant, int n_sm) {
+template <int NP, int VDT, bool XP = false>
+cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
+    if constexpr (Cfg<NP>::NB == 2) {
+        if (fwd_buffers<NP, XP>(L.max_ant) == 2) return launch_fwd_nb<NP, VDT, XP, 2>(L, n_sm, st);
+    }
+    return launch_fwd_nb<NP, VDT, XP, 1>(L, n_sm, st);
+}
+
+template <int NP, int VDT, int NB>
+int resident_fwd_workers_nb(int max_ant, int n_sm) {
     using G = Geo<NP>;
-    auto kern = moff_fwd_kernel<NP, VDT, false>;
-    const size_t smem = G::smem_bytes(max_ant);
-    if (ensure_smem<moff_fwd_kernel<NP, VDT, false>>(smem) != cudaSuccess) return 0;
+    auto kern = moff_fwd_kernel<NP, VDT, false, NB>;
+    const size_t smem = G::smem_bytes(max_ant, NB);
+    if (ensure_smem<moff_fwd_kernel<NP, VDT, false, NB>>(smem) != cudaSuccess) return 0;
     if constexpr (G::Q == 1) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem) != cudaSuccess) return 0;
@@ -356,6 +453,14 @@ int resident_fwd_workers_t(int max_ant, int n_sm) {
         if (cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg) != cudaSuccess) return 0;
         return n_cl;
     }
+}
+
+template <int NP, int VDT>
+int resident_fwd_workers_t(int max_ant, int n_sm) {
+    if constexpr (Cfg<NP>::NB == 2) {
+        if (fwd_buffers<NP, false>(max_ant) == 2) return resident_fwd_workers_nb<NP, VDT, 2>(max_ant, n_sm);
+    }
+    return resident_fwd_workers_nb<NP, VDT, 1>(max_ant, n_sm);
 }
 
 }  // namespace epic

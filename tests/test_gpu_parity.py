@@ -130,7 +130,10 @@ def _small_workload(n_pad, n_grid, n_ant, n_time, n_chan, n_pol, seed, vdtype="c
     (64, 20, 300, 17, 2, 1, "ci4"),    # ragged grid, A > threads per CTA
     (128, 64, 700, 9, 1, 2, "c64"),    # A beyond the register prefetch (4 per thread)
     (256, 100, 64, 3, 2, 1, "f16"),
+    (256, 90, 80, 150, 1, 1, "c64"),   # two row-pass buffers, several items (both parities) per cluster
+    (256, 60, 1600, 150, 1, 1, "ci4"), # one row-pass buffer (two do not fit beside 1600 antennas)
     (512, 40, 30, 3, 1, 1, "c64"),     # 16-CTA clusters
+    (512, 40, 30, 40, 1, 1, "c64"),    # several items per 16-CTA cluster
     (512, 256, 12, 2, 1, 1, "f16"),    # full 256 x 256 unpadded grid
 ])
 def test_small_sizes(epic, n_pad, n_grid, n_ant, n_time, n_chan, n_pol, vdtype):
