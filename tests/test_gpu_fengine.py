@@ -40,9 +40,12 @@ def raw_samples(rng, n, P, A, dtype):
 
 @pytest.mark.parametrize("C", [32, 64, 128, 256, 512])
 @pytest.mark.parametrize("dtype", ["c64", "f16", "ci4"])
-def test_spectra_match_oracle(epic, C, dtype):
-    rng = np.random.default_rng(C)
-    T, P, A = 3, 2, 33                                  # a ragged antenna tile
+@pytest.mark.parametrize("A", [33, 66])
+def test_spectra_match_oracle(epic, C, dtype, A):
+    """A = 33: one antenna per thread, a ragged 32-antenna tile; A = 66 (C <= 128): two antennas
+    per thread in packed pairs, a ragged 64-antenna tile."""
+    rng = np.random.default_rng(C + A)
+    T, P = 3, 2
     raw, dec = raw_samples(rng, T * C, P, A, dtype)
     want = moff.fengine(dec, C)
     got = epic.fengine(raw, C, dtype, "c64").cpu().numpy()
