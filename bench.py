@@ -1061,19 +1061,15 @@ def run_crossover(args):
         print(json.dumps(line))
 
 
-def run_fengine(args):
+def measure_fengine(steps, warmup, rank, local, dev, with_chain=True, with_oracle=True):
     """The F-engine on the headline shapes: 256 antennas x 2 pols x 1024 spectra of 128
-    channels from 4+4-bit time samples (seeded random bytes), written as FP16 spectra, then
-    imaged (epic_image, FP16 plan).  Roofline of the F-engine: HBM bytes (samples read once,
-    spectra written once) against the measured copy bandwidth."""
+    channels from 4+4-bit time samples (seeded random bytes), written as FP16 spectra, and (with
+    with_chain) the same spectra imaged (epic_image, FP16 plan).  Roofline of the F-engine: HBM
+    bytes (samples read once, spectra written once) against the measured copy bandwidth."""
     import numpy as np
     import torch
     from oracle import moff
-    from paper_1510_08318_gb300 import build, epic, synth
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
+    from paper_1510_08318_gb300 import epic, synth
     wl = synth.workload_lwa(n_chan=1, n_time=2, chan_index=[0])
     A, P, C, T = wl.n_ant, 2, 128, 1024
     rng = np.random.default_rng(11)
@@ -1096,36 +1092,49 @@ def run_fengine(args):
                         st.cuda_stream)
 
     def timed(fn, clocks=None):
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             fn()
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if clocks:
             clocks.start()
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             ev[i][0].record(st)
             fn()
             ev[i][1].record(st)
         torch.cuda.synchronize()
         clk = clocks.stop() if clocks else None
-        return sum(a.elapsed_time(b) for a, b in ev) / args.steps, clk
+        return sum(a.elapsed_time(b) for a, b in ev) / steps, clk
 
     f_ms, clk = timed(feng, Clocks(local))
-    c_ms, _ = timed(chain)
+    c_ms = timed(chain)[0] if with_chain else None
     nbytes = raw.numel() + spec.numel() * 2
     peak = MEASURED["hbm_gbs"]
     roof = {"bound": "hbm", "achieved": nbytes / (f_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s", "traffic": None,
             "algorithmic_bytes": nbytes, "peak_basis": "measured STREAM-style copy (read + write bytes), of measured"}
     roof["frac"] = roof["achieved"] / peak
     err = None
-    if rank == 0:
+    if rank == 0 and with_oracle:
         # oracle spectra of 2 spectra x all channels, pol 1, against the FP16 output
         want = moff.fengine(synth.decode_ci4(raw_h[:2 * C]), C)[:, :, 1]
         got = spec[:2, :, 1].float().cpu().numpy()
         got = got[..., 0] + 1j * got[..., 1]
         err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
-    units = A * T * C * P
+    return {"fengine_ms": f_ms, "chain_ms": c_ms, "roofline": roof, "clocks": clk, "err": err,
+            "units": A * T * C * P}
+
+
+def run_fengine(args):
+    """`--workload fengine`: the F-engine and the imaging of its spectra (measure_fengine)."""
+    import torch
+    from paper_1510_08318_gb300 import build
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    r = measure_fengine(args.steps, args.warmup, rank, local, dev)
+    f_ms, c_ms, roof, clk, err, units = r["fengine_ms"], r["chain_ms"], r["roofline"], r["clocks"], r["err"], r["units"]
     line = {"metric": METRIC, "value": units / (c_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": c_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP16 spectra)", "data": "synthetic (random 4+4-bit time samples)",
@@ -1324,7 +1333,9 @@ def main():
                                                                with_oracle=not args.no_cpu_baseline,
                                                                with_e2e=False)),
                         ("batch", lambda: measure_batch(n_x, args.warmup, local, dev)),
-                        ("calibration", lambda: measure_calib(n_x, args.warmup, local, dev))):
+                        ("calibration", lambda: measure_calib(n_x, args.warmup, local, dev)),
+                        ("fengine", lambda: measure_fengine(n_x, args.warmup, rank, local, dev, with_chain=False,
+                                                            with_oracle=not args.no_cpu_baseline))):
             try:
                 r = fn()
                 if key == "precision_256":
@@ -1332,6 +1343,11 @@ def main():
                          "err_vs_oracle": {"relative_l2": r["err"], "sample": "last 2 channels, image"},
                          "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks", "e2e_ms")}
                                    for k, v in r["forms"].items()}}
+                elif key == "fengine":
+                    r = {"config": "256 antennas x 2 pols x 1024 spectra of 128 channels from 4+4-bit time "
+                                   "samples, FP16 spectra (L2 flushed before every step)",
+                         "steps": n_x, "ms": r["fengine_ms"], "roofline": r["roofline"],
+                         "err_vs_oracle": {"fp16_relative_l2": r["err"], "sample": "2 spectra, pol 1"}}
                 else:
                     r["steps"] = n_x
                 extra[key] = r

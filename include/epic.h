@@ -373,8 +373,9 @@ epic_status epic_batch_image(epic_batch *batch, const void *const *volt, const i
 /*
  * Autotune the batch on representative inputs (same arguments as epic_batch_image; accum is
  * overwritten): for each size class, the kernel form and worker count that run it fastest
- * alone -- the persistent form with all, 3/4 or 1/2 of its resident CTAs (clusters), and for
- * N_p = 512 classes also the two-pass form -- then whether the classes run faster concurrently
+ * alone -- the persistent form with all, 3/4 or 1/2 of its resident CTAs (clusters), for
+ * N_p = 512 classes also the two-pass form, for N_p = 256 classes also the persistent form with
+ * one row-pass buffer -- then whether the classes run faster concurrently
  * or back to back (timed alternately; concurrent unless back to back is more than 2 % faster,
  * the stream fork and join per class that eager timing adds and a captured graph does not).
  * Synchronises the stream; not capturable.  The choice is kept in the batch (epic_batch_class
@@ -392,8 +393,9 @@ epic_status epic_batch_info(const epic_batch *batch, int *n_classes, int *concur
  * resident) and its kernel form, 0 = persistent (one CTA or cluster per image in flight), 1 =
  * two-pass (N_p = 512 classes: a row pass and a column pass over every SM with the row-
  * transformed grids staged in a scratch buffer the batch allocates at creation, 4 x SMs samples
- * of 1 MB for each such class).  The form is what epic_batch_autotune chose (persistent until
- * then).  Any out-pointer may be NULL. */
+ * of 1 MB for each such class), 2 = persistent with one row-pass buffer (N_p = 256 classes: a
+ * cluster barrier per image instead of two buffers used alternately).  The form is what
+ * epic_batch_autotune chose (persistent until then).  Any out-pointer may be NULL. */
 epic_status epic_batch_class(const epic_batch *batch, int k, int *n_pad, int *workers, int *form);
 
 /* Release the batch (not its plans).  NULL is accepted. */

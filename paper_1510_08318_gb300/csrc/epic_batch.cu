@@ -16,9 +16,11 @@
 namespace {
 
 // Kernel forms a size class can run in: the persistent one-launch form (one CTA, or one cluster
-// for N_p >= 256, per image in flight) and, for N_p = 512, the two-pass form (a row pass and a
-// column pass over every SM, the row-transformed grids staged in the class's scratch buffer).
-enum ClassForm { kFormPersistent = 0, kFormTwoPass = 1 };
+// for N_p >= 256, per image in flight; at N_p = 256 with two row-pass buffers where they fit),
+// for N_p = 512 the two-pass form (a row pass and a column pass over every SM, the row-
+// transformed grids staged in the class's scratch buffer), and for N_p = 256 the persistent form
+// with one row-pass buffer (less shared memory, a cluster barrier per item).
+enum ClassForm { kFormPersistent = 0, kFormTwoPass = 1, kFormOneBuffer = 2 };
 
 struct ClassRun {
     int n_pad = 0;
@@ -89,6 +91,7 @@ epic_status run_class(const epic_batch* b, const ClassRun& c, const void* const*
     L.n_seg = (int)c.members.size();
     L.max_ant = 0;
     L.max_workers = max_workers;
+    L.max_buffers = form == kFormOneBuffer ? 1 : 0;
     L.first[0] = 0;
     L.cost[0] = 0;
     for (int s = 0; s < L.n_seg; ++s) {
@@ -268,8 +271,8 @@ epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, cons
         return EPIC_OK;
     };
     // 1) per class: the kernel form and worker count that run it fastest alone -- the persistent
-    //    form with all, 3/4 or 1/2 of its resident CTAs (clusters), and for N_p = 512 also the
-    //    two-pass form on every SM
+    //    form with all, 3/4 or 1/2 of its resident CTAs (clusters), for N_p = 512 also the
+    //    two-pass form on every SM, for N_p = 256 also the one-buffer form at the best count
     std::vector<float> alone(batch->classes.size(), 0.f);
     for (size_t k = 0; k < batch->classes.size() && s == EPIC_OK; ++k) {
         ClassRun& c = batch->classes[k];
@@ -294,6 +297,15 @@ epic_status epic_batch_autotune(epic_batch* batch, const void* const* volt, cons
                 best_t = t;
                 best_w = 0;
                 best_f = kFormTwoPass;
+            }
+        }
+        if (s == EPIC_OK && c.n_pad == 256) {
+            float t = 0.f;
+            s = time_it([&] { return run_class(batch, c, volt, n_time, gains, accum, nullptr, st, best_w, kFormOneBuffer); },
+                        t);
+            if (s == EPIC_OK && t < best_t) {
+                best_t = t;
+                best_f = kFormOneBuffer;
             }
         }
         c.max_workers = best_w;

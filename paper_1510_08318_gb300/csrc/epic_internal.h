@@ -50,6 +50,8 @@ struct SegList {
     int n_seg;
     int max_ant;               // largest antenna count (shared-memory sizing)
     int max_workers;           // cap on CTAs (clusters) launched, 0 = every resident one
+    int max_buffers = 0;       // FFT form's row-pass buffers: 1 = one, 0 = as many as fit (two at
+                               // N_p = 256)
 };
 
 // Per-item cost estimate of a sub-array (relative units): transform work per padded pixel

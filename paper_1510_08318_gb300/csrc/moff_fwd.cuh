@@ -421,7 +421,7 @@ cudaError_t launch_fwd_nb(const SegList& L, int n_sm, cudaStream_t st) {
 template <int NP, int VDT, bool XP = false>
 cudaError_t launch_fwd_t(const SegList& L, int n_sm, cudaStream_t st) {
     if constexpr (Cfg<NP>::NB == 2) {
-        if (fwd_buffers<NP, XP>(L.max_ant) == 2) return launch_fwd_nb<NP, VDT, XP, 2>(L, n_sm, st);
+        if (L.max_buffers != 1 && fwd_buffers<NP, XP>(L.max_ant) == 2) return launch_fwd_nb<NP, VDT, XP, 2>(L, n_sm, st);
     }
     return launch_fwd_nb<NP, VDT, XP, 1>(L, n_sm, st);
 }

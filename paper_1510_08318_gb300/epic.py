@@ -242,7 +242,8 @@ def epic_batch_autotune(batch, volt, n_time, gains, accum, stream):
 def epic_batch_class(batch, k):
     npad, w, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().epic_batch_class(batch, int(k), ctypes.byref(npad), ctypes.byref(w), ctypes.byref(f)))
-    return {"n_pad": npad.value, "workers": w.value, "form": ("persistent", "two-pass")[f.value]}
+    return {"n_pad": npad.value, "workers": w.value,
+            "form": ("persistent", "two-pass", "persistent, one buffer")[f.value]}
 
 
 def epic_batch_info(batch, max_classes=16):

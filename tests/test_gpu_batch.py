@@ -92,7 +92,8 @@ def test_batch_graph_capture_and_autotune(epic, setup):
     info = batch.autotune(volts, acc)
     assert info["n_classes"] == len(info["workers"]) == len(info["classes"])
     for c in info["classes"]:
-        assert c["form"] == "persistent" or (c["form"] == "two-pass" and c["n_pad"] == 512)
+        assert (c["form"] == "persistent" or (c["form"] == "two-pass" and c["n_pad"] == 512)
+                or (c["form"] == "persistent, one buffer" and c["n_pad"] == 256))
     batch.image(volts, acc, img)
     torch.cuda.synchronize()
     for a, b in zip(ref, img):
