@@ -41,9 +41,11 @@
 // The gridding gathers cell pairs (x, y), (x, y + 1) from slot tables in which the 32 pairs of
 // a warp step have similar entry counts and store to 32 distinct shared-memory banks (on the
 // 256-antenna ellipse a cell-major walk kept 40 % of the lanes busy, these slots 81 %, with the
-// slowest warp at the heaviest slot); each cell's entries are still summed in cell-major order.
-// Entries are an FP32 weight and a 16-bit antenna index; the tables sit in shared memory when
-// they fit beside the operand tables, else they are read through L1.
+// slowest warp at the heaviest slot).  Within a cell the builder orders the entries so that the
+// antennas read at one warp step spread over the shared-memory banks of the 8-byte voltages
+// (a fixed order: the sums are deterministic).  Entries are an FP32 weight and a 16-bit antenna
+// index; the tables sit in shared memory when they fit beside the operand tables, else they are
+// read through L1.
 // Every wait on the tensor cores is bounded (the pipeline's waits by the plan's try count); on a
 // timeout the CTA sets the image-timeout bit of the plan's status word, writes NaN into its
 // accumulator block, waits with the full limit for the MMAs in flight and stops.
@@ -639,15 +641,55 @@ bool dftgemm_gather_tables_ng(int ng, int n_warps, const std::vector<int>& cptr,
         base[pos] = (int)wre.size();
         for (int i = 0; i < 32; ++i)
             lane[(size_t)pos * 32 + i] = int2{(int)((unsigned)P[i]->c0 | ((unsigned)P[i]->cnt << 16)), P[i]->off};
-        for (int k = 0; k < P[0]->cnt; ++k)
-            for (int i = 0; i < 32 && P[i]->cnt > k; ++i) {
-                const int e = k < P[i]->c0 ? cptr[P[i]->cell] + k : cptr[P[i]->cell + ng] + (k - P[i]->c0);
+        // Each lane takes its first cell's entries, then its second's; within a cell the order is
+        // free (any fixed order is deterministic), so step by step each lane takes, of its cell's
+        // remaining entries, one whose antenna shares a shared-memory bank pair (8-byte voltages:
+        // antenna mod 16) with as few antennas already read at this step by its half-warp as
+        // possible; lanes with the fewest candidates choose first.
+        std::vector<int> rem[32][2];
+        for (int i = 0; i < 32; ++i) {
+            for (int e = cptr[P[i]->cell]; e < cptr[P[i]->cell + 1]; ++e) rem[i][0].push_back(e);
+            for (int e = cptr[P[i]->cell + ng]; e < cptr[P[i]->cell + ng + 1]; ++e) rem[i][1].push_back(e);
+        }
+        for (int k = 0; k < P[0]->cnt; ++k) {
+            int n_act = 0;
+            while (n_act < 32 && P[n_act]->cnt > k) ++n_act;
+            auto cand = [&](int i) -> std::vector<int>& { return rem[i][k < P[i]->c0 ? 0 : 1]; };
+            int ord[32], pick[32], load[2][16] = {};
+            std::vector<int> seen[2];            // antennas read at this step, per half-warp
+            for (int i = 0; i < n_act; ++i) ord[i] = i;
+            std::stable_sort(ord, ord + n_act, [&](int u, int v) { return cand(u).size() < cand(v).size(); });
+            for (int t = 0; t < n_act; ++t) {
+                const int i = ord[t], h = i / 16;
+                std::vector<int>& c = cand(i);
+                size_t best = 0;
+                int best_cost = 1 << 30;
+                for (size_t j = 0; j < c.size(); ++j) {
+                    const int an = cent[c[j]].y;
+                    const bool dup = std::find(seen[h].begin(), seen[h].end(), an) != seen[h].end();
+                    const int cost = dup ? -1 : load[h][an & 15];
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        best = j;
+                    }
+                }
+                pick[i] = c[best];
+                c.erase(c.begin() + (long)best);
+                const int an = cent[pick[i]].y;
+                if (best_cost >= 0) {
+                    ++load[h][an & 15];
+                    seen[h].push_back(an);
+                }
+            }
+            for (int i = 0; i < n_act; ++i) {
+                const int e = pick[i];
                 float wv;
                 std::memcpy(&wv, &cent[e].x, sizeof(float));
                 wre.push_back(wv);
                 wim.push_back(cwim[e]);
                 ant.push_back((uint16_t)cent[e].y);
             }
+        }
     }
     return true;
 }

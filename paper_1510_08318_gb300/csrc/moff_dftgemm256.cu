@@ -45,7 +45,7 @@
 // end.
 //
 // Gridding gathers cell pairs (x, y), (x, y + 1) from the slot tables of the 128 x 128 grid (256
-// slots of 32 pairs over 15 warps; each cell's entries summed in cell-major order), read through
+// slots of 32 pairs over 15 warps; each cell's entries in the builder's fixed order), read through
 // L1 (the operand buffers leave no room for them in shared memory).  The per-image scale is a
 // power of two that keeps |E| below 256, so |X| stays below 2^15 and its FP16 split in range.
 // Every wait is bounded (the pipeline's by the plan's try count); on a timeout the CTA sets the
