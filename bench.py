@@ -34,9 +34,12 @@ SM_MAX_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch on this workload, from ncu captures
 # of the 8-channel case (16,384 images) scaled by the units per launch (x16); None until
 # captured for the current kernel.  Forward FFT kernel: 6.48 MB per capture; tensor-core
-# DFT-GEMM kernel: 6.58 MB per capture.
+# DFT-GEMM kernel: 6.57 MB per capture.
 FWD_TRAFFIC_BYTES = 103.7e6
-DG_TRAFFIC_BYTES = 105.3e6
+DG_TRAFFIC_BYTES = 105.2e6
+# F-engine on the headline shapes (one full launch captured: 67.1 MB read, 207.1 MB written;
+# the last spectra written are still in L2 when the kernel ends)
+FENGINE_TRAFFIC_BYTES = 274.2e6
 # Work of the tensor-core DFT form per 128 x 128 image.  Algorithmic: the pruned transform as
 # two complex matrix products, each four real products -- stage 1 X = W E (128 x 64 outputs,
 # K = 64), stage 2 F = X W^T (128 x 128 outputs, K = 64): 12.58 MFLOP.  Executed: every real
@@ -45,7 +48,7 @@ DG_ALG_FLOP_PER_IMAGE = 4 * 2.0 * 128 * 64 * 64 + 4 * 2.0 * 128 * 128 * 64
 DG_FLOP_PER_IMAGE = 3 * DG_ALG_FLOP_PER_IMAGE
 # sm__pipe_tensor_cycles_active of the tensor-core kernel in its latest small-case ncu capture
 # (8 channels x 2 pols x 1024 samples, one launch)
-DG_TENSOR_ACTIVE_NCU = 0.577
+DG_TENSOR_ACTIVE_NCU = 0.591
 # standalone gridder: 479.8 MB per capture launch (1,024 of the 16,384 units), scaled x16
 GRID_TRAFFIC_BYTES = 7.677e9
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -1111,8 +1114,8 @@ def measure_fengine(steps, warmup, rank, local, dev, with_chain=True, with_oracl
     c_ms = timed(chain)[0] if with_chain else None
     nbytes = raw.numel() + spec.numel() * 2
     peak = MEASURED["hbm_gbs"]
-    roof = {"bound": "hbm", "achieved": nbytes / (f_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s", "traffic": None,
-            "algorithmic_bytes": nbytes, "peak_basis": "measured STREAM-style copy (read + write bytes), of measured"}
+    roof = {"bound": "hbm", "achieved": nbytes / (f_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+            "traffic": FENGINE_TRAFFIC_BYTES, "algorithmic_bytes": nbytes, "peak_basis": "measured STREAM-style copy (read + write bytes), of measured"}
     roof["frac"] = roof["achieved"] / peak
     err = None
     if rank == 0 and with_oracle:
