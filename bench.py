@@ -334,11 +334,13 @@ def run_reference(args):
 
 def measure_hera(steps, warmup, world, rank, local, dev, with_oracle=True, with_e2e=True, n_chan=1024):
     """The dense layout: a HERA-331-like hexagon (331 antennas of 14 m, 14 m spacing), 1 pol,
-    n_chan channels x 256 samples of FP16 voltages, 256 x 256 images, in both transform forms: the
-    FP32 FFT (4-CTA clusters) and the tensor-core DFT-GEMM with FP16 hi + lo operands (two CTAs
-    per image, one per half of the rows).  Same timing rules as the headline: one epic_image call
-    per step (image + auto-correlation term), L2 flushed before each step, the oracle on a bounded
-    sample (its error per form decides the chosen form: the faster one within the FP32 bound)."""
+    n_chan channels x 256 samples of FP16 voltages, 256 x 256 images, in three transform forms: the
+    FP32 FFT (4-CTA clusters), the tensor-core DFT-GEMM with FP16 hi + lo operands (two CTAs per
+    image, one per half of the rows), and the same DFT-GEMM after gridding with FP16 operands
+    (weights and voltages rounded to FP16, FP32 sums; stated bound 3e-3).  Same timing rules as the
+    headline: one epic_image call per step (image + auto-correlation term), L2 flushed before each
+    step, the oracle on a bounded sample (its error per form decides the chosen form: the fastest
+    one within the FP32 bound 1e-4)."""
     import torch
     from paper_1510_08318_gb300 import epic, synth
     wl = synth.workload_hera(n_chan=n_chan)
@@ -384,7 +386,8 @@ def measure_hera(steps, warmup, world, rank, local, dev, with_oracle=True, with_
 
     units = A * T * C * P
     forms = {}
-    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm")):
+    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm"),
+                     ("fp16grid_fp16x3_dftgemm", "dftgemm_fp16grid")):
         plan.set_transform(xf)
         for _ in range(max(warmup, 3)):
             step()
@@ -403,14 +406,16 @@ def measure_hera(steps, warmup, world, rank, local, dev, with_oracle=True, with_
     # the pruned 256 x 256 DFT as real products: stage 1 256 x 128 outputs over K = 128, stage 2
     # 256 x 256 outputs over K = 128, four real products per complex one; executed 3x (hi / lo)
     alg = (4 * 2.0 * 256 * 128 * 128 + 4 * 2.0 * 256 * 256 * 128) * T * C * P
-    f = forms["fp16x3_dftgemm"]
-    forms["fp16x3_dftgemm"]["roofline"] = tensor_roofline(
-        alg, 3 * alg, f["kernel_ms"], f["clocks"],
-        flop_basis="algorithmic: the pruned 256 x 256 DFT of each image as real products, 100.7 MFLOP; "
-                   "executed: 3 FP16 products per real product, 302.0 MFLOP")
+    for name in ("fp16x3_dftgemm", "fp16grid_fp16x3_dftgemm"):
+        f = forms[name]
+        forms[name]["roofline"] = tensor_roofline(
+            alg, 3 * alg, f["kernel_ms"], f["clocks"],
+            flop_basis="algorithmic: the pruned 256 x 256 DFT of each image as real products, 100.7 MFLOP; "
+                       "executed: 3 FP16 products per real product, 302.0 MFLOP")
     cb, err = None, {}
     if rank == 0 and with_oracle:
-        cb, err = cpu_baseline_sample(wl, plan, torch, n_chan=2, n_time=T, forms=("fft", "dftgemm"))
+        cb, err = cpu_baseline_sample(wl, plan, torch, n_chan=2, n_time=T,
+                                      forms=("fft", "dftgemm", "dftgemm_fp16grid"))
     ok = [k for k in forms if err.get(forms[k]["xform"], 0.0) < 1e-4]
     chosen = min(ok, key=lambda k: forms[k]["ms_per_step"])
     config = {"workload": wl.name, "antennas": A, "time_samples": T, "channels": C, "pols": P,
@@ -438,7 +443,8 @@ def run_hera(args):
     line = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": f["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16x3" if chosen == "fp16x3_dftgemm" else "f32", "data": "synthetic",
+            "dtype": {"fp16x3_dftgemm": "f16x3", "fp16grid_fp16x3_dftgemm": "f16 gridding, f16x3"}.get(chosen, "f32"),
+            "data": "synthetic",
             "config": r["config"],
             "chosen_form": {"name": chosen, "rule": "the faster form whose relative L2 error against the FP64 "
                                                     "oracle (err_vs_oracle sample) is below 1e-4"},
@@ -754,7 +760,8 @@ def run_xpol(args):
         return max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / args.steps], world, dev)[0], clk
 
     forms = {}
-    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm")):
+    for name, xf in (("fp32_fft", "fft"), ("fp16x3_dftgemm", "dftgemm"),
+                     ("fp16grid_fp16x3_dftgemm", "dftgemm_fp16grid")):
         plan.set_transform(xf)
         for _ in range(max(args.warmup, 3)):
             step()

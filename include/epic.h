@@ -65,8 +65,11 @@ typedef enum {
     EPIC_XFORM_DFTGEMM_FP16 = 2,/* reduced precision: FP16 gridding operands (weights and gained
                                    voltages rounded to FP16, products exact, FP32 sums) and one
                                    FP16 product per real product of the DFT (N_p = 128) */
-    EPIC_XFORM_FFT_TWOPASS = 3  /* FP32 FFT as a row pass and a column pass with the row-
+    EPIC_XFORM_FFT_TWOPASS = 3, /* FP32 FFT as a row pass and a column pass with the row-
                                    transformed grid staged in device memory (N_p = 512) */
+    EPIC_XFORM_DFTGEMM_FP16_GRID = 4 /* FP16 gridding operands (weights and calibrated voltages
+                                   rounded to FP16, products exact, FP32 sums) and the
+                                   EPIC_XFORM_DFTGEMM transform with hi+lo operands (N_p = 256) */
 } epic_xform;
 
 /*
@@ -123,8 +126,14 @@ epic_status epic_create(epic_plan **plan, int n_ant, const double *pos_xy,
  * default form in two passes over every SM instead of one 16-CTA cluster per image (only one
  * such cluster fits a GPC): the row pass writes each sample's row-transformed grid (1 MB) to a
  * scratch buffer the plan allocates on the first call (4 x SMs samples, about 608 MB on 152
- * SMs), the column pass reads it back; no cross-polarisation variant.  epic_image_backward
- * always uses the FFT form.
+ * SMs), the column pass reads it back; no cross-polarisation variant.
+ * EPIC_XFORM_DFTGEMM_FP16_GRID (n_pad == 256, single polarisation products only) grids with FP16
+ * operands -- each weight and each calibrated voltage rounded to FP16 (normal FP16 range: about
+ * 6e-5 to 65504 in magnitude), each product exact in FP32, the cells' sums in FP32 -- and then
+ * runs the EPIC_XFORM_DFTGEMM transform (hi+lo operands).  Real weights are read as one packed
+ * word per mapping entry (the plan builds these for n_pad 256 when every weight is real).  The
+ * error is that of the FP16 roundings of the gridding operands (relative L2 about 1e-4 against
+ * the exact image; the stated bound is 3e-3).  epic_image_backward always uses the FFT form.
  */
 epic_status epic_set_transform(epic_plan *plan, int xform);
 

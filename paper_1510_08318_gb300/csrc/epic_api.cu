@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 #include <vector>
+#include <cuda_fp16.h>
 
 #include "../../include/epic.h"
 #include "epic_internal.h"
@@ -70,6 +71,7 @@ void free_plan(epic_plan* p) {
     cudaFree(p->dg_wre);
     cudaFree(p->dg_wim);
     cudaFree(p->dg_ant);
+    cudaFree(p->dg_wpk);
     cudaFree(p->status);
     cudaFree(p->tp_scratch);
     cudaFree(p->fx_lag_ptr);
@@ -327,6 +329,14 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
                        (n_pad == 256 &&
                         epic::dftgemm_gather_tables_ng(128, epic::kDg256GridWarps, cptr, cent, cwim, dlane, dbase,
                                                        dwre, dwim, dant));
+    // N_p = 256 with real weights: the same entries packed one word each for the FP16-gridding
+    // form, (FP16 weight, rounded to nearest) << 16 | antenna
+    std::vector<uint32_t> dwpk;
+    if (dg_ok && n_pad == 256 && !complex_w) {
+        dwpk.resize(dwre.size());
+        for (size_t q = 0; q < dwre.size(); ++q)
+            dwpk[q] = ((uint32_t)__half_as_ushort(__float2half_rn(dwre[q])) << 16) | (uint32_t)dant[q];
+    }
 
     // antenna-major CSR per row block (degridding side of the adjoint); cells are stored as
     // offsets into the adjoint kernel's shared-memory row buffer
@@ -442,7 +452,8 @@ epic_status epic_create(epic_plan** plan, int n_ant, const double* pos_xy, const
                     (complex_w && (e = upload(&p->wwim, wwim)) != cudaSuccess))) ||
         (dg_ok && ((e = upload(&p->dg_lane, dlane)) != cudaSuccess || (e = upload(&p->dg_base, dbase)) != cudaSuccess ||
                    (e = upload(&p->dg_wre, dwre)) != cudaSuccess || (e = upload(&p->dg_ant, dant)) != cudaSuccess ||
-                   (complex_w && (e = upload(&p->dg_wim, dwim)) != cudaSuccess)))) {
+                   (complex_w && (e = upload(&p->dg_wim, dwim)) != cudaSuccess) ||
+                   (!dwpk.empty() && (e = upload(&p->dg_wpk, dwpk)) != cudaSuccess)))) {
         free_plan(p);
         return e == cudaErrorMemoryAllocation ? epic_fail(EPIC_ENOMEM, "plan tables: %s", cudaGetErrorString(e))
                                               : epic_cuda_fail(e, "plan upload");
@@ -623,15 +634,21 @@ epic_status epic_set_transform(epic_plan* plan, int xform) {
         plan->xform = xform;
         return EPIC_OK;
     }
-    if (xform != EPIC_XFORM_DFTGEMM && xform != EPIC_XFORM_DFTGEMM_FP16) return epic_fail(EPIC_EINVAL, "xform %d", xform);
+    if (xform != EPIC_XFORM_DFTGEMM && xform != EPIC_XFORM_DFTGEMM_FP16 && xform != EPIC_XFORM_DFTGEMM_FP16_GRID)
+        return epic_fail(EPIC_EINVAL, "xform %d", xform);
     if (plan->n_pad != 128 && plan->n_pad != 256)
         return epic_fail(EPIC_EUNSUPPORTED, "the tensor-core transform needs n_pad 128 or 256 (plan: %d)", plan->n_pad);
     if (xform == EPIC_XFORM_DFTGEMM_FP16 && plan->n_pad != 128)
         return epic_fail(EPIC_EUNSUPPORTED, "the reduced-precision tensor-core form exists for n_pad 128 only (plan: %d)",
                          plan->n_pad);
+    if (xform == EPIC_XFORM_DFTGEMM_FP16_GRID && plan->n_pad != 256)
+        return epic_fail(EPIC_EUNSUPPORTED, "the FP16-gridding tensor-core form exists for n_pad 256 only (plan: %d)",
+                         plan->n_pad);
     if (!plan->dg_lane)
         return epic_fail(EPIC_EUNSUPPORTED, "a pair of grid cells has more than 65535 mapping entries, or more than "
                                             "65536 antennas");
+    if (xform == EPIC_XFORM_DFTGEMM_FP16_GRID && !plan->dg_wim && !plan->dg_wpk)
+        return epic_fail(EPIC_EUNSUPPORTED, "the plan has no packed FP16 gather entries");
     EpicDeviceGuard guard(plan->device);
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
@@ -708,11 +725,14 @@ epic_status epic_image(const epic_plan* plan, const void* volt, int n_time, cons
     const epic::FwdArgs a =
         epic_plan_fwd_args(plan, volt, n_time, reinterpret_cast<const float2*>(gains), accum, power);
     epic_status s;
-    if (plan->xform == EPIC_XFORM_DFTGEMM || plan->xform == EPIC_XFORM_DFTGEMM_FP16) {
-        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_wre, plan->dg_wim, plan->dg_ant, (int)plan->nnz};
+    if (plan->xform == EPIC_XFORM_DFTGEMM || plan->xform == EPIC_XFORM_DFTGEMM_FP16 ||
+        plan->xform == EPIC_XFORM_DFTGEMM_FP16_GRID) {
+        const epic::DgGather g{plan->dg_lane, plan->dg_base, plan->dg_wre, plan->dg_wim, plan->dg_ant, (int)plan->nnz,
+                               plan->dg_wpk};
         e = plan->n_pad == 128 ? epic::launch_dftgemm(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st, false,
                                                       plan->xform == EPIC_XFORM_DFTGEMM_FP16)
-                               : epic::launch_dftgemm256(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st);
+                               : epic::launch_dftgemm256(plan->vdt, a, plan->dg_tab, g, plan->n_sm, st,
+                                                         plan->xform == EPIC_XFORM_DFTGEMM_FP16_GRID);
         s = e == cudaSuccess ? EPIC_OK : epic_cuda_fail(e, "tensor-core imaging kernel launch");
     } else if (plan->xform == EPIC_XFORM_FFT_TWOPASS) {
         epic::SegList L;
@@ -805,7 +825,8 @@ epic_status epic_image_xpol(const epic_plan* plan, const void* volt, int n_time,
     if (!guard.ok) return epic_fail(EPIC_ECUDA, "cannot select CUDA device %d", plan->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
-    if (plan->xform == EPIC_XFORM_DFTGEMM_FP16 || plan->xform == EPIC_XFORM_FFT_TWOPASS)
+    if (plan->xform == EPIC_XFORM_DFTGEMM_FP16 || plan->xform == EPIC_XFORM_FFT_TWOPASS ||
+        plan->xform == EPIC_XFORM_DFTGEMM_FP16_GRID)
         return epic_fail(EPIC_EUNSUPPORTED, "the %s form has no cross-polarisation variant; use EPIC_XFORM_FFT%s",
                          plan->xform == EPIC_XFORM_FFT_TWOPASS ? "two-pass" : "reduced-precision tensor-core",
                          plan->xform == EPIC_XFORM_FFT_TWOPASS ? "" : " or EPIC_XFORM_DFTGEMM");

@@ -163,6 +163,9 @@ struct DgGather {
     const float* wim;      // entry weights, imaginary parts, or nullptr when every weight is real
     const uint16_t* ant;   // entry antennas
     int n_ent;             // number of entries
+    // entries as one word each, (FP16 weight bits << 16) | antenna, for real weights at N_p = 256
+    // (read by the FP16-gridding form); nullptr otherwise
+    const uint32_t* wpk = nullptr;
 };
 // the least a launch needs (tables read through L1); lp: the reduced-precision form (FP16
 // operands and one product per real product)
@@ -188,8 +191,10 @@ cudaError_t launch_dftgemm(int vdt, const FwdArgs& a, const void* wtab, const Dg
 constexpr int kDg256GridWarps = 15;   // gridding warps of the N_p = 256 kernel (the 16th issues)
 size_t dftgemm256_smem_bytes(int n_ant);
 void dftgemm256_tables(std::vector<uint16_t>& out);
+// fp16_grid: FP16 gridding operands (weights and calibrated voltages rounded to FP16, FP32 sums),
+// the transform unchanged; real weights need g.wpk
 cudaError_t launch_dftgemm256(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm,
-                              cudaStream_t st);
+                              cudaStream_t st, bool fp16_grid = false);
 
 // Two-pass form for N_p = 512 (moff_np512x2.cu): a row pass writes each item's row-transformed
 // grid (256 x 512 complex64, 1 MB) to scratch, a column pass transforms, squares and accumulates;

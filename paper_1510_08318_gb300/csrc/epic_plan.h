@@ -46,6 +46,7 @@ struct epic_plan {
     float* dg_wre = nullptr;
     float* dg_wim = nullptr;
     uint16_t* dg_ant = nullptr;
+    uint32_t* dg_wpk = nullptr;   // packed FP16 weight | antenna entries (N_p = 256, real weights)
     float wsum_max = 0.f;         // max over cells of sum_a |M[g, a]|
     float2* tp_scratch = nullptr; // two-pass form (N_p = 512): row-transformed grids of one chunk
     int tp_chunk = 0;             // items per chunk of the two-pass form

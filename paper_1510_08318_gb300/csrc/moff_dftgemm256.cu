@@ -51,6 +51,14 @@
 // Every wait is bounded (the pipeline's by the plan's try count); on a timeout the CTA sets the
 // image-timeout bit of the plan's status word, writes NaN into its accumulator block, waits with
 // the full limit for the copies and products in flight and stops.
+//
+// FP16 gridding (LPG, EPIC_XFORM_DFTGEMM_FP16_GRID): the gridding operands are FP16 -- each
+// weight and each calibrated voltage is rounded to FP16, so every product is exact in FP32 --
+// and the cells' sums stay FP32; the transform keeps its hi + lo operands.  The voltages are
+// held as FP16 pairs (4 bytes per antenna instead of 8) and, for real weights, each gather entry
+// is one 32-bit word (FP16 weight in the high half, antenna in the low half) instead of an FP32
+// weight and a 16-bit antenna in two arrays: one 4-byte read per step instead of two reads of
+// 6 bytes.  Complex weights are read from the FP32 tables and rounded as they are read.
 #include <cuda_fp16.h>
 #include <algorithm>
 #include <cmath>
@@ -96,7 +104,12 @@ constexpr size_t smem_fixed() {
 }
 constexpr size_t ant_bytes() { return 28; }   // two voltage buffers, gains, power
 
-template <int VDT>
+__device__ __forceinline__ float round_h(float x) { return __half2float(__float2half_rn(x)); }
+__device__ __forceinline__ float2 half2_bits_to_float2(uint32_t u) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
+
+template <int VDT, bool LPG>
 __global__ void __launch_bounds__(NTH, 1) moff_dftgemm256_kernel(const FwdArgs a, const __half* __restrict__ wtab,
                                                                  const DgGather g) {
     using VT = typename Volt<VDT>::T;
@@ -108,6 +121,7 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm256_kernel(const FwdArgs a
     unsigned int* vmax = reinterpret_cast<unsigned int*>(tslot + 2);      // [4]
     const int A = a.n_ant, T = a.n_time;
     float2* VB = reinterpret_cast<float2*>(smem_raw + smem_fixed());      // [2][A]
+    uint32_t* VBh = reinterpret_cast<uint32_t*>(VB);                      // LPG: [2][A] FP16 pairs
     float2* GN = VB + 2 * A;
     float* PW = reinterpret_cast<float*>(GN + A);
 
@@ -171,6 +185,16 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm256_kernel(const FwdArgs a
             PW[aa] = 0.f;
         }
     };
+    // calibrated voltage of antenna aa into buffer vb: FP32 pair, or (LPG) rounded to an FP16
+    // pair in the same buffer slot's half-size array
+    auto store_volt = [&](float2* vb, int aa, float2 vp) {
+        if constexpr (LPG) {
+            const __half2 hv = __floats2half2_rn(vp.x, vp.y);
+            VBh[(vb - VB) + aa] = *reinterpret_cast<const uint32_t*>(&hv);
+        } else {
+            vb[aa] = vp;
+        }
+    };
     auto decode = [&](int j) {
         const int item = beg + j, cp = item / T, t = item - cp * T;
         if (j == 0 || (item - 1) / T != cp) {
@@ -185,14 +209,14 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm256_kernel(const FwdArgs a
             const int aa = tid + NGT * q;
             if (aa < A) {
                 const float2 vp = cmul(GN[aa], Volt<VDT>::dec(raw[q]));
-                vb[aa] = vp;
+                store_volt(vb, aa, vp);
                 PW[aa] += cnorm(vp);
                 m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
             }
         }
         for (int aa = tid + NGT * VPT; aa < A; aa += NGT) {
             const float2 vp = cmul(GN[aa], Volt<VDT>::dec(__ldg(base + aa)));
-            vb[aa] = vp;
+            store_volt(vb, aa, vp);
             PW[aa] += cnorm(vp);
             m = fmaxf(m, fmaxf(fabsf(vp.x), fabsf(vp.y)));
         }
@@ -216,6 +240,7 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm256_kernel(const FwdArgs a
     auto grid = [&](int j) {
         const float down = ldexpf(1.f, -image_exp(j));
         const float2* vb = VB + (j & 1) * A;
+        const uint32_t* vbh = VBh + (j & 1) * A;
 #pragma unroll 1
         for (int jj = 0; jj < SPW; ++jj) {
             const int slot = warp * SPW + jj;
@@ -224,7 +249,39 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm256_kernel(const FwdArgs a
             const int kmax = __shfl_sync(0xffffffffu, cnt, 0);   // lane 0 has the longest list
             int e = __ldg(g.base + slot) + lane;
             float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-            if (g.wim) {
+            if constexpr (LPG) {
+                if (g.wim) {
+                    // complex weights: the FP32 tables, each part rounded to FP16 as it is read
+                    for (int k = 0; k < kmax; ++k) {
+                        const bool on = k < cnt;
+                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                        if (on) {
+                            const float2 w = make_float2(round_h(__ldg(g.wre + e)), round_h(__ldg(g.wim + e)));
+                            const float2 v = half2_bits_to_float2(vbh[__ldg(g.ant + e)]);
+                            if (k < c0) cfma(s0, w, v);
+                            else cfma(s1, w, v);
+                        }
+                        e += n_k;
+                    }
+                } else {
+                    // real weights: one packed word per entry, FP16 weight | antenna
+                    for (int k = 0; k < kmax; ++k) {
+                        const bool on = k < cnt;
+                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
+                        if (on) {
+                            const uint32_t pk = __ldg(g.wpk + e);
+                            const float w = __half2float(__ushort_as_half((unsigned short)(pk >> 16)));
+                            const float2 v = half2_bits_to_float2(vbh[pk & 0xffffu]);
+                            const float w0 = k < c0 ? w : 0.f, w1 = w - w0;
+                            s0.x = fmaf(w0, v.x, s0.x);
+                            s0.y = fmaf(w0, v.y, s0.y);
+                            s1.x = fmaf(w1, v.x, s1.x);
+                            s1.y = fmaf(w1, v.y, s1.y);
+                        }
+                        e += n_k;
+                    }
+                }
+            } else if (g.wim) {
                 for (int k = 0; k < kmax; ++k) {
                     const bool on = k < cnt;
                     const int n_k = __popc(__ballot_sync(0xffffffffu, on));
@@ -492,7 +549,9 @@ void dftgemm256_tables(std::vector<uint16_t>& out) {
 }
 
 cudaError_t launch_dftgemm256(int vdt, const FwdArgs& a, const void* wtab, const DgGather& g, int n_sm,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool fp16_grid) {
+    // the FP16-gridding form reads real weights from the packed entries
+    if (fp16_grid && !g.wim && !g.wpk) return cudaErrorInvalidValue;
     const __half* w = static_cast<const __half*>(wtab);
     const size_t smem = dftgemm256_smem_bytes(a.n_ant);
     long long pairs = n_sm / 2;
@@ -500,16 +559,23 @@ cudaError_t launch_dftgemm256(int vdt, const FwdArgs& a, const void* wtab, const
     const unsigned grid = (unsigned)(2 * pairs);
     cudaError_t e;
     switch (vdt) {
+#define EPIC_DG2_LAUNCH(V, LPG)                                                                      \
+    e = ensure_smem<dg2::moff_dftgemm256_kernel<V, LPG>>(smem);                                      \
+    if (e != cudaSuccess) return e;                                                                  \
+    if (grid > 0) dg2::moff_dftgemm256_kernel<V, LPG><<<grid, dg2::NTH, smem, st>>>(a, w, g);        \
+    return cudaGetLastError();
 #define EPIC_DG2_CASE(V)                                                                             \
     case V:                                                                                          \
-        e = ensure_smem<dg2::moff_dftgemm256_kernel<V>>(smem);                                      \
-        if (e != cudaSuccess) return e;                                                              \
-        if (grid > 0) dg2::moff_dftgemm256_kernel<V><<<grid, dg2::NTH, smem, st>>>(a, w, g);         \
-        return cudaGetLastError();
+        if (fp16_grid) {                                                                             \
+            EPIC_DG2_LAUNCH(V, true)                                                                 \
+        } else {                                                                                     \
+            EPIC_DG2_LAUNCH(V, false)                                                                \
+        }
         EPIC_DG2_CASE(0)
         EPIC_DG2_CASE(1)
         EPIC_DG2_CASE(2)
 #undef EPIC_DG2_CASE
+#undef EPIC_DG2_LAUNCH
         default:
             return cudaErrorInvalidValue;
     }

@@ -24,9 +24,9 @@ SYMBOLS = ("epic_create", "epic_destroy", "epic_image", "epic_image_backward", "
            "epic_last_error", "epic_set_transform", "epic_batch_create", "epic_batch_image",
            "epic_batch_autotune", "epic_batch_info", "epic_batch_destroy", "epic_grid", "epic_image_xpol", "epic_correlate", "epic_weff", "epic_isotropic", "epic_fengine", "epic_fx_image",
            "epic_sync", "epic_set_wait_limit", "epic_batch_class", "epic_image_noalloc")
-XFORM_FFT, XFORM_DFTGEMM, XFORM_DFTGEMM_FP16, XFORM_FFT_TWOPASS = 0, 1, 2, 3
+XFORM_FFT, XFORM_DFTGEMM, XFORM_DFTGEMM_FP16, XFORM_FFT_TWOPASS, XFORM_DFTGEMM_FP16_GRID = 0, 1, 2, 3, 4
 XFORMS = {"fft": XFORM_FFT, "dftgemm": XFORM_DFTGEMM, "dftgemm_fp16": XFORM_DFTGEMM_FP16,
-          "fft_twopass": XFORM_FFT_TWOPASS}
+          "fft_twopass": XFORM_FFT_TWOPASS, "dftgemm_fp16grid": XFORM_DFTGEMM_FP16_GRID}
 
 _lib = None
 
@@ -281,8 +281,9 @@ class Plan:
     def set_transform(self, xform):
         """'fft' (FP32 shared-memory FFT), 'dftgemm' (tensor-core DFT, FP16 hi+lo, N_p = 128 or
         256), 'dftgemm_fp16' (reduced precision: FP16 gridding operands and one FP16 product
-        per real product, N_p = 128) or 'fft_twopass' (FP32 FFT in a row and a column pass
-        through a scratch buffer, N_p = 512)."""
+        per real product, N_p = 128), 'dftgemm_fp16grid' (FP16 gridding operands with FP32
+        sums, then the hi+lo tensor-core DFT, N_p = 256) or 'fft_twopass' (FP32 FFT in a row and
+        a column pass through a scratch buffer, N_p = 512)."""
         epic_set_transform(self._h, XFORMS[xform])
         self.xform = xform
         return self
