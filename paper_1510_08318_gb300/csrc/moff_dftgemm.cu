@@ -644,7 +644,7 @@ bool dftgemm_gather_tables_ng(int ng, int n_warps, const std::vector<int>& cptr,
     std::vector<int> order;
     for (const auto& sl : slots) order.insert(order.end(), sl.begin(), sl.end());
     lane.assign((size_t)NW * per_warp * 32, int2{0, 0});
-    base.assign((size_t)NW * per_warp, 0);
+    base.assign((size_t)NW * per_warp, -1);   // -1: a position no slot takes (skipped by the kernels)
     wre.clear();
     wim.clear();
     ant.clear();

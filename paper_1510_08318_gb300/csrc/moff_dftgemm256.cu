@@ -45,8 +45,9 @@
 // end.
 //
 // Gridding gathers cell pairs (x, y), (x, y + 1) from the slot tables of the 128 x 128 grid (256
-// slots of 32 pairs over 15 warps; each cell's entries in the builder's fixed order), read through
-// L1 (the operand buffers leave no room for them in shared memory).  The per-image scale is a
+// slots of 32 pairs over 15 warps of 18 positions each; each cell's entries in the builder's
+// fixed order; a position no slot took has base -1 and is skipped), read through L1 (the
+// operand buffers leave no room for them in shared memory).  The per-image scale is a
 // power of two that keeps |E| below 256, so |X| stays below 2^15 and its FP16 split in range.
 // Every wait is bounded (the pipeline's by the plan's try count); on a timeout the CTA sets the
 // image-timeout bit of the plan's status word, writes NaN into its accumulator block, waits with
@@ -63,6 +64,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 #include "moff_common.cuh"
 #include "tcgen05.cuh"
@@ -241,75 +243,86 @@ __global__ void __launch_bounds__(NTH, 1) moff_dftgemm256_kernel(const FwdArgs a
         const float down = ldexpf(1.f, -image_exp(j));
         const float2* vb = VB + (j & 1) * A;
         const uint32_t* vbh = VBh + (j & 1) * A;
+        // weight as the gridding uses it: FP32, or (LPG) rounded to FP16
+        auto wt = [&](float w) -> float {
+            if constexpr (LPG) return round_h(w);
+            else return w;
+        };
+        // calibrated voltage of an antenna: FP32 pair, or (LPG) the FP16 pair widened exactly
+        auto volt_of = [&](int an) -> float2 {
+            if constexpr (LPG) return half2_bits_to_float2(vbh[an]);
+            else return vb[an];
+        };
+        // A warp walks its slots one after another, and each step's entry and voltage reads
+        // depend on the table reads before them; so the next slot's header is loaded while this
+        // slot is walked, and U = 2 steps are taken per iteration, their table reads issued
+        // before their voltage reads and products (each lane still sums its entries in table
+        // order: the sums are those of one step per iteration, bit for bit).
+        constexpr int U = 2;
+        int slot = warp * SPW;
+        int2 lw_next = __ldg(g.lane + slot * 32 + lane);
+        int base_next = __ldg(g.base + slot);
 #pragma unroll 1
-        for (int jj = 0; jj < SPW; ++jj) {
-            const int slot = warp * SPW + jj;
-            const int2 lw = __ldg(g.lane + slot * 32 + lane);
+        for (int jj = 0; jj < SPW; ++jj, ++slot) {
+            const int2 lw = lw_next;
+            const int sbase = base_next;
+            if (jj + 1 < SPW) {
+                lw_next = __ldg(g.lane + (slot + 1) * 32 + lane);
+                base_next = __ldg(g.base + slot + 1);
+            }
+            if (sbase < 0) continue;   // a position no slot took (uniform across the warp)
             const int c0 = lw.x & 0xffff, cnt = (int)((unsigned)lw.x >> 16);
             const int kmax = __shfl_sync(0xffffffffu, cnt, 0);   // lane 0 has the longest list
-            int e = __ldg(g.base + slot) + lane;
+            int e = sbase + lane;
             float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-            if constexpr (LPG) {
-                if (g.wim) {
-                    // complex weights: the FP32 tables, each part rounded to FP16 as it is read
-                    for (int k = 0; k < kmax; ++k) {
-                        const bool on = k < cnt;
-                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
-                        if (on) {
-                            const float2 w = make_float2(round_h(__ldg(g.wre + e)), round_h(__ldg(g.wim + e)));
-                            const float2 v = half2_bits_to_float2(vbh[__ldg(g.ant + e)]);
-                            if (k < c0) cfma(s0, w, v);
-                            else cfma(s1, w, v);
+            // cw_tag: complex weights; pk_tag: packed FP16 weight | antenna entries (LPG, real)
+            auto walk = [&](auto cw_tag, auto pk_tag) {
+                constexpr bool CW = decltype(cw_tag)::value, PK = decltype(pk_tag)::value;
+                for (int k = 0; k < kmax; k += U) {
+                    bool on[U];
+                    int ek[U], an[U];
+                    float2 w[U], v[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        on[u] = k + u < cnt;
+                        ek[u] = u == 0 ? e : ek[u - 1] + __popc(__ballot_sync(0xffffffffu, on[u - 1]));
+                        w[u] = make_float2(0.f, 0.f);
+                        an[u] = 0;
+                        if (on[u]) {
+                            if constexpr (PK) {
+                                const uint32_t pk = __ldg(g.wpk + ek[u]);
+                                w[u].x = __half2float(__ushort_as_half((unsigned short)(pk >> 16)));
+                                an[u] = (int)(pk & 0xffffu);
+                            } else {
+                                w[u].x = wt(__ldg(g.wre + ek[u]));
+                                if constexpr (CW) w[u].y = wt(__ldg(g.wim + ek[u]));
+                                an[u] = __ldg(g.ant + ek[u]);
+                            }
                         }
-                        e += n_k;
                     }
-                } else {
-                    // real weights: one packed word per entry, FP16 weight | antenna
-                    for (int k = 0; k < kmax; ++k) {
-                        const bool on = k < cnt;
-                        const int n_k = __popc(__ballot_sync(0xffffffffu, on));
-                        if (on) {
-                            const uint32_t pk = __ldg(g.wpk + e);
-                            const float w = __half2float(__ushort_as_half((unsigned short)(pk >> 16)));
-                            const float2 v = half2_bits_to_float2(vbh[pk & 0xffffu]);
-                            const float w0 = k < c0 ? w : 0.f, w1 = w - w0;
-                            s0.x = fmaf(w0, v.x, s0.x);
-                            s0.y = fmaf(w0, v.y, s0.y);
-                            s1.x = fmaf(w1, v.x, s1.x);
-                            s1.y = fmaf(w1, v.y, s1.y);
+#pragma unroll
+                    for (int u = 0; u < U; ++u) v[u] = on[u] ? volt_of(an[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (!on[u]) continue;
+                        if constexpr (CW) {
+                            if (k + u < c0) cfma(s0, w[u], v[u]);
+                            else cfma(s1, w[u], v[u]);
+                        } else {
+                            // both cells take the entry, one with weight 0 (adds an exact 0)
+                            const float x0 = k + u < c0 ? w[u].x : 0.f, x1 = w[u].x - x0;
+                            s0.x = fmaf(x0, v[u].x, s0.x);
+                            s0.y = fmaf(x0, v[u].y, s0.y);
+                            s1.x = fmaf(x1, v[u].x, s1.x);
+                            s1.y = fmaf(x1, v[u].y, s1.y);
                         }
-                        e += n_k;
                     }
+                    e = ek[U - 1] + __popc(__ballot_sync(0xffffffffu, on[U - 1]));
                 }
-            } else if (g.wim) {
-                for (int k = 0; k < kmax; ++k) {
-                    const bool on = k < cnt;
-                    const int n_k = __popc(__ballot_sync(0xffffffffu, on));
-                    if (on) {
-                        const float2 w = make_float2(__ldg(g.wre + e), __ldg(g.wim + e));
-                        const float2 v = vb[__ldg(g.ant + e)];
-                        if (k < c0) cfma(s0, w, v);
-                        else cfma(s1, w, v);
-                    }
-                    e += n_k;
-                }
-            } else {
-                for (int k = 0; k < kmax; ++k) {
-                    const bool on = k < cnt;
-                    const int n_k = __popc(__ballot_sync(0xffffffffu, on));
-                    if (on) {
-                        // both cells take the entry, one with weight 0 (adds an exact 0)
-                        const float w = __ldg(g.wre + e);
-                        const float2 v = vb[__ldg(g.ant + e)];
-                        const float w0 = k < c0 ? w : 0.f, w1 = w - w0;
-                        s0.x = fmaf(w0, v.x, s0.x);
-                        s0.y = fmaf(w0, v.y, s0.y);
-                        s1.x = fmaf(w1, v.x, s1.x);
-                        s1.y = fmaf(w1, v.y, s1.y);
-                    }
-                    e += n_k;
-                }
-            }
+            };
+            if (g.wim) walk(std::true_type{}, std::false_type{});
+            else if constexpr (LPG) walk(std::false_type{}, std::true_type{});
+            else walk(std::false_type{}, std::false_type{});
             uint32_t rh, rl, ih, il;
             split2(s0.x * down, s1.x * down, rh, rl);
             split2(s0.y * down, s1.y * down, ih, il);

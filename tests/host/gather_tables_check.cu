@@ -8,7 +8,9 @@
 //   every cell pair (x, y), (x, y + 1) is stored exactly once, at an in-range even offset,
 //   the 32 lanes of a slot store to 32 distinct shared-memory banks,
 //   lanes are in decreasing entry count, every slot is held by one position of some warp (a warp
-//   holds at most ceil(slots / warps) of them: positions per warp, the rest all zero),
+//   holds at most ceil(slots / warps) of them: positions per warp; the rest have all-zero lanes
+//   and base -1, the mark that makes the kernel skip them instead of storing their zero sums
+//   over the cell pair at offset 0),
 //   every cell's walked entries are a permutation of its mapping entries (the builder orders a
 //   cell's entries to spread the antennas read at one step over shared-memory banks), and its
 //   sum equals the sum of the same entries in the CSR order within FP32 rounding (a few units in
@@ -72,10 +74,15 @@ int main(int argc, char** argv) {
     std::vector<std::vector<int>> walked(ETAB);   // table entries summed into each E^T element
     int used = 0;
     for (int slot = 0; slot < NPOS; ++slot) {
-        // positions no slot took (when the slots do not divide evenly over the warps) are all zero
+        // positions no slot took (when the slots do not divide evenly over the warps) carry base -1,
+        // which the kernels skip, and all-zero lanes; every other position a base >= 0
         bool empty = true;
         for (int l = 0; l < 32; ++l) empty = empty && lane[slot * 32 + l].x == 0 && lane[slot * 32 + l].y == 0;
-        if (empty) continue;
+        if (base[slot] < 0) {
+            if (!empty || base[slot] != -1) ++bad;
+            continue;
+        }
+        if (empty) ++bad;
         ++used;
         int c0[32], cnt[32], e[32];
         unsigned banks = 0;

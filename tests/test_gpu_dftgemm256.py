@@ -173,3 +173,32 @@ def test_timeout_reported_then_cleared(epic):
     plan.sync()
     want = moff.moff_image(oracle_map(wl), wl.volt, None, wl.n_grid, wl.n_pad)
     check_close(out["image"].cpu().numpy(), want, "image after a timeout")
+
+
+@pytest.mark.parametrize("xform, bound", [("dftgemm", RTOL_L2), ("dftgemm_fp16grid", 3e-3)])
+def test_grid_corner_cells(epic, xform, bound):
+    """Antennas whose footprints fall on the grid's first cells, (x, y) = (0, 0), (0, 1) and (1, 0):
+    the word of E^T that holds the cell pair (0, 0), (0, 1) is written by its own slot only (the
+    slot table's positions that no slot took are marked and skipped, not stored as zeros)."""
+    rng = np.random.default_rng(43)
+    n_grid, n_ant, n_time = 128, 64, 6
+    corner = np.array([[0.1, 0.1], [0.1, 1.1], [1.1, 0.1]])
+    pos = np.vstack([corner, rng.uniform(2.5, n_grid - 3.5, (n_ant - 3, 2))])
+    kerns = ([synth.kernel_square(0.3, 0.1) for _ in range(3)]
+             + [synth.kernel_square(rng.uniform(0.5, 2.5), 1 / 3) for _ in range(n_ant - 3)])
+    ptr, dxdy, w = synth.pack_kernels(kerns)
+    wl = synth.Workload("corner", pos, ptr, dxdy, w, 1.0, np.zeros(2), n_grid, 256,
+                        np.full(1, 1e8), 1, n_time, "c64")
+    v = rng.standard_normal((n_time, 1, 1, n_ant)) + 1j * rng.standard_normal((n_time, 1, 1, n_ant))
+    v[:, :, :, :3] *= 20.0      # the corner antennas dominate their cells
+    wl = synth._finish(wl, v, "c64")
+    M = oracle_map(wl)
+    assert all(M[c].nnz > 0 for c in (0, 1, n_grid))   # cells (0, 0), (1, 0), (0, 1) are occupied
+    plan = epic.Plan.from_workload(wl).set_transform(xform)
+    out = plan.image(torch.from_numpy(np.ascontiguousarray(wl.volt_raw)).cuda())
+    plan.sync()
+    got = out["image"].cpu().numpy().astype(np.float64)
+    want = moff.moff_image(M, wl.volt, None, wl.n_grid, wl.n_pad)
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    worst = np.abs(got - want).max() / np.abs(want).max()
+    assert rel < bound and worst < bound, (rel, worst)
