@@ -27,6 +27,36 @@ def _declared():
     return names
 
 
+def _enum_values(prefix):
+    """Name -> value of the header's enumerators that start with prefix (explicit or implicit)."""
+    src = open(os.path.join(ROOT, "include", "epic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}", src, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            m = re.match(r"\s*(\w+)\s*(?:=\s*(-?\d+))?\s*$", item)
+            if not m:
+                continue
+            nxt = int(m.group(2)) if m.group(2) is not None else nxt
+            if m.group(1).startswith(prefix):
+                out[m.group(1)] = nxt
+            nxt += 1
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """The binding's transform codes and status codes are the header's enumerators."""
+    xf = _enum_values("EPIC_XFORM_")
+    assert xf, "no EPIC_XFORM_ enumerators found"
+    for name, value in xf.items():
+        assert getattr(epic, name[len("EPIC_"):]) == value, name
+    assert sorted(epic.XFORMS.values()) == sorted(xf.values())
+    st = _enum_values("EPIC_E") | _enum_values("EPIC_OK")
+    for name, value in st.items():
+        assert getattr(epic, name) == value, name
+
+
 def test_exports_every_declared_symbol(lib):
     declared = _declared()
     assert {"epic_create", "epic_image", "epic_image_backward", "epic_destroy"} <= declared
